@@ -1,0 +1,280 @@
+"""Particle forces, time integration, wall impacts, condenser charging (FP64).
+
+Part of the FP64 CPU oracle: test infrastructure only.
+
+Sec. 2.2, Eq. (particle-motion): du_p/dt = f_ad + f_coll + f_g + f_el.  The hot
+path keeps drag (Schiller-Naumann, Sec. 2.2), the mesh (Gauss) electrostatic
+force q E / m_p with m_p = pi d^3 rho_p / 6, and hard-sphere particle-wall
+collisions (wall-normal velocity flips, tangential unchanged).  Gravity is zero
+in all of the paper's runs (Sec. 3.1).
+
+Sec. 2.3.1, condenser model for particle-wall impacts (after John et al.):
+  dq_w = dq_c + dq_t                             Eq. (particle-wall charge sum)
+  dq_c = -C U_c (1 - exp(-dt_w / T_w))           Eq. particle-wall-exchange
+  C = eps A_iw / h                               Eq. capacity-capacitor
+  A_iw = pi (d/2) alpha_iw                       Eq. charge-contact-area
+  alpha_iw = (d/2) (5/8 pi rho_p (1+k_e) |u_i|^2
+              ((1-mu_p^2)/E_p + (1-mu_w^2)/E_w))^(2/5)   Eq. charge-contact-area-alpha2
+  dt_w = 2.94 alpha_iw / |u_i|,  T_w = eps_w eps0 phi_p
+  dq_t: Eq. precharge-surface.
+
+Readings (the paper is silent or inconsistent):
+* integrator: exponential (exact for gas velocity and field frozen over the
+  step); Re_p from the relative speed at the start of the step.
+* drag: the source formula drops the (u - u_p) factor; the specific drag is
+  f_ad = (u - u_p) / tau with 1/tau = (3/4) rho nu C_D Re_p / (rho_p d^2).
+* order within a step: locate, deposit, Poisson and E from the state at the
+  start of the step, then push.
+* collision is elastic (e = 1, "fully elastic", Sec. 2.2); k_e only enters
+  alpha_iw.
+* contact: the centre comes closer than r = d/2 to a wall; the position is
+  mirrored about the contact plane y = r (or Ly - r) and v_y flips.
+* |u_i|: full particle speed after the push (literal reading); the switch
+  IMPACT_NORMAL uses the wall-normal speed instead.
+* dq_t = -(1/4) alpha_iw q is dimensionally inconsistent (alpha is a length);
+  with the pre-charge spread uniformly over the surface, the transferred
+  fraction is the contact area over the sphere area, dq_t = -A_iw/(pi d^2) q,
+  which equals -(1/4)(alpha_iw / r) q.
+* 1 - exp(-x) is evaluated as -expm1(-x) (x ~ 1e-8 here).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from .constants import (DRAG_OFF, DRAG_SCHILLER_NAUMANN, DRAG_STOKES,
+                        IMPACT_NORMAL, Params)
+from .grid import Grid, locate, trilinear
+from .poisson import deposit, efield, poisson
+
+
+@dataclasses.dataclass
+class State:
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    vz: np.ndarray
+    q: np.ndarray
+    d: np.ndarray
+    n_imp: np.ndarray
+    q_wall: np.ndarray
+
+    @staticmethod
+    def from_arrays(x, y, z, vx, vy, vz, q, d, n_imp=None, q_wall=None) -> "State":
+        n = np.asarray(x).shape[0]
+        f = lambda a: np.array(a, dtype=np.float64)
+        return State(f(x), f(y), f(z), f(vx), f(vy), f(vz), f(q), f(d),
+                     np.zeros(n, np.int64) if n_imp is None else np.array(n_imp, np.int64),
+                     np.zeros(n) if q_wall is None else f(q_wall))
+
+    def copy(self) -> "State":
+        return State(*(np.array(getattr(self, f.name)) for f in dataclasses.fields(self)))
+
+    @property
+    def n(self) -> int:
+        return self.x.shape[0]
+
+
+def particle_mass(p: Params, d):
+    """m_p = (1/6) pi d^3 rho_p (Sec. 2.2)."""
+    return math.pi * np.asarray(d, np.float64) ** 3 * p.rho_p / 6.0
+
+
+def relaxation_time(p: Params, d, rel_speed):
+    """Drag relaxation time tau with f_ad = (u - u_p) / tau (Sec. 2.2).
+
+    Stokes: tau_p = rho_p d^2 / (18 rho nu).  Schiller-Naumann:
+    C_D = 24/Re_p (1 + Re_p^(2/3)/6) for Re_p <= 1000, 0.424 above, with
+    1/tau = (3/4) rho nu C_D Re_p / (rho_p d^2).  DRAG_OFF returns inf.
+    """
+    d = np.asarray(d, np.float64)
+    rel_speed = np.asarray(rel_speed, np.float64)
+    if p.drag_law == DRAG_OFF:
+        return np.full(np.broadcast(d, rel_speed).shape, np.inf)
+    tau_p = p.rho_p * d ** 2 / (18.0 * p.rho * p.nu)
+    if p.drag_law == DRAG_STOKES:
+        return np.broadcast_to(tau_p, np.broadcast(d, rel_speed).shape).copy()
+    re_p = rel_speed * d / p.nu
+    cd = np.where(re_p <= 1000.0,
+                  24.0 / np.where(re_p > 0, re_p, 1.0) * (1.0 + re_p ** (2.0 / 3.0) / 6.0),
+                  0.424)
+    inv_tau = 0.75 * p.rho * p.nu * cd * re_p / (p.rho_p * d ** 2)
+    # Re_p -> 0 limit of the Schiller-Naumann branch is the Stokes time
+    return np.where(re_p > 0, 1.0 / np.where(inv_tau > 0, inv_tau, 1.0), tau_p)
+
+
+def _phi12(s):
+    """phi1 = 1 - e^-s and phi2 = s - phi1 = e^-s - 1 + s (series for small s)."""
+    s = np.asarray(s, np.float64)
+    phi1 = -np.expm1(-s)
+    small = s < 0.5
+    ss = np.where(small, s, 0.0)
+    # sum_{n=2}^{22} (-1)^n s^n / n!  (truncation below 1e-16 relative for s < 0.5)
+    acc = np.zeros_like(ss)
+    pw = ss * ss
+    for n in range(2, 23):
+        acc = acc + ((-1.0) ** n) * pw / math.factorial(n)
+        pw = pw * ss
+    phi2 = np.where(small, acc, s - phi1)
+    return phi1, phi2
+
+
+def push(p: Params, x, v, uf, acc, d, dt):
+    """Advance position and velocity over dt with u, a frozen (exponential).
+
+    dv/dt = (u - v)/tau + a  gives
+      v' = v + (u + a tau - v) phi1,  x' = x + tau (v phi1 + (u + a tau) phi2),
+    phi1 = 1 - e^-s, phi2 = s - phi1, s = dt / tau.  With drag off:
+      v' = v + a dt, x' = x + v dt + a dt^2 / 2.
+    x, v, uf, acc: (n, 3).  Returns x', v', tau.
+    """
+    rel = np.linalg.norm(v - uf, axis=1)
+    tau = relaxation_time(p, d, rel)
+    if p.drag_law == DRAG_OFF:
+        return x + v * dt + 0.5 * acc * dt * dt, v + acc * dt, tau
+    s = dt / tau
+    phi1, phi2 = _phi12(s)
+    term = uf + acc * tau[:, None]
+    vn = v + (term - v) * phi1[:, None]
+    xn = x + tau[:, None] * (v * phi1[:, None] + term * phi2[:, None])
+    return xn, vn, tau
+
+
+def wrap(s, length):
+    """Periodic wrap into [0, L); a result equal to L (rounding) becomes 0."""
+    w = s - length * np.floor(s / length)
+    return np.where(w >= length, w - length, w)
+
+
+def condenser_wall(p: Params, d, speed, q):
+    """Charge gained by a particle in one wall impact (condenser model).
+
+    Returns (dq_c, dq_t, details) with details = dict(alpha, A, C, dt_w, T_w).
+    A zero impact speed transfers nothing.
+    """
+    d = np.asarray(d, np.float64)
+    speed = np.asarray(speed, np.float64)
+    q = np.asarray(q, np.float64)
+    r = 0.5 * d
+    elastic = (1.0 - p.mu_p ** 2) / p.E_p + (1.0 - p.mu_w ** 2) / p.E_w
+    alpha = r * (0.625 * math.pi * p.rho_p * (1.0 + p.k_e) * speed ** 2 * elastic) ** 0.4
+    A = p.kappa_A * math.pi * r * alpha
+    C = p.eps * A / p.h
+    pos = speed > 0
+    dt_w = np.where(pos, 2.94 * alpha / np.where(pos, speed, 1.0), 0.0)
+    T_w = p.eps_w * p.eps0 * p.phi_p
+    dq_c = -C * p.U_c * (-np.expm1(-dt_w / T_w))
+    dq_t = -(A / (math.pi * d ** 2)) * q if p.dq_t else np.zeros_like(q)
+    return dq_c, dq_t, dict(alpha=alpha, A=A, C=C, dt_w=dt_w, T_w=T_w)
+
+
+def wall_impacts(p: Params, ly: float, y, vy, d):
+    """Specular reflection at the walls (hard sphere, Sec. 2.2).
+
+    Returns (y', vy', hit) with hit = -1 (bottom), +1 (top), 0 (none), and a
+    flag array of particles still outside after one reflection.
+    """
+    r = 0.5 * np.asarray(d, np.float64)
+    lo = y < r
+    hi = y > ly - r
+    yn = np.where(lo, 2.0 * r - y, np.where(hi, 2.0 * (ly - r) - y, y))
+    vyn = np.where(lo | hi, -vy, vy)
+    hit = np.where(lo, -1, np.where(hi, 1, 0))
+    bad = (yn < r) | (yn > ly - r)
+    return yn, vyn, hit, bad
+
+
+def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
+         diag: dict | None = None) -> State:
+    """One coupled particle step (deposit -> Poisson -> E -> gather -> push -> wall).
+
+    u_lat: gas velocity on the wall-extended lattice (Nz, Ny+2, Nx, 3).
+    """
+    n = st.n
+    X = np.stack([st.x, st.y, st.z], axis=1)
+    V = np.stack([st.vx, st.vy, st.vz], axis=1)
+    uf = trilinear(g, u_lat, st.x, st.y, st.z)
+    if p.electrostatics:
+        i, j, k = locate(g, st.x, st.y, st.z)
+        rho = deposit(g, st.q, i, j, k)
+        phi = poisson(g, rho, p.eps)
+        E = efield(g, phi)
+        Ep = trilinear(g, E, st.x, st.y, st.z)
+        acc = (st.q / particle_mass(p, st.d))[:, None] * Ep
+        if diag is not None:
+            diag.update(rho=rho, phi=phi, E=E, Ep=Ep)
+    else:
+        acc = np.zeros((n, 3))
+    Xn, Vn, tau = push(p, X, V, uf, acc, st.d, dt)
+    xn = wrap(Xn[:, 0], g.lx)
+    zn = wrap(Xn[:, 2], g.lz)
+    yn, vyn, hit, bad = wall_impacts(p, g.ly, Xn[:, 1], Vn[:, 1], st.d)
+    if np.any(bad):
+        raise FloatingPointError("particle crossed both contact planes in one step")
+    vxn, vzn = Vn[:, 0], Vn[:, 2]
+    q = st.q.copy()
+    n_imp = st.n_imp.copy()
+    q_wall = st.q_wall.copy()
+    m = hit != 0
+    if np.any(m):
+        if p.impact_vel == IMPACT_NORMAL:
+            speed = np.abs(Vn[m, 1])
+        else:
+            speed = np.linalg.norm(Vn[m], axis=1)
+        dq_c, dq_t, _ = condenser_wall(p, st.d[m], speed, q[m])
+        dq = dq_c + dq_t
+        q[m] += dq
+        q_wall[m] += dq
+        n_imp[m] += 1
+    if diag is not None:
+        diag.update(uf=uf, hit=hit, tau=tau)
+    return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall)
+
+
+def run(g: Grid, p: Params, st: State, u_lat, dt: float, nsteps: int,
+        hist: np.ndarray | None = None) -> State:
+    """nsteps coupled steps; optionally accumulate the y-cell histogram.
+
+    u_lat may be an array or a callable t -> lattice (time-varying gas field).
+    """
+    for n in range(nsteps):
+        lat = u_lat(n * dt) if callable(u_lat) else u_lat
+        st = step(g, p, st, lat, dt)
+        if hist is not None:
+            hist += ystats(g, st)
+    return st
+
+
+def ystats(g: Grid, st: State) -> np.ndarray:
+    """Particle count per wall-normal cell (the bins of C_rel, Sec. 4.1)."""
+    _, j, _ = locate(g, st.x, st.y, st.z)
+    return np.bincount(j, minlength=g.ny).astype(np.float64)
+
+
+def c_rel(g: Grid, counts: np.ndarray) -> np.ndarray:
+    """Relative concentration C_rel = C / C0 per y-cell (Sec. 4.1)."""
+    conc = counts / (g.vol_y * g.nx * g.nz)
+    c0 = counts.sum() / (g.lx * g.ly * g.lz)
+    return conc / c0
+
+
+# ---------------------------------------------------------------------------
+# non-dimensional groups (Sec. 3.1, Table 2)
+
+def dplus(d, re_tau, delta):
+    """d_p+ = d_p u_tau / nu = d_p Re_tau / delta."""
+    return np.asarray(d) * re_tau / delta
+
+
+def stokes_number(p: Params, d, u_c, delta):
+    """St = (1/18)(rho_p/rho) d^2/nu * u_c/delta (Sec. 3.1)."""
+    return (1.0 / 18.0) * (p.rho_p / p.rho) * np.asarray(d) ** 2 / p.nu * u_c / delta
+
+
+def volume_fraction_ppm(number_density, d):
+    """omega = C pi d^3 / 6, in parts per million."""
+    return number_density * math.pi * np.asarray(d) ** 3 / 6.0 * 1e6
