@@ -1,0 +1,348 @@
+"""Benchmark: coupled particle steps of the Re_tau = 550 channel workload.
+
+One step = deposit -> Poisson (FFT x,z + FP64 tridiagonal y) -> E -> gather
+-> drag + q E / m integration -> wall impacts with condenser charging, for all
+particles of one channel (384 x 256 x 256 grid, 8M particles, mixed precision).
+
+Prints ONE JSON line.  --impl reference times the FP64 CPU oracle instead
+(on the host cores, a bounded sample of the same workload).  Multi-GPU runs
+(torchrun) advance one independent channel per rank (replicas; no collective
+on the data path) and report the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "particle-steps/s"
+WORKLOAD = "re550_384"
+PARTICLE_BYTES = 68      # algorithmic bytes per particle-step of the particle kernel (mixed)
+NODE_BYTES = 24          # u (3 x f32) + E (3 x f32) per lattice node touched
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(gpu_index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def touched_nodes(c, faces, x, y, z):
+    """Distinct lattice nodes the trilinear gather touches (host count)."""
+    nx, ny, nz = c.nx, c.ny, c.nz
+    Y = synth.node_y(faces)
+    dx, dz = c.lx / nx, c.lz / nz
+    i0 = np.floor(x / dx - 0.5).astype(np.int64) % nx
+    k0 = np.floor(z / dz - 0.5).astype(np.int64) % nz
+    j0 = np.clip(np.searchsorted(Y, y, side="right") - 1, 0, ny)
+    mark = np.zeros(nz * (ny + 2) * nx, dtype=bool)
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                mark[(((k0 + dk) % nz) * (ny + 2) + j0 + dj) * nx + (i0 + di) % nx] = True
+    return int(mark.sum())
+
+
+def make_inputs(c, n=None):
+    faces = synth.y_faces(c.ny, c.delta, c.gamma)
+    lat = synth.fluid_lattice(c, faces=faces).astype(np.float32)
+    P = synth.draw_particles(c, n)
+    return faces, lat, P
+
+
+def oracle_step_time(c, faces, lat, P, n_sample):
+    """Time one oracle step: the full-grid Poisson + a particle sample."""
+    import oracle
+    g = oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces)
+    p = oracle.Params(rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0)
+    sel = slice(0, n_sample)
+    st = oracle.State.from_arrays(P.x[sel], P.y[sel], P.z[sel], P.vx[sel], P.vy[sel], P.vz[sel],
+                                  P.q[sel], P.d[sel])
+    lat64 = lat.astype(np.float64)
+    # the deposit of the full ensemble feeds the Poisson solve
+    t0 = time.perf_counter()
+    i, j, k = oracle.locate(g, P.x, P.y, P.z)
+    rho = oracle.deposit(g, P.q, i, j, k)
+    phi = oracle.poisson(g, rho, p.eps)
+    oracle.efield(g, phi)
+    t_field = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    oracle.step(g, p.with_(electrostatics=False), st, lat64, c.dt)
+    t_part = time.perf_counter() - t1
+    # the per-particle gather of E (skipped in the electrostatics-off step) is one
+    # more trilinear call; time it on the sample too
+    t2 = time.perf_counter()
+    oracle.trilinear(g, np.zeros((c.nz, c.ny + 2, c.nx, 3)), st.x, st.y, st.z)
+    t_part += time.perf_counter() - t2
+    return t_field, t_part
+
+
+def cpu_baseline(c, faces, lat, P, n_sample):
+    t_field, t_part = oracle_step_time(c, faces, lat, P, n_sample)
+    t_full = t_field + t_part * (c.n_particles / n_sample)
+    return {"value": c.n_particles / t_full, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": (f"one FP64 oracle step on the host: full {c.nx}x{c.ny}x{c.nz} deposit+Poisson+E "
+                       f"({t_field:.2f} s) plus the particle update of {n_sample} of the "
+                       f"{c.n_particles} particles ({t_part:.2f} s), scaled to all particles; "
+                       f"numpy single-threaded; host has {os.cpu_count()} cores")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    c = synth.case(args.config)
+    faces, lat, P = make_inputs(c)
+    n_sample = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_step_time(c, faces, lat, P, min(n_sample, 20000))
+    times = []
+    for _ in range(args.steps):
+        tf, tp = oracle_step_time(c, faces, lat, P, n_sample)
+        times.append(tf + tp * (c.n_particles / n_sample))
+    t = sum(times) / len(times)
+    v = c.n_particles / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(c)},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: full-grid deposit+Poisson+E plus {n_sample} particles, "
+                                       f"scaled to {c.n_particles}"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_desc(c):
+    return (f"{c.name}: Re_tau={c.re_tau:g}, {c.nx}x{c.ny}x{c.nz} grid (Lx=2 pi h, Lz=pi h, tanh y "
+            f"stretching {c.gamma:g}), {c.n_particles} particles, d+={c.dplus[0]:g}, "
+            f"rho_p/rho={c.density_ratio:g}, dt+={c.dt_plus:g}, Stokes drag, mesh electrostatics "
+            f"every step, condenser wall charging; FP32 particles/FFT, FP64 y-solve and charges")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tribo", choices=["tribo", "reference"])
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-sample", type=int, default=200_000)
+    ap.add_argument("--ref-sample", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sort-every", type=int, default=0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2602_10761_gb300 as T
+    from paper_2602_10761_gb300 import build as B
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    T.load()
+
+    c = synth.case(args.config)
+    faces, lat, P = make_inputs(c)
+    stream = torch.cuda.current_stream()
+    params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0,
+                      sort_every=args.sort_every)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(),
+                   max_particles=c.n_particles, stream=stream)
+    parts = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
+    Pd = T.Particles.from_numpy(parts, T.TRIBO_MIXED, device=f"cuda:{local}")
+    nodes = touched_nodes(c, faces, P.x, P.y, P.z)
+
+    ch.step(Pd, c.dt, args.warmup)
+    ch.sync()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    launches0 = ch.launches
+    T.tribo_timing_enable(ch.ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ch.step(Pd, c.dt, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    phases = T.tribo_timing_read(ch.ctx)
+    T.tribo_timing_enable(ch.ctx, False)
+    launches = ch.launches - launches0
+    ch.sync()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * c.n_particles * args.steps / (ms * 1e-3)
+
+    # end to end through the public call with HOST buffers (pinned), copies inside
+    host = {}
+    for k in ("x", "y", "z", "vx", "vy", "vz", "d"):
+        host[k] = torch.from_numpy(np.asarray(getattr(P, k), np.float32)).pin_memory().numpy()
+    host["q"] = torch.from_numpy(np.asarray(P.q, np.float64)).pin_memory().numpy()
+    host["q_wall"] = torch.zeros(c.n_particles, dtype=torch.float64).pin_memory().numpy()
+    host["n_imp"] = torch.zeros(c.n_particles, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    host["id"] = torch.arange(c.n_particles, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    Ph = T.Particles(**host)
+    h2d = sum(host[k].nbytes for k in ("x", "y", "z", "vx", "vy", "vz", "d", "q", "q_wall", "n_imp", "id"))
+    d2h = sum(host[k].nbytes for k in ("x", "y", "z", "vx", "vy", "vz", "q", "q_wall", "n_imp", "id"))
+    ch.step(Ph, c.dt, 1)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ch.step(Ph, c.dt, 1)          # copies in, one step, copies out, synchronises
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * c.n_particles * args.e2e_steps / e2e_s
+
+    hbm_peak, peak_kind = measured_peaks()
+    kern = {}
+    poisson_ms = 0.0
+    for name, (tms, cnt) in phases.items():
+        if cnt:
+            kern[name] = {"ms_per_launch": tms / cnt, "launches": cnt, "share": tms / max(ms, 1e-9)}
+            if name.startswith("poisson"):
+                poisson_ms += tms
+    n_solves = phases["poisson_fwd_x"][1]
+    poisson_per_solve = poisson_ms / max(n_solves, 1)
+    cells = c.nx * c.ny * c.nz
+    nodes_all = c.nx * (c.ny + 2) * c.nz
+    alg = {
+        "particle_step": c.n_particles * PARTICLE_BYTES + nodes * NODE_BYTES,
+        "poisson": cells * 8 + nodes_all * 12,
+    }
+    dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+    step_ms = phases["particle_step"][0] / max(phases["particle_step"][1], 1)
+    ach_step = alg["particle_step"] / (step_ms * 1e-3) / 1e9
+    ach_pois = alg["poisson"] / (poisson_per_solve * 1e-3) / 1e9
+    if dom.startswith("poisson"):
+        roof = {"bound": "hbm", "achieved": ach_pois, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach_pois / hbm_peak, "traffic": None, "kernel": "poisson (all passes)",
+                "peak_kind": peak_kind}
+    else:
+        roof = {"bound": "hbm", "achieved": ach_step, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach_step / hbm_peak, "traffic": None, "kernel": "particle_step",
+                "peak_kind": peak_kind}
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(c), "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set > L2 (lattices 2 x 406 MB, particles 0.5 GB); no flush",
+                   "sort_every": args.sort_every},
+        "poisson_solves_per_s": 1e3 / poisson_per_solve if poisson_per_solve > 0 else None,
+        "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "roofline_all": {
+            "particle_step": {"achieved": ach_step, "frac": ach_step / hbm_peak,
+                              "alg_bytes": alg["particle_step"], "ms": step_ms},
+            "poisson": {"achieved": ach_pois, "frac": ach_pois / hbm_peak, "alg_bytes": alg["poisson"],
+                        "ms": poisson_per_solve}},
+        "kernels": kern,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(c, faces, lat, P, args.cpu_sample)
+    ch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

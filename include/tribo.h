@@ -1,0 +1,194 @@
+/*
+ * tribo.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of point-particle triboelectric charging in a turbulent channel
+ * (Wilms & Grosshans, "Effect of Reynolds number on triboelectric particle
+ * charging in turbulent channel flow").
+ *
+ * One coupled particle step (Sec. 2.2 and Sec. 2.3.1 of the paper):
+ *   1. locate each particle's cell and deposit its charge to the cell
+ *      (charge density = sum of charges in a cell / cell volume, Sec. 2.2);
+ *   2. solve laplacian(phi) = -rho/eps with grounded walls (Sec. 2.2; second
+ *      order finite volumes, Sec. 3.1): DFT in the periodic x, z directions,
+ *      tridiagonal solve in the wall-normal y direction; E = -grad(phi);
+ *   3. interpolate the gas velocity u and E trilinearly at each particle;
+ *   4. integrate du_p/dt = f_ad + f_el (Eq. particle-motion) with
+ *      Schiller-Naumann (or Stokes) drag and f_el = q E / m_p;
+ *   5. hard-sphere wall impacts (wall-normal velocity flips, Sec. 2.2) with
+ *      the condenser-model charge dq_w = dq_c + dq_t (Eqs. particle-wall-
+ *      exchange, capacity-capacitor, charge-contact-area, charge-contact-
+ *      area-alpha2, precharge-surface).
+ *
+ * Conventions
+ *   - All functions return tribo_status (0 = OK); no exception crosses the ABI.
+ *   - SI units throughout.
+ *   - Arrays are C-contiguous.  Lattice arrays are indexed [k][jn][i][c]
+ *     (z slowest, x fastest); cell arrays [k][j][i].
+ *   - "real" means double when params.precision == TRIBO_FP64 and float when
+ *     params.precision == TRIBO_MIXED.
+ *   - Device pointers are CUDA device (or managed) pointers on the device that
+ *     was current at tribo_init; host pointers are ordinary (preferably
+ *     pinned) host memory.
+ *   - Calls are stream-ordered on the context's stream unless stated
+ *     otherwise; errors detected on the device set a sticky error word that
+ *     the next synchronising call (tribo_sync, tribo_stats, any host-pointer
+ *     call) reports as TRIBO_ERR_DEVICE.
+ *   - Nothing falls back to the CPU.
+ */
+#ifndef TRIBO_H
+#define TRIBO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tribo_status;
+
+#define TRIBO_OK              0
+#define TRIBO_ERR_ARG         1  /* invalid argument (null pointer, size, layout) */
+#define TRIBO_ERR_UNSUPPORTED 2  /* e.g. an FFT length that is not 2^a 3^b */
+#define TRIBO_ERR_CUDA        3  /* CUDA runtime error (tribo_last_error has it) */
+#define TRIBO_ERR_OOM         4  /* device allocation failed */
+#define TRIBO_ERR_DEVICE      5  /* the device error word is set */
+#define TRIBO_ERR_CAPACITY    6  /* more particles than the context was sized for */
+
+/* bits of the device error word (tribo_error_bits) */
+#define TRIBO_DEV_ESCAPED   0x1u /* a particle was still outside the contact planes after one reflection */
+#define TRIBO_DEV_NONFINITE 0x2u /* a particle state became NaN or Inf */
+#define TRIBO_DEV_OUTSIDE   0x4u /* a particle position was outside the channel before a step */
+
+#define TRIBO_FP64  0   /* everything in FP64 */
+#define TRIBO_MIXED 1   /* FP32 particle state, interpolation, force math, FFT and
+                           fields; FP64 y-tridiagonal solve, wall-impact charge and
+                           time of flight, per-particle and cell charge accumulators */
+
+#define TRIBO_DRAG_STOKES           0
+#define TRIBO_DRAG_SCHILLER_NAUMANN 1
+#define TRIBO_DRAG_OFF              2
+
+#define TRIBO_IMPACT_SPEED  0   /* |u_i| = full particle speed at impact */
+#define TRIBO_IMPACT_NORMAL 1   /* |u_i| = wall-normal speed at impact */
+
+typedef struct tribo_ctx tribo_ctx;
+
+/* Channel grid (Sec. 3.1): periodic in x (length lx) and z (length lz), walls
+ * at y = y_faces[0] = 0 and y = y_faces[ny].  x and z cells are uniform.
+ * y_faces: HOST array of ny+1 strictly increasing faces, copied at init.
+ * nx, nz must be 2^a 3^b with 4 <= n <= 1024; nx even; 2 <= ny <= 1024. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double lx, lz;
+    const double* y_faces;
+} tribo_grid;
+
+/* Physical parameters (Table 1) and switches.
+ * eps: gas permittivity in Poisson's equation and in C = eps A / h;
+ * eps0: vacuum permittivity in T_w = eps_w eps0 phi_p;
+ * U_c: particle-wall contact potential [V] (not given in the paper);
+ * kappa_A: factor on the Hertz contact area (1 in the paper).
+ * dq_t: 1 to include the pre-charge transfer dq_t = -(A_iw / (pi d^2)) q
+ *       (Eq. precharge-surface read as contact-area fraction), 0 to omit it.
+ * electrostatics: 1 to deposit, solve and apply q E / m each step, 0 for none.
+ * sort_every: re-sort particles by cell every this many steps (0 = never);
+ *       sorting permutes all particle arrays, including id. */
+typedef struct {
+    double mu_p, E_p, phi_p, k_e, mu_w, E_w, eps_w, h, eps, eps0;
+    double nu, rho, rho_p;
+    double U_c, kappa_A;
+    int32_t drag_law, impact_vel, dq_t, electrostatics, precision;
+    int32_t sort_every;
+} tribo_params;
+
+/* Gas velocity on the wall-extended lattice (Nz, Ny+2, Nx, 3) of "real":
+ * node (k, jn, i) sits at x = (i + 1/2) dx, z = (k + 1/2) dz and
+ * y = 0 (jn = 0), cell centre jn - 1 (1 <= jn <= ny), 2 delta (jn = ny + 1).
+ * Copied into the context's own lattice (the caller keeps ownership). */
+typedef struct {
+    const void* u;
+    int32_t on_host;          /* 1: u is a host pointer, 0: device pointer */
+} tribo_fluid;
+
+/* Particle ensemble, structure of arrays, caller-owned.  Borrowed for the
+ * duration of a call (host pointers) or until the stream reaches the end of
+ * the call's work (device pointers).
+ *   x, y, z, vx, vy, vz, d : n "real"
+ *   q, q_wall              : n double (charge; cumulative charge received in
+ *                            wall impacts)
+ *   n_imp                  : n uint32 cumulative wall-impact count
+ *   id                     : n uint32, optional (NULL): permuted with the
+ *                            particles when they are re-sorted
+ *   cell                   : n uint32, optional (NULL) output: cell key
+ *                            (k * ny + j) * nx + i of each final position */
+typedef struct {
+    int64_t n;
+    void *x, *y, *z, *vx, *vy, *vz, *d;
+    double* q;
+    double* q_wall;
+    uint32_t* n_imp;
+    uint32_t* id;
+    uint32_t* cell;
+    int32_t on_host;          /* 1: all pointers are host pointers */
+} tribo_particles;
+
+/* Create a context on the current device.  stream: a cudaStream_t to order
+ * all work on (NULL = the legacy default stream).  max_particles sizes the
+ * context's staging and sort buffers.  On failure *out is NULL. */
+tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_fluid* fluid,
+                        const tribo_params* params, int64_t max_particles, void* stream);
+
+/* Replace the gas-velocity lattice (e.g. a time-varying field). */
+tribo_status tribo_set_fluid(tribo_ctx* ctx, const tribo_fluid* fluid);
+
+/* Replace the physical parameters and switches (precision must not change). */
+tribo_status tribo_set_params(tribo_ctx* ctx, const tribo_params* params);
+
+/* Advance the particles nsteps coupled steps of length dt [s].  Device
+ * pointers: asynchronous on the context's stream.  Host pointers: copies in,
+ * steps, copies out and synchronises before returning. */
+tribo_status tribo_step(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t nsteps);
+
+/* Standalone Poisson solve and field (step 2 above).  rho: device
+ * (Nz, Ny, Nx) double charge density [C/m^3].  phi: device (Nz, Ny, Nx)
+ * double, may be NULL.  E: device (Nz, Ny+2, Nx, 4) "real" with E_x, E_y,
+ * E_z in components 0..2 (component 3 is written as 0); the wall nodes hold
+ * E_x = E_z = 0 and the one-sided E_y.  Asynchronous. */
+tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void* E);
+
+/* Statistics since the last tribo_reset_stats (Sec. 4.1): sum of the current
+ * particle charges of p (may be NULL: sum_q is then not written), total wall
+ * impacts, total charge received from the walls, and the per-y-cell particle
+ * counts summed over the steps (hist_y: host, ny doubles, may be NULL);
+ * n_samples: number of steps summed.  Synchronises. */
+tribo_status tribo_stats(tribo_ctx* ctx, const tribo_particles* p, double* sum_q,
+                         uint64_t* n_impacts, double* sum_wall, double* hist_y,
+                         int64_t* n_samples);
+tribo_status tribo_reset_stats(tribo_ctx* ctx);
+
+/* Wait for the context's stream; report the sticky device error word. */
+tribo_status tribo_sync(tribo_ctx* ctx);
+uint32_t     tribo_error_bits(const tribo_ctx* ctx);
+tribo_status tribo_clear_error(tribo_ctx* ctx);
+
+/* Number of kernel launches the library issued since the context was made. */
+int64_t      tribo_launch_count(const tribo_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * each launch.  tribo_timing_enable(ctx, 1) clears and starts the
+ * accumulators, 0 stops them.  tribo_timing_read synchronises and returns,
+ * for phases 0..nphases-1, the summed device time [ms] and the launch count
+ * since the last enable (ms, counts: host arrays of nphases entries).
+ * tribo_phase_name gives the phase's kernel name (NULL past the last). */
+#define TRIBO_NPHASES 10
+tribo_status tribo_timing_enable(tribo_ctx* ctx, int32_t on);
+tribo_status tribo_timing_read(tribo_ctx* ctx, double* ms, int64_t* counts, int32_t nphases);
+const char*  tribo_phase_name(int32_t phase);
+
+const char*  tribo_strerror(tribo_status s);
+const char*  tribo_last_error(void);      /* thread-local detail of the last failure */
+void         tribo_destroy(tribo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRIBO_H */

@@ -1,0 +1,298 @@
+"""Python binding of the C ABI (argument marshalling only).
+
+Every function named tribo_* mirrors the C entry point of the same name in
+include/tribo.h.  PyTorch is used for device memory and streams only; all
+arithmetic of the hot path runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import check, load
+
+
+@dataclasses.dataclass
+class Params:
+    """Physical parameters (Table 1 of the paper) and switches.
+
+    U_c, the particle-wall contact potential, is not given in the paper.
+    """
+    mu_p: float = 0.4          # Poisson's ratio, particle
+    E_p: float = 1e8           # Young's modulus, particle [Pa]
+    phi_p: float = 1e13        # resistivity, particle [Ohm m]
+    k_e: float = 0.95          # restitution ratio
+    mu_w: float = 0.28         # Poisson's ratio, wall
+    E_w: float = 1e11          # Young's modulus, wall [Pa]
+    eps_w: float = 5.0         # relative permittivity, wall
+    h: float = 1e-9            # effective separation [m]
+    eps: float = 8.854e-12     # gas permittivity [F/m]
+    eps0: float = 8.854e-12    # vacuum permittivity [F/m]
+    nu: float = 1.46e-5        # gas kinematic viscosity [m^2/s]
+    rho: float = 1.2           # gas density [kg/m^3]
+    rho_p: float = 1150.0      # particle density [kg/m^3]
+    U_c: float = 1.0           # contact potential [V]
+    kappa_A: float = 1.0       # contact-area factor
+    drag_law: int = _abi.TRIBO_DRAG_STOKES
+    impact_vel: int = _abi.TRIBO_IMPACT_SPEED
+    dq_t: int = 1
+    electrostatics: int = 1
+    precision: int = _abi.TRIBO_MIXED
+    sort_every: int = 0
+
+    def to_c(self) -> _abi.tribo_params:
+        p = _abi.tribo_params()
+        for f in dataclasses.fields(self):
+            setattr(p, f.name, getattr(self, f.name))
+        return p
+
+    def with_(self, **kw) -> "Params":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def real_dtype(self):
+        return np.float64 if self.precision == _abi.TRIBO_FP64 else np.float32
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a contiguous torch tensor or numpy array (None for None)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _on_host(a) -> bool:
+    return isinstance(a, np.ndarray) or (hasattr(a, "is_cuda") and not a.is_cuda)
+
+
+class Particles:
+    """Structure-of-arrays particle ensemble (torch CUDA tensors or numpy)."""
+    REAL = ("x", "y", "z", "vx", "vy", "vz", "d")
+    ALL = REAL + ("q", "q_wall", "n_imp", "id", "cell")
+
+    def __init__(self, **arrays):
+        for name in self.ALL:
+            setattr(self, name, arrays.get(name))
+        self.n = int(self.x.shape[0])
+
+    @classmethod
+    def from_numpy(cls, src, precision: int, device: Optional[str] = "cuda", with_id: bool = True,
+                   with_cell: bool = False) -> "Particles":
+        """src: object or dict with x, y, z, vx, vy, vz, d, q (and optionally
+        q_wall, n_imp).  device=None keeps host (numpy) arrays."""
+        get = (lambda k: src.get(k)) if isinstance(src, dict) else (lambda k: getattr(src, k, None))
+        rdt = np.float64 if precision == _abi.TRIBO_FP64 else np.float32
+        n = np.asarray(get("x")).shape[0]
+        arr = {k: np.ascontiguousarray(np.asarray(get(k), dtype=rdt)) for k in cls.REAL}
+        arr["q"] = np.ascontiguousarray(np.asarray(get("q"), dtype=np.float64))
+        qw = get("q_wall")
+        arr["q_wall"] = np.zeros(n) if qw is None else np.ascontiguousarray(np.asarray(qw, np.float64))
+        ni = get("n_imp")
+        arr["n_imp"] = np.zeros(n, np.uint32) if ni is None else np.ascontiguousarray(np.asarray(ni, np.uint32))
+        if with_id:
+            ids = get("id")
+            arr["id"] = np.arange(n, dtype=np.uint32) if ids is None else np.asarray(ids, np.uint32)
+        if with_cell:
+            arr["cell"] = np.zeros(n, np.uint32)
+        if device is None:
+            return cls(**arr)
+        import torch
+        t = {}
+        for k, v in arr.items():
+            if v.dtype == np.uint32:
+                t[k] = torch.from_numpy(v.view(np.int32)).to(device)
+            else:
+                t[k] = torch.from_numpy(v).to(device)
+        return cls(**t)
+
+    def to_numpy(self) -> dict:
+        out = {}
+        for k in self.ALL:
+            v = getattr(self, k)
+            if v is None:
+                continue
+            if not isinstance(v, np.ndarray):
+                v = v.detach().cpu().numpy()
+            if k in ("n_imp", "id", "cell"):
+                v = v.view(np.uint32)
+            out[k] = v
+        return out
+
+    @property
+    def on_host(self) -> bool:
+        return _on_host(self.x)
+
+    def c_struct(self) -> _abi.tribo_particles:
+        s = _abi.tribo_particles()
+        s.n = self.n
+        for k in self.ALL:
+            setattr(s, k, _ptr(getattr(self, k)))
+        s.on_host = 1 if self.on_host else 0
+        return s
+
+
+# ---------------------------------------------------------------- C-named calls
+
+def tribo_init(nx: int, ny: int, nz: int, lx: float, lz: float, y_faces, params: Params,
+               u_lattice=None, max_particles: int = 0, stream=None) -> int:
+    lib = load()
+    yf = np.ascontiguousarray(np.asarray(y_faces, dtype=np.float64))
+    g = _abi.tribo_grid(nx, ny, nz, lx, lz, yf.ctypes.data_as(C.POINTER(C.c_double)))
+    fl = None
+    if u_lattice is not None:
+        fl = _abi.tribo_fluid(_ptr(u_lattice), 1 if _on_host(u_lattice) else 0)
+    ctx = C.c_void_p()
+    sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    p = params.to_c()
+    check(lib.tribo_init(C.byref(ctx), C.byref(g), C.byref(fl) if fl is not None else None, C.byref(p),
+                         int(max_particles), sp), "tribo_init")
+    return ctx.value
+
+
+def tribo_set_fluid(ctx: int, u_lattice) -> None:
+    fl = _abi.tribo_fluid(_ptr(u_lattice), 1 if _on_host(u_lattice) else 0)
+    check(load().tribo_set_fluid(ctx, C.byref(fl)), "tribo_set_fluid")
+
+
+def tribo_set_params(ctx: int, params: Params) -> None:
+    p = params.to_c()
+    check(load().tribo_set_params(ctx, C.byref(p)), "tribo_set_params")
+
+
+def tribo_step(ctx: int, particles: Particles, dt: float, nsteps: int = 1) -> None:
+    s = particles.c_struct()
+    check(load().tribo_step(ctx, C.byref(s), float(dt), int(nsteps)), "tribo_step")
+
+
+def tribo_poisson(ctx: int, rho, phi, E) -> None:
+    check(load().tribo_poisson(ctx, _ptr(rho), _ptr(phi), _ptr(E)), "tribo_poisson")
+
+
+def tribo_stats(ctx: int, particles: Optional[Particles], ny: int) -> dict:
+    lib = load()
+    sq = C.c_double(0.0)
+    ni = C.c_uint64(0)
+    sw = C.c_double(0.0)
+    ns = C.c_int64(0)
+    hist = np.zeros(ny)
+    s = particles.c_struct() if particles is not None else None
+    check(lib.tribo_stats(ctx, C.byref(s) if s is not None else None,
+                          C.byref(sq) if s is not None else None, C.byref(ni), C.byref(sw),
+                          hist.ctypes.data_as(C.POINTER(C.c_double)), C.byref(ns)), "tribo_stats")
+    return dict(sum_q=sq.value if s is not None else None, n_impacts=ni.value, sum_wall=sw.value,
+                hist_y=hist, n_samples=ns.value)
+
+
+def tribo_reset_stats(ctx: int) -> None:
+    check(load().tribo_reset_stats(ctx), "tribo_reset_stats")
+
+
+def tribo_sync(ctx: int) -> None:
+    check(load().tribo_sync(ctx), "tribo_sync")
+
+
+def tribo_error_bits(ctx: int) -> int:
+    return int(load().tribo_error_bits(ctx))
+
+
+def tribo_clear_error(ctx: int) -> None:
+    check(load().tribo_clear_error(ctx), "tribo_clear_error")
+
+
+def tribo_launch_count(ctx: int) -> int:
+    return int(load().tribo_launch_count(ctx))
+
+
+def tribo_timing_enable(ctx: int, on: bool) -> None:
+    check(load().tribo_timing_enable(ctx, 1 if on else 0), "tribo_timing_enable")
+
+
+def tribo_timing_read(ctx: int) -> dict:
+    """{kernel phase name: (total device ms, launches)} since the last enable."""
+    lib = load()
+    n = _abi.TRIBO_NPHASES
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    check(lib.tribo_timing_read(ctx, ms, cnt, n), "tribo_timing_read")
+    return {lib.tribo_phase_name(i).decode(): (ms[i], cnt[i]) for i in range(n)}
+
+
+def tribo_phase_name(phase: int):
+    r = load().tribo_phase_name(phase)
+    return None if r is None else r.decode()
+
+
+def tribo_destroy(ctx: int) -> None:
+    load().tribo_destroy(ctx)
+
+
+# ---------------------------------------------------------------- convenience
+
+class Channel:
+    """One channel context: grid, gas field, parameters and workspaces."""
+
+    def __init__(self, nx, ny, nz, lx, lz, y_faces, params: Params, u_lattice=None,
+                 max_particles: int = 0, stream=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.lx, self.lz = float(lx), float(lz)
+        self.y_faces = np.asarray(y_faces, np.float64)
+        self.params = params
+        self.ctx = tribo_init(nx, ny, nz, lx, lz, self.y_faces, params, u_lattice, max_particles, stream)
+
+    def step(self, particles: Particles, dt: float, nsteps: int = 1) -> None:
+        tribo_step(self.ctx, particles, dt, nsteps)
+
+    def set_fluid(self, u_lattice) -> None:
+        tribo_set_fluid(self.ctx, u_lattice)
+
+    def set_params(self, params: Params) -> None:
+        tribo_set_params(self.ctx, params)
+        self.params = params
+
+    def poisson(self, rho, want_phi: bool = False):
+        import torch
+        rdt = torch.float64 if self.params.precision == _abi.TRIBO_FP64 else torch.float32
+        E = torch.empty((self.nz, self.ny + 2, self.nx, 4), dtype=rdt, device=rho.device)
+        phi = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=rho.device) if want_phi else None
+        tribo_poisson(self.ctx, rho, phi, E)
+        return phi, E
+
+    def stats(self, particles: Optional[Particles] = None) -> dict:
+        return tribo_stats(self.ctx, particles, self.ny)
+
+    def reset_stats(self) -> None:
+        tribo_reset_stats(self.ctx)
+
+    def sync(self) -> None:
+        tribo_sync(self.ctx)
+
+    @property
+    def error_bits(self) -> int:
+        return tribo_error_bits(self.ctx)
+
+    @property
+    def launches(self) -> int:
+        return tribo_launch_count(self.ctx)
+
+    def close(self) -> None:
+        if self.ctx:
+            tribo_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

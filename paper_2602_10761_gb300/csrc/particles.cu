@@ -1,0 +1,464 @@
+// Particle kernels: locate, charge deposition, the fused particle step and
+// the charge reduction.
+//
+// Sec. 2.2, Eq. (particle-motion): du_p/dt = f_ad + f_el here (gravity is
+// zero in the paper's runs; particle-particle collisions are not part of this
+// path).  Drag after Schiller & Naumann (C_D = 24/Re_p (1 + Re_p^(2/3)/6) up
+// to Re_p = 1000, 0.424 above) or in the Stokes limit; f_el = q E / m_p with
+// m_p = pi d^3 rho_p / 6.  Hard-sphere wall collisions flip the wall-normal
+// velocity and keep the tangential ones.  Each wall impact transfers the
+// condenser-model charge of Sec. 2.3.1:
+//   dq_c = -C U_c (1 - exp(-dt_w / T_w)), C = eps A_iw / h,
+//   A_iw = pi (d/2) alpha_iw, alpha_iw = (d/2) (5/8 pi rho_p (1 + k_e) |u_i|^2
+//          ((1 - mu_p^2)/E_p + (1 - mu_w^2)/E_w))^(2/5),
+//   dt_w = 2.94 alpha_iw / |u_i|, T_w = eps_w eps0 phi_p,
+//   dq_t = -(A_iw / (pi d^2)) q (pre-charge over the contact-area fraction).
+//
+// Integration over one step with u and E frozen at the start of the step
+// (exponential integrator, exact for constant u, a):
+//   s = dt / tau, phi1 = 1 - e^-s, phi2 = s - phi1,
+//   v' = v + (u + a tau - v) phi1,  x' = x + tau (v phi1 + (u + a tau) phi2).
+// Contact: the centre closer than r = d/2 to a wall; the position is mirrored
+// about the contact plane and v_y flips.  The impact charge, the per-particle
+// charge and all charge sums are FP64 in both precisions.
+//
+// Cell location is exact in both precisions: the cell index is the largest i
+// with x >= i dx (FP64), so in FP32 the coordinate is compared with the
+// smallest float not below each FP64 face.
+#include <cmath>
+
+#include "tribo_internal.cuh"
+
+namespace tribo {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <class R>
+struct StepArgs {
+    int nx, ny, nz, nyn;
+    R lx, ly, lz, inv_dx, inv_dz, dt;
+    double dx, dz;                 // FP64 cell sizes (exact locate in FP64 mode)
+    const double* yf;              // ny+1 FP64 faces
+    const float* yf_up;            // ny+1 rounded-up float faces
+    const float* xf_up;            // nx+1
+    const float* zf_up;            // nz+1
+    const int* ybin;
+    int ybins;
+    R ybin_scale;                  // ybins / ly
+    const R* Yr;                   // ny+2 lattice nodes
+    const R* invdY;                // ny+1 inverse node spacings
+    const vec4<R>* u;
+    const vec4<R>* E;
+    double* Q;                     // cell charge sums for the next step (may be NULL)
+    unsigned long long* hist;      // ny (may be NULL)
+    Accum* acc;
+    // physics
+    int drag_law, impact_vel, dq_t, electro;
+    R tau_coef;                    // rho_p / (18 rho nu)
+    R inv_nu;
+    R sn_coef;                     // (4/3)(rho_p/rho) / 0.424
+    R mass_coef;                   // pi rho_p / 6
+    double alpha_coef;             // 5/8 pi rho_p (1 + k_e) ((1-mu_p^2)/E_p + (1-mu_w^2)/E_w)
+    double kappa_pi;               // kappa_A pi
+    double eps_over_h;
+    double inv_T_w;
+    double U_c;
+};
+
+template <class R> __device__ __forceinline__ R rfloor(R v);
+template <> __device__ __forceinline__ float rfloor<float>(float v) { return floorf(v); }
+template <> __device__ __forceinline__ double rfloor<double>(double v) { return floor(v); }
+template <class R> __device__ __forceinline__ R rexpm1(R v);
+template <> __device__ __forceinline__ float rexpm1<float>(float v) { return expm1f(v); }
+template <> __device__ __forceinline__ double rexpm1<double>(double v) { return expm1(v); }
+template <class R> __device__ __forceinline__ R rsqrt_(R v);
+template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return sqrt(v); }
+template <class R> __device__ __forceinline__ R rpow23(R v);
+template <> __device__ __forceinline__ float rpow23<float>(float v) { return cbrtf(v * v); }
+template <> __device__ __forceinline__ double rpow23<double>(double v) { return cbrt(v * v); }
+template <class R> __device__ __forceinline__ bool rfinite(R v) { return isfinite(v); }
+
+// largest i in [0, n-1] with s >= face_i, faces i*h (FP64) -------------------
+__device__ __forceinline__ int cell_uniform(double s, double h, int n, const float*) {
+    int i = (int)floor(s / h);
+    i = min(max(i, 0), n - 1);
+    while (i > 0 && s < (double)i * h) --i;
+    while (i < n - 1 && s >= (double)(i + 1) * h) ++i;
+    return i;
+}
+__device__ __forceinline__ int cell_uniform(float s, double h, int n, const float* f_up) {
+    int i = (int)floorf(s * (float)(1.0 / h));
+    i = min(max(i, 0), n - 1);
+    while (i > 0 && s < f_up[i]) --i;
+    while (i < n - 1 && s >= f_up[i + 1]) ++i;
+    return i;
+}
+template <class R>
+__device__ __forceinline__ int cell_y(R y, const StepArgs<R>& a) {
+    int b = (int)(y * a.ybin_scale);
+    b = min(max(b, 0), a.ybins - 1);
+    int j = a.ybin[b];
+    if (sizeof(R) == 8) {
+        const double yd = (double)y;
+        while (j > 0 && yd < a.yf[j]) --j;
+        while (j < a.ny - 1 && yd >= a.yf[j + 1]) ++j;
+    } else {
+        const float yfl = (float)y;
+        while (j > 0 && yfl < a.yf_up[j]) --j;
+        while (j < a.ny - 1 && yfl >= a.yf_up[j + 1]) ++j;
+    }
+    return j;
+}
+
+template <class R>
+__device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a, int* jout) {
+    const int i = cell_uniform(x, a.dx, a.nx, a.xf_up);
+    const int k = cell_uniform(z, a.dz, a.nz, a.zf_up);
+    const int j = cell_y(y, a);
+    *jout = j;
+    return ((uint32_t)k * (uint32_t)a.ny + (uint32_t)j) * (uint32_t)a.nx + (uint32_t)i;
+}
+
+template <class R>
+__device__ __forceinline__ vec4<R> ld4(const vec4<R>* p) { return *p; }
+template <>
+__device__ __forceinline__ vec4<float> ld4<float>(const vec4<float>* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return vec4<float>{v.x, v.y, v.z, v.w};
+}
+
+// trilinear gather of one or two lattice fields at (x, y, z) given the cell j
+template <class R>
+__device__ __forceinline__ void gather(const StepArgs<R>& a, R x, R y, R z, int j, R uf[3], R Ef[3],
+                                       bool withE, unsigned int* err) {
+    R sx = x * a.inv_dx - (R)0.5;
+    R fx = rfloor(sx);
+    R wx = sx - fx;
+    R sz = z * a.inv_dz - (R)0.5;
+    R fz = rfloor(sz);
+    R wz = sz - fz;
+    if (!(fx >= (R)-1 && fx <= (R)(a.nx - 1)) || !(fz >= (R)-1 && fz <= (R)(a.nz - 1))) {
+        *err |= TRIBO_DEV_OUTSIDE;
+        fx = 0; fz = 0; wx = 0; wz = 0;
+    }
+    int i0 = (int)fx, k0 = (int)fz;
+    int i1 = i0 + 1, k1 = k0 + 1;
+    if (i0 < 0) i0 += a.nx;
+    if (i1 >= a.nx) i1 -= a.nx;
+    if (k0 < 0) k0 += a.nz;
+    if (k1 >= a.nz) k1 -= a.nz;
+    const int jn0 = (y >= a.Yr[j + 1]) ? j + 1 : j;
+    const R wy = (y - a.Yr[jn0]) * a.invdY[jn0];
+    const R wx0 = (R)1 - wx, wy0 = (R)1 - wy, wz0 = (R)1 - wz;
+    const size_t r00 = ((size_t)k0 * a.nyn + jn0) * a.nx;
+    const size_t r01 = ((size_t)k0 * a.nyn + jn0 + 1) * a.nx;
+    const size_t r10 = ((size_t)k1 * a.nyn + jn0) * a.nx;
+    const size_t r11 = ((size_t)k1 * a.nyn + jn0 + 1) * a.nx;
+    const size_t idx[8] = {r00 + i0, r00 + i1, r01 + i0, r01 + i1, r10 + i0, r10 + i1, r11 + i0, r11 + i1};
+    const R w[8] = {wz0 * wy0 * wx0, wz0 * wy0 * wx, wz0 * wy * wx0, wz0 * wy * wx,
+                    wz * wy0 * wx0,  wz * wy0 * wx,  wz * wy * wx0,  wz * wy * wx};
+    R u0 = 0, u1 = 0, u2 = 0, e0 = 0, e1 = 0, e2 = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const vec4<R> v = ld4<R>(a.u + idx[c]);
+        u0 += w[c] * v.x;
+        u1 += w[c] * v.y;
+        u2 += w[c] * v.z;
+    }
+    if (withE) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const vec4<R> v = ld4<R>(a.E + idx[c]);
+            e0 += w[c] * v.x;
+            e1 += w[c] * v.y;
+            e2 += w[c] * v.z;
+        }
+    }
+    uf[0] = u0; uf[1] = u1; uf[2] = u2;
+    Ef[0] = e0; Ef[1] = e1; Ef[2] = e2;
+}
+
+template <class R>
+__device__ __forceinline__ R phi2_of(R s, R phi1) {
+    if (s < (R)0.5) {
+        // sum_{n>=2} (-1)^n s^n / n!, truncated below the precision's epsilon
+        const int nt = sizeof(R) == 8 ? 18 : 10;
+        R term = s * s * (R)0.5;
+        R sum = term;
+        for (int n = 3; n <= nt; ++n) {
+            term = -term * s / (R)n;
+            sum += term;
+        }
+        return sum;
+    }
+    return s - phi1;
+}
+
+// the condenser-model charge of one wall impact (FP64)
+template <class R>
+__device__ __forceinline__ double impact_charge(const StepArgs<R>& a, double d, double speed, double q) {
+    if (!(speed > 0.0)) return 0.0;
+    const double r = 0.5 * d;
+    const double alpha = r * pow(a.alpha_coef * speed * speed, 0.4);
+    const double A = a.kappa_pi * r * alpha;
+    const double C = a.eps_over_h * A;
+    const double dt_w = 2.94 * alpha / speed;
+    double dq = -C * a.U_c * (-expm1(-dt_w * a.inv_T_w));
+    if (a.dq_t) dq += -(A / (M_PI * d * d)) * q;
+    return dq;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_step(StepArgs<R> a, PView p, int write_cell) {
+    extern __shared__ unsigned int sh_hist[];
+    const bool use_hist = a.hist != nullptr;
+    if (use_hist) {
+        for (int b = threadIdx.x; b < a.ny; b += blockDim.x) sh_hist[b] = 0u;
+        __syncthreads();
+    }
+    R* X = (R*)p.x; R* Y = (R*)p.y; R* Z = (R*)p.z;
+    R* VX = (R*)p.vx; R* VY = (R*)p.vy; R* VZ = (R*)p.vz;
+    const R* D = (const R*)p.d;
+    unsigned int err = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride) {
+        R x = X[n], y = Y[n], z = Z[n];
+        R vx = VX[n], vy = VY[n], vz = VZ[n];
+        const R d = D[n];
+        double q = p.q[n];
+        if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
+        int j;
+        (void)cell_key<R>(x, y, z, a, &j);
+        R uf[3], Ef[3];
+        gather<R>(a, x, y, z, j, uf, Ef, a.electro != 0, &err);
+        // acceleration q E / m
+        R ax = 0, ay = 0, az = 0;
+        if (a.electro) {
+            const R qm = (R)q / (a.mass_coef * d * d * d);
+            ax = qm * Ef[0]; ay = qm * Ef[1]; az = qm * Ef[2];
+        }
+        R xn, yn, zn, vxn, vyn, vzn;
+        if (a.drag_law == TRIBO_DRAG_OFF) {
+            const R h = (R)0.5 * a.dt * a.dt;
+            xn = x + vx * a.dt + ax * h;
+            yn = y + vy * a.dt + ay * h;
+            zn = z + vz * a.dt + az * h;
+            vxn = vx + ax * a.dt; vyn = vy + ay * a.dt; vzn = vz + az * a.dt;
+        } else {
+            const R rx = vx - uf[0], ry = vy - uf[1], rz = vz - uf[2];
+            const R rel = rsqrt_(rx * rx + ry * ry + rz * rz);
+            const R tau_p = a.tau_coef * d * d;
+            R tau = tau_p;
+            if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN) {
+                const R re = rel * d * a.inv_nu;
+                if (re > (R)1000) tau = a.sn_coef * d / rel;
+                else tau = tau_p / ((R)1 + rpow23(re) / (R)6);
+            }
+            const R s = a.dt / tau;
+            const R phi1 = -rexpm1(-s);
+            const R phi2 = phi2_of(s, phi1);
+            const R tx = uf[0] + ax * tau, ty = uf[1] + ay * tau, tz = uf[2] + az * tau;
+            vxn = vx + (tx - vx) * phi1;
+            vyn = vy + (ty - vy) * phi1;
+            vzn = vz + (tz - vz) * phi1;
+            xn = x + tau * (vx * phi1 + tx * phi2);
+            yn = y + tau * (vy * phi1 + ty * phi2);
+            zn = z + tau * (vz * phi1 + tz * phi2);
+        }
+        // periodic wrap in x and z
+        xn = xn - a.lx * rfloor(xn / a.lx);
+        if (xn >= a.lx) xn -= a.lx;
+        zn = zn - a.lz * rfloor(zn / a.lz);
+        if (zn >= a.lz) zn -= a.lz;
+        // wall contact (hard sphere, specular)
+        const R r = (R)0.5 * d;
+        const bool lo = yn < r;
+        const bool hi = yn > a.ly - r;
+        if (lo || hi) {
+            // mirror about the contact plane; the charge transfer is FP64
+            const double rd = 0.5 * (double)d;
+            const double plane = lo ? rd : (double)a.ly - rd;
+            const double ym = 2.0 * plane - (double)yn;
+            yn = (R)ym;
+            vyn = -vyn;
+            if (yn < r || yn > a.ly - r) err |= TRIBO_DEV_ESCAPED;
+            double speed;
+            if (a.impact_vel == TRIBO_IMPACT_NORMAL) {
+                speed = fabs((double)vyn);
+            } else {
+                speed = sqrt((double)vxn * (double)vxn + (double)vyn * (double)vyn + (double)vzn * (double)vzn);
+            }
+            const double dq = impact_charge<R>(a, (double)d, speed, q);
+            q += dq;
+            p.q[n] = q;
+            p.q_wall[n] += dq;
+            p.n_imp[n] += 1u;
+            atomicAdd(&a.acc->sum_wall, dq);
+            atomicAdd(&a.acc->n_impacts, 1ull);
+        }
+        if (!(rfinite(xn) && rfinite(yn) && rfinite(zn) && rfinite(vxn) && rfinite(vyn) && rfinite(vzn)))
+            err |= TRIBO_DEV_NONFINITE;
+        X[n] = xn; Y[n] = yn; Z[n] = zn;
+        VX[n] = vxn; VY[n] = vyn; VZ[n] = vzn;
+        int jn;
+        const uint32_t key = cell_key<R>(xn, yn, zn, a, &jn);
+        if (a.Q) atomicAdd(&a.Q[key], q);
+        if (write_cell) p.cell[n] = key;
+        if (use_hist) atomicAdd(&sh_hist[jn], 1u);
+    }
+    if (err) atomicOr(&a.acc->err, err);
+    if (use_hist) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < a.ny; b += blockDim.x) {
+            const unsigned int v = sh_hist[b];
+            if (v) atomicAdd(&a.hist[b], (unsigned long long)v);
+        }
+    }
+}
+
+template <class R>
+__global__ void k_deposit(StepArgs<R> a, PView p) {
+    const R* X = (const R*)p.x; const R* Y = (const R*)p.y; const R* Z = (const R*)p.z;
+    unsigned int err = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride) {
+        R y = Y[n];
+        if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
+        int j;
+        const uint32_t key = cell_key<R>(X[n], y, Z[n], a, &j);
+        atomicAdd(&a.Q[key], p.q[n]);
+    }
+    if (err) atomicOr(&a.acc->err, err);
+}
+
+__global__ void k_sum_q(const double* __restrict__ q, int64_t n, double* out) {
+    __shared__ double sh[kThreads / 32];
+    double s = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) s += q[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) atomicAdd(out, s);
+    }
+}
+
+template <class R>
+__global__ void k_lattice_from_aos3(const R* __restrict__ src, vec4<R>* __restrict__ dst, size_t nodes) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += (size_t)gridDim.x * blockDim.x) {
+        vec4<R> v;
+        v.x = src[3 * i + 0];
+        v.y = src[3 * i + 1];
+        v.z = src[3 * i + 2];
+        v.w = (R)0;
+        dst[i] = v;
+    }
+}
+
+template <class R>
+StepArgs<R> make_args(tribo_ctx* c, double dt) {
+    StepArgs<R> a{};
+    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.nyn = c->ny + 2;
+    a.lx = (R)c->lx; a.ly = (R)c->ly; a.lz = (R)c->lz;
+    a.inv_dx = (R)(1.0 / c->dx); a.inv_dz = (R)(1.0 / c->dz);
+    a.dt = (R)dt;
+    a.dx = c->dx; a.dz = c->dz;
+    a.yf = c->d_yf; a.yf_up = c->d_yf_up; a.xf_up = c->d_xf_up; a.zf_up = c->d_zf_up;
+    a.ybin = c->d_ybin; a.ybins = c->ybins; a.ybin_scale = (R)((double)c->ybins / c->ly);
+    a.Yr = (const R*)c->d_Yr; a.invdY = (const R*)c->d_invdY;
+    a.u = (const vec4<R>*)c->u_lat; a.E = (const vec4<R>*)c->E_lat;
+    a.Q = nullptr; a.hist = nullptr; a.acc = c->d_acc;
+    const tribo_params& P = c->P;
+    a.drag_law = P.drag_law; a.impact_vel = P.impact_vel; a.dq_t = P.dq_t; a.electro = P.electrostatics;
+    a.tau_coef = (R)(P.rho_p / (18.0 * P.rho * P.nu));
+    a.inv_nu = (R)(1.0 / P.nu);
+    a.sn_coef = (R)((4.0 / 3.0) * (P.rho_p / P.rho) / 0.424);
+    a.mass_coef = (R)(M_PI * P.rho_p / 6.0);
+    const double elastic = (1.0 - P.mu_p * P.mu_p) / P.E_p + (1.0 - P.mu_w * P.mu_w) / P.E_w;
+    a.alpha_coef = 0.625 * M_PI * P.rho_p * (1.0 + P.k_e) * elastic;
+    a.kappa_pi = P.kappa_A * M_PI;
+    a.eps_over_h = P.eps / P.h;
+    a.inv_T_w = 1.0 / (P.eps_w * P.eps0 * P.phi_p);
+    a.U_c = P.U_c;
+    return a;
+}
+
+int grid_for(int64_t n) {
+    int64_t b = (n + kThreads - 1) / kThreads;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+template <class R>
+tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell) {
+    StepArgs<R> a = make_args<R>(c, dt);
+    a.Q = deposit_next ? c->Q : nullptr;
+    a.hist = c->d_hist;
+    const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
+    phase_begin(c, PH_STEP);
+    k_step<R><<<grid_for(p.n), kThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
+template <class R>
+tribo_status deposit_impl(tribo_ctx* c, const PView& p) {
+    StepArgs<R> a = make_args<R>(c, 0.0);
+    a.Q = c->Q;
+    phase_begin(c, PH_DEPOSIT);
+    k_deposit<R><<<grid_for(p.n), kThreads, 0, c->stream>>>(a, p);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
+}  // namespace
+
+tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell) {
+    if (p.n == 0) return TRIBO_OK;
+    if (c->prec == TRIBO_FP64) return step_impl<double>(c, p, dt, deposit_next, write_cell);
+    return step_impl<float>(c, p, dt, deposit_next, write_cell);
+}
+
+tribo_status particles_deposit(tribo_ctx* c, const PView& p) {
+    if (p.n == 0) return TRIBO_OK;
+    if (c->prec == TRIBO_FP64) return deposit_impl<double>(c, p);
+    return deposit_impl<float>(c, p);
+}
+
+tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out) {
+    TRIBO_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double), c->stream));
+    if (p.n == 0) return TRIBO_OK;
+    phase_begin(c, PH_AUX);
+    k_sum_q<<<grid_for(p.n), kThreads, 0, c->stream>>>(p.q, p.n, d_out);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
+tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev) {
+    const size_t nodes = (size_t)c->nz * (c->ny + 2) * c->nx;
+    const int blocks = (int)std::min<size_t>((nodes + kThreads - 1) / kThreads, 152 * 32);
+    phase_begin(c, PH_AUX);
+    if (c->prec == TRIBO_FP64)
+        k_lattice_from_aos3<double><<<blocks, kThreads, 0, c->stream>>>((const double*)src_dev,
+                                                                        (vec4<double>*)c->u_lat, nodes);
+    else
+        k_lattice_from_aos3<float><<<blocks, kThreads, 0, c->stream>>>((const float*)src_dev,
+                                                                       (vec4<float>*)c->u_lat, nodes);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
+tribo_status particles_setup(tribo_ctx* c) {
+    TRIBO_CUDA(cudaFuncSetAttribute(k_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 1024 * 4));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 1024 * 4));
+    return TRIBO_OK;
+}
+
+}  // namespace tribo

@@ -1,0 +1,468 @@
+// Electrostatic Poisson solve and E = -grad(phi) on the channel grid.
+//
+// Sec. 2.2: laplacian(phi) = -rho_el / eps, the charge density of a grid cell
+// being the sum of its particles' charges over the cell volume, and
+// E = -grad(phi).  Sec. 3.1: second-order finite volumes; the walls are
+// grounded conductors (phi = 0), which gives the image-charge attraction
+// discussed in Sec. 4.2.
+//
+// Discretisation (the paper gives neither stencil nor gradient scheme): the
+// 3-point operator in x and z and the flux form on the stretched y grid, with
+// phi = 0 on the wall faces.  The DFT in x and z diagonalises the x and z
+// parts with modified wavenumbers lam(m) = (4/h^2) sin^2(pi m / N), leaving a
+// real tridiagonal system in y per (m_x, m_z) pencil, solved in FP64 by the
+// Thomas algorithm.  E is formed in spectral space: the central difference in
+// x (z) is the multiplier -i sin(2 pi m / N) / h, and the Gauss-linear E_y at
+// each lattice node is a 3-point combination of phi in y; the spectra are then
+// transformed back to the wall-extended lattice.
+//
+// Passes (each a kernel):
+//   fwd_x : real line FFT in x of -rho/eps (charge sums scaled per row),
+//           optionally zeroing the charge buffer for the next deposit
+//   fwd_z : complex FFT in z of each (j, m_x) column
+//   solve : FP64 Thomas per pencil, then the E (and phi) spectra per node
+//   inv_z : inverse complex FFT in z of each field column
+//   inv_x : inverse real FFT in x, writing float4/double4 E nodes (and phi)
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "tribo_internal.cuh"
+
+namespace tribo {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+bool make_plan_radices(int n, FftPlan& p) {
+    p.n = n;
+    p.npass = 0;
+    int m = n;
+    while (m % 4 == 0) { p.radix[p.npass++] = 4; m /= 4; }
+    while (m % 2 == 0) { p.radix[p.npass++] = 2; m /= 2; }
+    while (m % 3 == 0) { p.radix[p.npass++] = 3; m /= 3; }
+    return m == 1 && p.npass <= 24;
+}
+
+template <class R>
+tribo_status make_plan(int n, FftPlan& p) {
+    if (!make_plan_radices(n, p)) {
+        set_last_error("FFT length " + std::to_string(n) + " is not 2^a 3^b");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    std::vector<cplx<R>> tw(n);
+    for (int e = 0; e < n; ++e) {
+        double a = 2.0 * M_PI * (double)e / (double)n;
+        tw[e] = cplx<R>{(R)std::cos(a), (R)(-std::sin(a))};
+    }
+    TRIBO_CUDA(cudaMalloc(&p.tw, sizeof(cplx<R>) * n));
+    TRIBO_CUDA(cudaMemcpy(p.tw, tw.data(), sizeof(cplx<R>) * n, cudaMemcpyHostToDevice));
+    return TRIBO_OK;
+}
+
+// In-place radix-r DFT of y[0..r) with direction sgn (-1 forward, +1 inverse).
+template <class R>
+__device__ __forceinline__ void small_dft(cplx<R>* y, int r, R sgn) {
+    if (r == 2) {
+        cplx<R> a = y[0], b = y[1];
+        y[0] = a + b;
+        y[1] = a - b;
+    } else if (r == 4) {
+        cplx<R> a = y[0] + y[2], b = y[0] - y[2], c = y[1] + y[3], d = mul_si(y[1] - y[3], sgn);
+        y[0] = a + c;
+        y[2] = a - c;
+        y[1] = b + d;
+        y[3] = b - d;
+    } else {  // r == 3
+        const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+        cplx<R> t1 = y[1] + y[2];
+        cplx<R> t2 = y[0] - scale(t1, (R)0.5);
+        cplx<R> t3 = mul_si(scale(y[1] - y[2], h), sgn);
+        y[0] = y[0] + t1;
+        y[1] = t2 + t3;
+        y[2] = t2 - t3;
+    }
+}
+
+// Stockham autosort FFT of nl lines of length n held line-major in A; B is a
+// scratch buffer of the same size.  All threads of the block take part.
+// Returns the buffer that holds the (naturally ordered) result.
+template <class R>
+__device__ cplx<R>* fft_smem(cplx<R>* A, cplx<R>* B, const FftPlan& plan, int nl, R sgn,
+                             const cplx<R>* __restrict__ tw) {
+    const int n = plan.n;
+    int Ls = 1;
+    for (int p = 0; p < plan.npass; ++p) {
+        const int r = plan.radix[p];
+        const int m = n / r;
+        const int stride = n / (r * Ls);
+        for (int idx = threadIdx.x; idx < nl * m; idx += blockDim.x) {
+            const int line = idx / m;
+            const int j = idx - line * m;
+            const int k = j % Ls;
+            const cplx<R>* in = A + line * n;
+            cplx<R> y[4];
+            y[0] = in[j];
+            for (int t = 1; t < r; ++t) {
+                cplx<R> w = tw[t * k * stride];
+                if (sgn > 0) w = conj(w);
+                y[t] = in[j + t * m] * w;
+            }
+            small_dft(y, r, sgn);
+            cplx<R>* out = B + line * n + (j - k) * r + k;
+            for (int u = 0; u < r; ++u) out[u * Ls] = y[u];
+        }
+        __syncthreads();
+        cplx<R>* t = A;
+        A = B;
+        B = t;
+        Ls *= r;
+    }
+    return A;
+}
+
+// ---------------------------------------------------------------- fwd_x
+template <class R>
+__global__ void k_fwd_x(double* __restrict__ src, const double* __restrict__ scale_row, int zero_src,
+                        cplx<R>* __restrict__ S, int nx, int ny, int nlines, int nxh, FftPlan plan,
+                        int lpb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* A = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* B = A + lpb * nx;
+    const int line0 = blockIdx.x * lpb;
+    const int nl = min(lpb, nlines - line0);
+    for (int idx = threadIdx.x; idx < nl * nx; idx += blockDim.x) {
+        const int line = line0 + idx / nx;
+        const int i = idx - (idx / nx) * nx;
+        const int j = line % ny;
+        const size_t g = (size_t)line * nx + i;
+        const double v = src[g];
+        if (zero_src) src[g] = 0.0;
+        A[idx] = cplx<R>{(R)v * (R)scale_row[j], (R)0};
+    }
+    __syncthreads();
+    cplx<R>* res = fft_smem<R>(A, B, plan, nl, (R)-1, (const cplx<R>*)plan.tw);
+    for (int idx = threadIdx.x; idx < nl * nxh; idx += blockDim.x) {
+        const int l = idx / nxh;
+        const int mx = idx - l * nxh;
+        S[(size_t)(line0 + l) * nxh + mx] = res[l * nx + mx];
+    }
+}
+
+// ---------------------------------------------------------------- z transforms
+// Columns along z of an array laid out [k][plane][mx] with nplanes planes per
+// z index: block (plane, mx tile) transforms `mt` columns in place.
+template <class R>
+__global__ void k_fft_z(cplx<R>* __restrict__ arr, int nz, int nplanes, int nxh, int mt, FftPlan plan,
+                        R sgn, size_t field_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* A = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* B = A + mt * nz;
+    const int plane = blockIdx.x;
+    const int mx0 = blockIdx.y * mt;
+    const int nt = min(mt, nxh - mx0);
+    cplx<R>* base = arr + field_stride * blockIdx.z;
+    for (int idx = threadIdx.x; idx < nz * nt; idx += blockDim.x) {
+        const int k = idx / nt;
+        const int t = idx - k * nt;
+        A[t * nz + k] = base[((size_t)k * nplanes + plane) * nxh + mx0 + t];
+    }
+    __syncthreads();
+    cplx<R>* res = fft_smem<R>(A, B, plan, nt, sgn, (const cplx<R>*)plan.tw);
+    for (int idx = threadIdx.x; idx < nz * nt; idx += blockDim.x) {
+        const int k = idx / nt;
+        const int t = idx - k * nt;
+        base[((size_t)k * nplanes + plane) * nxh + mx0 + t] = res[t * nz + k];
+    }
+}
+
+// ---------------------------------------------------------------- y solve
+// One thread per (m_z, m_x) pencil.  Thomas forward sweep with the shifted
+// diagonal b_j - lam, backward substitution, then the E spectra per node.
+// W holds dp (later phi) and Wc holds c'_j, both FP64, laid out [j][pencil].
+template <class R>
+__global__ void k_solve_y(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F, double2* __restrict__ W,
+                          double* __restrict__ Wc, const double* __restrict__ ycoef,
+                          const double* __restrict__ lamx, const double* __restrict__ lamz,
+                          const double* __restrict__ sinx, const double* __restrict__ sinz,
+                          const double* __restrict__ ey, int ny, int nz, int nxh, int want_phi) {
+    const int np = nz * nxh;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const int mz = p / nxh;
+    const int mx = p - mz * nxh;
+    const double lam = lamx[mx] + lamz[mz];
+    const double* a = ycoef;
+    const double* b = ycoef + ny;
+    const double* c = ycoef + 2 * ny;
+    // row j of the spectrum for pencil (mz, mx) sits at S[(mz*ny + j)*nxh + mx]
+    const cplx<R>* s = S + (size_t)mz * ny * nxh + mx;
+    double cp = 0.0;
+    double2 dp = make_double2(0.0, 0.0);
+    for (int j = 0; j < ny; ++j) {
+        const double den = (b[j] - lam) - a[j] * cp;
+        const double inv = 1.0 / den;
+        const cplx<R> r = s[(size_t)j * nxh];
+        dp = make_double2(((double)r.re - a[j] * dp.x) * inv, ((double)r.im - a[j] * dp.y) * inv);
+        cp = c[j] * inv;
+        W[(size_t)j * np + p] = dp;
+        Wc[(size_t)j * np + p] = cp;
+    }
+    double2 x = dp;
+    for (int j = ny - 2; j >= 0; --j) {
+        const double2 d = W[(size_t)j * np + p];
+        const double cj = Wc[(size_t)j * np + p];
+        x = make_double2(d.x - cj * x.x, d.y - cj * x.y);
+        W[(size_t)j * np + p] = x;
+    }
+    // fields: 0 = E_x, 1 = E_y, 2 = E_z, 3 = phi ; layout [f][mz][jn][mx]
+    const int nyn = ny + 2;
+    const size_t fstride = (size_t)nz * nyn * nxh;
+    const double sx = sinx[mx], sz = sinz[mz];
+    for (int jn = 0; jn < nyn; ++jn) {
+        const int jc = jn - 1;  // cell of this node (interior nodes)
+        double2 ph = make_double2(0.0, 0.0);
+        if (jc >= 0 && jc < ny) ph = W[(size_t)jc * np + p];
+        double2 eyv = make_double2(0.0, 0.0);
+        const double cm = ey[3 * jn + 0], c0 = ey[3 * jn + 1], cpv = ey[3 * jn + 2];
+        if (jc - 1 >= 0 && jc - 1 < ny && cm != 0.0) {
+            const double2 v = W[(size_t)(jc - 1) * np + p];
+            eyv.x += cm * v.x; eyv.y += cm * v.y;
+        }
+        if (jc >= 0 && jc < ny && c0 != 0.0) { eyv.x += c0 * ph.x; eyv.y += c0 * ph.y; }
+        if (jc + 1 >= 0 && jc + 1 < ny && cpv != 0.0) {
+            const double2 v = W[(size_t)(jc + 1) * np + p];
+            eyv.x += cpv * v.x; eyv.y += cpv * v.y;
+        }
+        const size_t o = ((size_t)mz * nyn + jn) * nxh + mx;
+        // -i s phi = (s * im, -s * re)
+        F[o] = cplx<R>{(R)(sx * ph.y), (R)(-sx * ph.x)};
+        F[fstride + o] = cplx<R>{(R)eyv.x, (R)eyv.y};
+        F[2 * fstride + o] = cplx<R>{(R)(sz * ph.y), (R)(-sz * ph.x)};
+        if (want_phi) F[3 * fstride + o] = cplx<R>{(R)ph.x, (R)ph.y};
+    }
+}
+
+// ---------------------------------------------------------------- inv_x
+template <class R>
+__global__ void k_inv_x(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E, double* __restrict__ phi,
+                        int nx, int ny, int nz, int nxh, FftPlan plan, int lpb, int nf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* A = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* B = A + lpb * nx;
+    R* out = reinterpret_cast<R*>(B + lpb * nx);   // [lpb][nx][4]
+    const int nyn = ny + 2;
+    const int nlines = nz * nyn;
+    const size_t fstride = (size_t)nz * nyn * nxh;
+    const int line0 = blockIdx.x * lpb;
+    const int nl = min(lpb, nlines - line0);
+    const R norm = (R)(1.0 / ((double)nx * (double)nz));
+    for (int f = 0; f < nf; ++f) {
+        for (int idx = threadIdx.x; idx < nl * nx; idx += blockDim.x) {
+            const int l = idx / nx;
+            const int m = idx - l * nx;
+            const cplx<R>* src = F + f * fstride + (size_t)(line0 + l) * nxh;
+            A[idx] = (m < nxh) ? src[m] : conj(src[nx - m]);
+        }
+        __syncthreads();
+        cplx<R>* res = fft_smem<R>(A, B, plan, nl, (R)1, (const cplx<R>*)plan.tw);
+        for (int idx = threadIdx.x; idx < nl * nx; idx += blockDim.x) {
+            const R v = res[idx].re * norm;
+            if (f < 3) {
+                out[idx * 4 + f] = v;
+            } else {
+                const int line = line0 + idx / nx;
+                const int k = line / nyn;
+                const int jn = line - k * nyn;
+                const int i = idx - (idx / nx) * nx;
+                if (jn >= 1 && jn <= ny) phi[((size_t)k * ny + (jn - 1)) * nx + i] = (double)v;
+            }
+        }
+        __syncthreads();
+        if (res != A) {  // keep A as the input buffer of the next field
+            cplx<R>* t = A; A = B; B = t;
+        }
+    }
+    for (int idx = threadIdx.x; idx < nl * nx; idx += blockDim.x) {
+        vec4<R> v;
+        v.x = out[idx * 4 + 0];
+        v.y = out[idx * 4 + 1];
+        v.z = out[idx * 4 + 2];
+        v.w = (R)0;
+        E[(size_t)line0 * nx + idx] = v;
+    }
+}
+
+template <class R>
+size_t smem_fwd_x(int nx, int lpb) { return sizeof(cplx<R>) * 2 * (size_t)lpb * nx; }
+template <class R>
+size_t smem_inv_x(int nx, int lpb) { return sizeof(cplx<R>) * 2 * (size_t)lpb * nx + sizeof(R) * 4 * (size_t)lpb * nx; }
+
+template <class R> int lines_per_block() { return sizeof(R) == 4 ? 4 : 2; }
+template <class R> int z_tile() { return sizeof(R) == 4 ? 8 : 4; }
+
+template <class R>
+tribo_status setup_kernels(tribo_ctx* c) {
+    const int lpb = lines_per_block<R>();
+    TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_fwd_x<R>(c->nx, lpb)));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_inv_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem_inv_x<R>(c->nx, lpb)));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_fft_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(cplx<R>) * 2 * z_tile<R>() * c->nz)));
+    return TRIBO_OK;
+}
+
+template <class R>
+tribo_status solve_impl(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+                        void* Evoid) {
+    const int nx = c->nx, ny = c->ny, nz = c->nz, nxh = c->nxh;
+    cplx<R>* S = (cplx<R>*)c->S;
+    cplx<R>* F = (cplx<R>*)c->F;
+    const int lpb = lines_per_block<R>();
+    const int mt = z_tile<R>();
+    {
+        const int nlines = ny * nz;
+        dim3 grid((nlines + lpb - 1) / lpb);
+        phase_begin(c, PH_FWD_X);
+        k_fwd_x<R><<<grid, kThreads, smem_fwd_x<R>(nx, lpb), c->stream>>>(
+            src, scale, zero_src ? 1 : 0, S, nx, ny, nlines, nxh, c->plan_x, lpb);
+        TRIBO_LAUNCHED(c);
+    }
+    {
+        dim3 grid(ny, (nxh + mt - 1) / mt, 1);
+        phase_begin(c, PH_FWD_Z);
+        k_fft_z<R><<<grid, kThreads, sizeof(cplx<R>) * 2 * mt * nz, c->stream>>>(
+            S, nz, ny, nxh, mt, c->plan_z, (R)-1, 0);
+        TRIBO_LAUNCHED(c);
+    }
+    const int want_phi = phi != nullptr ? 1 : 0;
+    const int nf = 3 + want_phi;
+    {
+        const int np = nz * nxh;
+        double2* W = (double2*)c->W;
+        double* Wc = (double*)(W + (size_t)ny * np);
+        phase_begin(c, PH_SOLVE_Y);
+        k_solve_y<R><<<(np + 127) / 128, 128, 0, c->stream>>>(S, F, W, Wc, c->d_ycoef, c->d_lamx, c->d_lamz,
+                                                             c->d_sinx, c->d_sinz, c->d_ey, ny, nz, nxh,
+                                                             want_phi);
+        TRIBO_LAUNCHED(c);
+    }
+    {
+        const size_t fstride = (size_t)nz * (ny + 2) * nxh;
+        dim3 grid(ny + 2, (nxh + mt - 1) / mt, nf);
+        phase_begin(c, PH_INV_Z);
+        k_fft_z<R><<<grid, kThreads, sizeof(cplx<R>) * 2 * mt * nz, c->stream>>>(
+            F, nz, ny + 2, nxh, mt, c->plan_z, (R)1, fstride);
+        TRIBO_LAUNCHED(c);
+    }
+    {
+        const int nlines = nz * (ny + 2);
+        dim3 grid((nlines + lpb - 1) / lpb);
+        phase_begin(c, PH_INV_X);
+        k_inv_x<R><<<grid, kThreads, smem_inv_x<R>(nx, lpb), c->stream>>>(
+            F, (vec4<R>*)Evoid, phi, nx, ny, nz, nxh, c->plan_x, lpb, nf);
+        TRIBO_LAUNCHED(c);
+    }
+    return TRIBO_OK;
+}
+
+}  // namespace
+
+tribo_status poisson_setup(tribo_ctx* c) {
+    const int nx = c->nx, ny = c->ny, nz = c->nz, nxh = c->nxh;
+    const std::vector<double>& yf = c->yf;
+    const std::vector<double>& yc = c->yc;
+    const std::vector<double>& dy = c->dy;
+    // y operator coefficients (rows: a[j] phi[j-1] + b[j] phi[j] + c[j] phi[j+1])
+    std::vector<double> coef(3 * ny, 0.0);
+    double* a = coef.data();
+    double* b = a + ny;
+    double* cc = b + ny;
+    for (int j = 0; j < ny; ++j) {
+        if (j >= 1) a[j] = 1.0 / (dy[j] * (yc[j] - yc[j - 1]));
+        if (j <= ny - 2) cc[j] = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
+        b[j] = -(a[j] + cc[j]);
+    }
+    b[0] -= 1.0 / (dy[0] * (yc[0] - yf[0]));
+    b[ny - 1] -= 1.0 / (dy[ny - 1] * (yf[ny] - yc[ny - 1]));
+    std::vector<double> lamx(nx), lamz(nz), sinx(nxh), sinz(nz);
+    for (int m = 0; m < nx; ++m) {
+        const double s = std::sin(M_PI * m / nx);
+        lamx[m] = 4.0 / (c->dx * c->dx) * s * s;
+    }
+    for (int m = 0; m < nz; ++m) {
+        const double s = std::sin(M_PI * m / nz);
+        lamz[m] = 4.0 / (c->dz * c->dz) * s * s;
+        sinz[m] = std::sin(2.0 * M_PI * m / nz) / c->dz;
+    }
+    for (int m = 0; m < nxh; ++m) sinx[m] = std::sin(2.0 * M_PI * m / nx) / c->dx;
+    // E_y at lattice node jn = cm phi[jn-2] + c0 phi[jn-1] + cp phi[jn]
+    std::vector<double> ey(3 * (ny + 2), 0.0);
+    auto w = [&](int f) { return (yf[f] - yc[f - 1]) / (yc[f] - yc[f - 1]); };  // interior face f
+    for (int j = 0; j < ny; ++j) {
+        const int jn = j + 1;
+        double cm = 0, c0 = 0, cp = 0;
+        // + phi_f[j] / dy_j
+        if (j >= 1) { cm += (1.0 - w(j)) / dy[j]; c0 += w(j) / dy[j]; }
+        // - phi_f[j+1] / dy_j
+        if (j + 1 <= ny - 1) { c0 -= (1.0 - w(j + 1)) / dy[j]; cp -= w(j + 1) / dy[j]; }
+        ey[3 * jn + 0] = cm;
+        ey[3 * jn + 1] = c0;
+        ey[3 * jn + 2] = cp;
+    }
+    ey[3 * 0 + 2] = -1.0 / (yc[0] - yf[0]);                    // bottom wall node
+    ey[3 * (ny + 1) + 0] = 1.0 / (yf[ny] - yc[ny - 1]);        // top wall node
+
+    TRIBO_CUDA(cudaMalloc(&c->d_ycoef, sizeof(double) * 3 * ny));
+    TRIBO_CUDA(cudaMalloc(&c->d_lamx, sizeof(double) * nx));
+    TRIBO_CUDA(cudaMalloc(&c->d_lamz, sizeof(double) * nz));
+    TRIBO_CUDA(cudaMalloc(&c->d_sinx, sizeof(double) * nxh));
+    TRIBO_CUDA(cudaMalloc(&c->d_sinz, sizeof(double) * nz));
+    TRIBO_CUDA(cudaMalloc(&c->d_ey, sizeof(double) * 3 * (ny + 2)));
+    TRIBO_CUDA(cudaMemcpy(c->d_ycoef, coef.data(), sizeof(double) * 3 * ny, cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemcpy(c->d_lamx, lamx.data(), sizeof(double) * nx, cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemcpy(c->d_lamz, lamz.data(), sizeof(double) * nz, cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemcpy(c->d_sinx, sinx.data(), sizeof(double) * nxh, cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemcpy(c->d_sinz, sinz.data(), sizeof(double) * nz, cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemcpy(c->d_ey, ey.data(), sizeof(double) * 3 * (ny + 2), cudaMemcpyHostToDevice));
+
+    const size_t rsz = c->prec == TRIBO_FP64 ? sizeof(double) : sizeof(float);
+    const size_t csz = 2 * rsz;
+    TRIBO_CUDA(cudaMalloc(&c->S, csz * (size_t)nz * ny * nxh));
+    TRIBO_CUDA(cudaMalloc(&c->F, csz * 4 * (size_t)nz * (ny + 2) * nxh));
+    TRIBO_CUDA(cudaMalloc(&c->W, (sizeof(double2) + sizeof(double)) * (size_t)ny * nz * nxh));
+    tribo_status st;
+    if (c->prec == TRIBO_FP64) {
+        if ((st = make_plan<double>(nx, c->plan_x)) != TRIBO_OK) return st;
+        if ((st = make_plan<double>(nz, c->plan_z)) != TRIBO_OK) return st;
+        return setup_kernels<double>(c);
+    }
+    if ((st = make_plan<float>(nx, c->plan_x)) != TRIBO_OK) return st;
+    if ((st = make_plan<float>(nz, c->plan_z)) != TRIBO_OK) return st;
+    return setup_kernels<float>(c);
+}
+
+tribo_status poisson_free(tribo_ctx* c) {
+    cudaFree(c->d_ycoef);
+    cudaFree(c->d_lamx);
+    cudaFree(c->d_lamz);
+    cudaFree(c->d_sinx);
+    cudaFree(c->d_sinz);
+    cudaFree(c->d_ey);
+    cudaFree(c->S);
+    cudaFree(c->F);
+    cudaFree(c->W);
+    cudaFree(c->plan_x.tw);
+    cudaFree(c->plan_z.tw);
+    return TRIBO_OK;
+}
+
+tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+                           void* E) {
+    if (c->prec == TRIBO_FP64) return solve_impl<double>(c, src, scale, zero_src, phi, E);
+    return solve_impl<float>(c, src, scale, zero_src, phi, E);
+}
+
+}  // namespace tribo

@@ -1,0 +1,547 @@
+// C ABI of the library: context set-up, the coupled step loop, the
+// standalone Poisson call, statistics and error reporting.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tribo_internal.cuh"
+
+namespace tribo {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+
+tribo_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? TRIBO_ERR_OOM : TRIBO_ERR_CUDA;
+}
+
+namespace {
+
+bool is_2a3b(int n) {
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+float float_up(double v) {
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+size_t real_size(const tribo_ctx* c) { return c->prec == TRIBO_FP64 ? sizeof(double) : sizeof(float); }
+
+template <class T>
+tribo_status upload(T** dst, const std::vector<T>& v) {
+    TRIBO_CUDA(cudaMalloc((void**)dst, sizeof(T) * v.size()));
+    TRIBO_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+    return TRIBO_OK;
+}
+
+tribo_status check_params(const tribo_params* p) {
+    if (!p) { set_last_error("params is NULL"); return TRIBO_ERR_ARG; }
+    if (p->precision != TRIBO_FP64 && p->precision != TRIBO_MIXED) {
+        set_last_error("precision must be TRIBO_FP64 or TRIBO_MIXED");
+        return TRIBO_ERR_ARG;
+    }
+    if (p->drag_law < 0 || p->drag_law > 2 || p->impact_vel < 0 || p->impact_vel > 1) {
+        set_last_error("unknown drag_law or impact_vel");
+        return TRIBO_ERR_ARG;
+    }
+    if (!(p->rho_p > 0 && p->rho > 0 && p->nu > 0 && p->eps > 0 && p->eps0 > 0 && p->h > 0 &&
+          p->E_p > 0 && p->E_w > 0 && p->phi_p > 0 && p->eps_w > 0)) {
+        set_last_error("material constants must be positive");
+        return TRIBO_ERR_ARG;
+    }
+    if (p->sort_every < 0) { set_last_error("sort_every must be >= 0"); return TRIBO_ERR_ARG; }
+    return TRIBO_OK;
+}
+
+tribo_status build_tables(tribo_ctx* c) {
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    std::vector<float> xf(nx + 1), zf(nz + 1), yfu(ny + 1);
+    for (int i = 0; i <= nx; ++i) xf[i] = float_up((double)i * c->dx);
+    for (int k = 0; k <= nz; ++k) zf[k] = float_up((double)k * c->dz);
+    for (int j = 0; j <= ny; ++j) yfu[j] = float_up(c->yf[j]);
+    tribo_status st;
+    if ((st = upload(&c->d_xf_up, xf)) || (st = upload(&c->d_zf_up, zf)) || (st = upload(&c->d_yf_up, yfu)))
+        return st;
+    if ((st = upload(&c->d_yf, c->yf)) || (st = upload(&c->d_Y, c->Y))) return st;
+    // first candidate cell of each uniform y bin
+    c->ybins = 8192;
+    std::vector<int> bins(c->ybins);
+    for (int b = 0; b < c->ybins; ++b) {
+        const double yb = (double)b * c->ly / c->ybins;
+        int j = 0;
+        while (j < ny - 1 && c->yf[j + 1] <= yb) ++j;
+        bins[b] = j;
+    }
+    if ((st = upload(&c->d_ybin, bins))) return st;
+    std::vector<double> sq(ny), sr(ny);
+    for (int j = 0; j < ny; ++j) {
+        sq[j] = -1.0 / (c->P.eps * c->dx * c->dy[j] * c->dz);
+        sr[j] = -1.0 / c->P.eps;
+    }
+    if ((st = upload(&c->d_scale_q, sq)) || (st = upload(&c->d_scale_rho, sr))) return st;
+    const size_t rs = real_size(c);
+    std::vector<double> Yd = c->Y, inv(ny + 1);
+    for (int jn = 0; jn <= ny; ++jn) inv[jn] = 1.0 / (c->Y[jn + 1] - c->Y[jn]);
+    TRIBO_CUDA(cudaMalloc(&c->d_Yr, rs * (ny + 2)));
+    TRIBO_CUDA(cudaMalloc(&c->d_invdY, rs * (ny + 1)));
+    if (c->prec == TRIBO_FP64) {
+        TRIBO_CUDA(cudaMemcpy(c->d_Yr, Yd.data(), rs * (ny + 2), cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMemcpy(c->d_invdY, inv.data(), rs * (ny + 1), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> Yf(Yd.begin(), Yd.end()), invf(inv.begin(), inv.end());
+        TRIBO_CUDA(cudaMemcpy(c->d_Yr, Yf.data(), rs * (ny + 2), cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMemcpy(c->d_invdY, invf.data(), rs * (ny + 1), cudaMemcpyHostToDevice));
+    }
+    return TRIBO_OK;
+}
+
+// device-resident particle arrays used for host-pointer calls
+struct Stage {
+    static size_t bytes(int64_t n, size_t rs) { return (size_t)n * (7 * rs + 2 * sizeof(double) + 3 * sizeof(uint32_t)) + 1024; }
+};
+
+PView stage_view(tribo_ctx* c, int64_t n) {
+    const size_t rs = real_size(c);
+    char* b = (char*)c->stage;
+    const size_t cap = (size_t)c->max_particles;
+    PView v{};
+    v.n = n;
+    size_t off = 0;
+    auto take = [&](size_t elem) { void* p = b + off; off += ((elem * cap + 255) / 256) * 256; return p; };
+    v.x = take(rs); v.y = take(rs); v.z = take(rs);
+    v.vx = take(rs); v.vy = take(rs); v.vz = take(rs); v.d = take(rs);
+    v.q = (double*)take(sizeof(double));
+    v.q_wall = (double*)take(sizeof(double));
+    v.n_imp = (uint32_t*)take(sizeof(uint32_t));
+    v.id = (uint32_t*)take(sizeof(uint32_t));
+    v.cell = (uint32_t*)take(sizeof(uint32_t));
+    return v;
+}
+
+tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particles* src, cudaMemcpyKind kind,
+                            bool to_device) {
+    const size_t rs = real_size(c);
+    const size_t n = (size_t)src->n;
+    auto cp = [&](void* dev, void* host, size_t elem) -> tribo_status {
+        if (!host) return TRIBO_OK;
+        if (to_device) TRIBO_CUDA(cudaMemcpyAsync(dev, host, elem * n, kind, c->stream));
+        else TRIBO_CUDA(cudaMemcpyAsync(host, dev, elem * n, kind, c->stream));
+        return TRIBO_OK;
+    };
+    tribo_status st;
+    if ((st = cp(dst.x, src->x, rs)) || (st = cp(dst.y, src->y, rs)) || (st = cp(dst.z, src->z, rs)) ||
+        (st = cp(dst.vx, src->vx, rs)) || (st = cp(dst.vy, src->vy, rs)) || (st = cp(dst.vz, src->vz, rs)) ||
+        (st = cp(dst.q, src->q, sizeof(double))) || (st = cp(dst.q_wall, src->q_wall, sizeof(double))) ||
+        (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))))
+        return st;
+    if (to_device) {
+        if ((st = cp(dst.d, src->d, rs)) || (st = cp(dst.id, src->id, sizeof(uint32_t)))) return st;
+    } else {
+        if ((st = cp(dst.id, src->id, sizeof(uint32_t))) || (st = cp(dst.cell, src->cell, sizeof(uint32_t))))
+            return st;
+    }
+    return TRIBO_OK;
+}
+
+tribo_status check_particles(const tribo_ctx* c, const tribo_particles* p) {
+    if (!p) { set_last_error("particles is NULL"); return TRIBO_ERR_ARG; }
+    if (p->n < 0) { set_last_error("negative particle count"); return TRIBO_ERR_ARG; }
+    if (p->n == 0) return TRIBO_OK;
+    if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->d || !p->q || !p->q_wall || !p->n_imp) {
+        set_last_error("a required particle array is NULL");
+        return TRIBO_ERR_ARG;
+    }
+    if (p->n > 0xffffffffLL) { set_last_error("more than 2^32 particles"); return TRIBO_ERR_ARG; }
+    if (p->on_host && p->n > c->max_particles) {
+        set_last_error("host-pointer call with more particles than max_particles");
+        return TRIBO_ERR_CAPACITY;
+    }
+    return TRIBO_OK;
+}
+
+tribo_status read_error(tribo_ctx* c, uint32_t* bits) {
+    Accum a;
+    TRIBO_CUDA(cudaMemcpy(&a, c->d_acc, sizeof(Accum), cudaMemcpyDeviceToHost));
+    *bits = a.err;
+    return TRIBO_OK;
+}
+
+}  // namespace
+}  // namespace tribo
+
+using namespace tribo;
+
+namespace {
+
+void free_ctx(tribo_ctx* c) {
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    poisson_free(c);
+    void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
+                    c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
+                    c->d_hist, c->d_scalar};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    cudaSetDevice(prev);
+    delete c;
+}
+
+tribo_status set_fluid_impl(tribo_ctx* c, const tribo_fluid* f) {
+    if (!f || !f->u) { set_last_error("fluid lattice is NULL"); return TRIBO_ERR_ARG; }
+    const size_t nodes = (size_t)c->nz * (c->ny + 2) * c->nx;
+    const size_t bytes = nodes * 3 * real_size(c);
+    void* tmp = nullptr;
+    TRIBO_CUDA(cudaMalloc(&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, f->u, bytes, f->on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                    c->stream);
+    tribo_status st = TRIBO_OK;
+    if (e != cudaSuccess) st = cuda_fail(e, "copy fluid lattice");
+    if (st == TRIBO_OK) st = lattice_from_aos3(c, tmp);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (st == TRIBO_OK && e2 != cudaSuccess) st = cuda_fail(e2, "set fluid");
+    return st;
+}
+
+PView device_view(const tribo_particles* p) {
+    PView v{};
+    v.n = p->n;
+    v.x = p->x; v.y = p->y; v.z = p->z;
+    v.vx = p->vx; v.vy = p->vy; v.vz = p->vz; v.d = p->d;
+    v.q = p->q; v.q_wall = p->q_wall; v.n_imp = p->n_imp; v.id = p->id; v.cell = p->cell;
+    return v;
+}
+
+tribo_status sync_and_check(tribo_ctx* c) {
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    uint32_t bits = 0;
+    tribo_status st = read_error(c, &bits);
+    if (st) return st;
+    c->err_bits = bits;
+    if (bits) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "device error word 0x%x", bits);
+        set_last_error(buf);
+        return TRIBO_ERR_DEVICE;
+    }
+    return TRIBO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_fluid* fluid,
+                        const tribo_params* params, int64_t max_particles, void* stream) {
+    if (!out) { set_last_error("out is NULL"); return TRIBO_ERR_ARG; }
+    *out = nullptr;
+    if (!grid || !grid->y_faces) { set_last_error("grid or y_faces is NULL"); return TRIBO_ERR_ARG; }
+    tribo_status st = check_params(params);
+    if (st) return st;
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    if (nx < 4 || nx > 1024 || nz < 4 || nz > 1024 || nx % 2 || !is_2a3b(nx) || !is_2a3b(nz)) {
+        set_last_error("nx and nz must be 2^a 3^b in [4, 1024], nx even");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    if (ny < 2 || ny > 1024) { set_last_error("ny must be in [2, 1024]"); return TRIBO_ERR_UNSUPPORTED; }
+    if (!(grid->lx > 0 && grid->lz > 0)) { set_last_error("lx, lz must be positive"); return TRIBO_ERR_ARG; }
+    if ((int64_t)nx * ny * nz >= (int64_t)1 << 32) { set_last_error("too many cells"); return TRIBO_ERR_UNSUPPORTED; }
+    if (grid->y_faces[0] != 0.0) { set_last_error("y_faces[0] must be 0"); return TRIBO_ERR_ARG; }
+    for (int j = 0; j < ny; ++j)
+        if (!(grid->y_faces[j + 1] > grid->y_faces[j])) {
+            set_last_error("y_faces must increase strictly");
+            return TRIBO_ERR_ARG;
+        }
+    if (max_particles < 0) { set_last_error("max_particles < 0"); return TRIBO_ERR_ARG; }
+
+    tribo_ctx* c = new (std::nothrow) tribo_ctx();
+    if (!c) { set_last_error("host allocation failed"); return TRIBO_ERR_OOM; }
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)stream;
+    c->prec = params->precision;
+    c->P = *params;
+    c->nx = nx; c->ny = ny; c->nz = nz; c->nxh = nx / 2 + 1;
+    c->lx = grid->lx; c->lz = grid->lz;
+    c->dx = c->lx / nx; c->dz = c->lz / nz;
+    c->max_particles = max_particles;
+    c->yf.assign(grid->y_faces, grid->y_faces + ny + 1);
+    c->ly = c->yf[ny];
+    c->yc.resize(ny); c->dy.resize(ny); c->Y.resize(ny + 2);
+    for (int j = 0; j < ny; ++j) {
+        c->yc[j] = 0.5 * (c->yf[j] + c->yf[j + 1]);
+        c->dy[j] = c->yf[j + 1] - c->yf[j];
+    }
+    c->Y[0] = c->yf[0];
+    for (int j = 0; j < ny; ++j) c->Y[j + 1] = c->yc[j];
+    c->Y[ny + 1] = c->yf[ny];
+
+#define TRY(expr)                    \
+    do {                             \
+        tribo_status s_ = (expr);    \
+        if (s_) { free_ctx(c); return s_; } \
+    } while (0)
+#define TRYC(call)                                        \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) { tribo_status s_ = cuda_fail(e_, #call); free_ctx(c); return s_; } \
+    } while (0)
+
+    TRY(build_tables(c));
+    const size_t nodes = (size_t)nz * (ny + 2) * nx;
+    const size_t rs = real_size(c);
+    TRYC(cudaMalloc(&c->u_lat, nodes * 4 * rs));
+    TRYC(cudaMalloc(&c->E_lat, nodes * 4 * rs));
+    TRYC(cudaMemset(c->E_lat, 0, nodes * 4 * rs));
+    TRYC(cudaMalloc(&c->Q, sizeof(double) * (size_t)nx * ny * nz));
+    TRYC(cudaMemset(c->Q, 0, sizeof(double) * (size_t)nx * ny * nz));
+    TRYC(cudaMalloc(&c->d_acc, sizeof(Accum)));
+    TRYC(cudaMemset(c->d_acc, 0, sizeof(Accum)));
+    TRYC(cudaMalloc(&c->d_hist, sizeof(unsigned long long) * ny));
+    TRYC(cudaMemset(c->d_hist, 0, sizeof(unsigned long long) * ny));
+    TRYC(cudaMalloc(&c->d_scalar, sizeof(double)));
+    if (max_particles > 0) {
+        c->stage_bytes = Stage::bytes(max_particles, rs) + 12 * 256;
+        TRYC(cudaMalloc(&c->stage, c->stage_bytes));
+    }
+    TRY(poisson_setup(c));
+    TRY(particles_setup(c));
+    if (fluid) TRY(set_fluid_impl(c, fluid));
+    else TRYC(cudaMemset(c->u_lat, 0, nodes * 4 * rs));
+    TRYC(cudaDeviceSynchronize());
+#undef TRY
+#undef TRYC
+    *out = c;
+    return TRIBO_OK;
+}
+
+tribo_status tribo_set_fluid(tribo_ctx* c, const tribo_fluid* fluid) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    return set_fluid_impl(c, fluid);
+}
+
+tribo_status tribo_set_params(tribo_ctx* c, const tribo_params* params) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    tribo_status st = check_params(params);
+    if (st) return st;
+    if (params->precision != c->prec) { set_last_error("precision cannot change"); return TRIBO_ERR_ARG; }
+    const bool eps_changed = params->eps != c->P.eps;
+    c->P = *params;
+    if (eps_changed) {
+        std::vector<double> sq(c->ny), sr(c->ny);
+        for (int j = 0; j < c->ny; ++j) {
+            sq[j] = -1.0 / (c->P.eps * c->dx * c->dy[j] * c->dz);
+            sr[j] = -1.0 / c->P.eps;
+        }
+        TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+        TRIBO_CUDA(cudaMemcpy(c->d_scale_q, sq.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMemcpy(c->d_scale_rho, sr.data(), sizeof(double) * c->ny, cudaMemcpyHostToDevice));
+    }
+    return TRIBO_OK;
+}
+
+tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nsteps) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    tribo_status st = check_particles(c, p);
+    if (st) return st;
+    if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) { set_last_error("need nsteps >= 0 and dt > 0"); return TRIBO_ERR_ARG; }
+    if (nsteps == 0 || p->n == 0) {
+        c->n_samples += nsteps;
+        return TRIBO_OK;
+    }
+    PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
+    if (p->on_host) {
+        if (!p->id) v.id = nullptr;
+        if (!p->cell) v.cell = nullptr;
+        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true))) return st;
+    }
+    const bool electro = c->P.electrostatics != 0;
+    const bool want_cell = v.cell != nullptr;
+    if (electro) {
+        TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
+        if ((st = particles_deposit(c, v))) return st;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        const bool last = s == nsteps - 1;
+        if (electro) {
+            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
+        }
+        if ((st = particles_step(c, v, dt, electro && !last, want_cell && last))) return st;
+    }
+    c->n_samples += nsteps;
+    if (p->on_host) {
+        if ((st = copy_particles(c, v, p, cudaMemcpyDeviceToHost, false))) return st;
+        return sync_and_check(c);
+    }
+    return TRIBO_OK;
+}
+
+tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E) {
+    if (!c || !rho || !E) { set_last_error("ctx, rho and E must not be NULL"); return TRIBO_ERR_ARG; }
+    return poisson_solve(c, const_cast<double*>(rho), c->d_scale_rho, false, phi, E);
+}
+
+tribo_status tribo_stats(tribo_ctx* c, const tribo_particles* p, double* sum_q, uint64_t* n_impacts,
+                         double* sum_wall, double* hist_y, int64_t* n_samples) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    tribo_status st;
+    if (p && sum_q) {
+        if ((st = check_particles(c, p))) return st;
+        if (p->on_host) {
+            double s = 0.0;
+            for (int64_t i = 0; i < p->n; ++i) s += p->q[i];
+            *sum_q = s;
+        } else {
+            if ((st = particles_sum_q(c, device_view(p), c->d_scalar))) return st;
+            TRIBO_CUDA(cudaMemcpyAsync(sum_q, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        }
+    }
+    Accum a;
+    TRIBO_CUDA(cudaMemcpyAsync(&a, c->d_acc, sizeof(Accum), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<unsigned long long> h(c->ny);
+    TRIBO_CUDA(cudaMemcpyAsync(h.data(), c->d_hist, sizeof(unsigned long long) * c->ny, cudaMemcpyDeviceToHost,
+                               c->stream));
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    if (n_impacts) *n_impacts = a.n_impacts;
+    if (sum_wall) *sum_wall = a.sum_wall;
+    if (hist_y)
+        for (int j = 0; j < c->ny; ++j) hist_y[j] = (double)h[j];
+    if (n_samples) *n_samples = c->n_samples;
+    c->err_bits = a.err;
+    if (a.err) {
+        set_last_error("device error word set");
+        return TRIBO_ERR_DEVICE;
+    }
+    return TRIBO_OK;
+}
+
+tribo_status tribo_reset_stats(tribo_ctx* c) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    TRIBO_CUDA(cudaMemsetAsync(c->d_acc, 0, offsetof(Accum, err), c->stream));
+    TRIBO_CUDA(cudaMemsetAsync(c->d_hist, 0, sizeof(unsigned long long) * c->ny, c->stream));
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    c->n_samples = 0;
+    return TRIBO_OK;
+}
+
+tribo_status tribo_sync(tribo_ctx* c) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    return sync_and_check(c);
+}
+
+uint32_t tribo_error_bits(const tribo_ctx* c) { return c ? c->err_bits : 0u; }
+
+tribo_status tribo_clear_error(tribo_ctx* c) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    TRIBO_CUDA(cudaMemsetAsync(&c->d_acc->err, 0, sizeof(unsigned int), c->stream));
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    c->err_bits = 0;
+    return TRIBO_OK;
+}
+
+int64_t tribo_launch_count(const tribo_ctx* c) { return c ? c->launches : 0; }
+
+void tribo_destroy(tribo_ctx* c) { free_ctx(c); }
+
+}  // extern "C"
+
+extern "C" {
+
+const char* tribo_strerror(tribo_status s) {
+    switch (s) {
+        case TRIBO_OK: return "ok";
+        case TRIBO_ERR_ARG: return "invalid argument";
+        case TRIBO_ERR_UNSUPPORTED: return "unsupported size or option";
+        case TRIBO_ERR_CUDA: return "CUDA runtime error";
+        case TRIBO_ERR_OOM: return "device allocation failed";
+        case TRIBO_ERR_DEVICE: return "device error word set";
+        case TRIBO_ERR_CAPACITY: return "particle capacity exceeded";
+        default: return "unknown status";
+    }
+}
+
+const char* tribo_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+namespace tribo {
+
+static const char* kPhaseNames[TRIBO_NPHASES] = {
+    "particle_step", "deposit", "poisson_fwd_x", "poisson_fwd_z", "poisson_solve_y",
+    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux"};
+
+static void flush_timing(tribo_ctx* c) {
+    if (c->ev_used == 0) return;
+    cudaEventSynchronize(c->ev[2 * c->ev_used - 1]);
+    for (int i = 0; i < c->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess) {
+            c->phase_ms[c->ev_phase[i]] += ms;
+            c->phase_n[c->ev_phase[i]] += 1;
+        }
+    }
+    c->ev_used = 0;
+}
+
+void phase_begin(tribo_ctx* c, int phase) {
+    if (!c->timing) return;
+    if (c->ev_used == (int)c->ev_phase.size()) flush_timing(c);
+    cudaEventRecord(c->ev[2 * c->ev_used], c->stream);
+    c->ev_phase[c->ev_used] = phase;
+    c->open_phase = phase;
+}
+
+void phase_end(tribo_ctx* c) {
+    if (!c->timing || c->open_phase < 0) return;
+    cudaEventRecord(c->ev[2 * c->ev_used + 1], c->stream);
+    c->ev_used++;
+    c->open_phase = -1;
+}
+
+}  // namespace tribo
+
+extern "C" {
+
+tribo_status tribo_timing_enable(tribo_ctx* c, int32_t on) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    if (on && c->ev.empty()) {
+        const int pairs = 8192;
+        c->ev.resize(2 * pairs);
+        c->ev_phase.resize(pairs);
+        for (auto& e : c->ev) TRIBO_CUDA(cudaEventCreate(&e));
+    }
+    if (c->timing) flush_timing(c);
+    c->timing = on != 0;
+    c->ev_used = 0;
+    c->open_phase = -1;
+    for (int i = 0; i < TRIBO_NPHASES; ++i) { c->phase_ms[i] = 0; c->phase_n[i] = 0; }
+    return TRIBO_OK;
+}
+
+tribo_status tribo_timing_read(tribo_ctx* c, double* ms, int64_t* counts, int32_t nphases) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    flush_timing(c);
+    for (int i = 0; i < nphases && i < TRIBO_NPHASES; ++i) {
+        if (ms) ms[i] = c->phase_ms[i];
+        if (counts) counts[i] = c->phase_n[i];
+    }
+    return TRIBO_OK;
+}
+
+const char* tribo_phase_name(int32_t phase) {
+    return (phase >= 0 && phase < TRIBO_NPHASES) ? tribo::kPhaseNames[phase] : nullptr;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tribo.h"
+
+namespace tribo {
+
+// ------------------------------------------------------------------ complex
+template <class R> struct cplx { R re, im; };
+
+template <class R> __host__ __device__ __forceinline__ cplx<R> mk(R a, R b) { return cplx<R>{a, b}; }
+template <class R> __host__ __device__ __forceinline__ cplx<R> operator+(cplx<R> a, cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> __host__ __device__ __forceinline__ cplx<R> operator-(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> __host__ __device__ __forceinline__ cplx<R> operator*(cplx<R> a, cplx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> __host__ __device__ __forceinline__ cplx<R> scale(cplx<R> a, R s) { return {a.re * s, a.im * s}; }
+template <class R> __host__ __device__ __forceinline__ cplx<R> conj(cplx<R> a) { return {a.re, -a.im}; }
+// multiply by s*i (s = +-1)
+template <class R> __host__ __device__ __forceinline__ cplx<R> mul_si(cplx<R> a, R s) { return {-s * a.im, s * a.re}; }
+
+template <class R> struct vec4 { R x, y, z, w; };
+template <> struct vec4<float> { float x, y, z, w; };
+
+// ------------------------------------------------------------------ FFT plan
+// Mixed-radix (4, 2, 3) Stockham plan for one transform length.
+struct FftPlan {
+    int n = 0;
+    int npass = 0;
+    int radix[24];
+    void* tw = nullptr;      // device table, n entries of cplx<R>: exp(-2 pi i e / n)
+};
+
+// ------------------------------------------------------------------ context
+struct Accum {                // device-side statistics accumulators
+    double sum_wall;          // total charge received from walls
+    unsigned long long n_impacts;
+    long long n_samples;
+    unsigned int err;         // sticky error bits
+    unsigned int pad;
+};
+
+}  // namespace tribo
+
+struct tribo_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int prec = TRIBO_FP64;
+    tribo_params P{};
+    int nx = 0, ny = 0, nz = 0, nxh = 0;
+    double lx = 0, lz = 0, ly = 0, dx = 0, dz = 0;
+    int64_t max_particles = 0;
+    int64_t launches = 0;
+
+    std::vector<double> yf, yc, dy, Y;       // host FP64 grid
+
+    // device grid tables (FP64 and rounded-up FP32 copies for exact compares)
+    double* d_yf = nullptr;      // ny+1
+    double* d_Y = nullptr;       // ny+2 lattice nodes
+    double* d_scale_q = nullptr; // ny: -1 / (eps V_j) (charge sum -> RHS)
+    double* d_scale_rho = nullptr; // ny: -1 / eps (density -> RHS)
+    float* d_yf_up = nullptr;    // ny+1: smallest float >= yf
+    float* d_xf_up = nullptr;    // nx+1
+    float* d_zf_up = nullptr;    // nz+1
+    int* d_ybin = nullptr;       // ybins: first candidate cell of each uniform y bin
+    int ybins = 0;
+    void* d_Yr = nullptr;        // ny+2 lattice nodes in real precision
+    void* d_invdY = nullptr;     // ny+1 inverse node spacings in real precision
+    double* d_ycoef = nullptr;   // 3*ny: a, b, c of the y FV operator
+    double* d_lamx = nullptr;    // nx modified wavenumbers
+    double* d_lamz = nullptr;    // nz
+    double* d_sinx = nullptr;    // nx: sin(2 pi m / nx) / dx
+    double* d_sinz = nullptr;    // nz
+    double* d_ey = nullptr;      // 4*(ny+2): coefficients of E_y at each lattice node
+
+    // fields
+    void* u_lat = nullptr;       // (nz, ny+2, nx) vec4<real>
+    void* E_lat = nullptr;       // (nz, ny+2, nx) vec4<real>
+    double* Q = nullptr;         // (nz, ny, nx) cell charge sums
+    void* S = nullptr;           // (nz, ny, nxh) cplx<real> spectrum
+    void* F = nullptr;           // (4, nz, ny+2, nxh) cplx<real> field spectra
+    void* W = nullptr;           // (ny, nz*nxh) cplx<double> Thomas scratch
+    tribo::FftPlan plan_x, plan_z;
+
+    // particle staging (host-pointer calls) and sort scratch
+    void* stage = nullptr;
+    size_t stage_bytes = 0;
+
+    // statistics
+    tribo::Accum* d_acc = nullptr;
+    unsigned long long* d_hist = nullptr;   // ny
+    double* d_scalar = nullptr;             // reduction result
+    int64_t n_samples = 0;
+    uint32_t err_bits = 0;
+
+    // per-phase CUDA-event timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;            // event pool
+    std::vector<int> ev_phase;              // phase of each recorded (start, stop) pair
+    int ev_used = 0;
+    int open_phase = -1;
+    double phase_ms[TRIBO_NPHASES] = {0};
+    int64_t phase_n[TRIBO_NPHASES] = {0};
+};
+
+namespace tribo {
+
+// kernel phases for timing
+enum Phase { PH_STEP = 0, PH_DEPOSIT, PH_FWD_X, PH_FWD_Z, PH_SOLVE_Y, PH_INV_Z, PH_INV_X, PH_SORT, PH_MISC,
+             PH_AUX };
+void phase_begin(tribo_ctx* c, int phase);
+void phase_end(tribo_ctx* c);
+
+// error plumbing
+void set_last_error(const std::string& s);
+tribo_status cuda_fail(cudaError_t e, const char* what);
+#define TRIBO_CUDA(call)                                              \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return ::tribo::cuda_fail(e_, #call); \
+    } while (0)
+#define TRIBO_LAUNCHED(ctx)                                                   \
+    do {                                                                      \
+        (ctx)->launches++;                                                    \
+        ::tribo::phase_end(ctx);                                              \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess) return ::tribo::cuda_fail(e_, "kernel launch"); \
+    } while (0)
+
+// Poisson (poisson.cu)
+tribo_status poisson_setup(tribo_ctx* c);
+tribo_status poisson_free(tribo_ctx* c);
+// src: device (nz, ny, nx) double; scale: device ny per-row factor giving the
+// RHS -rho/eps; zero_src: write zeros back into src after reading.
+// phi may be NULL.  E: (nz, ny+2, nx) vec4<real>.
+tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src,
+                           double* phi, void* E);
+
+// particles (particles.cu)
+struct PView {               // device views of one particle ensemble
+    int64_t n;
+    void *x, *y, *z, *vx, *vy, *vz, *d;
+    double* q;
+    double* q_wall;
+    uint32_t* n_imp;
+    uint32_t* id;
+    uint32_t* cell;
+};
+tribo_status particles_deposit(tribo_ctx* c, const PView& p);
+tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next,
+                            bool write_cell);
+tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out);
+tribo_status particles_setup(tribo_ctx* c);
+tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev);
+
+}  // namespace tribo

@@ -1,0 +1,83 @@
+"""The C ABI library builds for sm_103a, loads, exports every entry point the
+header declares, and the Python binding's struct layouts match the header.
+No compute call is made (no GPU needed)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2602_10761_gb300 import _abi, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(tribo_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return C.CDLL(build.LIB)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    assert set(declared_functions()) <= set(_abi.exported_names()) | set()
+
+
+def test_struct_layouts_match_header(tmp_path):
+    prog = tmp_path / "layout.c"
+    prog.write_text(r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "tribo.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("tribo_grid %zu\n", sizeof(tribo_grid));
+  printf("tribo_params %zu\n", sizeof(tribo_params));
+  printf("tribo_fluid %zu\n", sizeof(tribo_fluid));
+  printf("tribo_particles %zu\n", sizeof(tribo_particles));
+  P(tribo_grid, lx) P(tribo_grid, y_faces)
+  P(tribo_params, kappa_A) P(tribo_params, drag_law) P(tribo_params, sort_every)
+  P(tribo_particles, x) P(tribo_particles, q) P(tribo_particles, cell) P(tribo_particles, on_host)
+  return 0;
+}
+''')
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.split("\n") if l)
+    assert int(out["tribo_grid"]) == C.sizeof(_abi.tribo_grid)
+    assert int(out["tribo_params"]) == C.sizeof(_abi.tribo_params)
+    assert int(out["tribo_fluid"]) == C.sizeof(_abi.tribo_fluid)
+    assert int(out["tribo_particles"]) == C.sizeof(_abi.tribo_particles)
+    for key, val in out.items():
+        if "." in key:
+            st, f = key.split(".")
+            assert getattr(getattr(_abi, st), f).offset == int(val), key
+
+
+def test_error_strings(lib):
+    lib.tribo_strerror.restype = C.c_char_p
+    for s in range(7):
+        assert lib.tribo_strerror(s)
+    lib.tribo_init.restype = C.c_int32
+    # a NULL output pointer is an argument error, reported without touching a GPU
+    assert lib.tribo_init(None, None, None, None, C.c_int64(0), None) == _abi.TRIBO_ERR_ARG
