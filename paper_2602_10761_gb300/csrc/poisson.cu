@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 
 #include "tribo_internal.cuh"
 
@@ -302,15 +303,25 @@ size_t smem_inv_x(int nx, int lpb) { return sizeof(cplx<R>) * 2 * (size_t)lpb * 
 template <class R> int lines_per_block() { return sizeof(R) == 4 ? 4 : 2; }
 template <class R> int z_tile() { return sizeof(R) == 4 ? 8 : 4; }
 
+// The per-function dynamic shared-memory limit is process-wide state shared by
+// every context on the device, so it is raised to the device's opt-in maximum
+// (never lowered to one context's need); each launch still requests only what
+// it uses.
 template <class R>
 tribo_status setup_kernels(tribo_ctx* c) {
     const int lpb = lines_per_block<R>();
-    TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_fwd_x<R>(c->nx, lpb)));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_inv_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem_inv_x<R>(c->nx, lpb)));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_fft_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(cplx<R>) * 2 * z_tile<R>() * c->nz)));
+    int dev = 0, optin = 0;
+    TRIBO_CUDA(cudaGetDevice(&dev));
+    TRIBO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t need = std::max({smem_fwd_x<R>(c->nx, lpb), smem_inv_x<R>(c->nx, lpb),
+                                  sizeof(cplx<R>) * 2 * z_tile<R>() * c->nz});
+    if (need > (size_t)optin) {
+        set_last_error("grid needs more shared memory per block than the device offers");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_inv_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_fft_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return TRIBO_OK;
 }
 
