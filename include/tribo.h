@@ -184,6 +184,24 @@ tribo_status tribo_timing_enable(tribo_ctx* ctx, int32_t on);
 tribo_status tribo_timing_read(tribo_ctx* ctx, double* ms, int64_t* counts, int32_t nphases);
 const char*  tribo_phase_name(int32_t phase);
 
+/* The Poisson solve of tribo_poisson without a context and without any device
+ * allocation, for callers that cannot allocate device memory while they run
+ * (an embedding whose caching allocator already holds the device's memory, a
+ * real-time loop that must not wait on or fail in an allocation, a plug-in
+ * that is only handed pre-allocated buffers).  The paper has no counterpart;
+ * it is an interface convenience.  rho, phi (may be NULL) and E have the
+ * layouts and meaning of tribo_poisson; grid as for tribo_init; eps is the
+ * gas permittivity; precision TRIBO_FP64 or TRIBO_MIXED selects the "real"
+ * type of E; stream: a cudaStream_t (NULL = legacy default).  Asynchronous.
+ * All scratch lives in one static device array of 32 MiB that the library
+ * reserves on every device it is loaded on until the process exits; grids
+ * that need more, or more than 256 cells in any direction, are rejected with
+ * TRIBO_ERR_CAPACITY (tribo_last_error gives the sizes).  The first call on a
+ * device looks up that array's address (so make it before any stream
+ * capture).  Calls share the array: calls whose GPU work overlaps race. */
+tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps, int32_t precision,
+                                   const double* rho, double* phi, void* E, void* stream);
+
 const char*  tribo_strerror(tribo_status s);
 const char*  tribo_last_error(void);      /* thread-local detail of the last failure */
 void         tribo_destroy(tribo_ctx* ctx);

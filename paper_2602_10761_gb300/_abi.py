@@ -58,6 +58,8 @@ _SIGS = {
     "tribo_set_params": (C.c_int32, [C.c_void_p, C.POINTER(tribo_params)]),
     "tribo_step": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.c_double, C.c_int32]),
     "tribo_poisson": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tribo_poisson_noalloc": (C.c_int32, [C.POINTER(tribo_grid), C.c_double, C.c_int32, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "tribo_stats": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.POINTER(C.c_double),
                                 C.POINTER(C.c_uint64), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                 C.POINTER(C.c_int64)]),

@@ -180,6 +180,18 @@ def tribo_poisson(ctx: int, rho, phi, E) -> None:
     check(load().tribo_poisson(ctx, _ptr(rho), _ptr(phi), _ptr(E)), "tribo_poisson")
 
 
+def tribo_poisson_noalloc(nx: int, ny: int, nz: int, lx: float, lz: float, y_faces, eps: float,
+                          precision: int, rho, phi, E, stream=None) -> None:
+    """Context-free Poisson solve that allocates no device memory (for callers
+    that cannot allocate while running); scratch is the library's static
+    32 MiB device array, shared by all calls."""
+    yf = np.ascontiguousarray(np.asarray(y_faces, dtype=np.float64))
+    g = _abi.tribo_grid(nx, ny, nz, lx, lz, yf.ctypes.data_as(C.POINTER(C.c_double)))
+    sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    check(load().tribo_poisson_noalloc(C.byref(g), float(eps), int(precision), _ptr(rho), _ptr(phi), _ptr(E), sp),
+          "tribo_poisson_noalloc")
+
+
 def tribo_stats(ctx: int, particles: Optional[Particles], ny: int) -> dict:
     lib = load()
     sq = C.c_double(0.0)

@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <mutex>
 
 #include "tribo_internal.cuh"
 
@@ -477,3 +478,275 @@ tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool 
 }
 
 }  // namespace tribo
+
+// ---------------------------------------------------------------------------
+// tribo_poisson_noalloc: the standalone Poisson solve for callers that must
+// not allocate device memory.  Some hosts cannot call cudaMalloc once they are
+// running: a framework whose caching allocator has already reserved the
+// device's memory, a real-time loop where an allocation's latency or failure
+// mid-run is not acceptable, or a plug-in that is only ever handed
+// pre-allocated buffers.  This variant keeps its scratch (coefficient tables,
+// twiddles, spectra, Thomas sweep storage) in one fixed file-scope device
+// array instead of a context's allocations.  It has no counterpart in the
+// paper.
+//
+// The array is static device memory of this library: every GPU that loads
+// the library holds it until the process exits.  Host code cannot use the
+// array's name as a device address, so the first call on each device (with
+// that device current) looks the address up once with cudaGetSymbolAddress
+// and keeps it; that first call should therefore come before any stream
+// capture.  All calls share the array and it keeps the last call's contents:
+// each call rewrites every byte it reads before reading it, and two calls
+// whose work overlaps on the GPU (different streams or devices sharing
+// nothing but this array on one device) race with each other.
+namespace tribo {
+namespace {
+
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;   // 32 MiB
+constexpr int kNoallocMaxN = 256;                            // nx, ny, nz limit
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+struct NoallocDevice {
+    unsigned char* base = nullptr;
+    bool ready = false;
+};
+NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+struct NoallocLayout {
+    size_t tables, twx, twz, S, F, W, total;
+};
+
+size_t noalloc_table_doubles(int nx, int ny, int nz) {
+    const int nxh = nx / 2 + 1;
+    return (size_t)3 * ny + nx + nz + nxh + nz + 3 * (ny + 2) + ny;
+}
+
+NoallocLayout noalloc_layout(int nx, int ny, int nz, int nf, size_t rsz) {
+    const size_t csz = 2 * rsz;
+    const int nxh = nx / 2 + 1;
+    NoallocLayout L{};
+    size_t off = 0;
+    L.tables = off; off += round256(noalloc_table_doubles(nx, ny, nz) * sizeof(double));
+    L.twx = off;    off += round256((size_t)nx * csz);
+    L.twz = off;    off += round256((size_t)nz * csz);
+    L.S = off;      off += round256((size_t)nz * ny * nxh * csz);
+    L.F = off;      off += round256((size_t)nf * nz * (ny + 2) * nxh * csz);
+    L.W = off;      off += round256((size_t)ny * nz * nxh * (sizeof(double2) + sizeof(double)));
+    L.total = off;
+    return L;
+}
+
+template <class R>
+void noalloc_twiddles(int n, unsigned char* dst) {
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(dst);
+    for (int e = 0; e < n; ++e) {
+        const double a = 2.0 * M_PI * (double)e / (double)n;
+        tw[e] = cplx<R>{(R)std::cos(a), (R)(-std::sin(a))};
+    }
+}
+
+template <class R>
+tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, double* phi, void* E,
+                           cudaStream_t stream, unsigned char* base, const NoallocLayout& L) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = nx / 2 + 1;
+    const double* yf = g->y_faces;
+    const double dx = g->lx / nx, dz = g->lz / nz;
+    // host tables on the stack, laid out like the front of the scratch array
+    alignas(16) unsigned char hbuf[32768];
+    if (L.S > sizeof(hbuf)) {
+        set_last_error("tribo_poisson_noalloc: internal table buffer too small");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    double yc[kNoallocMaxN], dy[kNoallocMaxN];
+    for (int j = 0; j < ny; ++j) {
+        yc[j] = 0.5 * (yf[j] + yf[j + 1]);
+        dy[j] = yf[j + 1] - yf[j];
+    }
+    double* T = reinterpret_cast<double*>(hbuf + L.tables);
+    double* a = T;
+    double* b = a + ny;
+    double* cc = b + ny;
+    double* lamx = T + 3 * ny;
+    double* lamz = lamx + nx;
+    double* sinx = lamz + nz;
+    double* sinz = sinx + nxh;
+    double* ey = sinz + nz;
+    double* scale = ey + 3 * (ny + 2);
+    for (int j = 0; j < ny; ++j) {
+        a[j] = (j >= 1) ? 1.0 / (dy[j] * (yc[j] - yc[j - 1])) : 0.0;
+        cc[j] = (j <= ny - 2) ? 1.0 / (dy[j] * (yc[j + 1] - yc[j])) : 0.0;
+        b[j] = -(a[j] + cc[j]);
+        scale[j] = -1.0 / eps;
+    }
+    b[0] -= 1.0 / (dy[0] * (yc[0] - yf[0]));
+    b[ny - 1] -= 1.0 / (dy[ny - 1] * (yf[ny] - yc[ny - 1]));
+    for (int m = 0; m < nx; ++m) {
+        const double s = std::sin(M_PI * m / nx);
+        lamx[m] = 4.0 / (dx * dx) * s * s;
+    }
+    for (int m = 0; m < nz; ++m) {
+        const double s = std::sin(M_PI * m / nz);
+        lamz[m] = 4.0 / (dz * dz) * s * s;
+        sinz[m] = std::sin(2.0 * M_PI * m / nz) / dz;
+    }
+    for (int m = 0; m < nxh; ++m) sinx[m] = std::sin(2.0 * M_PI * m / nx) / dx;
+    for (int i = 0; i < 3 * (ny + 2); ++i) ey[i] = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        const int jn = j + 1;
+        double cm = 0, c0 = 0, cp = 0;
+        if (j >= 1) {
+            const double w = (yf[j] - yc[j - 1]) / (yc[j] - yc[j - 1]);
+            cm += (1.0 - w) / dy[j];
+            c0 += w / dy[j];
+        }
+        if (j + 1 <= ny - 1) {
+            const double w = (yf[j + 1] - yc[j]) / (yc[j + 1] - yc[j]);
+            c0 -= (1.0 - w) / dy[j];
+            cp -= w / dy[j];
+        }
+        ey[3 * jn + 0] = cm;
+        ey[3 * jn + 1] = c0;
+        ey[3 * jn + 2] = cp;
+    }
+    ey[2] = -1.0 / (yc[0] - yf[0]);
+    ey[3 * (ny + 1)] = 1.0 / (yf[ny] - yc[ny - 1]);
+    noalloc_twiddles<R>(nx, hbuf + L.twx);
+    noalloc_twiddles<R>(nz, hbuf + L.twz);
+    cudaError_t e = cudaMemcpyAsync(base, hbuf, L.S, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: table upload");
+
+    FftPlan px{}, pz{};
+    make_plan_radices(nx, px);
+    make_plan_radices(nz, pz);
+    px.tw = base + L.twx;
+    pz.tw = base + L.twz;
+    const double* dT = reinterpret_cast<const double*>(base + L.tables);
+    const double* d_ycoef = dT;
+    const double* d_lamx = dT + 3 * ny;
+    const double* d_lamz = d_lamx + nx;
+    const double* d_sinx = d_lamz + nz;
+    const double* d_sinz = d_sinx + nxh;
+    const double* d_ey = d_sinz + nz;
+    const double* d_scale = d_ey + 3 * (ny + 2);
+    cplx<R>* S = reinterpret_cast<cplx<R>*>(base + L.S);
+    cplx<R>* F = reinterpret_cast<cplx<R>*>(base + L.F);
+    double2* W = reinterpret_cast<double2*>(base + L.W);
+    double* Wc = reinterpret_cast<double*>(W + (size_t)ny * nz * nxh);
+    const int lpb = lines_per_block<R>();
+    const int mt = z_tile<R>();
+    const int want_phi = phi != nullptr ? 1 : 0;
+    const int nf = 3 + want_phi;
+    const int nlines = ny * nz;
+    k_fwd_x<R><<<(nlines + lpb - 1) / lpb, kThreads, smem_fwd_x<R>(nx, lpb), stream>>>(
+        const_cast<double*>(rho), d_scale, 0, S, nx, ny, nlines, nxh, px, lpb);
+    k_fft_z<R><<<dim3(ny, (nxh + mt - 1) / mt, 1), kThreads, sizeof(cplx<R>) * 2 * mt * nz, stream>>>(
+        S, nz, ny, nxh, mt, pz, (R)-1, 0);
+    const int np = nz * nxh;
+    k_solve_y<R><<<(np + 127) / 128, 128, 0, stream>>>(S, F, W, Wc, d_ycoef, d_lamx, d_lamz, d_sinx, d_sinz,
+                                                       d_ey, ny, nz, nxh, want_phi);
+    const size_t fstride = (size_t)nz * (ny + 2) * nxh;
+    k_fft_z<R><<<dim3(ny + 2, (nxh + mt - 1) / mt, nf), kThreads, sizeof(cplx<R>) * 2 * mt * nz, stream>>>(
+        F, nz, ny + 2, nxh, mt, pz, (R)1, fstride);
+    const int nl2 = nz * (ny + 2);
+    k_inv_x<R><<<(nl2 + lpb - 1) / lpb, kThreads, smem_inv_x<R>(nx, lpb), stream>>>(
+        F, (vec4<R>*)E, phi, nx, ny, nz, nxh, px, lpb, nf);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: kernel launch");
+    return TRIBO_OK;
+}
+
+bool noalloc_2a3b(int n) {
+    if (n < 1) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+// one-time set-up of the current device: the array's device address and the
+// kernels' shared-memory limit
+tribo_status noalloc_device(int dev, unsigned char** base) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: cudaGetSymbolAddress");
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: device attribute");
+        const void* fns[] = {(const void*)k_fwd_x<float>, (const void*)k_inv_x<float>, (const void*)k_fft_z<float>,
+                             (const void*)k_fwd_x<double>, (const void*)k_inv_x<double>,
+                             (const void*)k_fft_z<double>};
+        for (const void* f : fns) {
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: shared-memory limit");
+        }
+        d.base = static_cast<unsigned char*>(p);
+        d.ready = true;
+    }
+    *base = d.base;
+    return TRIBO_OK;
+}
+
+}  // namespace
+}  // namespace tribo
+
+extern "C" tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps, int32_t precision,
+                                              const double* rho, double* phi, void* E, void* stream) {
+    using namespace tribo;
+    if (!grid || !grid->y_faces || !rho || !E) {
+        set_last_error("tribo_poisson_noalloc: grid, y_faces, rho and E must not be NULL");
+        return TRIBO_ERR_ARG;
+    }
+    if (precision != TRIBO_FP64 && precision != TRIBO_MIXED) {
+        set_last_error("tribo_poisson_noalloc: unknown precision");
+        return TRIBO_ERR_ARG;
+    }
+    if (!(eps > 0) || !(grid->lx > 0) || !(grid->lz > 0)) {
+        set_last_error("tribo_poisson_noalloc: eps, lx and lz must be positive");
+        return TRIBO_ERR_ARG;
+    }
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    if (nx < 4 || nz < 4 || nx % 2 || !noalloc_2a3b(nx) || !noalloc_2a3b(nz) || ny < 2) {
+        set_last_error("tribo_poisson_noalloc: nx and nz must be 2^a 3^b >= 4 (nx even), ny >= 2");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    const size_t rsz = precision == TRIBO_FP64 ? sizeof(double) : sizeof(float);
+    const NoallocLayout L = noalloc_layout(nx, ny, nz, phi ? 4 : 3, rsz);
+    if (nx > kNoallocMaxN || ny > kNoallocMaxN || nz > kNoallocMaxN || L.total > kNoallocScratchBytes) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "tribo_poisson_noalloc: a %dx%dx%d grid needs %.1f MiB of static scratch; the limit is "
+                 "%d MiB and %d cells per direction",
+                 nx, ny, nz, L.total / 1048576.0, (int)(kNoallocScratchBytes >> 20), kNoallocMaxN);
+        set_last_error(buf);
+        return TRIBO_ERR_CAPACITY;
+    }
+    if (grid->y_faces[0] != 0.0) {
+        set_last_error("tribo_poisson_noalloc: y_faces[0] must be 0");
+        return TRIBO_ERR_ARG;
+    }
+    for (int j = 0; j < ny; ++j)
+        if (!(grid->y_faces[j + 1] > grid->y_faces[j])) {
+            set_last_error("tribo_poisson_noalloc: y_faces must increase strictly");
+            return TRIBO_ERR_ARG;
+        }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices) {
+        set_last_error("tribo_poisson_noalloc: device ordinal out of range");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    unsigned char* base = nullptr;
+    tribo_status st = noalloc_device(dev, &base);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == TRIBO_FP64) return noalloc_solve<double>(grid, eps, rho, phi, E, s, base, L);
+    return noalloc_solve<float>(grid, eps, rho, phi, E, s, base, L);
+}
