@@ -200,7 +200,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sort-every", type=int, default=0)
+    ap.add_argument("--sort-every", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kThreads) k_step(StepArgs<R> a, PView p, int w
         // acceleration q E / m
         R ax = 0, ay = 0, az = 0;
         if (a.electro) {
-            const R qm = (R)q / (a.mass_coef * d * d * d);
+            const R qm = from_f64<R>(q) / (a.mass_coef * d * d * d);
             ax = qm * Ef[0]; ay = qm * Ef[1]; az = qm * Ef[2];
         }
         R xn, yn, zn, vxn, vyn, vzn;
@@ -418,7 +418,162 @@ tribo_status deposit_impl(tribo_ctx* c, const PView& p) {
     return TRIBO_OK;
 }
 
+// ---------------------------------------------------------------- sort by cell
+// Counting sort on the cell key: count (the atomic's return value is the
+// particle's rank inside its cell), exclusive scan of the counts over all
+// cells, scatter of every particle array to offset[key] + rank.  The order
+// inside a cell follows the atomics and is not deterministic.
+template <class R>
+__global__ void k_sort_count(StepArgs<R> a, PView p, uint32_t* __restrict__ counts, uint32_t* __restrict__ key,
+                             uint32_t* __restrict__ rank) {
+    const R* X = (const R*)p.x; const R* Y = (const R*)p.y; const R* Z = (const R*)p.z;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride) {
+        R y = Y[n];
+        if (!(y >= (R)0 && y <= a.ly)) y = a.ly * (R)0.5;   // reported by the step kernel
+        int j;
+        const uint32_t k = cell_key<R>(X[n], y, Z[n], a, &j);
+        key[n] = k;
+        rank[n] = atomicAdd(&counts[k], 1u);
+    }
+}
+
+template <class R>
+__global__ void k_sort_scatter(PView src, PView dst, const uint32_t* __restrict__ offsets,
+                               const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < src.n; n += stride) {
+        const uint32_t d = offsets[key[n]] + rank[n];
+        ((R*)dst.x)[d] = ((const R*)src.x)[n];
+        ((R*)dst.y)[d] = ((const R*)src.y)[n];
+        ((R*)dst.z)[d] = ((const R*)src.z)[n];
+        ((R*)dst.vx)[d] = ((const R*)src.vx)[n];
+        ((R*)dst.vy)[d] = ((const R*)src.vy)[n];
+        ((R*)dst.vz)[d] = ((const R*)src.vz)[n];
+        ((R*)dst.d)[d] = ((const R*)src.d)[n];
+        dst.q[d] = src.q[n];
+        dst.q_wall[d] = src.q_wall[n];
+        dst.n_imp[d] = src.n_imp[n];
+        if (src.id) dst.id[d] = src.id[n];
+    }
+}
+
+// exclusive scan of n uint32 values in place: per-tile sums, a scan of the
+// tile sums in one block, then the per-tile scans
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* sh, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        sh[lane] = w;   // inclusive warp totals
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? sh[warp - 1] : 0u;
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __restrict__ in, size_t n,
+                                                             uint32_t* __restrict__ tile_sums) {
+    __shared__ uint32_t sh[32];
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) s += in[base + i];
+    uint32_t total;
+    block_exclusive_scan(s, sh, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict__ sums, int nt) {
+    __shared__ uint32_t sh[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nt; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nt ? sums[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, sh, &total);
+        if (i < nt) sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restrict__ data, size_t n,
+                                                             const uint32_t* __restrict__ tile_off) {
+    __shared__ uint32_t sh[32];
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer];
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = base + i < n ? data[base + i] : 0u;
+        s += v[i];
+    }
+    uint32_t total;
+    uint32_t run = tile_off[blockIdx.x] + block_exclusive_scan(s, sh, &total);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (base + i < n) data[base + i] = run;
+        run += v[i];
+    }
+}
+
+template <class R>
+tribo_status sort_impl(tribo_ctx* c, const PView& src, const PView& dst) {
+    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+    uint32_t* counts = c->sort_counts;
+    uint32_t* key = c->sort_key;
+    uint32_t* rank = c->sort_rank;
+    const int ntiles = (int)((ncell + kScanTile - 1) / kScanTile);
+    phase_begin(c, PH_SORT);
+    TRIBO_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ncell, c->stream));
+    StepArgs<R> a = make_args<R>(c, 0.0);
+    k_sort_count<R><<<grid_for(src.n), kThreads, 0, c->stream>>>(a, src, counts, key, rank);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_SORT);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, c->stream>>>(counts, ncell, c->sort_tiles);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_SORT);
+    k_scan_sums<<<1, kScanThreads, 0, c->stream>>>(c->sort_tiles, ntiles);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_SORT);
+    k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(counts, ncell, c->sort_tiles);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_SORT);
+    k_sort_scatter<R><<<grid_for(src.n), kThreads, 0, c->stream>>>(src, dst, counts, key, rank);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
 }  // namespace
+
+tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst) {
+    if (src.n == 0) return TRIBO_OK;
+    if (c->prec == TRIBO_FP64) return sort_impl<double>(c, src, dst);
+    return sort_impl<float>(c, src, dst);
+}
 
 tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell) {
     if (p.n == 0) return TRIBO_OK;

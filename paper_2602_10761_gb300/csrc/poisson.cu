@@ -444,8 +444,17 @@ tribo_status poisson_setup(tribo_ctx* c) {
     const size_t csz = 2 * rsz;
     TRIBO_CUDA(cudaMalloc(&c->S, csz * (size_t)nz * ny * nxh));
     TRIBO_CUDA(cudaMalloc(&c->F, csz * 4 * (size_t)nz * (ny + 2) * nxh));
-    TRIBO_CUDA(cudaMalloc(&c->W, (sizeof(double2) + sizeof(double)) * (size_t)ny * nz * nxh));
     tribo_status st;
+    c->fast = poisson_fast_supported(nx, nz);
+    if (c->fast) {
+        st = poisson_fast_setup(c);
+        if (st == TRIBO_OK) return TRIBO_OK;
+        if (st != TRIBO_ERR_UNSUPPORTED) return st;
+        poisson_fast_free(c);
+        c->d_ytab = c->W2 = c->d_twx = c->d_twz = nullptr;
+        c->fast = false;
+    }
+    TRIBO_CUDA(cudaMalloc(&c->W, (sizeof(double2) + sizeof(double)) * (size_t)ny * nz * nxh));
     if (c->prec == TRIBO_FP64) {
         if ((st = make_plan<double>(nx, c->plan_x)) != TRIBO_OK) return st;
         if ((st = make_plan<double>(nz, c->plan_z)) != TRIBO_OK) return st;
@@ -468,11 +477,13 @@ tribo_status poisson_free(tribo_ctx* c) {
     cudaFree(c->W);
     cudaFree(c->plan_x.tw);
     cudaFree(c->plan_z.tw);
+    poisson_fast_free(c);
     return TRIBO_OK;
 }
 
 tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
                            void* E) {
+    if (c->fast) return poisson_fast_solve(c, src, scale, zero_src, phi, E);
     if (c->prec == TRIBO_FP64) return solve_impl<double>(c, src, scale, zero_src, phi, E);
     return solve_impl<float>(c, src, scale, zero_src, phi, E);
 }

@@ -1,0 +1,960 @@
+// Poisson solve and E field, bandwidth-oriented path for compile-time
+// transform lengths (nx/2 and nz in {2, 3, 4, 6, 8, 12, ..., 384, 512}).
+//
+// Same discretisation and result as the generic path in poisson.cu (Sec. 2.2
+// Poisson equation with grounded walls, second-order finite volumes of
+// Sec. 3.1, E = -grad(phi) with Gauss-linear E_y and central E_x, E_z), but:
+//  * the x transforms are real: a length-nx/2 complex FFT of the packed line
+//    plus the split step (half the work and shared memory);
+//  * the y factorisation depends only on lam = lam_x + lam_z, so the factors
+//    (1/pivot_j, c'_j) are computed once in FP64 at set-up, one table row per
+//    (|m_z|, m_x); each thread solves the pencils m_z and N_z - m_z, which
+//    share the table row;
+//  * E_y is formed from phi in the y sweep, where phi still carries more than
+//    FP32 precision (a difference of FP32 values would lose the near-wall
+//    field); E_z takes its spectral multiplier before the inverse z transform
+//    and E_x before the inverse x transform.
+// In FP64 mode everything is FP64.  In mixed mode the sweeps run in
+// double-single arithmetic (value = hi + lo, two FP32 numbers; Dekker's
+// product and Knuth's sum), which keeps about 46 significant bits on the FP32
+// pipes: on this GPU FP64 instructions, conversions included, issue at 1/64
+// of the FP32 rate.
+// Passes: xfwd (zeroes the charge buffer), zfwd, ysolve, zinv, xinv.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fft.cuh"
+#include "tribo_internal.cuh"
+
+namespace tribo {
+
+namespace {
+
+using fft::pad;
+using fft::padded;
+
+constexpr int kThreads = 256;
+constexpr int kZTile = 16;      // m_x columns per forward z-transform block
+constexpr int kZTileInv = 8;    // m_x columns per inverse z-transform block (three fields)
+
+// ---------------------------------------------------------------- double-single
+struct ds {
+    float hi, lo;
+};
+// Knuth's two-sum: s + e == a + b exactly
+__device__ __forceinline__ ds two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+// Dekker's fast two-sum, |a| >= |b|
+__device__ __forceinline__ ds fast_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ds ds_mul(ds a, ds b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ds ds_add(ds a, ds b) {
+    ds s = two_sum(a.hi, b.hi);
+    const ds t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ds ds_neg(ds a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
+
+// ---------------------------------------------------------------- x forward
+// One block: LPB lines (k, j) of the charge-sum array.  z_n = x_2n + i x_2n+1,
+// Z = FFT_{nx/2}(z), X_m = (Z_m + conj Z_{M-m})/2 - (i/2) W^m (Z_m - conj Z_{M-m}).
+template <class R, int M, int LPB>
+__global__ void __launch_bounds__(kThreads) k_xfwd(double* __restrict__ src, const double* __restrict__ scale_row,
+                                                   int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
+                                                   const cplx<R>* __restrict__ tw_g) {
+    constexpr int NX = 2 * M;
+    constexpr int NXH = M + 1;
+    constexpr int ST = padded<R, M>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* A = tw + NX;
+    cplx<R>* B = A + LPB * ST;
+    R* sc = reinterpret_cast<R*>(B + LPB * ST);
+    const int line0 = blockIdx.x * LPB;
+    const int nl = min(LPB, nlines - line0);
+    for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
+    if (threadIdx.x < nl) sc[threadIdx.x] = from_f64<R>(scale_row[(line0 + threadIdx.x) % ny]);
+    __syncthreads();
+    // all loads first: the zeroing stores go to the same buffer, and issuing
+    // them between loads would serialise the loads
+    constexpr int PER = (LPB * M + kThreads - 1) / kThreads;
+    const double2* src2 = reinterpret_cast<const double2*>(src) + (size_t)line0 * M;
+    double2 v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        v[r] = idx < nl * M ? src2[idx] : make_double2(0.0, 0.0);
+    }
+    if (zero_src) {
+        double2* dst2 = reinterpret_cast<double2*>(src) + (size_t)line0 * M;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int idx = threadIdx.x + r * kThreads;
+            if (idx < nl * M) dst2[idx] = make_double2(0.0, 0.0);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        if (idx < nl * M) {
+            const int l = idx / M;
+            const int n = idx - l * M;
+            const R s = sc[l];
+            A[l * ST + pad<R>(n)] = cplx<R>{from_f64<R>(v[r].x) * s, from_f64<R>(v[r].y) * s};
+        }
+    }
+    __syncthreads();
+    cplx<R>* Z = fft::transform<R, -1, M>(A, B, nl, tw, 2);
+    for (int idx = threadIdx.x; idx < nl * NXH; idx += blockDim.x) {
+        const int l = idx / NXH;
+        const int m = idx - l * NXH;
+        const cplx<R> zm = Z[l * ST + pad<R>(m == M ? 0 : m)];
+        const cplx<R> zc = conj(Z[l * ST + pad<R>(m == 0 ? 0 : M - m)]);
+        const cplx<R> sum = zm + zc, dif = zm - zc;
+        const cplx<R> t = tw[m] * dif;
+        // X = sum/2 - (i/2) t
+        S[(size_t)(line0 + l) * NXH + m] = cplx<R>{(R)0.5 * (sum.re + t.im), (R)0.5 * (sum.im - t.re)};
+    }
+}
+
+// ---------------------------------------------------------------- z forward
+// Block (plane j, m_x tile): columns along k of S[k][j][m_x], in place.
+template <class R, int NZ>
+__global__ void __launch_bounds__(kThreads) k_zfwd(cplx<R>* __restrict__ S, int ny, int nxh,
+                                                   const cplx<R>* __restrict__ tw_g) {
+    constexpr int ST = padded<R, NZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* A = tw + NZ;
+    cplx<R>* B = A + kZTile * ST;
+    for (int i = threadIdx.x; i < NZ; i += blockDim.x) tw[i] = tw_g[i];
+    const int j = blockIdx.x;
+    const int mx0 = blockIdx.y * kZTile;
+    const int nt = min(kZTile, nxh - mx0);
+    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
+        const int k = idx / nt;
+        const int t = idx - k * nt;
+        A[t * ST + pad<R>(k)] = S[((size_t)k * ny + j) * nxh + mx0 + t];
+    }
+    __syncthreads();
+    cplx<R>* res = fft::transform<R, -1, NZ>(A, B, nt, tw, 1);
+    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
+        const int k = idx / nt;
+        const int t = idx - k * nt;
+        S[((size_t)k * ny + j) * nxh + mx0 + t] = res[t * ST + pad<R>(k)];
+    }
+}
+
+// ---------------------------------------------------------------- y solve, FP64
+// Thread per table row (|m_z|, m_x): the pencil m_z = |m_z| and, unless it is
+// self-conjugate, m_z = nz - |m_z|.  FP64 Thomas with the precomputed
+// factors tab[j][item] = (1/pivot_j, c'_j); dp in W[j][item][2].  Writes
+// phi-hat back into S and the E_y spectrum (all ny+2 nodes) into Fy, with
+// E_y(node jn) = cm phi[jn-2] + c0 phi[jn-1] + cp phi[jn].
+__global__ void __launch_bounds__(128) k_ysolve64(cplx<double>* __restrict__ S, cplx<double>* __restrict__ Fy,
+                                                  const double2* __restrict__ tab, double2* __restrict__ W,
+                                                  const double* __restrict__ ycoef, const double* __restrict__ ey,
+                                                  int ny, int nz, int nxh) {
+    const int ni = (nz / 2 + 1) * nxh;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= ni) return;
+    const int mzp = item / nxh;
+    const int mx = item - mzp * nxh;
+    const bool two = mzp != 0 && 2 * mzp != nz;
+    const int mzs[2] = {mzp, nz - mzp};
+    const int np = two ? 2 : 1;
+    const double* a = ycoef;
+    const int nyn = ny + 2;
+    double2 dp[2] = {make_double2(0, 0), make_double2(0, 0)};
+    for (int j = 0; j < ny; ++j) {
+        const double inv = tab[(size_t)j * ni + item].x;
+        const double aj = a[j];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s < np) {
+                const cplx<double> r = S[((size_t)mzs[s] * ny + j) * nxh + mx];
+                dp[s] = make_double2((r.re - aj * dp[s].x) * inv, (r.im - aj * dp[s].y) * inv);
+                W[((size_t)j * ni + item) * 2 + s] = dp[s];
+            }
+        }
+    }
+    for (int s = 0; s < np; ++s) {
+        const int mz = mzs[s];
+        cplx<double>* srow = S + (size_t)mz * ny * nxh + mx;
+        cplx<double>* frow = Fy + (size_t)mz * nyn * nxh + mx;
+        double2 x1 = make_double2(0, 0), x2 = make_double2(0, 0);   // x[j+1], x[j+2]
+        for (int j = ny - 1; j >= 0; --j) {
+            const double2 d = W[((size_t)j * ni + item) * 2 + s];
+            double2 x;
+            if (j == ny - 1) {
+                x = d;
+            } else {
+                const double cp = tab[(size_t)j * ni + item].y;
+                x = make_double2(d.x - cp * x1.x, d.y - cp * x1.y);
+            }
+            srow[(size_t)j * nxh] = cplx<double>{x.x, x.y};
+            const int jn = j + 2;
+            if (jn <= ny + 1) {
+                const double cm = ey[3 * jn], c0 = ey[3 * jn + 1], cq = ey[3 * jn + 2];
+                frow[(size_t)jn * nxh] = cplx<double>{cm * x.x + c0 * x1.x + cq * x2.x,
+                                                      cm * x.y + c0 * x1.y + cq * x2.y};
+            }
+            x2 = x1;
+            x1 = x;
+        }
+        const double c0 = ey[3 * 1 + 1], cq = ey[3 * 1 + 2];
+        frow[(size_t)1 * nxh] = cplx<double>{c0 * x1.x + cq * x2.x, c0 * x1.y + cq * x2.y};
+        const double cw = ey[3 * 0 + 2];
+        frow[0] = cplx<double>{cw * x1.x, cw * x1.y};
+    }
+}
+
+// ---------------------------------------------------------------- y solve, double-single
+// Same sweeps in double-single arithmetic.  tab[j][item] = (1/pivot hi, lo,
+// c' hi, lo); a_ds[j] = sub-diagonal (hi, lo); W[j][item][2] = dp (re hi, re
+// lo, im hi, im lo).  E_y per cell j = A_j phi_j + Bm_j (phi_j - phi_j-1) +
+// Bp_j (phi_j+1 - phi_j) with the differences taken in double-single;
+// wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
+__global__ void __launch_bounds__(128) k_ysolve_ds(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
+                                                   const float4* __restrict__ tab, float4* __restrict__ W,
+                                                   const float2* __restrict__ a_ds, const float4* __restrict__ ec,
+                                                   int ny, int nz, int nxh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sa = reinterpret_cast<float2*>(smem_raw);          // ny
+    float4* se = reinterpret_cast<float4*>(sa + ((ny + 1) & ~1)); // ny+1: (A, Bm, Bp, -) per cell, [ny] = walls
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) sa[j] = a_ds[j];
+    for (int j = threadIdx.x; j <= ny; j += blockDim.x) se[j] = ec[j];
+    __syncthreads();
+    const int ni = (nz / 2 + 1) * nxh;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= ni) return;
+    const int mzp = item / nxh;
+    const int mx = item - mzp * nxh;
+    const bool two = mzp != 0 && 2 * mzp != nz;
+    const int mzs[2] = {mzp, nz - mzp};
+    const int np = two ? 2 : 1;
+    const int nyn = ny + 2;
+    ds pr[2] = {{0.f, 0.f}, {0.f, 0.f}}, pi[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int j = 0; j < ny; ++j) {
+        const float4 t = tab[(size_t)j * ni + item];
+        const ds inv = {t.x, t.y};
+        const ds aj = {sa[j].x, sa[j].y};
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (s < np) {
+                const cplx<float> r = S[((size_t)mzs[s] * ny + j) * nxh + mx];
+                // dp = (r - a dp) / pivot
+                pr[s] = ds_mul(ds_add(ds{r.re, 0.f}, ds_neg(ds_mul(aj, pr[s]))), inv);
+                pi[s] = ds_mul(ds_add(ds{r.im, 0.f}, ds_neg(ds_mul(aj, pi[s]))), inv);
+                W[((size_t)j * ni + item) * 2 + s] = make_float4(pr[s].hi, pr[s].lo, pi[s].hi, pi[s].lo);
+            }
+        }
+    }
+    const float4 walls = se[ny];   // (bottom coefficient, top coefficient, -, -)
+    for (int s = 0; s < np; ++s) {
+        const int mz = mzs[s];
+        cplx<float>* srow = S + (size_t)mz * ny * nxh + mx;
+        cplx<float>* frow = Fy + (size_t)mz * nyn * nxh + mx;
+        ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};         // phi[j+1]
+        float dr_next = 0.f, di_next = 0.f;           // phi[j+2] - phi[j+1]
+        for (int j = ny - 1; j >= 0; --j) {
+            const float4 w = W[((size_t)j * ni + item) * 2 + s];
+            ds xr = {w.x, w.y}, xi = {w.z, w.w};
+            if (j != ny - 1) {
+                const float4 t = tab[(size_t)j * ni + item];
+                const ds cp = {t.z, t.w};
+                xr = ds_add(xr, ds_neg(ds_mul(cp, xr1)));
+                xi = ds_add(xi, ds_neg(ds_mul(cp, xi1)));
+            } else {
+                // top wall node from phi[ny-1]
+                frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * ds_f(xr), walls.y * ds_f(xi)};
+            }
+            srow[(size_t)j * nxh] = cplx<float>{ds_f(xr), ds_f(xi)};
+            // E_y of cell j+1 (node j+2): phi[j+1], d0 = phi[j+1]-phi[j], d1 = phi[j+2]-phi[j+1]
+            float d0r = 0.f, d0i = 0.f;
+            if (j + 1 <= ny - 1) {
+                d0r = ds_f(ds_add(xr1, ds_neg(xr)));
+                d0i = ds_f(ds_add(xi1, ds_neg(xi)));
+                const float4 c = se[j + 1];
+                frow[(size_t)(j + 2) * nxh] = cplx<float>{c.x * ds_f(xr1) + c.y * d0r + c.z * dr_next,
+                                                          c.x * ds_f(xi1) + c.y * d0i + c.z * di_next};
+            }
+            dr_next = d0r;
+            di_next = d0i;
+            xr1 = xr;
+            xi1 = xi;
+        }
+        // cell 0 (node 1) and the bottom wall node 0
+        const float4 c = se[0];
+        const float x0r = ds_f(xr1), x0i = ds_f(xi1);
+        frow[(size_t)1 * nxh] = cplx<float>{c.x * x0r + c.z * dr_next, c.x * x0i + c.z * di_next};
+        frow[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
+    }
+}
+
+// ---------------------------------------------------------------- y solve, warp-cooperative
+// One warp per table row (|m_z|, m_x), both pencils.  Lane l holds rows
+// [l*RL, l*RL + RL) in registers.  The forward recurrence y_j = (r_j - a_j
+// y_j-1) / pivot_j is affine in the carry y_j0-1 entering the lane:
+// y_j = yh_j + P_j c with yh from a zero carry and P_j the product of
+// -a_t/pivot_t; the lanes' end maps are combined by a Kogge-Stone prefix
+// over shuffles, giving each lane its carry.  The backward recurrence
+// x_j = y_j - c'_j x_j+1 is treated the same way with a suffix combination.
+// All arithmetic is double-single; nothing leaves the registers but the
+// outputs (phi-hat and the E_y spectrum, as in k_ysolve_ds).
+__device__ __forceinline__ ds shfl_up_ds(ds v, int d) {
+    return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ ds shfl_down_ds(ds v, int d) {
+    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ ds ds_fma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }   // a b + c
+
+template <int RL>
+__global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
+                                                     const float4* __restrict__ tab,
+                                                     const float2* __restrict__ a_ds,
+                                                     const float4* __restrict__ ec, int ny, int nz, int nxh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* sa = reinterpret_cast<float2*>(smem_raw);
+    float4* se = reinterpret_cast<float4*>(sa + ((ny + 1) & ~1));
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) sa[j] = a_ds[j];
+    for (int j = threadIdx.x; j <= ny; j += blockDim.x) se[j] = ec[j];
+    __syncthreads();
+    const int ni = (nz / 2 + 1) * nxh;
+    const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (item >= ni) return;          // whole warps leave together
+    const int lane = threadIdx.x & 31;
+    const int mzp = item / nxh;
+    const int mx = item - mzp * nxh;
+    const int np = (mzp != 0 && 2 * mzp != nz) ? 2 : 1;
+    const int j0 = lane * RL;
+    const int nv = max(0, min(RL, ny - j0));           // valid rows of this lane
+    const size_t row0[2] = {(size_t)mzp * ny * nxh + mx, (size_t)(nz - mzp) * ny * nxh + mx};
+
+    float4 t[RL];
+    ds yr[2][RL], yi[2][RL], P[RL];
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        if (i < nv) {
+            t[i] = tab[(size_t)(j0 + i) * ni + item];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const cplx<float> r = (s < np) ? S[row0[s] + (size_t)(j0 + i) * nxh] : cplx<float>{0.f, 0.f};
+                yr[s][i] = {r.re, 0.f};
+                yi[s][i] = {r.im, 0.f};
+            }
+        }
+    }
+    // forward, zero carry; P_i = prod (-a/pivot)
+    ds prun = {1.f, 0.f};
+    ds pr[2] = {{0.f, 0.f}, {0.f, 0.f}}, pim[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        if (i < nv) {
+            const ds inv = {t[i].x, t[i].y};
+            const ds aj = {sa[j0 + i].x, sa[j0 + i].y};
+            const ds at = ds_mul(aj, inv);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                pr[s] = ds_add(ds_mul(yr[s][i], inv), ds_neg(ds_mul(at, pr[s])));
+                pim[s] = ds_add(ds_mul(yi[s][i], inv), ds_neg(ds_mul(at, pim[s])));
+                yr[s][i] = pr[s];
+                yi[s][i] = pim[s];
+            }
+            prun = ds_mul(prun, ds_neg(at));
+            P[i] = prun;
+        }
+    }
+    // prefix combination of the lanes' maps c -> yh_last + P_last c
+    ds beta = nv > 0 ? prun : ds{1.f, 0.f};
+    ds al[2][2] = {{pr[0], pim[0]}, {pr[1], pim[1]}};   // [pencil][re/im]
+    if (nv == 0) { al[0][0] = al[0][1] = al[1][0] = al[1][1] = ds{0.f, 0.f}; }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const ds b2 = shfl_up_ds(beta, d);
+        ds a2[2][2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            a2[s][0] = shfl_up_ds(al[s][0], d);
+            a2[s][1] = shfl_up_ds(al[s][1], d);
+        }
+        if (lane >= d) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                al[s][0] = ds_fma(beta, a2[s][0], al[s][0]);
+                al[s][1] = ds_fma(beta, a2[s][1], al[s][1]);
+            }
+            beta = ds_mul(beta, b2);
+        }
+    }
+    ds cr[2], ci[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        cr[s] = shfl_up_ds(al[s][0], 1);
+        ci[s] = shfl_up_ds(al[s][1], 1);
+        if (lane == 0) { cr[s] = ds{0.f, 0.f}; ci[s] = ds{0.f, 0.f}; }
+    }
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        if (i < nv) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                yr[s][i] = ds_fma(P[i], cr[s], yr[s][i]);
+                yi[s][i] = ds_fma(P[i], ci[s], yi[s][i]);
+            }
+        }
+    }
+    // backward, zero carry from above; Q_i = prod over rows i..last of (-c')
+    ds qrun = {1.f, 0.f};
+    ds xr[2] = {{0.f, 0.f}, {0.f, 0.f}}, xi[2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int i = RL - 1; i >= 0; --i) {
+        if (i < nv) {
+            const ds cp = {t[i].z, t[i].w};
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                xr[s] = ds_add(yr[s][i], ds_neg(ds_mul(cp, xr[s])));
+                xi[s] = ds_add(yi[s][i], ds_neg(ds_mul(cp, xi[s])));
+                yr[s][i] = xr[s];
+                yi[s][i] = xi[s];
+            }
+            qrun = ds_mul(qrun, ds_neg(cp));
+            P[i] = qrun;
+        }
+    }
+    // suffix combination of the lanes' maps d -> xh_first + Q_first d
+    beta = nv > 0 ? qrun : ds{1.f, 0.f};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        al[s][0] = nv > 0 ? xr[s] : ds{0.f, 0.f};
+        al[s][1] = nv > 0 ? xi[s] : ds{0.f, 0.f};
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const ds b2 = shfl_down_ds(beta, d);
+        ds a2[2][2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            a2[s][0] = shfl_down_ds(al[s][0], d);
+            a2[s][1] = shfl_down_ds(al[s][1], d);
+        }
+        if (lane + d < 32) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                al[s][0] = ds_fma(beta, a2[s][0], al[s][0]);
+                al[s][1] = ds_fma(beta, a2[s][1], al[s][1]);
+            }
+            beta = ds_mul(beta, b2);
+        }
+    }
+    ds dr[2], di[2];   // x of the first row of the next lane
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        dr[s] = shfl_down_ds(al[s][0], 1);
+        di[s] = shfl_down_ds(al[s][1], 1);
+        if (lane == 31) { dr[s] = ds{0.f, 0.f}; di[s] = ds{0.f, 0.f}; }
+    }
+#pragma unroll
+    for (int i = 0; i < RL; ++i) {
+        if (i < nv) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                yr[s][i] = ds_fma(P[i], dr[s], yr[s][i]);
+                yi[s][i] = ds_fma(P[i], di[s], yi[s][i]);
+            }
+        }
+    }
+    // x of the previous lane's last row, for the E_y differences
+    const int nyn = ny + 2;
+    const float4 walls = se[ny];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        // x of this lane's last valid row (selects, no indexing by nv)
+        ds lr = yr[s][RL - 1], li = yi[s][RL - 1];
+#pragma unroll
+        for (int i = 0; i + 1 < RL; ++i) {
+            const bool sel = (i + 1 == nv);
+            lr.hi = sel ? yr[s][i].hi : lr.hi;
+            lr.lo = sel ? yr[s][i].lo : lr.lo;
+            li.hi = sel ? yi[s][i].hi : li.hi;
+            li.lo = sel ? yi[s][i].lo : li.lo;
+        }
+        const ds br = shfl_up_ds(lr, 1), bi = shfl_up_ds(li, 1);
+        if (s < np) {
+        const size_t mz = s == 0 ? (size_t)mzp : (size_t)(nz - mzp);
+        cplx<float>* srow = S + mz * ny * nxh + mx;
+        cplx<float>* frow = Fy + mz * nyn * nxh + mx;
+        ds prv_r = br, prv_i = bi;     // x[j-1]
+#pragma unroll
+        for (int i = 0; i < RL; ++i) {
+            if (i < nv) {
+                const int j = j0 + i;
+                const ds cur_r = yr[s][i], cur_i = yi[s][i];
+                ds nxt_r = dr[s], nxt_i = di[s];
+                if (i + 1 < RL) {
+                    if (i + 1 < nv) {
+                        nxt_r = yr[s][i + 1];
+                        nxt_i = yi[s][i + 1];
+                    }
+                }
+                const float fr = ds_f(cur_r), fi = ds_f(cur_i);
+                srow[(size_t)j * nxh] = cplx<float>{fr, fi};
+                const float4 c = se[j];
+                const float d0r = ds_f(ds_add(cur_r, ds_neg(prv_r))), d0i = ds_f(ds_add(cur_i, ds_neg(prv_i)));
+                const float d1r = ds_f(ds_add(nxt_r, ds_neg(cur_r))), d1i = ds_f(ds_add(nxt_i, ds_neg(cur_i)));
+                frow[(size_t)(j + 1) * nxh] = cplx<float>{c.x * fr + c.y * d0r + c.z * d1r,
+                                                          c.x * fi + c.y * d0i + c.z * d1i};
+                if (j == 0) frow[0] = cplx<float>{walls.x * fr, walls.x * fi};
+                if (j == ny - 1) frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * fr, walls.y * fi};
+                prv_r = cur_r;
+                prv_i = cur_i;
+            }
+        }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- z inverse
+// Block (node plane jn, m_x tile).  Interior planes: phi-hat of cell jn-1 ->
+// F0 = IFFT_z(phi-hat) and F2 = IFFT_z(-i sin(2 pi m_z/nz)/dz phi-hat); all
+// planes: F1 = IFFT_z(E_y-hat) in place.
+template <class R, int NZ>
+__global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
+                                                   int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
+                                                   const cplx<R>* __restrict__ tw_g) {
+    constexpr int ST = padded<R, NZ>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* A = tw + NZ;        // 3 tiles: phi, E_z, E_y
+    cplx<R>* B = A + 3 * kZTileInv * ST;
+    R* sz = reinterpret_cast<R*>(B + 3 * kZTileInv * ST);
+    for (int i = threadIdx.x; i < NZ; i += blockDim.x) {
+        tw[i] = tw_g[i];
+        sz[i] = from_f64<R>(sinz[i]);
+    }
+    const int nyn = ny + 2;
+    const int jn = blockIdx.x;
+    const bool interior = jn >= 1 && jn <= ny;
+    const int mx0 = blockIdx.y * kZTileInv;
+    const int nt = min(kZTileInv, nxh - mx0);
+    const int nlines = interior ? 3 * kZTileInv : kZTileInv;   // E_y tile first when alone
+    __syncthreads();
+    cplx<R>* Fy = F + fstride;
+    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
+        const int k = idx / nt;
+        const int t = idx - k * nt;
+        const int kp = pad<R>(k);
+        A[t * ST + kp] = Fy[((size_t)k * nyn + jn) * nxh + mx0 + t];
+        if (interior) {
+            const cplx<R> ph = S[((size_t)k * ny + (jn - 1)) * nxh + mx0 + t];
+            A[(kZTileInv + t) * ST + kp] = ph;
+            A[(2 * kZTileInv + t) * ST + kp] = cplx<R>{sz[k] * ph.im, -sz[k] * ph.re};   // -i s phi
+        }
+    }
+    __syncthreads();
+    cplx<R>* res = fft::transform<R, 1, NZ>(A, B, nlines, tw, 1);
+    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
+        const int k = idx / nt;
+        const int t = idx - k * nt;
+        const int kp = pad<R>(k);
+        const size_t o = ((size_t)k * nyn + jn) * nxh + mx0 + t;
+        Fy[o] = res[t * ST + kp];
+        if (interior) {
+            F[o] = res[(kZTileInv + t) * ST + kp];
+            F[2 * fstride + o] = res[(2 * kZTileInv + t) * ST + kp];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- x inverse
+// One block: LPB node lines (k, jn).  Fields E_x (F0 times -i sin(2 pi m/nx)/dx),
+// E_y (F1), E_z (F2), and optionally phi (F0); real inverse transform via the
+// split step Z_m = (X_m + conj X_{M-m}) + i W^-m (X_m - conj X_{M-m}) and a
+// length-M inverse FFT; x_2n = Re z_n / (nx nz), x_2n+1 = Im z_n / (nx nz).
+template <class R, int M, int LPB>
+__global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E,
+                                                   double* __restrict__ phi, int ny, int nz, size_t fstride,
+                                                   const double* __restrict__ sinx, const cplx<R>* __restrict__ tw_g,
+                                                   int want_phi) {
+    constexpr int NX = 2 * M;
+    constexpr int NXH = M + 1;
+    constexpr int NF = 4;
+    constexpr int ST = padded<R, M>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* A = tw + NX;
+    cplx<R>* B = A + NF * LPB * ST;
+    R* sx = reinterpret_cast<R*>(B + NF * LPB * ST);
+    for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
+    for (int i = threadIdx.x; i < NXH; i += blockDim.x) sx[i] = from_f64<R>(sinx[i]);
+    __syncthreads();
+    const int nyn = ny + 2;
+    const int nlines = nz * nyn;
+    const int line0 = blockIdx.x * LPB;
+    const int nl = min(LPB, nlines - line0);
+    const int nf = want_phi ? 4 : 3;
+    for (int idx = threadIdx.x; idx < nf * nl * M; idx += blockDim.x) {
+        const int fl = idx / M;
+        const int m = idx - fl * M;
+        const int f = fl / nl;
+        const int l = fl - f * nl;
+        const int line = line0 + l;
+        const int jn = line % nyn;
+        const bool interior = jn >= 1 && jn <= ny;
+        const int src_field = (f == 3) ? 0 : f;
+        cplx<R> xm = {0, 0}, xc = {0, 0};
+        if (src_field == 1 || interior) {
+            const cplx<R>* row = F + src_field * fstride + (size_t)line * NXH;
+            xm = row[m];
+            xc = conj(row[M - m]);
+            if (f == 0) {   // E_x multiplier -i s_m, at m and (conjugated) at M-m
+                xm = cplx<R>{sx[m] * xm.im, -sx[m] * xm.re};
+                xc = cplx<R>{-sx[M - m] * xc.im, sx[M - m] * xc.re};
+            }
+        }
+        const cplx<R> sum = xm + xc, dif = xm - xc;
+        const cplx<R> t = conj(tw[m]) * dif;    // W^-m (X_m - conj X_{M-m})
+        A[fl * ST + pad<R>(m)] = cplx<R>{sum.re - t.im, sum.im + t.re};   // sum + i t
+    }
+    __syncthreads();
+    cplx<R>* z = fft::transform<R, 1, M>(A, B, nf * nl, tw, 2);
+    const R norm = (R)(1.0 / ((double)NX * (double)nz));
+    for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
+        const int l = idx / M;
+        const int n = idx - l * M;
+        const int np_ = pad<R>(n);
+        const cplx<R> ex = z[(0 * nl + l) * ST + np_];
+        const cplx<R> ey_ = z[(1 * nl + l) * ST + np_];
+        const cplx<R> ez = z[(2 * nl + l) * ST + np_];
+        vec4<R> v0, v1;
+        v0.x = ex.re * norm; v0.y = ey_.re * norm; v0.z = ez.re * norm; v0.w = (R)0;
+        v1.x = ex.im * norm; v1.y = ey_.im * norm; v1.z = ez.im * norm; v1.w = (R)0;
+        const size_t o = (size_t)(line0 + l) * NX + 2 * n;
+        E[o] = v0;
+        E[o + 1] = v1;
+        if (want_phi) {
+            const int line = line0 + l;
+            const int k = line / nyn;
+            const int jn = line - k * nyn;
+            if (jn >= 1 && jn <= ny) {
+                const cplx<R> p = z[(3 * nl + l) * ST + np_];
+                double* prow = phi + ((size_t)k * ny + (jn - 1)) * NX + 2 * n;
+                prow[0] = (double)(p.re * norm);
+                prow[1] = (double)(p.im * norm);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- dispatch
+template <class R, int M>
+constexpr int xfwd_lpb() {
+    constexpr int lines = (int)(2048 * 8 / sizeof(cplx<R>)) / M;
+    return lines > 8 ? 8 : (lines < 1 ? 1 : lines);
+}
+template <class R, int M>
+constexpr int xinv_lpb() {
+    constexpr int lines = (int)(512 * 8 / sizeof(cplx<R>)) / M;
+    return lines > 4 ? 4 : (lines < 1 ? 1 : lines);
+}
+template <class R, int M>
+size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + 2 * xfwd_lpb<R, M>() * padded<R, M>()) + sizeof(R) * 8; }
+template <class R, int M>
+size_t xinv_smem() { return sizeof(cplx<R>) * (2 * M + 2 * 4 * xinv_lpb<R, M>() * padded<R, M>()) + sizeof(R) * (M + 1); }
+template <class R, int NZ>
+size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + 2 * kZTile * padded<R, NZ>()); }
+template <class R, int NZ>
+size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + 6 * kZTileInv * padded<R, NZ>()) + sizeof(R) * NZ; }
+
+template <class R, int M>
+void launch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
+    constexpr int LPB = xfwd_lpb<R, M>();
+    const int nlines = c->ny * c->nz;
+    k_xfwd<R, M, LPB><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
+        src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx);
+}
+template <class R, int M>
+void launch_xinv(tribo_ctx* c, void* E, double* phi) {
+    constexpr int LPB = xinv_lpb<R, M>();
+    const int nlines = c->nz * (c->ny + 2);
+    const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
+    k_xinv<R, M, LPB><<<(nlines + LPB - 1) / LPB, kThreads, xinv_smem<R, M>(), c->stream>>>(
+        (const cplx<R>*)c->F, (vec4<R>*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
+        phi != nullptr ? 1 : 0);
+}
+template <class R, int NZ>
+void launch_zfwd(tribo_ctx* c) {
+    dim3 grid(c->ny, (c->nxh + kZTile - 1) / kZTile);
+    k_zfwd<R, NZ><<<grid, kThreads, zfwd_smem<R, NZ>(), c->stream>>>((cplx<R>*)c->S, c->ny, c->nxh,
+                                                                     (const cplx<R>*)c->d_twz);
+}
+template <class R, int NZ>
+void launch_zinv(tribo_ctx* c) {
+    dim3 grid(c->ny + 2, (c->nxh + kZTileInv - 1) / kZTileInv);
+    const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
+    k_zinv<R, NZ><<<grid, kThreads, zinv_smem<R, NZ>(), c->stream>>>(
+        (const cplx<R>*)c->S, (cplx<R>*)c->F, c->ny, c->nxh, fstride, c->d_sinz, (const cplx<R>*)c->d_twz);
+}
+template <class R, int NZ>
+tribo_status attr_z(int optin) {
+    if (zfwd_smem<R, NZ>() > (size_t)optin || zinv_smem<R, NZ>() > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
+    TRIBO_CUDA(cudaFuncSetAttribute(k_zfwd<R, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_zinv<R, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    return TRIBO_OK;
+}
+template <class R, int M>
+tribo_status attr_x(int optin) {
+    if (xfwd_smem<R, M>() > (size_t)optin || xinv_smem<R, M>() > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
+    TRIBO_CUDA(cudaFuncSetAttribute(k_xfwd<R, M, xfwd_lpb<R, M>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_xinv<R, M, xinv_lpb<R, M>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin));
+    return TRIBO_OK;
+}
+
+#define TRIBO_FAST_SIZES(X) X(2) X(3) X(4) X(6) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+bool fast_len(int n) {
+    switch (n) {
+#define CASE(N) case N:
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        return true;
+        default: return false;
+    }
+}
+
+template <class R>
+bool dispatch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
+    switch (c->nx / 2) {
+#define CASE(N) case N: launch_xfwd<R, N>(c, src, scale, zero); return true;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+template <class R>
+bool dispatch_xinv(tribo_ctx* c, void* E, double* phi) {
+    switch (c->nx / 2) {
+#define CASE(N) case N: launch_xinv<R, N>(c, E, phi); return true;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+template <class R>
+bool dispatch_zfwd(tribo_ctx* c) {
+    switch (c->nz) {
+#define CASE(N) case N: launch_zfwd<R, N>(c); return true;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+template <class R>
+bool dispatch_zinv(tribo_ctx* c) {
+    switch (c->nz) {
+#define CASE(N) case N: launch_zinv<R, N>(c); return true;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+template <class R>
+tribo_status dispatch_attr(int nx, int nz, int optin) {
+    tribo_status st = TRIBO_ERR_UNSUPPORTED;
+    switch (nz) {
+#define CASE(N) case N: st = attr_z<R, N>(optin); break;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: break;
+    }
+    if (st) return st;
+    switch (nx / 2) {
+#define CASE(N) case N: return attr_x<R, N>(optin);
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: return TRIBO_ERR_UNSUPPORTED;
+    }
+}
+
+template <class R>
+tribo_status twiddles(int n, void** dst) {
+    std::vector<cplx<R>> tw(n);
+    for (int e = 0; e < n; ++e) {
+        const double a = 2.0 * M_PI * (double)e / (double)n;
+        tw[e] = cplx<R>{(R)std::cos(a), (R)(-std::sin(a))};
+    }
+    TRIBO_CUDA(cudaMalloc(dst, sizeof(cplx<R>) * n));
+    TRIBO_CUDA(cudaMemcpy(*dst, tw.data(), sizeof(cplx<R>) * n, cudaMemcpyHostToDevice));
+    return TRIBO_OK;
+}
+
+void split_ds(double v, float* hi, float* lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+}
+
+template <class R>
+tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi, void* E) {
+    const int ny = c->ny, nz = c->nz, nxh = c->nxh;
+    phase_begin(c, PH_FWD_X);
+    dispatch_xfwd<R>(c, src, scale, zero_src);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_FWD_Z);
+    dispatch_zfwd<R>(c);
+    TRIBO_LAUNCHED(c);
+    const size_t fstride = (size_t)nz * (ny + 2) * nxh;
+    const int ni = (nz / 2 + 1) * nxh;
+    phase_begin(c, PH_SOLVE_Y);
+    if constexpr (sizeof(R) == 8) {
+        k_ysolve64<<<(ni + 127) / 128, 128, 0, c->stream>>>((cplx<double>*)c->S, (cplx<double>*)c->F + fstride,
+                                                            (const double2*)c->d_ytab, (double2*)c->W2,
+                                                            c->d_ycoef, c->d_ey, ny, nz, nxh);
+    } else {
+        const size_t sh = sizeof(float2) * ((ny + 1) & ~1) + sizeof(float4) * (ny + 1);
+        cplx<float>* Sf = (cplx<float>*)c->S;
+        cplx<float>* Fy = (cplx<float>*)c->F + fstride;
+        const float4* tab = (const float4*)c->d_ytab;
+        const float2* ads = (const float2*)c->d_yads;
+        const float4* ec = (const float4*)c->d_yec;
+        const int wblocks = (int)(((size_t)ni * 32 + 127) / 128);
+        if (ny <= 32) k_ysolve_warp<1><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else if (ny <= 64) k_ysolve_warp<2><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else if (ny <= 128) k_ysolve_warp<4><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else if (ny <= 256) k_ysolve_warp<8><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else
+            k_ysolve_ds<<<(ni + 127) / 128, 128, sh, c->stream>>>(Sf, Fy, tab, (float4*)c->W2, ads, ec, ny, nz, nxh);
+    }
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_INV_Z);
+    dispatch_zinv<R>(c);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_INV_X);
+    dispatch_xinv<R>(c, E, phi);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
+}  // namespace
+
+bool poisson_fast_supported(int nx, int nz) { return nx >= 4 && nx % 2 == 0 && fast_len(nx / 2) && fast_len(nz); }
+
+tribo_status poisson_fast_setup(tribo_ctx* c) {
+    const int nx = c->nx, ny = c->ny, nz = c->nz, nxh = c->nxh;
+    const int ni = (nz / 2 + 1) * nxh;
+    const std::vector<double>& yf = c->yf;
+    const std::vector<double>& yc = c->yc;
+    const std::vector<double>& dy = c->dy;
+    // factor table: per (|m_z|, m_x) and row j, (1/pivot_j, c'_j) of the
+    // shifted y operator, in FP64
+    std::vector<double> lamx(nxh), lamz(nz / 2 + 1);
+    for (int m = 0; m < nxh; ++m) {
+        const double s = std::sin(M_PI * m / nx);
+        lamx[m] = 4.0 / (c->dx * c->dx) * s * s;
+    }
+    for (int m = 0; m <= nz / 2; ++m) {
+        const double s = std::sin(M_PI * m / nz);
+        lamz[m] = 4.0 / (c->dz * c->dz) * s * s;
+    }
+    std::vector<double> a(ny, 0.0), b(ny), cc(ny, 0.0);
+    for (int j = 0; j < ny; ++j) {
+        if (j >= 1) a[j] = 1.0 / (dy[j] * (yc[j] - yc[j - 1]));
+        if (j <= ny - 2) cc[j] = 1.0 / (dy[j] * (yc[j + 1] - yc[j]));
+        b[j] = -(a[j] + cc[j]);
+    }
+    b[0] -= 1.0 / (dy[0] * (yc[0] - yf[0]));
+    b[ny - 1] -= 1.0 / (dy[ny - 1] * (yf[ny] - yc[ny - 1]));
+    const bool ds_mode = c->prec != TRIBO_FP64;
+    std::vector<double2> tab64;
+    std::vector<float4> tab32;
+    if (ds_mode) tab32.resize((size_t)ny * ni);
+    else tab64.resize((size_t)ny * ni);
+    for (int item = 0; item < ni; ++item) {
+        const double lam = lamz[item / nxh] + lamx[item % nxh];
+        double cp = 0.0;
+        for (int j = 0; j < ny; ++j) {
+            const double inv = 1.0 / ((b[j] - lam) - a[j] * cp);
+            cp = cc[j] * inv;
+            if (ds_mode) {
+                float4 t;
+                split_ds(inv, &t.x, &t.y);
+                split_ds(cp, &t.z, &t.w);
+                tab32[(size_t)j * ni + item] = t;
+            } else {
+                tab64[(size_t)j * ni + item] = make_double2(inv, cp);
+            }
+        }
+    }
+    const size_t tab_bytes = 16 * (size_t)ny * ni;
+    TRIBO_CUDA(cudaMalloc(&c->d_ytab, tab_bytes));
+    TRIBO_CUDA(cudaMemcpy(c->d_ytab, ds_mode ? (const void*)tab32.data() : (const void*)tab64.data(), tab_bytes,
+                          cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMalloc(&c->W2, 32 * (size_t)ny * ni));
+    if (ds_mode) {
+        // sub-diagonal in double-single, E_y coefficients per cell and walls
+        std::vector<float2> ads(ny);
+        for (int j = 0; j < ny; ++j) split_ds(a[j], &ads[j].x, &ads[j].y);
+        auto w = [&](int f) { return (yf[f] - yc[f - 1]) / (yc[f] - yc[f - 1]); };
+        std::vector<float4> ec(ny + 1, make_float4(0, 0, 0, 0));
+        for (int j = 0; j < ny; ++j) {
+            double A = 0, Bm = 0, Bp = 0;
+            if (j == 0) A -= 1.0 / dy[j];           // -phi_f[1] / dy_0 = -(phi_0 + w_1 d1) / dy_0
+            if (j == ny - 1) A += 1.0 / dy[j];      // +phi_f[ny-1] / dy = (phi_ny-1 - (1-w) d0) / dy
+            if (j >= 1) Bm = -(1.0 - w(j)) / dy[j];
+            if (j <= ny - 2) Bp = -w(j + 1) / dy[j];
+            ec[j] = make_float4((float)A, (float)Bm, (float)Bp, 0.f);
+        }
+        ec[ny] = make_float4((float)(-1.0 / (yc[0] - yf[0])), (float)(1.0 / (yf[ny] - yc[ny - 1])), 0.f, 0.f);
+        TRIBO_CUDA(cudaMalloc(&c->d_yads, sizeof(float2) * ny));
+        TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMalloc(&c->d_yec, sizeof(float4) * (ny + 1)));
+        TRIBO_CUDA(cudaMemcpy(c->d_yec, ec.data(), sizeof(float4) * (ny + 1), cudaMemcpyHostToDevice));
+    }
+    int dev = 0, optin = 0;
+    TRIBO_CUDA(cudaGetDevice(&dev));
+    TRIBO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    tribo_status st;
+    if (c->prec == TRIBO_FP64) {
+        if ((st = twiddles<double>(nx, &c->d_twx)) || (st = twiddles<double>(nz, &c->d_twz))) return st;
+        return dispatch_attr<double>(nx, nz, optin);
+    }
+    if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
+    return dispatch_attr<float>(nx, nz, optin);
+}
+
+void poisson_fast_free(tribo_ctx* c) {
+    cudaFree(c->d_ytab);
+    cudaFree(c->W2);
+    cudaFree(c->d_twx);
+    cudaFree(c->d_twz);
+    cudaFree(c->d_yads);
+    cudaFree(c->d_yec);
+    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = nullptr;
+}
+
+tribo_status poisson_fast_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+                                void* E) {
+    if (c->prec == TRIBO_FP64) return solve_fast<double>(c, src, scale, zero_src, phi, E);
+    return solve_fast<float>(c, src, scale, zero_src, phi, E);
+}
+
+}  // namespace tribo

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "tribo_internal.cuh"
 
@@ -109,9 +110,9 @@ struct Stage {
     static size_t bytes(int64_t n, size_t rs) { return (size_t)n * (7 * rs + 2 * sizeof(double) + 3 * sizeof(uint32_t)) + 1024; }
 };
 
-PView stage_view(tribo_ctx* c, int64_t n) {
+PView set_view(tribo_ctx* c, void* base, int64_t n) {
     const size_t rs = real_size(c);
-    char* b = (char*)c->stage;
+    char* b = (char*)base;
     const size_t cap = (size_t)c->max_particles;
     PView v{};
     v.n = n;
@@ -125,6 +126,27 @@ PView stage_view(tribo_ctx* c, int64_t n) {
     v.id = (uint32_t*)take(sizeof(uint32_t));
     v.cell = (uint32_t*)take(sizeof(uint32_t));
     return v;
+}
+
+PView stage_view(tribo_ctx* c, int64_t n) { return set_view(c, c->stage, n); }
+
+// copy every array of a particle set (device to device)
+tribo_status copy_view(tribo_ctx* c, const PView& dst, const PView& src) {
+    const size_t rs = real_size(c);
+    const size_t n = (size_t)src.n;
+    auto cp = [&](void* d, const void* s_, size_t elem) -> tribo_status {
+        if (!d || !s_) return TRIBO_OK;
+        TRIBO_CUDA(cudaMemcpyAsync(d, s_, elem * n, cudaMemcpyDeviceToDevice, c->stream));
+        return TRIBO_OK;
+    };
+    tribo_status st;
+    if ((st = cp(dst.x, src.x, rs)) || (st = cp(dst.y, src.y, rs)) || (st = cp(dst.z, src.z, rs)) ||
+        (st = cp(dst.vx, src.vx, rs)) || (st = cp(dst.vy, src.vy, rs)) || (st = cp(dst.vz, src.vz, rs)) ||
+        (st = cp(dst.d, src.d, rs)) || (st = cp(dst.q, src.q, sizeof(double))) ||
+        (st = cp(dst.q_wall, src.q_wall, sizeof(double))) || (st = cp(dst.n_imp, src.n_imp, sizeof(uint32_t))) ||
+        (st = cp(dst.id, src.id, sizeof(uint32_t))) || (st = cp(dst.cell, src.cell, sizeof(uint32_t))))
+        return st;
+    return TRIBO_OK;
 }
 
 tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particles* src, cudaMemcpyKind kind,
@@ -191,7 +213,8 @@ void free_ctx(tribo_ctx* c) {
     poisson_free(c);
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
-                    c->d_hist, c->d_scalar};
+                    c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
+                    c->sort_tiles};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -315,6 +338,12 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
     if (max_particles > 0) {
         c->stage_bytes = Stage::bytes(max_particles, rs) + 12 * 256;
         TRYC(cudaMalloc(&c->stage, c->stage_bytes));
+        TRYC(cudaMalloc(&c->alt, c->stage_bytes));
+        const size_t ncell = (size_t)nx * ny * nz;
+        TRYC(cudaMalloc(&c->sort_counts, sizeof(uint32_t) * ncell));
+        TRYC(cudaMalloc(&c->sort_key, sizeof(uint32_t) * max_particles));
+        TRYC(cudaMalloc(&c->sort_rank, sizeof(uint32_t) * max_particles));
+        TRYC(cudaMalloc(&c->sort_tiles, sizeof(uint32_t) * (ncell / 8192 + 2)));
     }
     TRY(poisson_setup(c));
     TRY(particles_setup(c));
@@ -369,16 +398,34 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     }
     const bool electro = c->P.electrostatics != 0;
     const bool want_cell = v.cell != nullptr;
+    const int S = c->P.sort_every;
+    if (S > 0 && p->n > c->max_particles) {
+        set_last_error("sorting needs max_particles >= n");
+        return TRIBO_ERR_CAPACITY;
+    }
+    // the sort writes the other particle set; the sets swap after each sort
+    // and the caller's arrays receive the data back at the end if needed
+    PView home = v, cur = v, other = S > 0 ? set_view(c, c->alt, p->n) : v;
+    if (!v.id) other.id = nullptr;
+    if (!v.cell) other.cell = nullptr;
     if (electro) {
         TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
-        if ((st = particles_deposit(c, v))) return st;
+        if ((st = particles_deposit(c, cur))) return st;
     }
     for (int s = 0; s < nsteps; ++s) {
         const bool last = s == nsteps - 1;
+        if (S > 0 && c->steps_done % S == 0) {
+            if ((st = particles_sort(c, cur, other))) return st;
+            std::swap(cur, other);
+        }
         if (electro) {
             if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
         }
-        if ((st = particles_step(c, v, dt, electro && !last, want_cell && last))) return st;
+        if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last))) return st;
+        c->steps_done++;
+    }
+    if (cur.x != home.x) {
+        if ((st = copy_view(c, home, cur))) return st;
     }
     c->n_samples += nsteps;
     if (p->on_host) {
@@ -390,6 +437,10 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
 
 tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E) {
     if (!c || !rho || !E) { set_last_error("ctx, rho and E must not be NULL"); return TRIBO_ERR_ARG; }
+    if (((uintptr_t)rho | (uintptr_t)phi) % 16 || (uintptr_t)E % (4 * real_size(c))) {
+        set_last_error("rho and phi must be 16-byte aligned, E aligned to one node (4 reals)");
+        return TRIBO_ERR_ARG;
+    }
     return poisson_solve(c, const_cast<double*>(rho), c->d_scale_rho, false, phi, E);
 }
 

@@ -25,8 +25,32 @@ template <class R> __host__ __device__ __forceinline__ cplx<R> conj(cplx<R> a) {
 // multiply by s*i (s = +-1)
 template <class R> __host__ __device__ __forceinline__ cplx<R> mul_si(cplx<R> a, R s) { return {-s * a.im, s * a.re}; }
 
+// FP64 -> FP32 with IEEE round-to-nearest-even, done on the integer pipes
+// (on this GPU an F2F conversion issues at the FP64 rate, 1/64 of FP32).
+// Written from the binary64/binary32 formats: rebias the exponent, keep the
+// top 23 mantissa bits and round on the 29 dropped bits.  Results below the
+// FP32 normal range flush to a signed zero; Inf and NaN are preserved.
+__device__ __forceinline__ float f64_to_f32(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int ef = (int)((hi >> 20) & 0x7ffu);
+    if (ef == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u));
+    const int e = ef - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rest = lo & 0x1fffffffu;
+    const unsigned up = (rest > 0x10000000u) || (rest == 0x10000000u && (m & 1u));
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    return __uint_as_float(sign | ((((unsigned)e << 23) | m) + up));
+}
+
+template <class R> __device__ __forceinline__ R from_f64(double d) { return (R)d; }
+template <> __device__ __forceinline__ float from_f64<float>(double d) { return f64_to_f32(d); }
+
 template <class R> struct vec4 { R x, y, z, w; };
-template <> struct vec4<float> { float x, y, z, w; };
+template <> struct __align__(16) vec4<float> { float x, y, z, w; };
+template <> struct __align__(32) vec4<double> { double x, y, z, w; };
 
 // ------------------------------------------------------------------ FFT plan
 // Mixed-radix (4, 2, 3) Stockham plan for one transform length.
@@ -85,12 +109,26 @@ struct tribo_ctx {
     double* Q = nullptr;         // (nz, ny, nx) cell charge sums
     void* S = nullptr;           // (nz, ny, nxh) cplx<real> spectrum
     void* F = nullptr;           // (4, nz, ny+2, nxh) cplx<real> field spectra
-    void* W = nullptr;           // (ny, nz*nxh) cplx<double> Thomas scratch
+    void* W = nullptr;           // (ny, nz*nxh) cplx<double> Thomas scratch (generic path)
     tribo::FftPlan plan_x, plan_z;
+    // compile-time-length path (poisson_fast.cu)
+    bool fast = false;
+    void* d_ytab = nullptr;      // (ny, (nz/2+1)*nxh) double2: 1/pivot, c' per wavenumber pair
+    void* W2 = nullptr;          // (ny, (nz/2+1)*nxh, 2) double2 Thomas scratch
+    void* d_twx = nullptr;       // nx twiddles exp(-2 pi i e / nx), real precision
+    void* d_twz = nullptr;       // nz twiddles
+    void* d_yads = nullptr;      // ny float2: y sub-diagonal in double-single (mixed mode)
+    void* d_yec = nullptr;       // ny+1 float4: E_y coefficients per cell, walls (mixed mode)
 
     // particle staging (host-pointer calls) and sort scratch
-    void* stage = nullptr;
+    void* stage = nullptr;       // device copy of host-pointer ensembles
+    void* alt = nullptr;         // second particle set: the sort writes here, then the sets swap
     size_t stage_bytes = 0;
+    uint32_t* sort_counts = nullptr;   // ncells: counts, then offsets
+    uint32_t* sort_key = nullptr;      // max_particles
+    uint32_t* sort_rank = nullptr;     // max_particles
+    uint32_t* sort_tiles = nullptr;    // scan tile sums
+    int64_t steps_done = 0;            // steps taken by this context (sort schedule)
 
     // statistics
     tribo::Accum* d_acc = nullptr;
@@ -142,6 +180,13 @@ tribo_status poisson_free(tribo_ctx* c);
 tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src,
                            double* phi, void* E);
 
+// compile-time-length Poisson path (poisson_fast.cu)
+bool poisson_fast_supported(int nx, int nz);
+tribo_status poisson_fast_setup(tribo_ctx* c);
+void poisson_fast_free(tribo_ctx* c);
+tribo_status poisson_fast_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+                                void* E);
+
 // particles (particles.cu)
 struct PView {               // device views of one particle ensemble
     int64_t n;
@@ -156,6 +201,8 @@ tribo_status particles_deposit(tribo_ctx* c, const PView& p);
 tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next,
                             bool write_cell);
 tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out);
+// dst receives src sorted by cell key (all arrays; id if present)
+tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst);
 tribo_status particles_setup(tribo_ctx* c);
 tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev);
 

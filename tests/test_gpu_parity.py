@@ -78,7 +78,10 @@ def check_cells(g, got, ref, tol):
 # ---------------------------------------------------------------- Poisson
 
 @pytest.mark.parametrize("prec", [T.TRIBO_FP64, T.TRIBO_MIXED])
-@pytest.mark.parametrize("shape", [(12, 10, 18), (64, 64, 64), (48, 33, 36), (6, 2, 4)])
+@pytest.mark.parametrize("shape", [
+    (12, 10, 18), (48, 33, 36),                 # generic path (nz not a compiled length)
+    (64, 64, 64), (6, 2, 4), (16, 8, 12), (96, 24, 48), (384, 20, 256), (128, 37, 96), (8, 5, 512),
+])
 def test_poisson_matches_oracle(prec, shape):
     nx, ny, nz = shape
     c, faces, lat, _ = problem(nx, ny, nz, n=0)
@@ -105,15 +108,17 @@ def test_poisson_matches_oracle(prec, shape):
 
 # ---------------------------------------------------------------- coupled steps
 
+@pytest.mark.parametrize("sort_every", [0, 4, 5])
 @pytest.mark.parametrize("prec", [T.TRIBO_FP64, T.TRIBO_MIXED])
-def test_ten_steps_match_oracle(prec):
+def test_ten_steps_match_oracle(prec, sort_every):
     """Re_tau = 180, 64^3, 2,000 particles: charged, near-wall particles
-    impacting, Stokes drag, mesh electrostatics every step."""
+    impacting, Stokes drag, mesh electrostatics every step; particles
+    re-sorted by cell every 4 (three sorts) or 5 (two sorts) steps."""
     c, faces, lat, parts = problem(64, 64, 64, n=2000, q_scale=1e-12, vy_scale=0.3, near_wall=0.05)
     real = _real(prec)
     lat_r, parts_r = round_inputs(lat, parts, real)
     tol = TOL_FP64 if prec == T.TRIBO_FP64 else TOL_MIXED
-    got, st = run_gpu(c, faces, lat_r, parts_r, prec, 10, U_c=1e3)
+    got, st = run_gpu(c, faces, lat_r, parts_r, prec, 10, U_c=1e3, sort_every=sort_every)
     hist = np.zeros(c.ny)
     g, ref = run_oracle(c, faces, lat_r, parts_r, 10, hist=hist, U_c=1e3)
     assert ref.n_imp.sum() >= 50
@@ -166,8 +171,8 @@ def test_schiller_naumann_high_reynolds_branch():
 def test_host_pointer_call_matches_device_call():
     c, faces, lat, parts = problem(32, 24, 16, n=1500, q_scale=1e-12, vy_scale=0.3, near_wall=0.05, seed=9)
     lat_r, parts_r = round_inputs(lat, parts, np.float32)
-    a, sa = run_gpu(c, faces, lat_r, parts_r, T.TRIBO_MIXED, 5, U_c=1e3)
-    b, sb = run_gpu(c, faces, lat_r, parts_r, T.TRIBO_MIXED, 5, U_c=1e3, host=True)
+    a, sa = run_gpu(c, faces, lat_r, parts_r, T.TRIBO_MIXED, 5, U_c=1e3, sort_every=2)
+    b, sb = run_gpu(c, faces, lat_r, parts_r, T.TRIBO_MIXED, 5, U_c=1e3, host=True, sort_every=2)
     for k in ("x", "y", "z", "vx", "vy", "vz"):
         assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-9), k
     assert np.array_equal(a["n_imp"], b["n_imp"])
@@ -178,7 +183,7 @@ def test_host_pointer_call_matches_device_call():
 @pytest.mark.parametrize("n", [0, 1, 33, 257])
 def test_small_and_ragged_ensembles(n):
     c, faces, lat, parts = problem(12, 8, 6, n=n, q_scale=1e-12, vy_scale=0.3, near_wall=0.3, seed=n + 1)
-    got, st = run_gpu(c, faces, lat, parts, T.TRIBO_FP64, 4, U_c=10.0)
+    got, st = run_gpu(c, faces, lat, parts, T.TRIBO_FP64, 4, U_c=10.0, sort_every=1)
     g, ref = run_oracle(c, faces, lat, parts, 4, U_c=10.0)
     if n:
         compare_states(g, got, ref, TOL_FP64, label=f"n={n}")
