@@ -140,5 +140,73 @@ __device__ __forceinline__ cplx<R>* transform(cplx<R>* A, cplx<R>* B, int nl, co
     return Stockham<R, SIGN, N, 1, STRIDE>::run(A, B, nl, tw, tw_step);
 }
 
+
+// In-place variant: each pass first loads all of this thread's butterflies
+// into registers (with twiddles), synchronises, then writes the outputs
+// over the same buffer.  MAXL bounds the number of lines (compile time) so
+// that the per-thread butterfly count is static; the block has NT threads.
+template <class R, int SIGN, int N, int RAD, int LS, int STRIDE, int MAXL, int NT>
+__device__ __forceinline__ void pass_inplace(cplx<R>* __restrict__ A, int nl, const cplx<R>* __restrict__ tw,
+                                             int tw_step) {
+    constexpr int B = N / RAD;
+    constexpr int TWM = N / (RAD * LS);
+    constexpr int PER = (MAXL * B + NT - 1) / NT;
+    const int total = nl * B;
+    cplx<R> y[PER][RAD];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (idx < total) {
+            const int line = idx / B;
+            const int j = idx - line * B;
+            const int k = j % LS;
+            const cplx<R>* src = A + line * STRIDE;
+#pragma unroll
+            for (int t = 0; t < RAD; ++t) y[p][t] = src[pad<R>(j + t * B)];
+            if constexpr (LS > 1) {
+#pragma unroll
+                for (int t = 1; t < RAD; ++t) {
+                    cplx<R> w = tw[(t * k * TWM) * tw_step];
+                    if constexpr (SIGN > 0) w = conj(w);
+                    y[p][t] = y[p][t] * w;
+                }
+            }
+            dft<R, SIGN, RAD>(y[p]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int idx = threadIdx.x + p * NT;
+        if (idx < total) {
+            const int line = idx / B;
+            const int j = idx - line * B;
+            const int k = j % LS;
+            cplx<R>* dst = A + line * STRIDE;
+            const int o = (j - k) * RAD + k;
+#pragma unroll
+            for (int u = 0; u < RAD; ++u) dst[pad<R>(o + u * LS)] = y[p][u];
+        }
+    }
+    __syncthreads();
+}
+
+template <class R, int SIGN, int N, int LS, int STRIDE, int MAXL, int NT>
+struct StockhamInplace {
+    static __device__ __forceinline__ void run(cplx<R>* A, int nl, const cplx<R>* tw, int tw_step) {
+        if constexpr (LS < N) {
+            constexpr int RAD = pick_radix<N / LS>::value;
+            pass_inplace<R, SIGN, N, RAD, LS, STRIDE, MAXL, NT>(A, nl, tw, tw_step);
+            StockhamInplace<R, SIGN, N, LS * RAD, STRIDE, MAXL, NT>::run(A, nl, tw, tw_step);
+        }
+    }
+};
+
+// in-place transform of up to MAXL lines held in A (result in A)
+template <class R, int SIGN, int N, int MAXL, int NT, int STRIDE = padded<R, N>()>
+__device__ __forceinline__ void transform_inplace(cplx<R>* A, int nl, const cplx<R>* tw, int tw_step) {
+    StockhamInplace<R, SIGN, N, 1, STRIDE, MAXL, NT>::run(A, nl, tw, tw_step);
+}
+
 }  // namespace fft
 }  // namespace tribo

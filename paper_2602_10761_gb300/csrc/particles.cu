@@ -82,15 +82,15 @@ template <> __device__ __forceinline__ double rpow23<double>(double v) { return 
 template <class R> __device__ __forceinline__ bool rfinite(R v) { return isfinite(v); }
 
 // largest i in [0, n-1] with s >= face_i, faces i*h (FP64) -------------------
-__device__ __forceinline__ int cell_uniform(double s, double h, int n, const float*) {
+__device__ __forceinline__ int cell_uniform(double s, double h, int n, const float*, double) {
     int i = (int)floor(s / h);
     i = min(max(i, 0), n - 1);
     while (i > 0 && s < (double)i * h) --i;
     while (i < n - 1 && s >= (double)(i + 1) * h) ++i;
     return i;
 }
-__device__ __forceinline__ int cell_uniform(float s, double h, int n, const float* f_up) {
-    int i = (int)floorf(s * (float)(1.0 / h));
+__device__ __forceinline__ int cell_uniform(float s, float inv_h, int n, const float* f_up) {
+    int i = (int)floorf(s * inv_h);
     i = min(max(i, 0), n - 1);
     while (i > 0 && s < f_up[i]) --i;
     while (i < n - 1 && s >= f_up[i + 1]) ++i;
@@ -115,8 +115,14 @@ __device__ __forceinline__ int cell_y(R y, const StepArgs<R>& a) {
 
 template <class R>
 __device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a, int* jout) {
-    const int i = cell_uniform(x, a.dx, a.nx, a.xf_up);
-    const int k = cell_uniform(z, a.dz, a.nz, a.zf_up);
+    int i, k;
+    if constexpr (sizeof(R) == 8) {
+        i = cell_uniform((double)x, a.dx, a.nx, a.xf_up, 0.0);
+        k = cell_uniform((double)z, a.dz, a.nz, a.zf_up, 0.0);
+    } else {
+        i = cell_uniform((float)x, (float)a.inv_dx, a.nx, a.xf_up);
+        k = cell_uniform((float)z, (float)a.inv_dz, a.nz, a.zf_up);
+    }
     const int j = cell_y(y, a);
     *jout = j;
     return ((uint32_t)k * (uint32_t)a.ny + (uint32_t)j) * (uint32_t)a.nx + (uint32_t)i;
@@ -212,7 +218,7 @@ __device__ __forceinline__ double impact_charge(const StepArgs<R>& a, double d, 
 }
 
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_step(StepArgs<R> a, PView p, int write_cell) {
+__global__ void __launch_bounds__(kThreads, 4) k_step(StepArgs<R> a, PView p, int write_cell) {
     extern __shared__ unsigned int sh_hist[];
     const bool use_hist = a.hist != nullptr;
     if (use_hist) {

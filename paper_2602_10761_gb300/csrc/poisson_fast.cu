@@ -85,8 +85,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(double* __restrict__ src, con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
     cplx<R>* A = tw + NX;
-    cplx<R>* B = A + LPB * ST;
-    R* sc = reinterpret_cast<R*>(B + LPB * ST);
+    R* sc = reinterpret_cast<R*>(A + LPB * ST);
     const int line0 = blockIdx.x * LPB;
     const int nl = min(LPB, nlines - line0);
     for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
@@ -121,7 +120,8 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(double* __restrict__ src, con
         }
     }
     __syncthreads();
-    cplx<R>* Z = fft::transform<R, -1, M>(A, B, nl, tw, 2);
+    fft::transform_inplace<R, -1, M, LPB, kThreads>(A, nl, tw, 2);
+    const cplx<R>* Z = A;
     for (int idx = threadIdx.x; idx < nl * NXH; idx += blockDim.x) {
         const int l = idx / NXH;
         const int m = idx - l * NXH;
@@ -143,22 +143,33 @@ __global__ void __launch_bounds__(kThreads) k_zfwd(cplx<R>* __restrict__ S, int 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
     cplx<R>* A = tw + NZ;
-    cplx<R>* B = A + kZTile * ST;
     for (int i = threadIdx.x; i < NZ; i += blockDim.x) tw[i] = tw_g[i];
     const int j = blockIdx.x;
     const int mx0 = blockIdx.y * kZTile;
     const int nt = min(kZTile, nxh - mx0);
-    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
-        const int k = idx / nt;
-        const int t = idx - k * nt;
-        A[t * ST + pad<R>(k)] = S[((size_t)k * ny + j) * nxh + mx0 + t];
+    // loads first (all in flight together), then the transposed smem stores
+    constexpr int PER = (NZ * kZTile + kThreads - 1) / kThreads;
+    cplx<R> v[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        const int k = idx / kZTile;
+        const int t = idx - k * kZTile;
+        if (idx < NZ * kZTile && t < nt) v[r] = S[((size_t)k * ny + j) * nxh + mx0 + t];
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        const int k = idx / kZTile;
+        const int t = idx - k * kZTile;
+        if (idx < NZ * kZTile && t < nt) A[t * ST + pad<R>(k)] = v[r];
     }
     __syncthreads();
-    cplx<R>* res = fft::transform<R, -1, NZ>(A, B, nt, tw, 1);
-    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
-        const int k = idx / nt;
-        const int t = idx - k * nt;
-        S[((size_t)k * ny + j) * nxh + mx0 + t] = res[t * ST + pad<R>(k)];
+    fft::transform_inplace<R, -1, NZ, kZTile, kThreads>(A, nt, tw, 1);
+    for (int idx = threadIdx.x; idx < NZ * kZTile; idx += blockDim.x) {
+        const int k = idx / kZTile;
+        const int t = idx - k * kZTile;
+        if (t < nt) S[((size_t)k * ny + j) * nxh + mx0 + t] = A[t * ST + pad<R>(k)];
     }
 }
 
@@ -332,31 +343,40 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
                                                      const float4* __restrict__ tab,
                                                      const float2* __restrict__ a_ds,
                                                      const float4* __restrict__ ec, int ny, int nz, int nxh) {
+    // coefficients of row j at [(j % RL) * 32 + j / RL]: the lanes of a warp
+    // read rows lane*RL + i, i.e. 32 consecutive slots (no bank conflicts)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sa = reinterpret_cast<float2*>(smem_raw);
-    float4* se = reinterpret_cast<float4*>(sa + ((ny + 1) & ~1));
-    for (int j = threadIdx.x; j < ny; j += blockDim.x) sa[j] = a_ds[j];
-    for (int j = threadIdx.x; j <= ny; j += blockDim.x) se[j] = ec[j];
+    float4* se = reinterpret_cast<float4*>(smem_raw);          // 32*RL
+    float2* sa = reinterpret_cast<float2*>(se + 32 * RL);      // 32*RL
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+        const int sl = (j % RL) * 32 + j / RL;
+        sa[sl] = a_ds[j];
+        se[sl] = ec[j];
+    }
     __syncthreads();
+    const float4 walls = ec[ny];
     const int ni = (nz / 2 + 1) * nxh;
-    const int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (item >= ni) return;          // whole warps leave together
+    const int pencil = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pencil >= nz * nxh) return;  // whole warps leave together
     const int lane = threadIdx.x & 31;
-    const int mzp = item / nxh;
-    const int mx = item - mzp * nxh;
-    const int np = (mzp != 0 && 2 * mzp != nz) ? 2 : 1;
+    const int mz0 = pencil / nxh;
+    const int mx = pencil - mz0 * nxh;
+    const int mzp = min(mz0, nz - mz0);                 // table row of |m_z|
+    const int item = mzp * nxh + mx;
+    constexpr int NP = 1;                               // pencils per warp
+    const int np = 1;
     const int j0 = lane * RL;
     const int nv = max(0, min(RL, ny - j0));           // valid rows of this lane
-    const size_t row0[2] = {(size_t)mzp * ny * nxh + mx, (size_t)(nz - mzp) * ny * nxh + mx};
+    const size_t row0[1] = {(size_t)mz0 * ny * nxh + mx};
 
     float4 t[RL];
-    ds yr[2][RL], yi[2][RL], P[RL];
+    ds yr[NP][RL], yi[NP][RL], P[RL];
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
         if (i < nv) {
             t[i] = tab[(size_t)(j0 + i) * ni + item];
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 const cplx<float> r = (s < np) ? S[row0[s] + (size_t)(j0 + i) * nxh] : cplx<float>{0.f, 0.f};
                 yr[s][i] = {r.re, 0.f};
                 yi[s][i] = {r.im, 0.f};
@@ -365,15 +385,18 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     }
     // forward, zero carry; P_i = prod (-a/pivot)
     ds prun = {1.f, 0.f};
-    ds pr[2] = {{0.f, 0.f}, {0.f, 0.f}}, pim[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    ds pr[NP], pim[NP];
+#pragma unroll
+    for (int s = 0; s < NP; ++s) pr[s] = pim[s] = ds{0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
         if (i < nv) {
             const ds inv = {t[i].x, t[i].y};
-            const ds aj = {sa[j0 + i].x, sa[j0 + i].y};
+            const float2 av = sa[i * 32 + lane];
+            const ds aj = {av.x, av.y};
             const ds at = ds_mul(aj, inv);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 pr[s] = ds_add(ds_mul(yr[s][i], inv), ds_neg(ds_mul(at, pr[s])));
                 pim[s] = ds_add(ds_mul(yi[s][i], inv), ds_neg(ds_mul(at, pim[s])));
                 yr[s][i] = pr[s];
@@ -385,29 +408,33 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     }
     // prefix combination of the lanes' maps c -> yh_last + P_last c
     ds beta = nv > 0 ? prun : ds{1.f, 0.f};
-    ds al[2][2] = {{pr[0], pim[0]}, {pr[1], pim[1]}};   // [pencil][re/im]
-    if (nv == 0) { al[0][0] = al[0][1] = al[1][0] = al[1][1] = ds{0.f, 0.f}; }
+    ds al[NP][2];   // [pencil][re/im]
+#pragma unroll
+    for (int s = 0; s < NP; ++s) {
+        al[s][0] = nv > 0 ? pr[s] : ds{0.f, 0.f};
+        al[s][1] = nv > 0 ? pim[s] : ds{0.f, 0.f};
+    }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const ds b2 = shfl_up_ds(beta, d);
-        ds a2[2][2];
+        ds a2[NP][2];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < NP; ++s) {
             a2[s][0] = shfl_up_ds(al[s][0], d);
             a2[s][1] = shfl_up_ds(al[s][1], d);
         }
         if (lane >= d) {
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 al[s][0] = ds_fma(beta, a2[s][0], al[s][0]);
                 al[s][1] = ds_fma(beta, a2[s][1], al[s][1]);
             }
             beta = ds_mul(beta, b2);
         }
     }
-    ds cr[2], ci[2];
+    ds cr[NP], ci[NP];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NP; ++s) {
         cr[s] = shfl_up_ds(al[s][0], 1);
         ci[s] = shfl_up_ds(al[s][1], 1);
         if (lane == 0) { cr[s] = ds{0.f, 0.f}; ci[s] = ds{0.f, 0.f}; }
@@ -416,7 +443,7 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     for (int i = 0; i < RL; ++i) {
         if (i < nv) {
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 yr[s][i] = ds_fma(P[i], cr[s], yr[s][i]);
                 yi[s][i] = ds_fma(P[i], ci[s], yi[s][i]);
             }
@@ -424,13 +451,15 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     }
     // backward, zero carry from above; Q_i = prod over rows i..last of (-c')
     ds qrun = {1.f, 0.f};
-    ds xr[2] = {{0.f, 0.f}, {0.f, 0.f}}, xi[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    ds xr[NP], xi[NP];
+#pragma unroll
+    for (int s = 0; s < NP; ++s) xr[s] = xi[s] = ds{0.f, 0.f};
 #pragma unroll
     for (int i = RL - 1; i >= 0; --i) {
         if (i < nv) {
             const ds cp = {t[i].z, t[i].w};
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 xr[s] = ds_add(yr[s][i], ds_neg(ds_mul(cp, xr[s])));
                 xi[s] = ds_add(yi[s][i], ds_neg(ds_mul(cp, xi[s])));
                 yr[s][i] = xr[s];
@@ -443,31 +472,31 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     // suffix combination of the lanes' maps d -> xh_first + Q_first d
     beta = nv > 0 ? qrun : ds{1.f, 0.f};
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NP; ++s) {
         al[s][0] = nv > 0 ? xr[s] : ds{0.f, 0.f};
         al[s][1] = nv > 0 ? xi[s] : ds{0.f, 0.f};
     }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const ds b2 = shfl_down_ds(beta, d);
-        ds a2[2][2];
+        ds a2[NP][2];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < NP; ++s) {
             a2[s][0] = shfl_down_ds(al[s][0], d);
             a2[s][1] = shfl_down_ds(al[s][1], d);
         }
         if (lane + d < 32) {
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 al[s][0] = ds_fma(beta, a2[s][0], al[s][0]);
                 al[s][1] = ds_fma(beta, a2[s][1], al[s][1]);
             }
             beta = ds_mul(beta, b2);
         }
     }
-    ds dr[2], di[2];   // x of the first row of the next lane
+    ds dr[NP], di[NP];   // x of the first row of the next lane
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NP; ++s) {
         dr[s] = shfl_down_ds(al[s][0], 1);
         di[s] = shfl_down_ds(al[s][1], 1);
         if (lane == 31) { dr[s] = ds{0.f, 0.f}; di[s] = ds{0.f, 0.f}; }
@@ -476,7 +505,7 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     for (int i = 0; i < RL; ++i) {
         if (i < nv) {
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < NP; ++s) {
                 yr[s][i] = ds_fma(P[i], dr[s], yr[s][i]);
                 yi[s][i] = ds_fma(P[i], di[s], yi[s][i]);
             }
@@ -484,9 +513,8 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
     }
     // x of the previous lane's last row, for the E_y differences
     const int nyn = ny + 2;
-    const float4 walls = se[ny];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NP; ++s) {
         // x of this lane's last valid row (selects, no indexing by nv)
         ds lr = yr[s][RL - 1], li = yi[s][RL - 1];
 #pragma unroll
@@ -499,7 +527,7 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
         }
         const ds br = shfl_up_ds(lr, 1), bi = shfl_up_ds(li, 1);
         if (s < np) {
-        const size_t mz = s == 0 ? (size_t)mzp : (size_t)(nz - mzp);
+        const size_t mz = (size_t)mz0;
         cplx<float>* srow = S + mz * ny * nxh + mx;
         cplx<float>* frow = Fy + mz * nyn * nxh + mx;
         ds prv_r = br, prv_i = bi;     // x[j-1]
@@ -517,7 +545,7 @@ __global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S
                 }
                 const float fr = ds_f(cur_r), fi = ds_f(cur_i);
                 srow[(size_t)j * nxh] = cplx<float>{fr, fi};
-                const float4 c = se[j];
+                const float4 c = se[i * 32 + lane];
                 const float d0r = ds_f(ds_add(cur_r, ds_neg(prv_r))), d0i = ds_f(ds_add(cur_i, ds_neg(prv_i)));
                 const float d1r = ds_f(ds_add(nxt_r, ds_neg(cur_r))), d1i = ds_f(ds_add(nxt_i, ds_neg(cur_i)));
                 frow[(size_t)(j + 1) * nxh] = cplx<float>{c.x * fr + c.y * d0r + c.z * d1r,
@@ -543,9 +571,8 @@ __global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ S
     constexpr int ST = padded<R, NZ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* A = tw + NZ;        // 3 tiles: phi, E_z, E_y
-    cplx<R>* B = A + 3 * kZTileInv * ST;
-    R* sz = reinterpret_cast<R*>(B + 3 * kZTileInv * ST);
+    cplx<R>* A = tw + NZ;        // 3 tiles: E_y, phi, E_z
+    R* sz = reinterpret_cast<R*>(A + 3 * kZTileInv * ST);
     for (int i = threadIdx.x; i < NZ; i += blockDim.x) {
         tw[i] = tw_g[i];
         sz[i] = from_f64<R>(sinz[i]);
@@ -558,22 +585,40 @@ __global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ S
     const int nlines = interior ? 3 * kZTileInv : kZTileInv;   // E_y tile first when alone
     __syncthreads();
     cplx<R>* Fy = F + fstride;
-    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
-        const int k = idx / nt;
-        const int t = idx - k * nt;
-        const int kp = pad<R>(k);
-        A[t * ST + kp] = Fy[((size_t)k * nyn + jn) * nxh + mx0 + t];
-        if (interior) {
-            const cplx<R> ph = S[((size_t)k * ny + (jn - 1)) * nxh + mx0 + t];
-            A[(kZTileInv + t) * ST + kp] = ph;
-            A[(2 * kZTileInv + t) * ST + kp] = cplx<R>{sz[k] * ph.im, -sz[k] * ph.re};   // -i s phi
+    constexpr int PER = (NZ * kZTileInv + kThreads - 1) / kThreads;
+    cplx<R> vy[PER], vp[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        const int k = idx / kZTileInv;
+        const int t = idx - k * kZTileInv;
+        if (idx < NZ * kZTileInv && t < nt) {
+            vy[r] = Fy[((size_t)k * nyn + jn) * nxh + mx0 + t];
+            if (interior) vp[r] = S[((size_t)k * ny + (jn - 1)) * nxh + mx0 + t];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        const int k = idx / kZTileInv;
+        const int t = idx - k * kZTileInv;
+        if (idx < NZ * kZTileInv && t < nt) {
+            const int kp = pad<R>(k);
+            A[t * ST + kp] = vy[r];
+            if (interior) {
+                const cplx<R> ph = vp[r];
+                A[(kZTileInv + t) * ST + kp] = ph;
+                A[(2 * kZTileInv + t) * ST + kp] = cplx<R>{sz[k] * ph.im, -sz[k] * ph.re};   // -i s phi
+            }
         }
     }
     __syncthreads();
-    cplx<R>* res = fft::transform<R, 1, NZ>(A, B, nlines, tw, 1);
-    for (int idx = threadIdx.x; idx < NZ * nt; idx += blockDim.x) {
-        const int k = idx / nt;
-        const int t = idx - k * nt;
+    fft::transform_inplace<R, 1, NZ, 3 * kZTileInv, kThreads>(A, nlines, tw, 1);
+    const cplx<R>* res = A;
+    for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += blockDim.x) {
+        const int k = idx / kZTileInv;
+        const int t = idx - k * kZTileInv;
+        if (t >= nt) continue;
         const int kp = pad<R>(k);
         const size_t o = ((size_t)k * nyn + jn) * nxh + mx0 + t;
         Fy[o] = res[t * ST + kp];
@@ -593,57 +638,85 @@ template <class R, int M, int LPB>
 __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E,
                                                    double* __restrict__ phi, int ny, int nz, size_t fstride,
                                                    const double* __restrict__ sinx, const cplx<R>* __restrict__ tw_g,
-                                                   int want_phi) {
+                                                   int want_phi, R norm) {
     constexpr int NX = 2 * M;
     constexpr int NXH = M + 1;
     constexpr int NF = 4;
+    constexpr int H = M / 2 + 1;          // pairs (m, M-m), m = 0..M/2
     constexpr int ST = padded<R, M>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* A = tw + NX;
-    cplx<R>* B = A + NF * LPB * ST;
-    R* sx = reinterpret_cast<R*>(B + NF * LPB * ST);
-    for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
-    for (int i = threadIdx.x; i < NXH; i += blockDim.x) sx[i] = from_f64<R>(sinx[i]);
-    __syncthreads();
+    cplx<R>* A = tw + NX;                 // line f*LPB + l holds field f of line l
+    R* sx = reinterpret_cast<R*>(A + NF * LPB * ST);
+    int* sjn = reinterpret_cast<int*>(sx + NXH);   // node plane of each line, -1 past the end
     const int nyn = ny + 2;
     const int nlines = nz * nyn;
     const int line0 = blockIdx.x * LPB;
     const int nl = min(LPB, nlines - line0);
     const int nf = want_phi ? 4 : 3;
-    for (int idx = threadIdx.x; idx < nf * nl * M; idx += blockDim.x) {
-        const int fl = idx / M;
-        const int m = idx - fl * M;
-        const int f = fl / nl;
-        const int l = fl - f * nl;
-        const int line = line0 + l;
-        const int jn = line % nyn;
-        const bool interior = jn >= 1 && jn <= ny;
+    for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
+    for (int i = threadIdx.x; i < NXH; i += blockDim.x) sx[i] = from_f64<R>(sinx[i]);
+    if (threadIdx.x < LPB) sjn[threadIdx.x] = threadIdx.x < nl ? (line0 + threadIdx.x) % nyn : -1;
+    __syncthreads();
+    // split step: one thread per pair (m, M-m) produces Z_m and Z_M-m from X_m, X_M-m
+    constexpr int PER = (NF * LPB * H + kThreads - 1) / kThreads;
+    cplx<R> va[PER], vb[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {     // loads first
+        const int idx = threadIdx.x + r * kThreads;
+        va[r] = vb[r] = cplx<R>{0, 0};
+        if (idx >= nf * LPB * H) continue;
+        const int fl = idx / H;
+        const int m = idx - fl * H;
+        const int f = fl / LPB;
+        const int l = fl - f * LPB;
+        const int jn = sjn[l];
         const int src_field = (f == 3) ? 0 : f;
-        cplx<R> xm = {0, 0}, xc = {0, 0};
-        if (src_field == 1 || interior) {
-            const cplx<R>* row = F + src_field * fstride + (size_t)line * NXH;
-            xm = row[m];
-            xc = conj(row[M - m]);
-            if (f == 0) {   // E_x multiplier -i s_m, at m and (conjugated) at M-m
-                xm = cplx<R>{sx[m] * xm.im, -sx[m] * xm.re};
-                xc = cplx<R>{-sx[M - m] * xc.im, sx[M - m] * xc.re};
-            }
+        if (jn >= 0 && (src_field == 1 || (jn >= 1 && jn <= ny))) {
+            const cplx<R>* row = F + src_field * fstride + (size_t)(line0 + l) * NXH;
+            va[r] = row[m];
+            vb[r] = row[M - m];
         }
-        const cplx<R> sum = xm + xc, dif = xm - xc;
-        const cplx<R> t = conj(tw[m]) * dif;    // W^-m (X_m - conj X_{M-m})
-        A[fl * ST + pad<R>(m)] = cplx<R>{sum.re - t.im, sum.im + t.re};   // sum + i t
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int idx = threadIdx.x + r * kThreads;
+        if (idx >= nf * LPB * H) continue;
+        const int fl = idx / H;
+        const int m = idx - fl * H;
+        const int f = fl / LPB;
+        const int l = fl - f * LPB;
+        if (sjn[l] < 0) continue;
+        const int mb = M - m;
+        cplx<R> xa = va[r], xb = vb[r];
+        if (f == 0) {   // E_x multiplier -i s_m
+            xa = cplx<R>{sx[m] * xa.im, -sx[m] * xa.re};
+            xb = cplx<R>{sx[mb] * xb.im, -sx[mb] * xb.re};
+        }
+        cplx<R>* zl = A + fl * ST;
+        {
+            const cplx<R> cb = conj(xb);
+            const cplx<R> sum = xa + cb, dif = xa - cb;
+            const cplx<R> t = conj(tw[m]) * dif;      // W^-m (X_m - conj X_M-m)
+            zl[pad<R>(m)] = cplx<R>{sum.re - t.im, sum.im + t.re};
+        }
+        if (mb != m && mb != M) {
+            const cplx<R> ca = conj(xa);
+            const cplx<R> sum = xb + ca, dif = xb - ca;
+            const cplx<R> t = conj(tw[mb]) * dif;
+            zl[pad<R>(mb)] = cplx<R>{sum.re - t.im, sum.im + t.re};
+        }
     }
     __syncthreads();
-    cplx<R>* z = fft::transform<R, 1, M>(A, B, nf * nl, tw, 2);
-    const R norm = (R)(1.0 / ((double)NX * (double)nz));
-    for (int idx = threadIdx.x; idx < nl * M; idx += blockDim.x) {
+    fft::transform_inplace<R, 1, M, NF * LPB, kThreads>(A, nf * LPB, tw, 2);
+    for (int idx = threadIdx.x; idx < LPB * M; idx += blockDim.x) {
         const int l = idx / M;
         const int n = idx - l * M;
+        if (l >= nl) continue;
         const int np_ = pad<R>(n);
-        const cplx<R> ex = z[(0 * nl + l) * ST + np_];
-        const cplx<R> ey_ = z[(1 * nl + l) * ST + np_];
-        const cplx<R> ez = z[(2 * nl + l) * ST + np_];
+        const cplx<R> ex = A[(0 * LPB + l) * ST + np_];
+        const cplx<R> ey_ = A[(1 * LPB + l) * ST + np_];
+        const cplx<R> ez = A[(2 * LPB + l) * ST + np_];
         vec4<R> v0, v1;
         v0.x = ex.re * norm; v0.y = ey_.re * norm; v0.z = ez.re * norm; v0.w = (R)0;
         v1.x = ex.im * norm; v1.y = ey_.im * norm; v1.z = ez.im * norm; v1.w = (R)0;
@@ -651,11 +724,10 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F
         E[o] = v0;
         E[o + 1] = v1;
         if (want_phi) {
-            const int line = line0 + l;
-            const int k = line / nyn;
-            const int jn = line - k * nyn;
+            const int jn = sjn[l];
             if (jn >= 1 && jn <= ny) {
-                const cplx<R> p = z[(3 * nl + l) * ST + np_];
+                const int k = (line0 + l) / nyn;
+                const cplx<R> p = A[(3 * LPB + l) * ST + np_];
                 double* prow = phi + ((size_t)k * ny + (jn - 1)) * NX + 2 * n;
                 prow[0] = (double)(p.re * norm);
                 prow[1] = (double)(p.im * norm);
@@ -676,13 +748,16 @@ constexpr int xinv_lpb() {
     return lines > 4 ? 4 : (lines < 1 ? 1 : lines);
 }
 template <class R, int M>
-size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + 2 * xfwd_lpb<R, M>() * padded<R, M>()) + sizeof(R) * 8; }
+size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + xfwd_lpb<R, M>() * padded<R, M>()) + sizeof(R) * 8; }
 template <class R, int M>
-size_t xinv_smem() { return sizeof(cplx<R>) * (2 * M + 2 * 4 * xinv_lpb<R, M>() * padded<R, M>()) + sizeof(R) * (M + 1); }
+size_t xinv_smem() {
+    return sizeof(cplx<R>) * (2 * M + 4 * xinv_lpb<R, M>() * padded<R, M>()) + sizeof(R) * (M + 1) +
+           sizeof(int) * xinv_lpb<R, M>() + 16;
+}
 template <class R, int NZ>
-size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + 2 * kZTile * padded<R, NZ>()); }
+size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + kZTile * padded<R, NZ>()); }
 template <class R, int NZ>
-size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + 6 * kZTileInv * padded<R, NZ>()) + sizeof(R) * NZ; }
+size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + 3 * kZTileInv * padded<R, NZ>()) + sizeof(R) * NZ; }
 
 template <class R, int M>
 void launch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
@@ -698,7 +773,7 @@ void launch_xinv(tribo_ctx* c, void* E, double* phi) {
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
     k_xinv<R, M, LPB><<<(nlines + LPB - 1) / LPB, kThreads, xinv_smem<R, M>(), c->stream>>>(
         (const cplx<R>*)c->F, (vec4<R>*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
-        phi != nullptr ? 1 : 0);
+        phi != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)));
 }
 template <class R, int NZ>
 void launch_zfwd(tribo_ctx* c) {
@@ -831,16 +906,18 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
                                                             c->d_ycoef, c->d_ey, ny, nz, nxh);
     } else {
         const size_t sh = sizeof(float2) * ((ny + 1) & ~1) + sizeof(float4) * (ny + 1);
+        const int rl = ny <= 32 ? 1 : ny <= 64 ? 2 : ny <= 128 ? 4 : 8;
+        const size_t shw = (sizeof(float2) + sizeof(float4)) * 32 * rl;
         cplx<float>* Sf = (cplx<float>*)c->S;
         cplx<float>* Fy = (cplx<float>*)c->F + fstride;
         const float4* tab = (const float4*)c->d_ytab;
         const float2* ads = (const float2*)c->d_yads;
         const float4* ec = (const float4*)c->d_yec;
-        const int wblocks = (int)(((size_t)ni * 32 + 127) / 128);
-        if (ny <= 32) k_ysolve_warp<1><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else if (ny <= 64) k_ysolve_warp<2><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else if (ny <= 128) k_ysolve_warp<4><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else if (ny <= 256) k_ysolve_warp<8><<<wblocks, 128, sh, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        const int wblocks = (int)(((size_t)nz * nxh * 32 + 127) / 128);
+        if (ny <= 32) k_ysolve_warp<1><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else if (ny <= 64) k_ysolve_warp<2><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else if (ny <= 128) k_ysolve_warp<4><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
+        else if (ny <= 256) k_ysolve_warp<8><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
         else
             k_ysolve_ds<<<(ni + 127) / 128, 128, sh, c->stream>>>(Sf, Fy, tab, (float4*)c->W2, ads, ec, ny, nz, nxh);
     }
