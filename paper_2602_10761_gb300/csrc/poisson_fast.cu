@@ -61,14 +61,6 @@ __device__ __forceinline__ ds ds_mul(ds a, ds b) {
     e = fmaf(a.lo, b.hi, e);
     return fast_two_sum(p, e);
 }
-__device__ __forceinline__ ds ds_add(ds a, ds b) {
-    ds s = two_sum(a.hi, b.hi);
-    const ds t = two_sum(a.lo, b.lo);
-    s.lo += t.hi;
-    s = fast_two_sum(s.hi, s.lo);
-    s.lo += t.lo;
-    return fast_two_sum(s.hi, s.lo);
-}
 __device__ __forceinline__ ds ds_neg(ds a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
 
@@ -237,327 +229,141 @@ __global__ void __launch_bounds__(128) k_ysolve64(cplx<double>* __restrict__ S, 
     }
 }
 
-// ---------------------------------------------------------------- y solve, double-single
-// Same sweeps in double-single arithmetic.  tab[j][item] = (1/pivot hi, lo,
-// c' hi, lo); a_ds[j] = sub-diagonal (hi, lo); W[j][item][2] = dp (re hi, re
-// lo, im hi, im lo).  E_y per cell j = A_j phi_j + Bm_j (phi_j - phi_j-1) +
-// Bp_j (phi_j+1 - phi_j) with the differences taken in double-single;
-// wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
-__global__ void __launch_bounds__(128) k_ysolve_ds(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
-                                                   const float4* __restrict__ tab, float4* __restrict__ W,
-                                                   const float2* __restrict__ a_ds, const float4* __restrict__ ec,
-                                                   int ny, int nz, int nxh) {
+// ---------------------------------------------------------------- y solve, chunked Thomas
+// One thread per pencil (m_z, m_x); the factors are those of |m_z|.  Thomas
+// in double-single: the forward sweep keeps only the value entering each
+// chunk of C rows (checkpoints in shared memory); the backward sweep walks
+// the chunks from the top, recomputes each chunk's forward values into
+// registers from its checkpoint and substitutes back.  E_y per cell j is
+// A_j phi_j + Bm_j (phi_j - phi_j-1) + Bp_j (phi_j+1 - phi_j), the
+// differences taken in double-single, written one row behind the backward
+// sweep; wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
+__device__ __forceinline__ ds ds_add_fast(ds a, ds b) {   // one two-sum on the high parts
+    ds s = two_sum(a.hi, b.hi);
+    s.lo += a.lo + b.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ ds ds_mul_f(ds a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+
+template <int C>
+__global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
+                                                      const float2* __restrict__ tinv,
+                                                      const float2* __restrict__ tcp,
+                                                      const float2* __restrict__ a_ds, const float4* __restrict__ ec,
+                                                      int ny, int nz, int nxh) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* sa = reinterpret_cast<float2*>(smem_raw);          // ny
-    float4* se = reinterpret_cast<float4*>(sa + ((ny + 1) & ~1)); // ny+1: (A, Bm, Bp, -) per cell, [ny] = walls
+    float4* ck = reinterpret_cast<float4*>(smem_raw);                 // [chunk][thread]
+    const int nch = (ny + C - 1) / C;
+    float4* se = ck + (size_t)nch * blockDim.x;                        // ny + 1
+    float2* sa = reinterpret_cast<float2*>(se + ny + 1);              // ny
     for (int j = threadIdx.x; j < ny; j += blockDim.x) sa[j] = a_ds[j];
     for (int j = threadIdx.x; j <= ny; j += blockDim.x) se[j] = ec[j];
     __syncthreads();
+    const int pencil = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pencil >= nz * nxh) return;
     const int ni = (nz / 2 + 1) * nxh;
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    if (item >= ni) return;
-    const int mzp = item / nxh;
-    const int mx = item - mzp * nxh;
-    const bool two = mzp != 0 && 2 * mzp != nz;
-    const int mzs[2] = {mzp, nz - mzp};
-    const int np = two ? 2 : 1;
-    const int nyn = ny + 2;
-    ds pr[2] = {{0.f, 0.f}, {0.f, 0.f}}, pi[2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (int j = 0; j < ny; ++j) {
-        const float4 t = tab[(size_t)j * ni + item];
-        const ds inv = {t.x, t.y};
-        const ds aj = {sa[j].x, sa[j].y};
+    const int mz = pencil / nxh;
+    const int mx = pencil - mz * nxh;
+    const int item = min(mz, nz - mz) * nxh + mx;
+    cplx<float>* srow = S + (size_t)mz * ny * nxh + mx;
+    cplx<float>* frow = Fy + (size_t)mz * (ny + 2) * nxh + mx;
+    const int tid = threadIdx.x;
+    // forward sweep, checkpoints at the end of each chunk
+    ds pr = {0.f, 0.f}, pim = {0.f, 0.f};
+    for (int c = 0; c < nch; ++c) {
+        float2 tv[C];
+        cplx<float> rv[C];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            if (s < np) {
-                const cplx<float> r = S[((size_t)mzs[s] * ny + j) * nxh + mx];
-                // dp = (r - a dp) / pivot
-                pr[s] = ds_mul(ds_add(ds{r.re, 0.f}, ds_neg(ds_mul(aj, pr[s]))), inv);
-                pi[s] = ds_mul(ds_add(ds{r.im, 0.f}, ds_neg(ds_mul(aj, pi[s]))), inv);
-                W[((size_t)j * ni + item) * 2 + s] = make_float4(pr[s].hi, pr[s].lo, pi[s].hi, pi[s].lo);
+        for (int i = 0; i < C; ++i) {
+            const int j = c * C + i;
+            if (j < ny) {
+                tv[i] = tinv[(size_t)j * ni + item];
+                rv[i] = srow[(size_t)j * nxh];
             }
         }
-    }
-    const float4 walls = se[ny];   // (bottom coefficient, top coefficient, -, -)
-    for (int s = 0; s < np; ++s) {
-        const int mz = mzs[s];
-        cplx<float>* srow = S + (size_t)mz * ny * nxh + mx;
-        cplx<float>* frow = Fy + (size_t)mz * nyn * nxh + mx;
-        ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};         // phi[j+1]
-        float dr_next = 0.f, di_next = 0.f;           // phi[j+2] - phi[j+1]
-        for (int j = ny - 1; j >= 0; --j) {
-            const float4 w = W[((size_t)j * ni + item) * 2 + s];
-            ds xr = {w.x, w.y}, xi = {w.z, w.w};
-            if (j != ny - 1) {
-                const float4 t = tab[(size_t)j * ni + item];
-                const ds cp = {t.z, t.w};
-                xr = ds_add(xr, ds_neg(ds_mul(cp, xr1)));
-                xi = ds_add(xi, ds_neg(ds_mul(cp, xi1)));
-            } else {
-                // top wall node from phi[ny-1]
-                frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * ds_f(xr), walls.y * ds_f(xi)};
-            }
-            srow[(size_t)j * nxh] = cplx<float>{ds_f(xr), ds_f(xi)};
-            // E_y of cell j+1 (node j+2): phi[j+1], d0 = phi[j+1]-phi[j], d1 = phi[j+2]-phi[j+1]
-            float d0r = 0.f, d0i = 0.f;
-            if (j + 1 <= ny - 1) {
-                d0r = ds_f(ds_add(xr1, ds_neg(xr)));
-                d0i = ds_f(ds_add(xi1, ds_neg(xi)));
-                const float4 c = se[j + 1];
-                frow[(size_t)(j + 2) * nxh] = cplx<float>{c.x * ds_f(xr1) + c.y * d0r + c.z * dr_next,
-                                                          c.x * ds_f(xi1) + c.y * d0i + c.z * di_next};
-            }
-            dr_next = d0r;
-            di_next = d0i;
-            xr1 = xr;
-            xi1 = xi;
-        }
-        // cell 0 (node 1) and the bottom wall node 0
-        const float4 c = se[0];
-        const float x0r = ds_f(xr1), x0i = ds_f(xi1);
-        frow[(size_t)1 * nxh] = cplx<float>{c.x * x0r + c.z * dr_next, c.x * x0i + c.z * di_next};
-        frow[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
-    }
-}
-
-// ---------------------------------------------------------------- y solve, warp-cooperative
-// One warp per table row (|m_z|, m_x), both pencils.  Lane l holds rows
-// [l*RL, l*RL + RL) in registers.  The forward recurrence y_j = (r_j - a_j
-// y_j-1) / pivot_j is affine in the carry y_j0-1 entering the lane:
-// y_j = yh_j + P_j c with yh from a zero carry and P_j the product of
-// -a_t/pivot_t; the lanes' end maps are combined by a Kogge-Stone prefix
-// over shuffles, giving each lane its carry.  The backward recurrence
-// x_j = y_j - c'_j x_j+1 is treated the same way with a suffix combination.
-// All arithmetic is double-single; nothing leaves the registers but the
-// outputs (phi-hat and the E_y spectrum, as in k_ysolve_ds).
-__device__ __forceinline__ ds shfl_up_ds(ds v, int d) {
-    return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
-}
-__device__ __forceinline__ ds shfl_down_ds(ds v, int d) {
-    return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
-}
-__device__ __forceinline__ ds ds_fma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }   // a b + c
-
-template <int RL>
-__global__ void __launch_bounds__(128) k_ysolve_warp(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
-                                                     const float4* __restrict__ tab,
-                                                     const float2* __restrict__ a_ds,
-                                                     const float4* __restrict__ ec, int ny, int nz, int nxh) {
-    // coefficients of row j at [(j % RL) * 32 + j / RL]: the lanes of a warp
-    // read rows lane*RL + i, i.e. 32 consecutive slots (no bank conflicts)
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* se = reinterpret_cast<float4*>(smem_raw);          // 32*RL
-    float2* sa = reinterpret_cast<float2*>(se + 32 * RL);      // 32*RL
-    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
-        const int sl = (j % RL) * 32 + j / RL;
-        sa[sl] = a_ds[j];
-        se[sl] = ec[j];
-    }
-    __syncthreads();
-    const float4 walls = ec[ny];
-    const int ni = (nz / 2 + 1) * nxh;
-    const int pencil = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (pencil >= nz * nxh) return;  // whole warps leave together
-    const int lane = threadIdx.x & 31;
-    const int mz0 = pencil / nxh;
-    const int mx = pencil - mz0 * nxh;
-    const int mzp = min(mz0, nz - mz0);                 // table row of |m_z|
-    const int item = mzp * nxh + mx;
-    constexpr int NP = 1;                               // pencils per warp
-    const int np = 1;
-    const int j0 = lane * RL;
-    const int nv = max(0, min(RL, ny - j0));           // valid rows of this lane
-    const size_t row0[1] = {(size_t)mz0 * ny * nxh + mx};
-
-    float4 t[RL];
-    ds yr[NP][RL], yi[NP][RL], P[RL];
 #pragma unroll
-    for (int i = 0; i < RL; ++i) {
-        if (i < nv) {
-            t[i] = tab[(size_t)(j0 + i) * ni + item];
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                const cplx<float> r = (s < np) ? S[row0[s] + (size_t)(j0 + i) * nxh] : cplx<float>{0.f, 0.f};
-                yr[s][i] = {r.re, 0.f};
-                yi[s][i] = {r.im, 0.f};
+        for (int i = 0; i < C; ++i) {
+            const int j = c * C + i;
+            if (j < ny) {
+                const ds inv = {tv[i].x, tv[i].y};
+                const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
+                pr = ds_add_fast(ds_mul_f(inv, rv[i].re), ds_neg(ds_mul(at, pr)));
+                pim = ds_add_fast(ds_mul_f(inv, rv[i].im), ds_neg(ds_mul(at, pim)));
             }
         }
+        ck[(size_t)c * blockDim.x + tid] = make_float4(pr.hi, pr.lo, pim.hi, pim.lo);
     }
-    // forward, zero carry; P_i = prod (-a/pivot)
-    ds prun = {1.f, 0.f};
-    ds pr[NP], pim[NP];
-#pragma unroll
-    for (int s = 0; s < NP; ++s) pr[s] = pim[s] = ds{0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-        if (i < nv) {
-            const ds inv = {t[i].x, t[i].y};
-            const float2 av = sa[i * 32 + lane];
-            const ds aj = {av.x, av.y};
-            const ds at = ds_mul(aj, inv);
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                pr[s] = ds_add(ds_mul(yr[s][i], inv), ds_neg(ds_mul(at, pr[s])));
-                pim[s] = ds_add(ds_mul(yi[s][i], inv), ds_neg(ds_mul(at, pim[s])));
-                yr[s][i] = pr[s];
-                yi[s][i] = pim[s];
-            }
-            prun = ds_mul(prun, ds_neg(at));
-            P[i] = prun;
+    const float4 walls = se[ny];
+    ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};      // x[j+1]
+    float dnr = 0.f, dni = 0.f;                 // x[j+2] - x[j+1]
+    for (int c = nch - 1; c >= 0; --c) {
+        ds qr = {0.f, 0.f}, qi = {0.f, 0.f};
+        if (c > 0) {
+            const float4 v = ck[(size_t)(c - 1) * blockDim.x + tid];
+            qr = ds{v.x, v.y};
+            qi = ds{v.z, v.w};
         }
-    }
-    // prefix combination of the lanes' maps c -> yh_last + P_last c
-    ds beta = nv > 0 ? prun : ds{1.f, 0.f};
-    ds al[NP][2];   // [pencil][re/im]
+        float2 tv[C], cv[C];
+        cplx<float> rv[C];
 #pragma unroll
-    for (int s = 0; s < NP; ++s) {
-        al[s][0] = nv > 0 ? pr[s] : ds{0.f, 0.f};
-        al[s][1] = nv > 0 ? pim[s] : ds{0.f, 0.f};
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const ds b2 = shfl_up_ds(beta, d);
-        ds a2[NP][2];
-#pragma unroll
-        for (int s = 0; s < NP; ++s) {
-            a2[s][0] = shfl_up_ds(al[s][0], d);
-            a2[s][1] = shfl_up_ds(al[s][1], d);
-        }
-        if (lane >= d) {
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                al[s][0] = ds_fma(beta, a2[s][0], al[s][0]);
-                al[s][1] = ds_fma(beta, a2[s][1], al[s][1]);
-            }
-            beta = ds_mul(beta, b2);
-        }
-    }
-    ds cr[NP], ci[NP];
-#pragma unroll
-    for (int s = 0; s < NP; ++s) {
-        cr[s] = shfl_up_ds(al[s][0], 1);
-        ci[s] = shfl_up_ds(al[s][1], 1);
-        if (lane == 0) { cr[s] = ds{0.f, 0.f}; ci[s] = ds{0.f, 0.f}; }
-    }
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-        if (i < nv) {
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                yr[s][i] = ds_fma(P[i], cr[s], yr[s][i]);
-                yi[s][i] = ds_fma(P[i], ci[s], yi[s][i]);
+        for (int i = 0; i < C; ++i) {
+            const int j = c * C + i;
+            if (j < ny) {
+                tv[i] = tinv[(size_t)j * ni + item];
+                cv[i] = tcp[(size_t)j * ni + item];
+                rv[i] = srow[(size_t)j * nxh];
             }
         }
-    }
-    // backward, zero carry from above; Q_i = prod over rows i..last of (-c')
-    ds qrun = {1.f, 0.f};
-    ds xr[NP], xi[NP];
+        ds dr[C], di[C];
 #pragma unroll
-    for (int s = 0; s < NP; ++s) xr[s] = xi[s] = ds{0.f, 0.f};
-#pragma unroll
-    for (int i = RL - 1; i >= 0; --i) {
-        if (i < nv) {
-            const ds cp = {t[i].z, t[i].w};
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                xr[s] = ds_add(yr[s][i], ds_neg(ds_mul(cp, xr[s])));
-                xi[s] = ds_add(yi[s][i], ds_neg(ds_mul(cp, xi[s])));
-                yr[s][i] = xr[s];
-                yi[s][i] = xi[s];
-            }
-            qrun = ds_mul(qrun, ds_neg(cp));
-            P[i] = qrun;
-        }
-    }
-    // suffix combination of the lanes' maps d -> xh_first + Q_first d
-    beta = nv > 0 ? qrun : ds{1.f, 0.f};
-#pragma unroll
-    for (int s = 0; s < NP; ++s) {
-        al[s][0] = nv > 0 ? xr[s] : ds{0.f, 0.f};
-        al[s][1] = nv > 0 ? xi[s] : ds{0.f, 0.f};
-    }
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const ds b2 = shfl_down_ds(beta, d);
-        ds a2[NP][2];
-#pragma unroll
-        for (int s = 0; s < NP; ++s) {
-            a2[s][0] = shfl_down_ds(al[s][0], d);
-            a2[s][1] = shfl_down_ds(al[s][1], d);
-        }
-        if (lane + d < 32) {
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                al[s][0] = ds_fma(beta, a2[s][0], al[s][0]);
-                al[s][1] = ds_fma(beta, a2[s][1], al[s][1]);
-            }
-            beta = ds_mul(beta, b2);
-        }
-    }
-    ds dr[NP], di[NP];   // x of the first row of the next lane
-#pragma unroll
-    for (int s = 0; s < NP; ++s) {
-        dr[s] = shfl_down_ds(al[s][0], 1);
-        di[s] = shfl_down_ds(al[s][1], 1);
-        if (lane == 31) { dr[s] = ds{0.f, 0.f}; di[s] = ds{0.f, 0.f}; }
-    }
-#pragma unroll
-    for (int i = 0; i < RL; ++i) {
-        if (i < nv) {
-#pragma unroll
-            for (int s = 0; s < NP; ++s) {
-                yr[s][i] = ds_fma(P[i], dr[s], yr[s][i]);
-                yi[s][i] = ds_fma(P[i], di[s], yi[s][i]);
+        for (int i = 0; i < C; ++i) {
+            const int j = c * C + i;
+            if (j < ny) {
+                const ds inv = {tv[i].x, tv[i].y};
+                const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
+                qr = ds_add_fast(ds_mul_f(inv, rv[i].re), ds_neg(ds_mul(at, qr)));
+                qi = ds_add_fast(ds_mul_f(inv, rv[i].im), ds_neg(ds_mul(at, qi)));
+                dr[i] = qr;
+                di[i] = qi;
             }
         }
-    }
-    // x of the previous lane's last row, for the E_y differences
-    const int nyn = ny + 2;
 #pragma unroll
-    for (int s = 0; s < NP; ++s) {
-        // x of this lane's last valid row (selects, no indexing by nv)
-        ds lr = yr[s][RL - 1], li = yi[s][RL - 1];
-#pragma unroll
-        for (int i = 0; i + 1 < RL; ++i) {
-            const bool sel = (i + 1 == nv);
-            lr.hi = sel ? yr[s][i].hi : lr.hi;
-            lr.lo = sel ? yr[s][i].lo : lr.lo;
-            li.hi = sel ? yi[s][i].hi : li.hi;
-            li.lo = sel ? yi[s][i].lo : li.lo;
-        }
-        const ds br = shfl_up_ds(lr, 1), bi = shfl_up_ds(li, 1);
-        if (s < np) {
-        const size_t mz = (size_t)mz0;
-        cplx<float>* srow = S + mz * ny * nxh + mx;
-        cplx<float>* frow = Fy + mz * nyn * nxh + mx;
-        ds prv_r = br, prv_i = bi;     // x[j-1]
-#pragma unroll
-        for (int i = 0; i < RL; ++i) {
-            if (i < nv) {
-                const int j = j0 + i;
-                const ds cur_r = yr[s][i], cur_i = yi[s][i];
-                ds nxt_r = dr[s], nxt_i = di[s];
-                if (i + 1 < RL) {
-                    if (i + 1 < nv) {
-                        nxt_r = yr[s][i + 1];
-                        nxt_i = yi[s][i + 1];
-                    }
+        for (int i = C - 1; i >= 0; --i) {
+            const int j = c * C + i;
+            if (j < ny) {
+                ds xr = dr[i], xi = di[i];
+                if (j != ny - 1) {
+                    const ds cp = {cv[i].x, cv[i].y};
+                    xr = ds_add_fast(xr, ds_neg(ds_mul(cp, xr1)));
+                    xi = ds_add_fast(xi, ds_neg(ds_mul(cp, xi1)));
                 }
-                const float fr = ds_f(cur_r), fi = ds_f(cur_i);
+                const float fr = ds_f(xr), fi = ds_f(xi);
                 srow[(size_t)j * nxh] = cplx<float>{fr, fi};
-                const float4 c = se[i * 32 + lane];
-                const float d0r = ds_f(ds_add(cur_r, ds_neg(prv_r))), d0i = ds_f(ds_add(cur_i, ds_neg(prv_i)));
-                const float d1r = ds_f(ds_add(nxt_r, ds_neg(cur_r))), d1i = ds_f(ds_add(nxt_i, ds_neg(cur_i)));
-                frow[(size_t)(j + 1) * nxh] = cplx<float>{c.x * fr + c.y * d0r + c.z * d1r,
-                                                          c.x * fi + c.y * d0i + c.z * d1i};
-                if (j == 0) frow[0] = cplx<float>{walls.x * fr, walls.x * fi};
                 if (j == ny - 1) frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * fr, walls.y * fi};
-                prv_r = cur_r;
-                prv_i = cur_i;
+                float d0r = 0.f, d0i = 0.f;
+                if (j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
+                    d0r = ds_f(ds_add_fast(xr1, ds_neg(xr)));
+                    d0i = ds_f(ds_add_fast(xi1, ds_neg(xi)));
+                    const float4 cf = se[j + 1];
+                    frow[(size_t)(j + 2) * nxh] = cplx<float>{cf.x * ds_f(xr1) + cf.y * d0r + cf.z * dnr,
+                                                              cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
+                }
+                dnr = d0r;
+                dni = d0i;
+                xr1 = xr;
+                xi1 = xi;
             }
         }
-        }
     }
+    const float4 cf = se[0];
+    const float x0r = ds_f(xr1), x0i = ds_f(xi1);
+    frow[(size_t)1 * nxh] = cplx<float>{cf.x * x0r + cf.z * dnr, cf.x * x0i + cf.z * dni};
+    frow[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
 }
 
 // ---------------------------------------------------------------- z inverse
@@ -656,7 +462,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F
     const int nf = want_phi ? 4 : 3;
     for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
     for (int i = threadIdx.x; i < NXH; i += blockDim.x) sx[i] = from_f64<R>(sinx[i]);
-    if (threadIdx.x < LPB) sjn[threadIdx.x] = threadIdx.x < nl ? (line0 + threadIdx.x) % nyn : -1;
+    if (threadIdx.x < LPB) sjn[threadIdx.x] = (int)threadIdx.x < nl ? (line0 + (int)threadIdx.x) % nyn : -1;
     __syncthreads();
     // split step: one thread per pair (m, M-m) produces Z_m and Z_M-m from X_m, X_M-m
     constexpr int PER = (NF * LPB * H + kThreads - 1) / kThreads;
@@ -905,21 +711,14 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
                                                             (const double2*)c->d_ytab, (double2*)c->W2,
                                                             c->d_ycoef, c->d_ey, ny, nz, nxh);
     } else {
-        const size_t sh = sizeof(float2) * ((ny + 1) & ~1) + sizeof(float4) * (ny + 1);
-        const int rl = ny <= 32 ? 1 : ny <= 64 ? 2 : ny <= 128 ? 4 : 8;
-        const size_t shw = (sizeof(float2) + sizeof(float4)) * 32 * rl;
-        cplx<float>* Sf = (cplx<float>*)c->S;
-        cplx<float>* Fy = (cplx<float>*)c->F + fstride;
-        const float4* tab = (const float4*)c->d_ytab;
-        const float2* ads = (const float2*)c->d_yads;
-        const float4* ec = (const float4*)c->d_yec;
-        const int wblocks = (int)(((size_t)nz * nxh * 32 + 127) / 128);
-        if (ny <= 32) k_ysolve_warp<1><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else if (ny <= 64) k_ysolve_warp<2><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else if (ny <= 128) k_ysolve_warp<4><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else if (ny <= 256) k_ysolve_warp<8><<<wblocks, 128, shw, c->stream>>>(Sf, Fy, tab, ads, ec, ny, nz, nxh);
-        else
-            k_ysolve_ds<<<(ni + 127) / 128, 128, sh, c->stream>>>(Sf, Fy, tab, (float4*)c->W2, ads, ec, ny, nz, nxh);
+        constexpr int CH = 8;
+        const int nch = (ny + CH - 1) / CH;
+        const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
+        const float2* tinv = (const float2*)c->d_ytab;
+        const float2* tcp = tinv + (size_t)ny * ni;
+        k_ysolve_chunk<CH><<<(nz * nxh + 127) / 128, 128, shc, c->stream>>>(
+            (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
+            (const float4*)c->d_yec, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_INV_Z);
@@ -962,8 +761,8 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     b[ny - 1] -= 1.0 / (dy[ny - 1] * (yf[ny] - yc[ny - 1]));
     const bool ds_mode = c->prec != TRIBO_FP64;
     std::vector<double2> tab64;
-    std::vector<float4> tab32;
-    if (ds_mode) tab32.resize((size_t)ny * ni);
+    std::vector<float2> tab32;
+    if (ds_mode) tab32.resize(2 * (size_t)ny * ni);
     else tab64.resize((size_t)ny * ni);
     for (int item = 0; item < ni; ++item) {
         const double lam = lamz[item / nxh] + lamx[item % nxh];
@@ -972,10 +771,11 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
             const double inv = 1.0 / ((b[j] - lam) - a[j] * cp);
             cp = cc[j] * inv;
             if (ds_mode) {
-                float4 t;
-                split_ds(inv, &t.x, &t.y);
-                split_ds(cp, &t.z, &t.w);
-                tab32[(size_t)j * ni + item] = t;
+                float2 ti, tc;
+                split_ds(inv, &ti.x, &ti.y);
+                split_ds(cp, &tc.x, &tc.y);
+                tab32[(size_t)j * ni + item] = ti;
+                tab32[(size_t)ny * ni + (size_t)j * ni + item] = tc;
             } else {
                 tab64[(size_t)j * ni + item] = make_double2(inv, cp);
             }
@@ -985,7 +785,7 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     TRIBO_CUDA(cudaMalloc(&c->d_ytab, tab_bytes));
     TRIBO_CUDA(cudaMemcpy(c->d_ytab, ds_mode ? (const void*)tab32.data() : (const void*)tab64.data(), tab_bytes,
                           cudaMemcpyHostToDevice));
-    TRIBO_CUDA(cudaMalloc(&c->W2, 32 * (size_t)ny * ni));
+    if (!ds_mode) TRIBO_CUDA(cudaMalloc(&c->W2, 32 * (size_t)ny * ni));
     if (ds_mode) {
         // sub-diagonal in double-single, E_y coefficients per cell and walls
         std::vector<float2> ads(ny);
@@ -1015,6 +815,7 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         return dispatch_attr<double>(nx, nz, optin);
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
+    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_chunk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return dispatch_attr<float>(nx, nz, optin);
 }
 
