@@ -15,6 +15,22 @@
 namespace tribo {
 namespace fft {
 
+// asynchronous global -> shared copies (no register staging)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+    if constexpr (sizeof(T) == 16) cp_async16(smem, gmem);
+    else cp_async8(smem, gmem);
+}
+
 // pad shift: one pad element per 32 (8-byte) or 16 (16-byte) elements
 template <class R> struct pad_shift { static constexpr int value = sizeof(R) == 4 ? 5 : 4; };
 template <class R>

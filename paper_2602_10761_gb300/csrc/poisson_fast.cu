@@ -77,39 +77,29 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(double* __restrict__ src, con
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
     cplx<R>* A = tw + NX;
-    R* sc = reinterpret_cast<R*>(A + LPB * ST);
+    double2* stg = reinterpret_cast<double2*>(A + LPB * ST + ((LPB * ST) & 1));   // 16-byte aligned
+    R* sc = reinterpret_cast<R*>(stg + LPB * M);
     const int line0 = blockIdx.x * LPB;
     const int nl = min(LPB, nlines - line0);
     for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
     if (threadIdx.x < nl) sc[threadIdx.x] = from_f64<R>(scale_row[(line0 + threadIdx.x) % ny]);
     __syncthreads();
-    // all loads first: the zeroing stores go to the same buffer, and issuing
-    // them between loads would serialise the loads
-    constexpr int PER = (LPB * M + kThreads - 1) / kThreads;
+    // stage the charge sums asynchronously; zero the source only after the
+    // copies have landed
     const double2* src2 = reinterpret_cast<const double2*>(src) + (size_t)line0 * M;
-    double2 v[PER];
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
-        v[r] = idx < nl * M ? src2[idx] : make_double2(0.0, 0.0);
-    }
+    for (int idx = threadIdx.x; idx < nl * M; idx += kThreads) fft::cp_async16(&stg[idx], &src2[idx]);
+    fft::cp_async_wait_all();
     if (zero_src) {
         double2* dst2 = reinterpret_cast<double2*>(src) + (size_t)line0 * M;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int idx = threadIdx.x + r * kThreads;
-            if (idx < nl * M) dst2[idx] = make_double2(0.0, 0.0);
-        }
+        for (int idx = threadIdx.x; idx < nl * M; idx += kThreads) dst2[idx] = make_double2(0.0, 0.0);
     }
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
-        if (idx < nl * M) {
-            const int l = idx / M;
-            const int n = idx - l * M;
-            const R s = sc[l];
-            A[l * ST + pad<R>(n)] = cplx<R>{from_f64<R>(v[r].x) * s, from_f64<R>(v[r].y) * s};
-        }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nl * M; idx += kThreads) {
+        const int l = idx / M;
+        const int n = idx - l * M;
+        const R s = sc[l];
+        const double2 v = stg[idx];
+        A[l * ST + pad<R>(n)] = cplx<R>{from_f64<R>(v.x) * s, from_f64<R>(v.y) * s};
     }
     __syncthreads();
     fft::transform_inplace<R, -1, M, LPB, kThreads>(A, nl, tw, 2);
@@ -139,23 +129,13 @@ __global__ void __launch_bounds__(kThreads) k_zfwd(cplx<R>* __restrict__ S, int 
     const int j = blockIdx.x;
     const int mx0 = blockIdx.y * kZTile;
     const int nt = min(kZTile, nxh - mx0);
-    // loads first (all in flight together), then the transposed smem stores
-    constexpr int PER = (NZ * kZTile + kThreads - 1) / kThreads;
-    cplx<R> v[PER];
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
+    // asynchronous copies straight into the transposed, padded tile
+    for (int idx = threadIdx.x; idx < NZ * kZTile; idx += kThreads) {
         const int k = idx / kZTile;
         const int t = idx - k * kZTile;
-        if (idx < NZ * kZTile && t < nt) v[r] = S[((size_t)k * ny + j) * nxh + mx0 + t];
+        if (t < nt) fft::cp_async_elem(&A[t * ST + pad<R>(k)], &S[((size_t)k * ny + j) * nxh + mx0 + t]);
     }
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
-        const int k = idx / kZTile;
-        const int t = idx - k * kZTile;
-        if (idx < NZ * kZTile && t < nt) A[t * ST + pad<R>(k)] = v[r];
-    }
+    fft::cp_async_wait_all();
     __syncthreads();
     fft::transform_inplace<R, -1, NZ, kZTile, kThreads>(A, nt, tw, 1);
     for (int idx = threadIdx.x; idx < NZ * kZTile; idx += blockDim.x) {
@@ -391,34 +371,30 @@ __global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ S
     const int nlines = interior ? 3 * kZTileInv : kZTileInv;   // E_y tile first when alone
     __syncthreads();
     cplx<R>* Fy = F + fstride;
-    constexpr int PER = (NZ * kZTileInv + kThreads - 1) / kThreads;
-    cplx<R> vy[PER], vp[PER];
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
+    for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += kThreads) {
         const int k = idx / kZTileInv;
         const int t = idx - k * kZTileInv;
-        if (idx < NZ * kZTileInv && t < nt) {
-            vy[r] = Fy[((size_t)k * nyn + jn) * nxh + mx0 + t];
-            if (interior) vp[r] = S[((size_t)k * ny + (jn - 1)) * nxh + mx0 + t];
+        if (t < nt) {
+            const int kp = pad<R>(k);
+            fft::cp_async_elem(&A[t * ST + kp], &Fy[((size_t)k * nyn + jn) * nxh + mx0 + t]);
+            if (interior)
+                fft::cp_async_elem(&A[(kZTileInv + t) * ST + kp], &S[((size_t)k * ny + (jn - 1)) * nxh + mx0 + t]);
         }
     }
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
-        const int k = idx / kZTileInv;
-        const int t = idx - k * kZTileInv;
-        if (idx < NZ * kZTileInv && t < nt) {
-            const int kp = pad<R>(k);
-            A[t * ST + kp] = vy[r];
-            if (interior) {
-                const cplx<R> ph = vp[r];
-                A[(kZTileInv + t) * ST + kp] = ph;
+    fft::cp_async_wait_all();
+    __syncthreads();
+    if (interior) {
+        for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += kThreads) {
+            const int k = idx / kZTileInv;
+            const int t = idx - k * kZTileInv;
+            if (t < nt) {
+                const int kp = pad<R>(k);
+                const cplx<R> ph = A[(kZTileInv + t) * ST + kp];
                 A[(2 * kZTileInv + t) * ST + kp] = cplx<R>{sz[k] * ph.im, -sz[k] * ph.re};   // -i s phi
             }
         }
+        __syncthreads();
     }
-    __syncthreads();
     fft::transform_inplace<R, 1, NZ, 3 * kZTileInv, kThreads>(A, nlines, tw, 1);
     const cplx<R>* res = A;
     for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += blockDim.x) {
@@ -449,7 +425,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F
     constexpr int NXH = M + 1;
     constexpr int NF = 4;
     constexpr int H = M / 2 + 1;          // pairs (m, M-m), m = 0..M/2
-    constexpr int ST = padded<R, M>();
+    constexpr int ST = padded<R, M + 1>();   // a staged line holds X_0 .. X_M
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
     cplx<R>* A = tw + NX;                 // line f*LPB + l holds field f of line l
@@ -464,42 +440,36 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F
     for (int i = threadIdx.x; i < NXH; i += blockDim.x) sx[i] = from_f64<R>(sinx[i]);
     if (threadIdx.x < LPB) sjn[threadIdx.x] = (int)threadIdx.x < nl ? (line0 + (int)threadIdx.x) % nyn : -1;
     __syncthreads();
-    // split step: one thread per pair (m, M-m) produces Z_m and Z_M-m from X_m, X_M-m
-    constexpr int PER = (NF * LPB * H + kThreads - 1) / kThreads;
-    cplx<R> va[PER], vb[PER];
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {     // loads first
-        const int idx = threadIdx.x + r * kThreads;
-        va[r] = vb[r] = cplx<R>{0, 0};
-        if (idx >= nf * LPB * H) continue;
-        const int fl = idx / H;
-        const int m = idx - fl * H;
+    // stage each (field, line) half spectrum into its FFT line, then the split
+    // step in place: one thread per pair (m, M-m) turns X_m, X_M-m into Z_m, Z_M-m
+    for (int idx = threadIdx.x; idx < nf * LPB * NXH; idx += kThreads) {
+        const int fl = idx / NXH;
+        const int m = idx - fl * NXH;
         const int f = fl / LPB;
         const int l = fl - f * LPB;
         const int jn = sjn[l];
         const int src_field = (f == 3) ? 0 : f;
-        if (jn >= 0 && (src_field == 1 || (jn >= 1 && jn <= ny))) {
-            const cplx<R>* row = F + src_field * fstride + (size_t)(line0 + l) * NXH;
-            va[r] = row[m];
-            vb[r] = row[M - m];
-        }
+        cplx<R>* dst = &A[fl * ST + pad<R>(m)];
+        if (jn >= 0 && (src_field == 1 || (jn >= 1 && jn <= ny)))
+            fft::cp_async_elem(dst, &F[src_field * fstride + (size_t)(line0 + l) * NXH + m]);
+        else
+            *dst = cplx<R>{0, 0};
     }
-#pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int idx = threadIdx.x + r * kThreads;
-        if (idx >= nf * LPB * H) continue;
+    fft::cp_async_wait_all();
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nf * LPB * H; idx += kThreads) {
         const int fl = idx / H;
         const int m = idx - fl * H;
         const int f = fl / LPB;
         const int l = fl - f * LPB;
         if (sjn[l] < 0) continue;
         const int mb = M - m;
-        cplx<R> xa = va[r], xb = vb[r];
+        cplx<R>* zl = A + fl * ST;
+        cplx<R> xa = zl[pad<R>(m)], xb = zl[pad<R>(mb)];
         if (f == 0) {   // E_x multiplier -i s_m
             xa = cplx<R>{sx[m] * xa.im, -sx[m] * xa.re};
             xb = cplx<R>{sx[mb] * xb.im, -sx[mb] * xb.re};
         }
-        cplx<R>* zl = A + fl * ST;
         {
             const cplx<R> cb = conj(xb);
             const cplx<R> sum = xa + cb, dif = xa - cb;
@@ -514,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F
         }
     }
     __syncthreads();
-    fft::transform_inplace<R, 1, M, NF * LPB, kThreads>(A, nf * LPB, tw, 2);
+    fft::transform_inplace<R, 1, M, NF * LPB, kThreads, ST>(A, nf * LPB, tw, 2);
     for (int idx = threadIdx.x; idx < LPB * M; idx += blockDim.x) {
         const int l = idx / M;
         const int n = idx - l * M;
@@ -550,14 +520,17 @@ constexpr int xfwd_lpb() {
 }
 template <class R, int M>
 constexpr int xinv_lpb() {
-    constexpr int lines = (int)(512 * 8 / sizeof(cplx<R>)) / M;
+    constexpr int lines = (int)(1024 * 8 / sizeof(cplx<R>)) / M;
     return lines > 4 ? 4 : (lines < 1 ? 1 : lines);
 }
 template <class R, int M>
-size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + xfwd_lpb<R, M>() * padded<R, M>()) + sizeof(R) * 8; }
+size_t xfwd_smem() {
+    return sizeof(cplx<R>) * (2 * M + xfwd_lpb<R, M>() * padded<R, M>() + 1) + sizeof(double2) * xfwd_lpb<R, M>() * M +
+           sizeof(R) * 8;
+}
 template <class R, int M>
 size_t xinv_smem() {
-    return sizeof(cplx<R>) * (2 * M + 4 * xinv_lpb<R, M>() * padded<R, M>()) + sizeof(R) * (M + 1) +
+    return sizeof(cplx<R>) * (2 * M + 4 * xinv_lpb<R, M>() * padded<R, M + 1>()) + sizeof(R) * (M + 1) +
            sizeof(int) * xinv_lpb<R, M>() + 16;
 }
 template <class R, int NZ>
