@@ -150,10 +150,10 @@ tribo_status tribo_step(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t n
 
 /* Standalone Poisson solve and field (step 2 above).  rho: device
  * (Nz, Ny, Nx) double charge density [C/m^3].  phi: device (Nz, Ny, Nx)
- * double, may be NULL.  E: device (Nz, Ny+2, Nx, 4) "real" with E_x, E_y,
- * E_z in components 0..2 (component 3 is written as 0); the wall nodes hold
- * E_x = E_z = 0 and the one-sided E_y.  rho and phi must be 16-byte aligned
- * and E aligned to one node (4 reals); TRIBO_ERR_ARG otherwise.  Asynchronous. */
+ * double, may be NULL.  E: device (3, Nz, Ny+2, Nx) "real", the planes
+ * E_x, E_y, E_z on the wall-extended lattice; the wall nodes hold E_x = E_z = 0
+ * and the one-sided E_y.  rho and phi must be 16-byte aligned and E aligned
+ * to its real type; TRIBO_ERR_ARG otherwise.  Asynchronous. */
 tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void* E);
 
 /* Statistics since the last tribo_reset_stats (Sec. 4.1): sum of the current

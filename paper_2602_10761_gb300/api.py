@@ -276,7 +276,7 @@ class Channel:
     def poisson(self, rho, want_phi: bool = False):
         import torch
         rdt = torch.float64 if self.params.precision == _abi.TRIBO_FP64 else torch.float32
-        E = torch.empty((self.nz, self.ny + 2, self.nx, 4), dtype=rdt, device=rho.device)
+        E = torch.empty((3, self.nz, self.ny + 2, self.nx), dtype=rdt, device=rho.device)
         phi = torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=rho.device) if want_phi else None
         tribo_poisson(self.ctx, rho, phi, E)
         return phi, E

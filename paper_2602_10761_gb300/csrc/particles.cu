@@ -49,8 +49,9 @@ struct StepArgs {
     R ybin_scale;                  // ybins / ly
     const R* Yr;                   // ny+2 lattice nodes
     const R* invdY;                // ny+1 inverse node spacings
-    const vec4<R>* u;
-    const vec4<R>* E;
+    const R* u;                    // planes u_x, u_y, u_z, each `nodes` long
+    const R* E;                    // planes E_x, E_y, E_z, each `nodes` long
+    size_t nodes;
     double* Q;                     // cell charge sums for the next step (may be NULL)
     unsigned long long* hist;      // ny (may be NULL)
     Accum* acc;
@@ -128,14 +129,6 @@ __device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a
     return ((uint32_t)k * (uint32_t)a.ny + (uint32_t)j) * (uint32_t)a.nx + (uint32_t)i;
 }
 
-template <class R>
-__device__ __forceinline__ vec4<R> ld4(const vec4<R>* p) { return *p; }
-template <>
-__device__ __forceinline__ vec4<float> ld4<float>(const vec4<float>* p) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    return vec4<float>{v.x, v.y, v.z, v.w};
-}
-
 // trilinear gather of one or two lattice fields at (x, y, z) given the cell j
 template <class R>
 __device__ __forceinline__ void gather(const StepArgs<R>& a, R x, R y, R z, int j, R uf[3], R Ef[3],
@@ -169,18 +162,16 @@ __device__ __forceinline__ void gather(const StepArgs<R>& a, R x, R y, R z, int 
     R u0 = 0, u1 = 0, u2 = 0, e0 = 0, e1 = 0, e2 = 0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const vec4<R> v = ld4<R>(a.u + idx[c]);
-        u0 += w[c] * v.x;
-        u1 += w[c] * v.y;
-        u2 += w[c] * v.z;
+        u0 += w[c] * __ldg(a.u + idx[c]);
+        u1 += w[c] * __ldg(a.u + a.nodes + idx[c]);
+        u2 += w[c] * __ldg(a.u + 2 * a.nodes + idx[c]);
     }
     if (withE) {
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const vec4<R> v = ld4<R>(a.E + idx[c]);
-            e0 += w[c] * v.x;
-            e1 += w[c] * v.y;
-            e2 += w[c] * v.z;
+            e0 += w[c] * __ldg(a.E + idx[c]);
+            e1 += w[c] * __ldg(a.E + a.nodes + idx[c]);
+            e2 += w[c] * __ldg(a.E + 2 * a.nodes + idx[c]);
         }
     }
     uf[0] = u0; uf[1] = u1; uf[2] = u2;
@@ -356,14 +347,11 @@ __global__ void k_sum_q(const double* __restrict__ q, int64_t n, double* out) {
 }
 
 template <class R>
-__global__ void k_lattice_from_aos3(const R* __restrict__ src, vec4<R>* __restrict__ dst, size_t nodes) {
+__global__ void k_lattice_from_aos3(const R* __restrict__ src, R* __restrict__ dst, size_t nodes) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes; i += (size_t)gridDim.x * blockDim.x) {
-        vec4<R> v;
-        v.x = src[3 * i + 0];
-        v.y = src[3 * i + 1];
-        v.z = src[3 * i + 2];
-        v.w = (R)0;
-        dst[i] = v;
+        dst[i] = src[3 * i + 0];
+        dst[nodes + i] = src[3 * i + 1];
+        dst[2 * nodes + i] = src[3 * i + 2];
     }
 }
 
@@ -378,7 +366,8 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     a.yf = c->d_yf; a.yf_up = c->d_yf_up; a.xf_up = c->d_xf_up; a.zf_up = c->d_zf_up;
     a.ybin = c->d_ybin; a.ybins = c->ybins; a.ybin_scale = (R)((double)c->ybins / c->ly);
     a.Yr = (const R*)c->d_Yr; a.invdY = (const R*)c->d_invdY;
-    a.u = (const vec4<R>*)c->u_lat; a.E = (const vec4<R>*)c->E_lat;
+    a.u = (const R*)c->u_lat; a.E = (const R*)c->E_lat;
+    a.nodes = (size_t)c->nz * (c->ny + 2) * c->nx;
     a.Q = nullptr; a.hist = nullptr; a.acc = c->d_acc;
     const tribo_params& P = c->P;
     a.drag_law = P.drag_law; a.impact_vel = P.impact_vel; a.dq_t = P.dq_t; a.electro = P.electrostatics;
@@ -608,10 +597,10 @@ tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev) {
     phase_begin(c, PH_AUX);
     if (c->prec == TRIBO_FP64)
         k_lattice_from_aos3<double><<<blocks, kThreads, 0, c->stream>>>((const double*)src_dev,
-                                                                        (vec4<double>*)c->u_lat, nodes);
+                                                                        (double*)c->u_lat, nodes);
     else
         k_lattice_from_aos3<float><<<blocks, kThreads, 0, c->stream>>>((const float*)src_dev,
-                                                                       (vec4<float>*)c->u_lat, nodes);
+                                                                       (float*)c->u_lat, nodes);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }

@@ -248,14 +248,14 @@ __global__ void k_solve_y(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F
 
 // ---------------------------------------------------------------- inv_x
 template <class R>
-__global__ void k_inv_x(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E, double* __restrict__ phi,
+__global__ void k_inv_x(const cplx<R>* __restrict__ F, R* __restrict__ E, double* __restrict__ phi,
                         int nx, int ny, int nz, int nxh, FftPlan plan, int lpb, int nf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* A = reinterpret_cast<cplx<R>*>(smem_raw);
     cplx<R>* B = A + lpb * nx;
-    R* out = reinterpret_cast<R*>(B + lpb * nx);   // [lpb][nx][4]
     const int nyn = ny + 2;
     const int nlines = nz * nyn;
+    const size_t nodes = (size_t)nlines * nx;   // E planes: E_x, E_y, E_z
     const size_t fstride = (size_t)nz * nyn * nxh;
     const int line0 = blockIdx.x * lpb;
     const int nl = min(lpb, nlines - line0);
@@ -272,7 +272,7 @@ __global__ void k_inv_x(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E, 
         for (int idx = threadIdx.x; idx < nl * nx; idx += blockDim.x) {
             const R v = res[idx].re * norm;
             if (f < 3) {
-                out[idx * 4 + f] = v;
+                E[f * nodes + (size_t)line0 * nx + idx] = v;
             } else {
                 const int line = line0 + idx / nx;
                 const int k = line / nyn;
@@ -286,20 +286,12 @@ __global__ void k_inv_x(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E, 
             cplx<R>* t = A; A = B; B = t;
         }
     }
-    for (int idx = threadIdx.x; idx < nl * nx; idx += blockDim.x) {
-        vec4<R> v;
-        v.x = out[idx * 4 + 0];
-        v.y = out[idx * 4 + 1];
-        v.z = out[idx * 4 + 2];
-        v.w = (R)0;
-        E[(size_t)line0 * nx + idx] = v;
-    }
 }
 
 template <class R>
 size_t smem_fwd_x(int nx, int lpb) { return sizeof(cplx<R>) * 2 * (size_t)lpb * nx; }
 template <class R>
-size_t smem_inv_x(int nx, int lpb) { return sizeof(cplx<R>) * 2 * (size_t)lpb * nx + sizeof(R) * 4 * (size_t)lpb * nx; }
+size_t smem_inv_x(int nx, int lpb) { return sizeof(cplx<R>) * 2 * (size_t)lpb * nx; }
 
 template <class R> int lines_per_block() { return sizeof(R) == 4 ? 4 : 2; }
 template <class R> int z_tile() { return sizeof(R) == 4 ? 8 : 4; }
@@ -374,7 +366,7 @@ tribo_status solve_impl(tribo_ctx* c, double* src, const double* scale, bool zer
         dim3 grid((nlines + lpb - 1) / lpb);
         phase_begin(c, PH_INV_X);
         k_inv_x<R><<<grid, kThreads, smem_inv_x<R>(nx, lpb), c->stream>>>(
-            F, (vec4<R>*)Evoid, phi, nx, ny, nz, nxh, c->plan_x, lpb, nf);
+            F, (R*)Evoid, phi, nx, ny, nz, nxh, c->plan_x, lpb, nf);
         TRIBO_LAUNCHED(c);
     }
     return TRIBO_OK;
@@ -665,7 +657,7 @@ tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, d
         F, nz, ny + 2, nxh, mt, pz, (R)1, fstride);
     const int nl2 = nz * (ny + 2);
     k_inv_x<R><<<(nl2 + lpb - 1) / lpb, kThreads, smem_inv_x<R>(nx, lpb), stream>>>(
-        F, (vec4<R>*)E, phi, nx, ny, nz, nxh, px, lpb, nf);
+        F, (R*)E, phi, nx, ny, nz, nxh, px, lpb, nf);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: kernel launch");
     return TRIBO_OK;

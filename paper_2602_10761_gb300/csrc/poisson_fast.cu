@@ -417,10 +417,10 @@ __global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ S
 // split step Z_m = (X_m + conj X_{M-m}) + i W^-m (X_m - conj X_{M-m}) and a
 // length-M inverse FFT; x_2n = Re z_n / (nx nz), x_2n+1 = Im z_n / (nx nz).
 template <class R, int M, int LPB>
-__global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F, vec4<R>* __restrict__ E,
+__global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F, R* __restrict__ E,
                                                    double* __restrict__ phi, int ny, int nz, size_t fstride,
                                                    const double* __restrict__ sinx, const cplx<R>* __restrict__ tw_g,
-                                                   int want_phi, R norm) {
+                                                   int want_phi, R norm, size_t nodes) {
     constexpr int NX = 2 * M;
     constexpr int NXH = M + 1;
     constexpr int NF = 4;
@@ -493,12 +493,13 @@ __global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F
         const cplx<R> ex = A[(0 * LPB + l) * ST + np_];
         const cplx<R> ey_ = A[(1 * LPB + l) * ST + np_];
         const cplx<R> ez = A[(2 * LPB + l) * ST + np_];
-        vec4<R> v0, v1;
-        v0.x = ex.re * norm; v0.y = ey_.re * norm; v0.z = ez.re * norm; v0.w = (R)0;
-        v1.x = ex.im * norm; v1.y = ey_.im * norm; v1.z = ez.im * norm; v1.w = (R)0;
         const size_t o = (size_t)(line0 + l) * NX + 2 * n;
-        E[o] = v0;
-        E[o + 1] = v1;
+        E[o] = ex.re * norm;
+        E[o + 1] = ex.im * norm;
+        E[nodes + o] = ey_.re * norm;
+        E[nodes + o + 1] = ey_.im * norm;
+        E[2 * nodes + o] = ez.re * norm;
+        E[2 * nodes + o + 1] = ez.im * norm;
         if (want_phi) {
             const int jn = sjn[l];
             if (jn >= 1 && jn <= ny) {
@@ -551,8 +552,8 @@ void launch_xinv(tribo_ctx* c, void* E, double* phi) {
     const int nlines = c->nz * (c->ny + 2);
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
     k_xinv<R, M, LPB><<<(nlines + LPB - 1) / LPB, kThreads, xinv_smem<R, M>(), c->stream>>>(
-        (const cplx<R>*)c->F, (vec4<R>*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
-        phi != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)));
+        (const cplx<R>*)c->F, (R*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
+        phi != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)), (size_t)c->nz * (c->ny + 2) * c->nx);
 }
 template <class R, int NZ>
 void launch_zfwd(tribo_ctx* c) {

@@ -325,9 +325,9 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
     TRY(build_tables(c));
     const size_t nodes = (size_t)nz * (ny + 2) * nx;
     const size_t rs = real_size(c);
-    TRYC(cudaMalloc(&c->u_lat, nodes * 4 * rs));
-    TRYC(cudaMalloc(&c->E_lat, nodes * 4 * rs));
-    TRYC(cudaMemset(c->E_lat, 0, nodes * 4 * rs));
+    TRYC(cudaMalloc(&c->u_lat, nodes * 3 * rs));
+    TRYC(cudaMalloc(&c->E_lat, nodes * 3 * rs));
+    TRYC(cudaMemset(c->E_lat, 0, nodes * 3 * rs));
     TRYC(cudaMalloc(&c->Q, sizeof(double) * (size_t)nx * ny * nz));
     TRYC(cudaMemset(c->Q, 0, sizeof(double) * (size_t)nx * ny * nz));
     TRYC(cudaMalloc(&c->d_acc, sizeof(Accum)));
@@ -348,7 +348,7 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
     TRY(poisson_setup(c));
     TRY(particles_setup(c));
     if (fluid) TRY(set_fluid_impl(c, fluid));
-    else TRYC(cudaMemset(c->u_lat, 0, nodes * 4 * rs));
+    else TRYC(cudaMemset(c->u_lat, 0, nodes * 3 * rs));
     TRYC(cudaDeviceSynchronize());
 #undef TRY
 #undef TRYC
@@ -437,8 +437,8 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
 
 tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E) {
     if (!c || !rho || !E) { set_last_error("ctx, rho and E must not be NULL"); return TRIBO_ERR_ARG; }
-    if (((uintptr_t)rho | (uintptr_t)phi) % 16 || (uintptr_t)E % (4 * real_size(c))) {
-        set_last_error("rho and phi must be 16-byte aligned, E aligned to one node (4 reals)");
+    if (((uintptr_t)rho | (uintptr_t)phi) % 16 || (uintptr_t)E % real_size(c)) {
+        set_last_error("rho and phi must be 16-byte aligned, E aligned to its real type");
         return TRIBO_ERR_ARG;
     }
     return poisson_solve(c, const_cast<double*>(rho), c->d_scale_rho, false, phi, E);

@@ -104,8 +104,8 @@ struct tribo_ctx {
     double* d_ey = nullptr;      // 4*(ny+2): coefficients of E_y at each lattice node
 
     // fields
-    void* u_lat = nullptr;       // (nz, ny+2, nx) vec4<real>
-    void* E_lat = nullptr;       // (nz, ny+2, nx) vec4<real>
+    void* u_lat = nullptr;       // (3, nz, ny+2, nx) real: u_x, u_y, u_z planes
+    void* E_lat = nullptr;       // (3, nz, ny+2, nx) real: E_x, E_y, E_z planes
     double* Q = nullptr;         // (nz, ny, nx) cell charge sums
     void* S = nullptr;           // (nz, ny, nxh) cplx<real> spectrum
     void* F = nullptr;           // (4, nz, ny+2, nxh) cplx<real> field spectra
@@ -176,7 +176,7 @@ tribo_status poisson_setup(tribo_ctx* c);
 tribo_status poisson_free(tribo_ctx* c);
 // src: device (nz, ny, nx) double; scale: device ny per-row factor giving the
 // RHS -rho/eps; zero_src: write zeros back into src after reading.
-// phi may be NULL.  E: (nz, ny+2, nx) vec4<real>.
+// phi may be NULL.  E: (3, nz, ny+2, nx) real (E_x, E_y, E_z).
 tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src,
                            double* phi, void* E);
 

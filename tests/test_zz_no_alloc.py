@@ -44,7 +44,7 @@ def test_noalloc_poisson_equals_context_poisson_twice(prec):
     for call, want_phi in ((0, True), (1, False)):
         rho = torch.from_numpy(rng.standard_normal((nz, ny, nx)) * 1e-6 + 1e-7 * call).cuda()
         phi_ref, E_ref = ch.poisson(rho, want_phi=want_phi)
-        E = torch.full((nz, ny + 2, nx, 4), float("nan"), dtype=rdt, device="cuda")
+        E = torch.full((3, nz, ny + 2, nx), float("nan"), dtype=rdt, device="cuda")
         phi = torch.full((nz, ny, nx), float("nan"), dtype=torch.float64, device="cuda") if want_phi else None
         T.tribo_poisson_noalloc(nx, ny, nz, lx, lz, faces, eps, prec, rho, phi, E)
         torch.cuda.synchronize()
