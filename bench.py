@@ -95,6 +95,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
+    when the kernel's sources changed after the counters were taken."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"{kernel}_re550_384.md")
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"<!-- traffic: (\{.*\}) -->", open(path).read())
+    if not m:
+        return None
+    info = json.loads(m.group(1))
+    h = hashlib.sha256()
+    for f in info["files"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return info["bytes_per_launch"] if h.hexdigest()[:16] == info["source_hash"] else None
+
+
 def touched_nodes(c, faces, x, y, z):
     """Distinct lattice nodes the trilinear gather touches (host count)."""
     nx, ny, nz = c.nx, c.ny, c.nz
@@ -312,8 +331,8 @@ def main():
                 "peak_kind": peak_kind}
     else:
         roof = {"bound": "hbm", "achieved": ach_step, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach_step / hbm_peak, "traffic": None, "kernel": "particle_step",
-                "peak_kind": peak_kind}
+                "frac": ach_step / hbm_peak, "traffic": measured_traffic("k_step"), "kernel": "k_step",
+                "alg_bytes": alg["particle_step"], "peak_kind": peak_kind}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
