@@ -140,6 +140,42 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
 /* Replace the gas-velocity lattice (e.g. a time-varying field). */
 tribo_status tribo_set_fluid(tribo_ctx* ctx, const tribo_fluid* fluid);
 
+/* Synthetic time-varying gas field, evaluated on the device at every step.
+ * It stands in for the paper's DNS/LES gas field (Sec. 2.1), which is not
+ * available; the paper has no counterpart for this recipe.  At lattice node
+ * (x, y, z) and time t:
+ *   u(x, t) = ubar(y) e_x + damp(y) sum_m amp_m cos(k_x,m (x - ubar(y) t)
+ *                                                  + ky_m y + k_z,m z + phase_m)
+ * with k_x,m = 2 pi nxi_m / lx and k_z,m = 2 pi nzi_m / lz: random Fourier
+ * modes advected with the local mean velocity.  All arrays are HOST arrays,
+ * copied by the call:
+ *   nxi, nzi : n_modes int32 integer wavenumbers, |nxi| < nx/2, |nzi| < nz/2
+ *   ky, phase: n_modes double [1/m], [rad]
+ *   amp      : (n_modes, 3) double amplitude vectors [m/s]
+ *   ubar, damp: ny+2 double at the lattice y nodes (wall nodes: ubar = damp = 0)
+ * t0 is the field time of the particle state at the next tribo_step; each
+ * step evaluates the field at the current time, then advances it by dt.
+ * 1 <= n_modes <= 4096.  Passing NULL switches back to the frozen lattice. */
+typedef struct {
+    int32_t n_modes;
+    const int32_t* nxi;
+    const int32_t* nzi;
+    const double* ky;
+    const double* amp;
+    const double* phase;
+    const double* ubar;
+    const double* damp;
+    double t0;
+} tribo_modes;
+
+tribo_status tribo_set_modes(tribo_ctx* ctx, const tribo_modes* modes);
+
+/* Evaluate the mode field of tribo_set_modes at time t.  u_out: device
+ * (3, Nz, Ny+2, Nx) "real" planes u_x, u_y, u_z, or NULL to write the
+ * context's own gas lattice.  TRIBO_ERR_ARG if no modes are set.
+ * Asynchronous. */
+tribo_status tribo_eval_modes(tribo_ctx* ctx, double t, void* u_out);
+
 /* Replace the physical parameters and switches (precision must not change). */
 tribo_status tribo_set_params(tribo_ctx* ctx, const tribo_params* params);
 
@@ -180,7 +216,7 @@ int64_t      tribo_launch_count(const tribo_ctx* ctx);
  * for phases 0..nphases-1, the summed device time [ms] and the launch count
  * since the last enable (ms, counts: host arrays of nphases entries).
  * tribo_phase_name gives the phase's kernel name (NULL past the last). */
-#define TRIBO_NPHASES 10
+#define TRIBO_NPHASES 11
 tribo_status tribo_timing_enable(tribo_ctx* ctx, int32_t on);
 tribo_status tribo_timing_read(tribo_ctx* ctx, double* ms, int64_t* counts, int32_t nphases);
 const char*  tribo_phase_name(int32_t phase);

@@ -189,16 +189,22 @@ def wall_impacts(p: Params, ly: float, y, vy, d):
 
 
 def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
-         diag: dict | None = None) -> State:
+         diag: dict | None = None, E_lat: np.ndarray | None = None) -> State:
     """One coupled particle step (deposit -> Poisson -> E -> gather -> push -> wall).
 
     u_lat: gas velocity on the wall-extended lattice (Nz, Ny+2, Nx, 3).
+    E_lat: optional field lattice of the same layout to use instead of the
+    field of st's own charges (replaying a subsample of a larger ensemble in
+    the field of all its particles).
     """
     n = st.n
     X = np.stack([st.x, st.y, st.z], axis=1)
     V = np.stack([st.vx, st.vy, st.vz], axis=1)
     uf = trilinear(g, u_lat, st.x, st.y, st.z)
-    if p.electrostatics:
+    if p.electrostatics and E_lat is not None:
+        Ep = trilinear(g, E_lat, st.x, st.y, st.z)
+        acc = (st.q / particle_mass(p, st.d))[:, None] * Ep
+    elif p.electrostatics:
         i, j, k = locate(g, st.x, st.y, st.z)
         rho = deposit(g, st.q, i, j, k)
         phi = poisson(g, rho, p.eps)

@@ -25,7 +25,7 @@ TRIBO_DRAG_SCHILLER_NAUMANN = 1
 TRIBO_DRAG_OFF = 2
 TRIBO_IMPACT_SPEED = 0
 TRIBO_IMPACT_NORMAL = 1
-TRIBO_NPHASES = 10
+TRIBO_NPHASES = 11
 
 
 class tribo_grid(C.Structure):
@@ -45,6 +45,12 @@ class tribo_fluid(C.Structure):
     _fields_ = [("u", C.c_void_p), ("on_host", C.c_int32)]
 
 
+class tribo_modes(C.Structure):
+    _fields_ = [("n_modes", C.c_int32), ("nxi", C.c_void_p), ("nzi", C.c_void_p), ("ky", C.c_void_p),
+                ("amp", C.c_void_p), ("phase", C.c_void_p), ("ubar", C.c_void_p), ("damp", C.c_void_p),
+                ("t0", C.c_double)]
+
+
 class tribo_particles(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(n, C.c_void_p) for n in ("x", "y", "z", "vx", "vy", "vz", "d")] + \
                [("q", C.c_void_p), ("q_wall", C.c_void_p), ("n_imp", C.c_void_p), ("id", C.c_void_p),
@@ -56,6 +62,8 @@ _SIGS = {
                                C.POINTER(tribo_params), C.c_int64, C.c_void_p]),
     "tribo_set_fluid": (C.c_int32, [C.c_void_p, C.POINTER(tribo_fluid)]),
     "tribo_set_params": (C.c_int32, [C.c_void_p, C.POINTER(tribo_params)]),
+    "tribo_set_modes": (C.c_int32, [C.c_void_p, C.POINTER(tribo_modes)]),
+    "tribo_eval_modes": (C.c_int32, [C.c_void_p, C.c_double, C.c_void_p]),
     "tribo_step": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.c_double, C.c_int32]),
     "tribo_poisson": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "tribo_poisson_noalloc": (C.c_int32, [C.POINTER(tribo_grid), C.c_double, C.c_int32, C.c_void_p,

@@ -166,6 +166,29 @@ def tribo_set_fluid(ctx: int, u_lattice) -> None:
     check(load().tribo_set_fluid(ctx, C.byref(fl)), "tribo_set_fluid")
 
 
+def tribo_set_modes(ctx: int, modes, ubar, damp, t0: float = 0.0) -> None:
+    """Time-varying synthetic gas field from Fourier modes (None: frozen lattice).
+
+    modes: object with nxi, nzi (integer wavenumbers), ky, amp (n, 3), phase;
+    ubar, damp: mean velocity and damping at the ny+2 lattice y nodes.
+    """
+    if modes is None:
+        check(load().tribo_set_modes(ctx, None), "tribo_set_modes")
+        return
+    keep = dict(nxi=np.ascontiguousarray(modes.nxi, np.int32), nzi=np.ascontiguousarray(modes.nzi, np.int32),
+                ky=np.ascontiguousarray(modes.ky, np.float64), amp=np.ascontiguousarray(modes.amp, np.float64),
+                phase=np.ascontiguousarray(modes.phase, np.float64), ubar=np.ascontiguousarray(ubar, np.float64),
+                damp=np.ascontiguousarray(damp, np.float64))
+    m = _abi.tribo_modes(int(keep["nxi"].shape[0]), *(keep[k].ctypes.data for k in
+                                                       ("nxi", "nzi", "ky", "amp", "phase", "ubar", "damp")),
+                         float(t0))
+    check(load().tribo_set_modes(ctx, C.byref(m)), "tribo_set_modes")
+
+
+def tribo_eval_modes(ctx: int, t: float, u_out=None) -> None:
+    check(load().tribo_eval_modes(ctx, float(t), _ptr(u_out)), "tribo_eval_modes")
+
+
 def tribo_set_params(ctx: int, params: Params) -> None:
     p = params.to_c()
     check(load().tribo_set_params(ctx, C.byref(p)), "tribo_set_params")
@@ -268,6 +291,17 @@ class Channel:
 
     def set_fluid(self, u_lattice) -> None:
         tribo_set_fluid(self.ctx, u_lattice)
+
+    def set_modes(self, modes, ubar=None, damp=None, t0: float = 0.0) -> None:
+        tribo_set_modes(self.ctx, modes, ubar, damp, t0)
+
+    def eval_modes(self, t: float):
+        """Mode field at time t as planes (3, Nz, Ny+2, Nx) on the device."""
+        import torch
+        rdt = torch.float64 if self.params.precision == _abi.TRIBO_FP64 else torch.float32
+        u = torch.empty((3, self.nz, self.ny + 2, self.nx), dtype=rdt, device="cuda")
+        tribo_eval_modes(self.ctx, t, u)
+        return u
 
     def set_params(self, params: Params) -> None:
         tribo_set_params(self.ctx, params)

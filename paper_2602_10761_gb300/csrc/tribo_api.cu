@@ -211,6 +211,7 @@ void free_ctx(tribo_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     poisson_free(c);
+    modes_free(c);
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
@@ -361,6 +362,17 @@ tribo_status tribo_set_fluid(tribo_ctx* c, const tribo_fluid* fluid) {
     return set_fluid_impl(c, fluid);
 }
 
+tribo_status tribo_set_modes(tribo_ctx* c, const tribo_modes* modes) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    return modes_set(c, modes);
+}
+
+tribo_status tribo_eval_modes(tribo_ctx* c, double t, void* u_out) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    if ((uintptr_t)u_out % real_size(c)) { set_last_error("u_out must be aligned to its real type"); return TRIBO_ERR_ARG; }
+    return modes_eval(c, t, u_out);
+}
+
 tribo_status tribo_set_params(tribo_ctx* c, const tribo_params* params) {
     if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
     tribo_status st = check_params(params);
@@ -418,11 +430,15 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             if ((st = particles_sort(c, cur, other))) return st;
             std::swap(cur, other);
         }
+        if (c->n_modes) {
+            if ((st = modes_eval(c, c->time, c->u_lat))) return st;
+        }
         if (electro) {
             if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
         }
         if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last))) return st;
         c->steps_done++;
+        c->time += dt;
     }
     if (cur.x != home.x) {
         if ((st = copy_view(c, home, cur))) return st;
@@ -531,7 +547,7 @@ namespace tribo {
 
 static const char* kPhaseNames[TRIBO_NPHASES] = {
     "particle_step", "deposit", "poisson_fwd_x", "poisson_fwd_z", "poisson_solve_y",
-    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux"};
+    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux", "fluid_modes"};
 
 static void flush_timing(tribo_ctx* c) {
     if (c->ev_used == 0) return;

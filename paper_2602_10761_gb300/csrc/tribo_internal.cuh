@@ -120,6 +120,17 @@ struct tribo_ctx {
     void* d_yads = nullptr;      // ny float2: y sub-diagonal in double-single (mixed mode)
     void* d_yec = nullptr;       // ny+1 float4: E_y coefficients per cell, walls (mixed mode)
 
+    // synthetic mode field (fluid.cu)
+    int n_modes = 0;
+    double time = 0.0;           // field time of the particle state at the next step
+    int2* d_mode_a = nullptr;    // per mode: nxi mod 2nx, nzi mod 2nz
+    double* d_mode_f = nullptr;  // per mode: kx, ky, phase, amp_x, amp_y, amp_z
+    double* d_ubar = nullptr;    // ny+2 mean velocity at the lattice y nodes
+    double* d_damp = nullptr;    // ny+2 damping factor
+    void* d_mode_c = nullptr;    // (ny+2, n_modes) cplx<real>: damp exp(i(ky y + phase - kx ubar t))
+    void* d_tabx = nullptr;      // 2nx cplx<real>: exp(i pi l / nx)
+    void* d_tabz = nullptr;      // 2nz cplx<real>
+
     // particle staging (host-pointer calls) and sort scratch
     void* stage = nullptr;       // device copy of host-pointer ensembles
     void* alt = nullptr;         // second particle set: the sort writes here, then the sets swap
@@ -151,7 +162,7 @@ namespace tribo {
 
 // kernel phases for timing
 enum Phase { PH_STEP = 0, PH_DEPOSIT, PH_FWD_X, PH_FWD_Z, PH_SOLVE_Y, PH_INV_Z, PH_INV_X, PH_SORT, PH_MISC,
-             PH_AUX };
+             PH_AUX, PH_FIELD };
 void phase_begin(tribo_ctx* c, int phase);
 void phase_end(tribo_ctx* c);
 
@@ -205,5 +216,11 @@ tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out);
 tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst);
 tribo_status particles_setup(tribo_ctx* c);
 tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev);
+
+// synthetic mode field (fluid.cu)
+tribo_status modes_set(tribo_ctx* c, const tribo_modes* m);
+void modes_free(tribo_ctx* c);
+// write the mode field at time t into dst (3 planes, real) or the context lattice
+tribo_status modes_eval(tribo_ctx* c, double t, void* dst);
 
 }  // namespace tribo

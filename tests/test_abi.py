@@ -54,9 +54,11 @@ int main(void) {
   printf("tribo_params %zu\n", sizeof(tribo_params));
   printf("tribo_fluid %zu\n", sizeof(tribo_fluid));
   printf("tribo_particles %zu\n", sizeof(tribo_particles));
+  printf("tribo_modes %zu\n", sizeof(tribo_modes));
   P(tribo_grid, lx) P(tribo_grid, y_faces)
   P(tribo_params, kappa_A) P(tribo_params, drag_law) P(tribo_params, sort_every)
   P(tribo_particles, x) P(tribo_particles, q) P(tribo_particles, cell) P(tribo_particles, on_host)
+  P(tribo_modes, nxi) P(tribo_modes, damp) P(tribo_modes, t0)
   return 0;
 }
 ''')
@@ -68,6 +70,7 @@ int main(void) {
     assert int(out["tribo_params"]) == C.sizeof(_abi.tribo_params)
     assert int(out["tribo_fluid"]) == C.sizeof(_abi.tribo_fluid)
     assert int(out["tribo_particles"]) == C.sizeof(_abi.tribo_particles)
+    assert int(out["tribo_modes"]) == C.sizeof(_abi.tribo_modes)
     for key, val in out.items():
         if "." in key:
             st, f = key.split(".")
