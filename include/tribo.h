@@ -192,6 +192,27 @@ tribo_status tribo_step(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t n
  * to its real type; TRIBO_ERR_ARG otherwise.  Asynchronous. */
 tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void* E);
 
+/* Reverse-mode derivative of the mean particle charge after nsteps coupled
+ * steps, J = (1/n) sum_p q_p(T) (the quantity behind the charging-rate
+ * statistics of Sec. 4.1), with respect to the condenser model's contact
+ * potential U_c and contact-area factor kappa_A (Sec. 2.3.1) and to each
+ * particle's diameter d_p (which enters the drag and the mass of Sec. 2.2 and
+ * the impact charge of Sec. 2.3.1).  It is the derivative of the discrete step
+ * map with every discrete decision (cell, interpolation stencil, wall
+ * contact) held at its forward value.
+ *   p: DEVICE particle arrays (on_host = 0), n >= 1; they are advanced
+ *      nsteps steps exactly as tribo_step would, except that they are never
+ *      re-sorted (sort_every is ignored), and the statistics accumulate.
+ *   ckpt_every >= 1: the forward pass stores the state every ckpt_every
+ *      steps; the backward pass recomputes each segment from its stored
+ *      state, keeping that segment's states (and field lattices) in a
+ *      workspace the context owns and keeps for later calls.
+ *   J, dJ_dUc, dJ_dkappaA: HOST doubles, each may be NULL.
+ *   dJ_dd: DEVICE array of n doubles (dJ/dd_p), may be NULL.
+ * Synchronises; TRIBO_ERR_OOM if the workspace cannot be allocated. */
+tribo_status tribo_adjoint(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t nsteps, int32_t ckpt_every,
+                           double* J, double* dJ_dUc, double* dJ_dkappaA, double* dJ_dd);
+
 /* Statistics since the last tribo_reset_stats (Sec. 4.1): sum of the current
  * particle charges of p (may be NULL: sum_q is then not written), total wall
  * impacts, total charge received from the walls, and the per-y-cell particle
@@ -216,7 +237,7 @@ int64_t      tribo_launch_count(const tribo_ctx* ctx);
  * for phases 0..nphases-1, the summed device time [ms] and the launch count
  * since the last enable (ms, counts: host arrays of nphases entries).
  * tribo_phase_name gives the phase's kernel name (NULL past the last). */
-#define TRIBO_NPHASES 11
+#define TRIBO_NPHASES 12
 tribo_status tribo_timing_enable(tribo_ctx* ctx, int32_t on);
 tribo_status tribo_timing_read(tribo_ctx* ctx, double* ms, int64_t* counts, int32_t nphases);
 const char*  tribo_phase_name(int32_t phase);

@@ -25,7 +25,7 @@ TRIBO_DRAG_SCHILLER_NAUMANN = 1
 TRIBO_DRAG_OFF = 2
 TRIBO_IMPACT_SPEED = 0
 TRIBO_IMPACT_NORMAL = 1
-TRIBO_NPHASES = 11
+TRIBO_NPHASES = 12
 
 
 class tribo_grid(C.Structure):
@@ -66,6 +66,9 @@ _SIGS = {
     "tribo_eval_modes": (C.c_int32, [C.c_void_p, C.c_double, C.c_void_p]),
     "tribo_step": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.c_double, C.c_int32]),
     "tribo_poisson": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "tribo_adjoint": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.c_double, C.c_int32, C.c_int32,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.c_void_p]),
     "tribo_poisson_noalloc": (C.c_int32, [C.POINTER(tribo_grid), C.c_double, C.c_int32, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]),
     "tribo_stats": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.POINTER(C.c_double),

@@ -203,6 +203,16 @@ def tribo_poisson(ctx: int, rho, phi, E) -> None:
     check(load().tribo_poisson(ctx, _ptr(rho), _ptr(phi), _ptr(E)), "tribo_poisson")
 
 
+def tribo_adjoint(ctx: int, particles: Particles, dt: float, nsteps: int, ckpt_every: int, dJ_dd=None):
+    """Advance the particles nsteps steps and return (J, dJ/dU_c, dJ/dkappa_A);
+    dJ_dd (device, n doubles) receives dJ/dd_p if given."""
+    s = particles.c_struct()
+    J, dU, dK = C.c_double(0.0), C.c_double(0.0), C.c_double(0.0)
+    check(load().tribo_adjoint(ctx, C.byref(s), float(dt), int(nsteps), int(ckpt_every), C.byref(J), C.byref(dU),
+                               C.byref(dK), _ptr(dJ_dd)), "tribo_adjoint")
+    return J.value, dU.value, dK.value
+
+
 def tribo_poisson_noalloc(nx: int, ny: int, nz: int, lx: float, lz: float, y_faces, eps: float,
                           precision: int, rho, phi, E, stream=None) -> None:
     """Context-free Poisson solve that allocates no device memory (for callers
@@ -291,6 +301,13 @@ class Channel:
 
     def set_fluid(self, u_lattice) -> None:
         tribo_set_fluid(self.ctx, u_lattice)
+
+    def adjoint(self, particles: Particles, dt: float, nsteps: int, ckpt_every: int = 50, want_dd: bool = True):
+        """(J, dJ/dU_c, dJ/dkappa_A, dJ/dd per particle or None); advances the particles."""
+        import torch
+        dd = torch.empty(particles.n, dtype=torch.float64, device="cuda") if want_dd else None
+        J, dU, dK = tribo_adjoint(self.ctx, particles, dt, nsteps, ckpt_every, dd)
+        return J, dU, dK, dd
 
     def set_modes(self, modes, ubar=None, damp=None, t0: float = 0.0) -> None:
         tribo_set_modes(self.ctx, modes, ubar, damp, t0)

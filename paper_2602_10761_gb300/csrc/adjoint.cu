@@ -1,0 +1,620 @@
+// Reverse-mode derivative of the mean particle charge after N coupled steps,
+//   J = (1/n) sum_p q_p(T),
+// with respect to the condenser model's contact potential U_c and contact-
+// area factor kappa_A (Sec. 2.3.1) and each particle's diameter d_p (which
+// enters the drag, the mass in q E / m_p and the impact charge).
+//
+// The derivative is that of the discrete step map with every discrete
+// decision held at its forward value: the cell of each particle (so the
+// nearest-grid-point deposit has no position derivative), the trilinear
+// stencil, and the wall contacts.  A step n -> n+1 is
+//   rho = deposit(q, cell(x));  phi = L^-1 (-rho/eps);  E = G phi;
+//   u_p = I(x) u;  E_p = I(x) E;  a = q E_p / m(d);  tau = tau(d, |v - u_p|);
+//   (x', v') = exponential push;  wall: y'' = 2 plane - y', v_y'' = -v_y';
+//   q'' = q + dq(d, |v''|, q; U_c, kappa_A).
+// Its transpose, per step, in reverse order:
+//   k_adj_step   per particle: recompute the forward step from the stored
+//                state n and the stored field, then propagate (x, v, q)-bar
+//                through the impact charge, the reflection, the push, the
+//                force and the gather; accumulate d-bar, U_c-bar, kappa_A-bar;
+//                scatter E_p-bar onto the field lattice (trilinear transpose).
+//   k_adj_grad   phi-bar = G^T E-bar (transpose of the Gauss-linear gradient).
+//   Poisson      the FV operator is L = D^-1 M with M symmetric and
+//                D = diag(dy_j), and the deposit scale is -1/(eps dx dy_j dz),
+//                so Q-bar = L^-1 (scale * phi-bar): the same solve as the
+//                forward field, with the same per-row scale.
+//   k_adj_deposit  q-bar_p += Q-bar[cell(x_p)] (transpose of the deposit).
+// Forward states are kept every ckpt_every steps; each segment is recomputed
+// from its checkpoint (states and field lattices of the segment stored) before
+// it is reversed.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "particle_math.cuh"
+
+namespace tribo {
+namespace {
+
+template <class R> __device__ __forceinline__ R rexp(R v);
+template <> __device__ __forceinline__ float rexp<float>(float v) { return expf(v); }
+template <> __device__ __forceinline__ double rexp<double>(double v) { return exp(v); }
+
+template <class R>
+__device__ __forceinline__ void atomic_add_r(R* p, R v);
+template <> __device__ __forceinline__ void atomic_add_r<float>(float* p, float v) { atomicAdd(p, v); }
+template <> __device__ __forceinline__ void atomic_add_r<double>(double* p, double v) { atomicAdd(p, v); }
+
+// one particle state (positions, velocities in real precision, charge FP64)
+template <class R>
+struct SView {
+    R *x, *y, *z, *vx, *vy, *vz;
+    double* q;
+};
+
+template <class R>
+struct AdjArgs {
+    SView<R> s;            // state n (read)
+    const R* d;            // diameters
+    SView<R> b;            // in: adjoint of state n+1; out: adjoint of state n
+    double* db;            // accumulated d-bar per particle
+    R* Eb;                 // field-lattice adjoint (3 planes), NULL without electrostatics
+    double* pacc;          // [0] U_c-bar, [1] kappa_A-bar
+    int64_t n;
+    double kappa_A;
+};
+
+// derivatives of the impact charge dq(d, speed, q) of impact_charge()
+struct ImpactGrad {
+    double dd, ds, dq, dU, dK;
+};
+
+template <class R>
+__device__ __forceinline__ ImpactGrad impact_grad(const StepArgs<R>& a, double kappa_A, double d, double speed,
+                                                  double q) {
+    ImpactGrad g{0, 0, 0, 0, 0};
+    if (!(speed > 0.0)) return g;
+    const double r = 0.5 * d;
+    const double P = pow(a.alpha_coef * speed * speed, 0.4);
+    const double alpha = r * P;
+    const double A = a.kappa_pi * r * alpha;
+    const double C = a.eps_over_h * A;
+    const double xw = 2.94 * alpha / speed * a.inv_T_w;     // dt_w / T_w
+    const double E1 = -expm1(-xw);
+    const double em = exp(-xw);
+    // dq_c = -C U_c E1 with C ~ d^2 speed^0.8, dt_w ~ d speed^-0.2
+    g.dU = -C * E1;
+    g.dK = -(a.eps_over_h * M_PI * r * alpha) * a.U_c * E1;
+    g.ds = -a.U_c * C / speed * (0.8 * E1 - 0.2 * xw * em);
+    g.dd = -a.U_c * C / d * (2.0 * E1 + xw * em);
+    if (a.dq_t) {
+        // dq_t = -(A / (pi d^2)) q; the area fraction does not depend on d
+        const double ft = A / (M_PI * d * d);
+        g.dq = -ft;
+        g.ds += -0.8 * ft * q / speed;
+        g.dK += -(M_PI * r * alpha / (M_PI * d * d)) * q;
+    }
+    (void)kappa_A;
+    return g;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kThreads) k_adj_step(StepArgs<R> a, AdjArgs<R> g) {
+    double pU = 0.0, pK = 0.0;
+    unsigned int err = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < g.n; n += stride) {
+        // ---- forward recomputation (the arithmetic of k_step) ----
+        const R x = g.s.x[n], z = g.s.z[n];
+        R y = g.s.y[n];
+        const R vx = g.s.vx[n], vy = g.s.vy[n], vz = g.s.vz[n];
+        const R d = g.d[n];
+        const double q = g.s.q[n];
+        if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
+        int j;
+        (void)cell_key<R>(x, y, z, a, &j);
+        Corners<R> cr;
+        corners<R>(a, x, y, z, j, cr, &err);
+        R uf[3] = {0, 0, 0}, Ep[3] = {0, 0, 0};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uf[0] += cr.w[c] * __ldg(a.u + cr.idx[c]);
+            uf[1] += cr.w[c] * __ldg(a.u + a.nodes + cr.idx[c]);
+            uf[2] += cr.w[c] * __ldg(a.u + 2 * a.nodes + cr.idx[c]);
+        }
+        R inv_m = 0, qm = 0;
+        if (a.electro) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                Ep[0] += cr.w[c] * __ldg(a.E + cr.idx[c]);
+                Ep[1] += cr.w[c] * __ldg(a.E + a.nodes + cr.idx[c]);
+                Ep[2] += cr.w[c] * __ldg(a.E + 2 * a.nodes + cr.idx[c]);
+            }
+            inv_m = (R)1 / (a.mass_coef * d * d * d);
+            qm = from_f64<R>(q) / (a.mass_coef * d * d * d);
+        }
+        const R acc[3] = {qm * Ep[0], qm * Ep[1], qm * Ep[2]};
+        const R v[3] = {vx, vy, vz};
+        R vn[3], T[3];
+        R tau = 0, s = 0, phi1 = 0, phi2 = 0, rel = 0, re = 0;
+        R yn;
+        if (a.drag_law == TRIBO_DRAG_OFF) {
+            const R h = (R)0.5 * a.dt * a.dt;
+            yn = y + vy * a.dt + acc[1] * h;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) vn[c] = v[c] + acc[c] * a.dt;
+        } else {
+            const R rx = vx - uf[0], ry = vy - uf[1], rz = vz - uf[2];
+            rel = rsqrt_(rx * rx + ry * ry + rz * rz);
+            const R tau_p = a.tau_coef * d * d;
+            tau = tau_p;
+            if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN) {
+                re = rel * d * a.inv_nu;
+                if (re > (R)1000) tau = a.sn_coef * d / rel;
+                else tau = tau_p / ((R)1 + rpow23(re) / (R)6);
+            }
+            s = a.dt / tau;
+            phi1 = -rexpm1(-s);
+            phi2 = phi2_of(s, phi1);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                T[c] = uf[c] + acc[c] * tau;
+                vn[c] = v[c] + (T[c] - v[c]) * phi1;
+            }
+            yn = y + tau * (vy * phi1 + T[1] * phi2);
+        }
+        const R r = (R)0.5 * d;
+        const bool lo = yn < r;
+        const bool hi = yn > a.ly - r;
+        const bool hit = lo || hi;
+
+        // ---- reverse ----
+        R xb[3] = {g.b.x[n], g.b.y[n], g.b.z[n]};
+        R vb[3] = {g.b.vx[n], g.b.vy[n], g.b.vz[n]};
+        const double qb = g.b.q[n];
+        double qb_in = qb;
+        double dbar = 0.0;
+        if (hit) {
+            const R vyh = -vn[1];                 // v_y after the reflection
+            double speed;
+            if (a.impact_vel == TRIBO_IMPACT_NORMAL) {
+                speed = fabs((double)vyh);
+            } else {
+                speed = sqrt((double)vn[0] * (double)vn[0] + (double)vyh * (double)vyh +
+                             (double)vn[2] * (double)vn[2]);
+            }
+            const ImpactGrad ig = impact_grad<R>(a, g.kappa_A, (double)d, speed, q);
+            qb_in += qb * ig.dq;
+            dbar += qb * ig.dd;
+            pU += qb * ig.dU;
+            pK += qb * ig.dK;
+            const double sb = qb * ig.ds;
+            if (speed > 0.0) {
+                if (a.impact_vel == TRIBO_IMPACT_NORMAL) {
+                    vb[1] += (R)(vyh > (R)0 ? sb : -sb);
+                } else {
+                    const double k = sb / speed;
+                    vb[0] += (R)(k * (double)vn[0]);
+                    vb[1] += (R)(k * (double)vyh);
+                    vb[2] += (R)(k * (double)vn[2]);
+                }
+            }
+            // y'' = 2 plane - y' with plane = r (bottom) or ly - r (top)
+            dbar += (double)(lo ? xb[1] : -xb[1]);
+            xb[1] = -xb[1];
+            vb[1] = -vb[1];
+        }
+        // push
+        R ab[3], ufb[3] = {0, 0, 0};
+        if (a.drag_law == TRIBO_DRAG_OFF) {
+            const R h = (R)0.5 * a.dt * a.dt;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ab[c] = a.dt * vb[c] + h * xb[c];
+                vb[c] = vb[c] + a.dt * xb[c];
+            }
+        } else {
+            R Tb[3];
+            R phi1b = 0, phi2b = 0, taub = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Tb[c] = phi1 * vb[c] + tau * phi2 * xb[c];
+                phi1b += vb[c] * (T[c] - v[c]) + tau * xb[c] * v[c];
+                phi2b += tau * xb[c] * T[c];
+                taub += xb[c] * (v[c] * phi1 + T[c] * phi2) + Tb[c] * acc[c];
+            }
+            const R em = rexp(-s);                // d phi1 / ds; d phi2 / ds = phi1
+            const R sbar = phi1b * em + phi2b * phi1;
+            taub += sbar * (-s / tau);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                vb[c] = ((R)1 - phi1) * vb[c] + tau * phi1 * xb[c];
+                ufb[c] = Tb[c];
+                ab[c] = tau * Tb[c];
+            }
+            // tau(d, rel)
+            R relb = 0;
+            if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN && re > (R)1000) {
+                dbar += (double)(taub * tau / d);
+                relb = -taub * tau / rel;
+            } else if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN) {
+                dbar += (double)(taub * (R)2 * tau / d);
+                if (re > (R)0) {
+                    const R f = (R)1 + rpow23(re) / (R)6;
+                    const R reb = -taub * tau / f * rpow23(re) / ((R)9 * re);
+                    dbar += (double)(reb * rel * a.inv_nu);
+                    relb = reb * d * a.inv_nu;
+                }
+            } else {
+                dbar += (double)(taub * (R)2 * tau / d);
+            }
+            if (rel > (R)0 && relb != (R)0) {
+                const R k = relb / rel;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const R dv = v[c] - uf[c];
+                    vb[c] += k * dv;
+                    ufb[c] -= k * dv;
+                }
+            }
+        }
+        // a = q E_p / m(d)
+        R Epb[3] = {0, 0, 0};
+        if (a.electro) {
+            R aE = 0, aa = 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Epb[c] = qm * ab[c];
+                aE += ab[c] * Ep[c];
+                aa += ab[c] * acc[c];
+            }
+            qb_in += (double)(aE * inv_m);
+            dbar += (double)((R)-3 * aa / d);
+        }
+        // gather: scatter E_p-bar, position derivative of the weights
+        R gc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            R gv = ufb[0] * __ldg(a.u + cr.idx[c]) + ufb[1] * __ldg(a.u + a.nodes + cr.idx[c]) +
+                   ufb[2] * __ldg(a.u + 2 * a.nodes + cr.idx[c]);
+            if (a.electro) {
+                gv += Epb[0] * __ldg(a.E + cr.idx[c]) + Epb[1] * __ldg(a.E + a.nodes + cr.idx[c]) +
+                      Epb[2] * __ldg(a.E + 2 * a.nodes + cr.idx[c]);
+            }
+            gc[c] = gv;
+        }
+        const R wx0 = (R)1 - cr.wx, wy0 = (R)1 - cr.wy, wz0 = (R)1 - cr.wz;
+        const R Wx[2] = {wx0, cr.wx}, Wy[2] = {wy0, cr.wy}, Wz[2] = {wz0, cr.wz};
+        R gx = 0, gy = 0, gz = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+            const R sx_ = bx ? (R)1 : (R)-1, sy_ = by ? (R)1 : (R)-1, sz_ = bz ? (R)1 : (R)-1;
+            gx += gc[c] * sx_ * Wz[bz] * Wy[by];
+            gy += gc[c] * sy_ * Wz[bz] * Wx[bx];
+            gz += gc[c] * sz_ * Wy[by] * Wx[bx];
+        }
+        xb[0] += gx * a.inv_dx;
+        xb[1] += gy * cr.inv_dy;
+        xb[2] += gz * a.inv_dz;
+        if (a.electro && (Epb[0] != (R)0 || Epb[1] != (R)0 || Epb[2] != (R)0)) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                atomic_add_r<R>(g.Eb + cr.idx[c], cr.w[c] * Epb[0]);
+                atomic_add_r<R>(g.Eb + a.nodes + cr.idx[c], cr.w[c] * Epb[1]);
+                atomic_add_r<R>(g.Eb + 2 * a.nodes + cr.idx[c], cr.w[c] * Epb[2]);
+            }
+        }
+        g.b.x[n] = xb[0]; g.b.y[n] = xb[1]; g.b.z[n] = xb[2];
+        g.b.vx[n] = vb[0]; g.b.vy[n] = vb[1]; g.b.vz[n] = vb[2];
+        g.b.q[n] = qb_in;
+        g.db[n] += dbar;
+    }
+    // parameter sums: warp reduction, one atomic per warp with a contribution
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pU += __shfl_down_sync(0xffffffffu, pU, o);
+        pK += __shfl_down_sync(0xffffffffu, pK, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (pU != 0.0 || pK != 0.0)) {
+        atomicAdd(&g.pacc[0], pU);
+        atomicAdd(&g.pacc[1], pK);
+    }
+    if (err) atomicOr(&a.acc->err, err);
+}
+
+// phi-bar = G^T E-bar on the cells.  E_x, E_z at interior node (k, j+1, i) are
+// -(phi[i+1] - phi[i-1]) / (2 dx) (and likewise in z); the wall nodes hold
+// E_x = E_z = 0.  E_y at the node of cell j' is -(phi_f[j'+1] - phi_f[j']) / dy_j'
+// with face values linear between centres and zero on the walls; the wall
+// nodes hold -phi_0 / (yc_0 - yf_0) and phi_ny-1 / (yf_ny - yc_ny-1).  So the
+// y part of phi-bar[j] is cym[j] E_y-bar[node j] + cy0[j] E_y-bar[node j+1] +
+// cyp[j] E_y-bar[node j+2] (node j is the bottom wall node for j = 0, node
+// j+2 the top wall node for j = ny-1).
+template <class R>
+__global__ void k_adj_grad(const R* __restrict__ Eb, const double* __restrict__ cy, double* __restrict__ out,
+                           int nx, int ny, int nz, double cx, double cz) {
+    const size_t ncell = (size_t)nx * ny * nz;
+    const size_t nodes = (size_t)nz * (ny + 2) * nx;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < ncell; e += stride) {
+        const int i = (int)(e % nx);
+        const size_t kj = e / nx;
+        const int j = (int)(kj % ny);
+        const int k = (int)(kj / ny);
+        const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+        const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
+        const size_t row = ((size_t)k * (ny + 2) + j + 1) * nx;
+        double v = cx * ((double)Eb[row + ip] - (double)Eb[row + im]);
+        const size_t rkp = ((size_t)kp * (ny + 2) + j + 1) * nx + i;
+        const size_t rkm = ((size_t)km * (ny + 2) + j + 1) * nx + i;
+        v += cz * ((double)Eb[2 * nodes + rkp] - (double)Eb[2 * nodes + rkm]);
+        const R* Ey = Eb + nodes;
+        v += cy[3 * j] * (double)Ey[row - nx + i] + cy[3 * j + 1] * (double)Ey[row + i] +
+             cy[3 * j + 2] * (double)Ey[row + nx + i];
+        out[e] = v;
+    }
+}
+
+// q-bar_p += Q-bar[cell of x_p]
+template <class R>
+__global__ void k_adj_deposit(StepArgs<R> a, SView<R> s, int64_t n, const double* __restrict__ Qb,
+                              double* __restrict__ qb) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        R y = s.y[p];
+        if (!(y >= (R)0 && y <= a.ly)) y = a.ly * (R)0.5;    // reported by k_adj_step
+        int j;
+        const uint32_t key = cell_key<R>(s.x[p], y, s.z[p], a, &j);
+        qb[p] += Qb[key];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+namespace {
+
+__global__ void k_fill_adjoint_start(double* qb, int64_t n, double v) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) qb[i] = v;
+}
+
+struct Carve {
+    char* base;
+    size_t off = 0;
+    void* take(size_t bytes) {
+        void* p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    }
+};
+
+template <class R>
+SView<R> take_state(Carve& cv, int64_t n) {
+    SView<R> s;
+    s.x = (R*)cv.take(n * sizeof(R)); s.y = (R*)cv.take(n * sizeof(R)); s.z = (R*)cv.take(n * sizeof(R));
+    s.vx = (R*)cv.take(n * sizeof(R)); s.vy = (R*)cv.take(n * sizeof(R)); s.vz = (R*)cv.take(n * sizeof(R));
+    s.q = (double*)cv.take(n * sizeof(double));
+    return s;
+}
+
+template <class R>
+struct AdjLayout {
+    std::vector<SView<R>> ckpt, seg;
+    std::vector<R*> segE;
+    SView<R> W, lam;
+    double* Wqw;
+    uint32_t* Wni;
+    R* Eb;
+    double* psi;
+    double* cy;
+    double* pacc;
+    double* db;
+    Accum* acc;
+};
+
+// carve the workspace (base NULL: only count the bytes)
+template <class R>
+size_t layout(AdjLayout<R>& L, char* base, int64_t n, int nseg, int C, bool electro, size_t nodes, size_t ncell,
+              int ny) {
+    Carve cv{base};
+    L.ckpt.resize(nseg);
+    for (int g = 0; g < nseg; ++g) L.ckpt[g] = take_state<R>(cv, n);
+    L.seg.resize(C);
+    for (int i = 0; i < C; ++i) L.seg[i] = take_state<R>(cv, n);
+    L.segE.assign(C, nullptr);
+    if (electro)
+        for (int i = 0; i < C; ++i) L.segE[i] = (R*)cv.take(3 * nodes * sizeof(R));
+    L.W = take_state<R>(cv, n);
+    L.Wqw = (double*)cv.take(n * sizeof(double));
+    L.Wni = (uint32_t*)cv.take(n * sizeof(uint32_t));
+    L.lam = take_state<R>(cv, n);
+    L.Eb = electro ? (R*)cv.take(3 * nodes * sizeof(R)) : nullptr;
+    L.psi = electro ? (double*)cv.take(ncell * sizeof(double)) : nullptr;
+    L.cy = (double*)cv.take(3 * (size_t)ny * sizeof(double));
+    L.pacc = (double*)cv.take(2 * sizeof(double));
+    L.db = (double*)cv.take(n * sizeof(double));
+    L.acc = (Accum*)cv.take(sizeof(Accum));
+    return cv.off;
+}
+
+template <class R>
+tribo_status copy_state(tribo_ctx* c, const SView<R>& dst, const SView<R>& src, int64_t n) {
+    R* d[6] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz};
+    const R* s[6] = {src.x, src.y, src.z, src.vx, src.vy, src.vz};
+    for (int k = 0; k < 6; ++k)
+        TRIBO_CUDA(cudaMemcpyAsync(d[k], s[k], n * sizeof(R), cudaMemcpyDeviceToDevice, c->stream));
+    TRIBO_CUDA(cudaMemcpyAsync(dst.q, src.q, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    return TRIBO_OK;
+}
+
+template <class R>
+SView<R> state_of(const PView& p) {
+    return SView<R>{(R*)p.x, (R*)p.y, (R*)p.z, (R*)p.vx, (R*)p.vy, (R*)p.vz, p.q};
+}
+
+// coefficients of the y part of G^T (see k_adj_grad), FP64
+std::vector<double> grad_transpose_y(const tribo_ctx* c) {
+    const int ny = c->ny;
+    std::vector<double> w(ny + 1, 0.0), cy(3 * (size_t)ny, 0.0);
+    for (int f = 1; f < ny; ++f) w[f] = (c->yf[f] - c->yc[f - 1]) / (c->yc[f] - c->yc[f - 1]);
+    const double h0 = c->yc[0] - c->yf[0], h1 = c->yf[ny] - c->yc[ny - 1];
+    for (int j = 0; j < ny; ++j) {
+        const double up = j <= ny - 2 ? 1.0 - w[j + 1] : 0.0;
+        const double dn = j >= 1 ? w[j] : 0.0;
+        cy[3 * j + 1] = -(up - dn) / c->dy[j];
+        cy[3 * j] = j >= 1 ? -w[j] / c->dy[j - 1] : -1.0 / h0;
+        cy[3 * j + 2] = j <= ny - 2 ? (1.0 - w[j + 1]) / c->dy[j + 1] : 1.0 / h1;
+    }
+    return cy;
+}
+
+template <class R>
+tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, int C, double* J, double* dUc,
+                          double* dK, double* dd) {
+    const int64_t n = P.n;
+    const bool electro = c->P.electrostatics != 0;
+    const int nseg = nsteps > 0 ? (nsteps + C - 1) / C : 0;
+    const int Cs = nsteps > 0 ? std::min(C, nsteps) : 0;
+    const size_t nodes = (size_t)c->nz * (c->ny + 2) * c->nx;
+    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+    AdjLayout<R> L;
+    const size_t bytes = layout<R>(L, nullptr, n, nseg, Cs, electro, nodes, ncell, c->ny);
+    if (bytes > c->adj_bytes) {
+        TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+        if (c->adj) cudaFree(c->adj);
+        c->adj = nullptr;
+        c->adj_bytes = 0;
+        TRIBO_CUDA(cudaMalloc(&c->adj, bytes));
+        c->adj_bytes = bytes;
+    }
+    layout<R>(L, (char*)c->adj, n, nseg, Cs, electro, nodes, ncell, c->ny);
+    double* db = dd ? dd : L.db;
+    const std::vector<double> cy = grad_transpose_y(c);
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    TRIBO_CUDA(cudaMemcpy(L.cy, cy.data(), sizeof(double) * cy.size(), cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemsetAsync(db, 0, n * sizeof(double), c->stream));
+    TRIBO_CUDA(cudaMemsetAsync(L.pacc, 0, 2 * sizeof(double), c->stream));
+    TRIBO_CUDA(cudaMemsetAsync(L.acc, 0, sizeof(Accum), c->stream));
+    tribo_status st;
+    const double t_start = c->time;
+    const size_t qbytes = ncell * sizeof(double);
+
+    // ---- forward pass on the caller's particles, with checkpoints
+    if (electro && nsteps > 0) {
+        TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, qbytes, c->stream));
+        if ((st = particles_deposit(c, P))) return st;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        if (s % C == 0 && (st = copy_state<R>(c, L.ckpt[s / C], state_of<R>(P), n))) return st;
+        if (c->n_modes && (st = modes_eval(c, t_start + s * dt, c->u_lat))) return st;
+        if (electro && (st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
+        if ((st = particles_step(c, P, dt, electro && s < nsteps - 1, P.cell != nullptr && s == nsteps - 1)))
+            return st;
+        c->steps_done++;
+    }
+    c->n_samples += nsteps;
+    c->time = t_start + nsteps * dt;
+    if ((st = particles_sum_q(c, P, c->d_scalar))) return st;
+
+    // ---- reverse sweep, one recomputed segment at a time
+    for (void* a : {(void*)L.lam.x, (void*)L.lam.y, (void*)L.lam.z, (void*)L.lam.vx, (void*)L.lam.vy,
+                    (void*)L.lam.vz})
+        TRIBO_CUDA(cudaMemsetAsync(a, 0, n * sizeof(R), c->stream));
+    phase_begin(c, PH_ADJOINT);
+    k_fill_adjoint_start<<<grid_for(n), kThreads, 0, c->stream>>>(L.lam.q, n, 1.0 / (double)n);
+    TRIBO_LAUNCHED(c);
+    PView Wp{};
+    Wp.n = n;
+    Wp.x = L.W.x; Wp.y = L.W.y; Wp.z = L.W.z; Wp.vx = L.W.vx; Wp.vy = L.W.vy; Wp.vz = L.W.vz;
+    Wp.d = P.d; Wp.q = L.W.q; Wp.q_wall = L.Wqw; Wp.n_imp = L.Wni;
+    StepIO io;
+    io.acc = L.acc;
+    io.stats = false;
+    for (int g = nseg - 1; g >= 0; --g) {
+        const int s0 = g * C;
+        const int len = std::min(C, nsteps - s0);
+        if ((st = copy_state<R>(c, L.W, L.ckpt[g], n))) return st;
+        if (electro) {
+            TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, qbytes, c->stream));
+            if ((st = particles_deposit(c, Wp))) return st;
+        }
+        for (int i = 0; i < len; ++i) {
+            if ((st = copy_state<R>(c, L.seg[i], L.W, n))) return st;
+            if (c->n_modes && (st = modes_eval(c, t_start + (s0 + i) * dt, c->u_lat))) return st;
+            if (electro && (st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, L.segE[i]))) return st;
+            if (i < len - 1) {
+                io.E = electro ? (const void*)L.segE[i] : nullptr;
+                if ((st = particles_step(c, Wp, dt, electro, false, io))) return st;
+            }
+        }
+        for (int i = len - 1; i >= 0; --i) {
+            if (c->n_modes && i < len - 1 && (st = modes_eval(c, t_start + (s0 + i) * dt, c->u_lat))) return st;
+            StepArgs<R> a = make_args<R>(c, dt);
+            if (electro) {
+                a.E = L.segE[i];
+                TRIBO_CUDA(cudaMemsetAsync(L.Eb, 0, 3 * nodes * sizeof(R), c->stream));
+            }
+            AdjArgs<R> ga{L.seg[i], (const R*)P.d, L.lam, db, L.Eb, L.pacc, n, c->P.kappa_A};
+            phase_begin(c, PH_ADJOINT);
+            k_adj_step<R><<<grid_for(n), kThreads, 0, c->stream>>>(a, ga);
+            TRIBO_LAUNCHED(c);
+            if (!electro) continue;
+            const int gb = (int)std::min<size_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
+            phase_begin(c, PH_ADJOINT);
+            k_adj_grad<R><<<gb, kThreads, 0, c->stream>>>(L.Eb, L.cy, c->Q, c->nx, c->ny, c->nz,
+                                                          0.5 / c->dx, 0.5 / c->dz);
+            TRIBO_LAUNCHED(c);
+            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, L.psi, c->E_lat))) return st;
+            phase_begin(c, PH_ADJOINT);
+            k_adj_deposit<R><<<grid_for(n), kThreads, 0, c->stream>>>(a, L.seg[i], n, L.psi, L.lam.q);
+            TRIBO_LAUNCHED(c);
+        }
+    }
+    double host[3] = {0, 0, 0};
+    TRIBO_CUDA(cudaMemcpyAsync(host, c->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TRIBO_CUDA(cudaMemcpyAsync(host + 1, L.pacc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    if (J) *J = host[0] / (double)n;
+    if (dUc) *dUc = host[1];
+    if (dK) *dK = host[2];
+    return TRIBO_OK;
+}
+
+}  // namespace
+}  // namespace tribo
+
+using namespace tribo;
+
+extern "C" tribo_status tribo_adjoint(tribo_ctx* c, tribo_particles* p, double dt, int32_t nsteps,
+                                      int32_t ckpt_every, double* J, double* dJ_dUc, double* dJ_dkappaA,
+                                      double* dJ_dd) {
+    if (!c || !p) { set_last_error("ctx and particles must not be NULL"); return TRIBO_ERR_ARG; }
+    if (p->on_host) { set_last_error("tribo_adjoint takes device particle arrays"); return TRIBO_ERR_ARG; }
+    if (p->n < 1 || p->n > 0xffffffffLL) { set_last_error("need 1 <= n < 2^32 particles"); return TRIBO_ERR_ARG; }
+    if (!p->x || !p->y || !p->z || !p->vx || !p->vy || !p->vz || !p->d || !p->q || !p->q_wall || !p->n_imp) {
+        set_last_error("a required particle array is NULL");
+        return TRIBO_ERR_ARG;
+    }
+    if (nsteps < 0 || ckpt_every < 1 || !(dt > 0) || !std::isfinite(dt)) {
+        set_last_error("need nsteps >= 0, ckpt_every >= 1 and dt > 0");
+        return TRIBO_ERR_ARG;
+    }
+    PView v{};
+    v.n = p->n;
+    v.x = p->x; v.y = p->y; v.z = p->z; v.vx = p->vx; v.vy = p->vy; v.vz = p->vz; v.d = p->d;
+    v.q = p->q; v.q_wall = p->q_wall; v.n_imp = p->n_imp; v.id = p->id; v.cell = p->cell;
+    tribo_status st = c->prec == TRIBO_FP64
+                          ? adjoint_impl<double>(c, v, dt, nsteps, ckpt_every, J, dJ_dUc, dJ_dkappaA, dJ_dd)
+                          : adjoint_impl<float>(c, v, dt, nsteps, ckpt_every, J, dJ_dUc, dJ_dkappaA, dJ_dd);
+    if (st) return st;
+    Accum a;
+    TRIBO_CUDA(cudaMemcpy(&a, c->d_acc, sizeof(Accum), cudaMemcpyDeviceToHost));
+    c->err_bits = a.err;
+    if (a.err) {
+        set_last_error("device error word set");
+        return TRIBO_ERR_DEVICE;
+    }
+    return TRIBO_OK;
+}

@@ -27,186 +27,11 @@
 // smallest float not below each FP64 face.
 #include <cmath>
 
-#include "tribo_internal.cuh"
+#include "particle_math.cuh"
 
 namespace tribo {
 
 namespace {
-
-constexpr int kThreads = 256;
-
-template <class R>
-struct StepArgs {
-    int nx, ny, nz, nyn;
-    R lx, ly, lz, inv_dx, inv_dz, dt;
-    double dx, dz;                 // FP64 cell sizes (exact locate in FP64 mode)
-    const double* yf;              // ny+1 FP64 faces
-    const float* yf_up;            // ny+1 rounded-up float faces
-    const float* xf_up;            // nx+1
-    const float* zf_up;            // nz+1
-    const int* ybin;
-    int ybins;
-    R ybin_scale;                  // ybins / ly
-    const R* Yr;                   // ny+2 lattice nodes
-    const R* invdY;                // ny+1 inverse node spacings
-    const R* u;                    // planes u_x, u_y, u_z, each `nodes` long
-    const R* E;                    // planes E_x, E_y, E_z, each `nodes` long
-    size_t nodes;
-    double* Q;                     // cell charge sums for the next step (may be NULL)
-    unsigned long long* hist;      // ny (may be NULL)
-    Accum* acc;
-    // physics
-    int drag_law, impact_vel, dq_t, electro;
-    R tau_coef;                    // rho_p / (18 rho nu)
-    R inv_nu;
-    R sn_coef;                     // (4/3)(rho_p/rho) / 0.424
-    R mass_coef;                   // pi rho_p / 6
-    double alpha_coef;             // 5/8 pi rho_p (1 + k_e) ((1-mu_p^2)/E_p + (1-mu_w^2)/E_w)
-    double kappa_pi;               // kappa_A pi
-    double eps_over_h;
-    double inv_T_w;
-    double U_c;
-};
-
-template <class R> __device__ __forceinline__ R rfloor(R v);
-template <> __device__ __forceinline__ float rfloor<float>(float v) { return floorf(v); }
-template <> __device__ __forceinline__ double rfloor<double>(double v) { return floor(v); }
-template <class R> __device__ __forceinline__ R rexpm1(R v);
-template <> __device__ __forceinline__ float rexpm1<float>(float v) { return expm1f(v); }
-template <> __device__ __forceinline__ double rexpm1<double>(double v) { return expm1(v); }
-template <class R> __device__ __forceinline__ R rsqrt_(R v);
-template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqrtf(v); }
-template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return sqrt(v); }
-template <class R> __device__ __forceinline__ R rpow23(R v);
-template <> __device__ __forceinline__ float rpow23<float>(float v) { return cbrtf(v * v); }
-template <> __device__ __forceinline__ double rpow23<double>(double v) { return cbrt(v * v); }
-template <class R> __device__ __forceinline__ bool rfinite(R v) { return isfinite(v); }
-
-// largest i in [0, n-1] with s >= face_i, faces i*h (FP64) -------------------
-__device__ __forceinline__ int cell_uniform(double s, double h, int n, const float*, double) {
-    int i = (int)floor(s / h);
-    i = min(max(i, 0), n - 1);
-    while (i > 0 && s < (double)i * h) --i;
-    while (i < n - 1 && s >= (double)(i + 1) * h) ++i;
-    return i;
-}
-__device__ __forceinline__ int cell_uniform(float s, float inv_h, int n, const float* f_up) {
-    int i = (int)floorf(s * inv_h);
-    i = min(max(i, 0), n - 1);
-    while (i > 0 && s < f_up[i]) --i;
-    while (i < n - 1 && s >= f_up[i + 1]) ++i;
-    return i;
-}
-template <class R>
-__device__ __forceinline__ int cell_y(R y, const StepArgs<R>& a) {
-    int b = (int)(y * a.ybin_scale);
-    b = min(max(b, 0), a.ybins - 1);
-    int j = a.ybin[b];
-    if (sizeof(R) == 8) {
-        const double yd = (double)y;
-        while (j > 0 && yd < a.yf[j]) --j;
-        while (j < a.ny - 1 && yd >= a.yf[j + 1]) ++j;
-    } else {
-        const float yfl = (float)y;
-        while (j > 0 && yfl < a.yf_up[j]) --j;
-        while (j < a.ny - 1 && yfl >= a.yf_up[j + 1]) ++j;
-    }
-    return j;
-}
-
-template <class R>
-__device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a, int* jout) {
-    int i, k;
-    if constexpr (sizeof(R) == 8) {
-        i = cell_uniform((double)x, a.dx, a.nx, a.xf_up, 0.0);
-        k = cell_uniform((double)z, a.dz, a.nz, a.zf_up, 0.0);
-    } else {
-        i = cell_uniform((float)x, (float)a.inv_dx, a.nx, a.xf_up);
-        k = cell_uniform((float)z, (float)a.inv_dz, a.nz, a.zf_up);
-    }
-    const int j = cell_y(y, a);
-    *jout = j;
-    return ((uint32_t)k * (uint32_t)a.ny + (uint32_t)j) * (uint32_t)a.nx + (uint32_t)i;
-}
-
-// trilinear gather of one or two lattice fields at (x, y, z) given the cell j
-template <class R>
-__device__ __forceinline__ void gather(const StepArgs<R>& a, R x, R y, R z, int j, R uf[3], R Ef[3],
-                                       bool withE, unsigned int* err) {
-    R sx = x * a.inv_dx - (R)0.5;
-    R fx = rfloor(sx);
-    R wx = sx - fx;
-    R sz = z * a.inv_dz - (R)0.5;
-    R fz = rfloor(sz);
-    R wz = sz - fz;
-    if (!(fx >= (R)-1 && fx <= (R)(a.nx - 1)) || !(fz >= (R)-1 && fz <= (R)(a.nz - 1))) {
-        *err |= TRIBO_DEV_OUTSIDE;
-        fx = 0; fz = 0; wx = 0; wz = 0;
-    }
-    int i0 = (int)fx, k0 = (int)fz;
-    int i1 = i0 + 1, k1 = k0 + 1;
-    if (i0 < 0) i0 += a.nx;
-    if (i1 >= a.nx) i1 -= a.nx;
-    if (k0 < 0) k0 += a.nz;
-    if (k1 >= a.nz) k1 -= a.nz;
-    const int jn0 = (y >= a.Yr[j + 1]) ? j + 1 : j;
-    const R wy = (y - a.Yr[jn0]) * a.invdY[jn0];
-    const R wx0 = (R)1 - wx, wy0 = (R)1 - wy, wz0 = (R)1 - wz;
-    const size_t r00 = ((size_t)k0 * a.nyn + jn0) * a.nx;
-    const size_t r01 = ((size_t)k0 * a.nyn + jn0 + 1) * a.nx;
-    const size_t r10 = ((size_t)k1 * a.nyn + jn0) * a.nx;
-    const size_t r11 = ((size_t)k1 * a.nyn + jn0 + 1) * a.nx;
-    const size_t idx[8] = {r00 + i0, r00 + i1, r01 + i0, r01 + i1, r10 + i0, r10 + i1, r11 + i0, r11 + i1};
-    const R w[8] = {wz0 * wy0 * wx0, wz0 * wy0 * wx, wz0 * wy * wx0, wz0 * wy * wx,
-                    wz * wy0 * wx0,  wz * wy0 * wx,  wz * wy * wx0,  wz * wy * wx};
-    R u0 = 0, u1 = 0, u2 = 0, e0 = 0, e1 = 0, e2 = 0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        u0 += w[c] * __ldg(a.u + idx[c]);
-        u1 += w[c] * __ldg(a.u + a.nodes + idx[c]);
-        u2 += w[c] * __ldg(a.u + 2 * a.nodes + idx[c]);
-    }
-    if (withE) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            e0 += w[c] * __ldg(a.E + idx[c]);
-            e1 += w[c] * __ldg(a.E + a.nodes + idx[c]);
-            e2 += w[c] * __ldg(a.E + 2 * a.nodes + idx[c]);
-        }
-    }
-    uf[0] = u0; uf[1] = u1; uf[2] = u2;
-    Ef[0] = e0; Ef[1] = e1; Ef[2] = e2;
-}
-
-template <class R>
-__device__ __forceinline__ R phi2_of(R s, R phi1) {
-    if (s < (R)0.5) {
-        // sum_{n>=2} (-1)^n s^n / n!, truncated below the precision's epsilon
-        const int nt = sizeof(R) == 8 ? 18 : 10;
-        R term = s * s * (R)0.5;
-        R sum = term;
-        for (int n = 3; n <= nt; ++n) {
-            term = -term * s / (R)n;
-            sum += term;
-        }
-        return sum;
-    }
-    return s - phi1;
-}
-
-// the condenser-model charge of one wall impact (FP64)
-template <class R>
-__device__ __forceinline__ double impact_charge(const StepArgs<R>& a, double d, double speed, double q) {
-    if (!(speed > 0.0)) return 0.0;
-    const double r = 0.5 * d;
-    const double alpha = r * pow(a.alpha_coef * speed * speed, 0.4);
-    const double A = a.kappa_pi * r * alpha;
-    const double C = a.eps_over_h * A;
-    const double dt_w = 2.94 * alpha / speed;
-    double dq = -C * a.U_c * (-expm1(-dt_w * a.inv_T_w));
-    if (a.dq_t) dq += -(A / (M_PI * d * d)) * q;
-    return dq;
-}
 
 template <class R>
 __global__ void __launch_bounds__(kThreads, 4) k_step(StepArgs<R> a, PView p, int write_cell) {
@@ -356,46 +181,13 @@ __global__ void k_lattice_from_aos3(const R* __restrict__ src, R* __restrict__ d
 }
 
 template <class R>
-StepArgs<R> make_args(tribo_ctx* c, double dt) {
-    StepArgs<R> a{};
-    a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.nyn = c->ny + 2;
-    a.lx = (R)c->lx; a.ly = (R)c->ly; a.lz = (R)c->lz;
-    a.inv_dx = (R)(1.0 / c->dx); a.inv_dz = (R)(1.0 / c->dz);
-    a.dt = (R)dt;
-    a.dx = c->dx; a.dz = c->dz;
-    a.yf = c->d_yf; a.yf_up = c->d_yf_up; a.xf_up = c->d_xf_up; a.zf_up = c->d_zf_up;
-    a.ybin = c->d_ybin; a.ybins = c->ybins; a.ybin_scale = (R)((double)c->ybins / c->ly);
-    a.Yr = (const R*)c->d_Yr; a.invdY = (const R*)c->d_invdY;
-    a.u = (const R*)c->u_lat; a.E = (const R*)c->E_lat;
-    a.nodes = (size_t)c->nz * (c->ny + 2) * c->nx;
-    a.Q = nullptr; a.hist = nullptr; a.acc = c->d_acc;
-    const tribo_params& P = c->P;
-    a.drag_law = P.drag_law; a.impact_vel = P.impact_vel; a.dq_t = P.dq_t; a.electro = P.electrostatics;
-    a.tau_coef = (R)(P.rho_p / (18.0 * P.rho * P.nu));
-    a.inv_nu = (R)(1.0 / P.nu);
-    a.sn_coef = (R)((4.0 / 3.0) * (P.rho_p / P.rho) / 0.424);
-    a.mass_coef = (R)(M_PI * P.rho_p / 6.0);
-    const double elastic = (1.0 - P.mu_p * P.mu_p) / P.E_p + (1.0 - P.mu_w * P.mu_w) / P.E_w;
-    a.alpha_coef = 0.625 * M_PI * P.rho_p * (1.0 + P.k_e) * elastic;
-    a.kappa_pi = P.kappa_A * M_PI;
-    a.eps_over_h = P.eps / P.h;
-    a.inv_T_w = 1.0 / (P.eps_w * P.eps0 * P.phi_p);
-    a.U_c = P.U_c;
-    return a;
-}
-
-int grid_for(int64_t n) {
-    int64_t b = (n + kThreads - 1) / kThreads;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    return (int)b;
-}
-
-template <class R>
-tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell) {
+tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell,
+                       const StepIO& io) {
     StepArgs<R> a = make_args<R>(c, dt);
     a.Q = deposit_next ? c->Q : nullptr;
-    a.hist = c->d_hist;
+    a.hist = io.stats ? c->d_hist : nullptr;
+    if (io.E) a.E = (const R*)io.E;
+    if (io.acc) a.acc = io.acc;
     const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
     phase_begin(c, PH_STEP);
     k_step<R><<<grid_for(p.n), kThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
@@ -570,10 +362,11 @@ tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst) {
     return sort_impl<float>(c, src, dst);
 }
 
-tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell) {
+tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell,
+                            const StepIO& io) {
     if (p.n == 0) return TRIBO_OK;
-    if (c->prec == TRIBO_FP64) return step_impl<double>(c, p, dt, deposit_next, write_cell);
-    return step_impl<float>(c, p, dt, deposit_next, write_cell);
+    if (c->prec == TRIBO_FP64) return step_impl<double>(c, p, dt, deposit_next, write_cell, io);
+    return step_impl<float>(c, p, dt, deposit_next, write_cell, io);
 }
 
 tribo_status particles_deposit(tribo_ctx* c, const PView& p) {

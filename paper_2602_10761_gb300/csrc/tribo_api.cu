@@ -215,7 +215,7 @@ void free_ctx(tribo_ctx* c) {
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
-                    c->sort_tiles};
+                    c->sort_tiles, c->adj};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -547,7 +547,7 @@ namespace tribo {
 
 static const char* kPhaseNames[TRIBO_NPHASES] = {
     "particle_step", "deposit", "poisson_fwd_x", "poisson_fwd_z", "poisson_solve_y",
-    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux", "fluid_modes"};
+    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux", "fluid_modes", "adjoint"};
 
 static void flush_timing(tribo_ctx* c) {
     if (c->ev_used == 0) return;

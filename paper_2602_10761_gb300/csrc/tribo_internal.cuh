@@ -140,6 +140,8 @@ struct tribo_ctx {
     uint32_t* sort_rank = nullptr;     // max_particles
     uint32_t* sort_tiles = nullptr;    // scan tile sums
     int64_t steps_done = 0;            // steps taken by this context (sort schedule)
+    void* adj = nullptr;               // adjoint workspace (checkpoints, segment states, adjoints)
+    size_t adj_bytes = 0;
 
     // statistics
     tribo::Accum* d_acc = nullptr;
@@ -162,7 +164,7 @@ namespace tribo {
 
 // kernel phases for timing
 enum Phase { PH_STEP = 0, PH_DEPOSIT, PH_FWD_X, PH_FWD_Z, PH_SOLVE_Y, PH_INV_Z, PH_INV_X, PH_SORT, PH_MISC,
-             PH_AUX, PH_FIELD };
+             PH_AUX, PH_FIELD, PH_ADJOINT };
 void phase_begin(tribo_ctx* c, int phase);
 void phase_end(tribo_ctx* c);
 
@@ -209,8 +211,13 @@ struct PView {               // device views of one particle ensemble
     uint32_t* cell;
 };
 tribo_status particles_deposit(tribo_ctx* c, const PView& p);
+struct StepIO {               // per-call overrides of the context's buffers
+    const void* E = nullptr;     // field lattice (NULL: the context's E lattice)
+    Accum* acc = nullptr;        // statistics and error word (NULL: the context's)
+    bool stats = true;           // add the positions to the y histogram
+};
 tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next,
-                            bool write_cell);
+                            bool write_cell, const StepIO& io = StepIO());
 tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out);
 // dst receives src sorted by cell key (all arrays; id if present)
 tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst);

@@ -1,0 +1,158 @@
+"""Parity of tribo_adjoint (reverse mode on the GPU, through the C ABI) with
+the oracle's gradient of the mean charge (autograd of the FP64 restatement
+of the oracle step, pinned in test_oracle_adjoint.py).
+
+FP64 mode: J to 1e-12, dJ/dU_c and dJ/dkappa_A to 1e-9, dJ/dd_p to 1e-9 of
+the largest |dJ/dd_p|.  Mixed mode (FP32 particle state and adjoints, FP64
+charge adjoints): 1e-4 for J, the parameter gradients and dJ/dd_p.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _problems import oracle_params, oracle_state, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2602_10761_gb300 as T  # noqa: E402
+from oracle.adjoint import mean_charge_gradient  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_10761_gb300 import build
+    build.build()
+    T.load()
+
+
+def _case(seed=4, n=150, shape=(16, 12, 8)):
+    c, faces, lat, parts = problem(*shape, n=n, q_scale=2e-13, vy_scale=0.4, near_wall=0.3, seed=seed,
+                                   dplus=(0.8, 2.5))
+    return c, faces, lat, parts
+
+
+def _round(parts, lat, prec):
+    real = np.float64 if prec == T.TRIBO_FP64 else np.float32
+    pr = {k: (v if k == "q" else np.asarray(v).astype(real).astype(np.float64)) for k, v in parts.items()}
+    return pr, lat.astype(real).astype(np.float64)
+
+
+def gpu_adjoint(c, faces, lat, parts, prec, dt, nsteps, ckpt, modes=None, **pkw):
+    real = np.float64 if prec == T.TRIBO_FP64 else np.float32
+    params = T.Params(precision=prec, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, **pkw)
+    u = torch.from_numpy(np.ascontiguousarray(lat.astype(real))).cuda()
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, u, max_particles=len(parts["x"]))
+    if modes is not None:
+        m, ub, dm = modes
+        ch.set_modes(m, ub, dm, 0.0)
+    P = T.Particles.from_numpy(parts, prec, device="cuda")
+    J, dU, dK, dd = ch.adjoint(P, dt, nsteps, ckpt)
+    out = P.to_numpy()
+    ch.close()
+    return dict(J=J, dU_c=dU, dkappa_A=dK, dd=dd.cpu().numpy(), final=out)
+
+
+def check(got, ref, tol, label):
+    assert abs(got["J"] - ref["J"]) <= tol * max(abs(ref["J"]), 1e-40), (label, got["J"], ref["J"])
+    for k in ("dU_c", "dkappa_A"):
+        assert abs(got[k] - ref[k]) <= tol * abs(ref[k]), (label, k, got[k], ref[k])
+    s = np.abs(ref["dd"]).max()
+    err = np.abs(got["dd"] - ref["dd"]).max() / s
+    assert err <= tol, (label, "dd", err)
+
+
+VARIANTS = [
+    dict(),
+    dict(drag_law=T.TRIBO_DRAG_SCHILLER_NAUMANN),
+    dict(drag_law=T.TRIBO_DRAG_OFF),
+    dict(impact_vel=T.TRIBO_IMPACT_NORMAL),
+    dict(dq_t=0),
+    dict(electrostatics=0),
+]
+
+
+def _okw(v):
+    o = dict(v)
+    if "electrostatics" in o:
+        o["electrostatics"] = bool(o["electrostatics"])
+    if "dq_t" in o:
+        o["dq_t"] = bool(o["dq_t"])
+    return o
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_adjoint_fp64_matches_oracle_gradient(variant):
+    c, faces, lat, parts = _case(seed=5)
+    dt, nsteps = 2 * c.dt, 7
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces),
+                               oracle_params(c, U_c=2e3, **_okw(variant)), oracle_state(parts), lat, dt, nsteps)
+    assert ref["final"]["n_imp"].sum() > 10
+    got = gpu_adjoint(c, faces, lat, parts, T.TRIBO_FP64, dt, nsteps, 3, U_c=2e3, **variant)
+    assert np.array_equal(got["final"]["n_imp"].astype(np.int64), ref["final"]["n_imp"])
+    check(got, ref, 1e-9, str(variant))
+
+
+@pytest.mark.parametrize("ckpt", [1, 2, 7, 50])
+def test_adjoint_independent_of_checkpoint_interval(ckpt):
+    c, faces, lat, parts = _case(seed=6, shape=(24, 16, 12))
+    dt, nsteps = 2 * c.dt, 7
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces), oracle_params(c, U_c=2e3),
+                               oracle_state(parts), lat, dt, nsteps)
+    got = gpu_adjoint(c, faces, lat, parts, T.TRIBO_FP64, dt, nsteps, ckpt, U_c=2e3)
+    check(got, ref, 1e-9, f"ckpt={ckpt}")
+
+
+def test_adjoint_mixed_precision():
+    c, faces, lat, parts = _case(seed=7, n=400, shape=(32, 24, 16))
+    pr, lat_r = _round(parts, lat, T.TRIBO_MIXED)
+    dt, nsteps = 2 * c.dt, 8
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces), oracle_params(c, U_c=2e3),
+                               oracle_state(pr), lat_r, dt, nsteps)
+    got = gpu_adjoint(c, faces, lat_r, pr, T.TRIBO_MIXED, dt, nsteps, 3, U_c=2e3)
+    assert np.array_equal(got["final"]["n_imp"].astype(np.int64), ref["final"]["n_imp"])
+    check(got, ref, 1e-4, "mixed")
+
+
+def test_adjoint_in_advected_field():
+    c, faces, _, parts = _case(seed=8, shape=(24, 16, 12))
+    modes = synth.draw_modes(c)
+    Y = synth.node_y(faces)
+    ub, dm = synth.mean_velocity(Y, c), synth.damping(Y, c)
+    dt, nsteps = 4 * c.dt, 6
+    lat_t = lambda t: synth.fluid_lattice(c, modes, t, faces)
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces), oracle_params(c, U_c=2e3),
+                               oracle_state(parts), lat_t, dt, nsteps)
+    got = gpu_adjoint(c, faces, lat_t(0.0), parts, T.TRIBO_FP64, dt, nsteps, 4, modes=(modes, ub, dm), U_c=2e3)
+    check(got, ref, 1e-9, "advected field")
+
+
+def test_adjoint_forward_state_equals_step():
+    c, faces, lat, parts = _case(seed=9, n=300, shape=(24, 16, 12))
+    dt, nsteps = 2 * c.dt, 9
+    got = gpu_adjoint(c, faces, lat, parts, T.TRIBO_FP64, dt, nsteps, 4, U_c=2e3)
+    params = T.Params(precision=T.TRIBO_FP64, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=2e3)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(), max_particles=300)
+    P = T.Particles.from_numpy(parts, T.TRIBO_FP64)
+    ch.step(P, dt, nsteps)
+    ref = P.to_numpy()
+    st = ch.stats(P)
+    ch.close()
+    for k in ("x", "y", "z", "vx", "vy", "vz", "q"):
+        s = max(np.abs(ref[k]).max(), 1e-40)
+        assert np.abs(got["final"][k] - ref[k]).max() <= 1e-13 * s, k
+    assert np.array_equal(got["final"]["n_imp"], ref["n_imp"])
+    assert abs(got["J"] - st["sum_q"] / 300) <= 1e-13 * np.abs(ref["q"]).max()
+
+
+def test_adjoint_rejects_host_arrays():
+    c, faces, lat, parts = _case(seed=2, n=10)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, T.Params(precision=T.TRIBO_FP64),
+                   torch.from_numpy(lat).cuda(), max_particles=10)
+    P = T.Particles.from_numpy(parts, T.TRIBO_FP64, device=None)
+    with pytest.raises(T.TriboError):
+        T.tribo_adjoint(ch.ctx, P, c.dt, 2, 1)
+    ch.close()
