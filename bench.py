@@ -164,6 +164,88 @@ def oracle_step_time(c, faces, lat, P, n_sample):
     return t_field, t_part
 
 
+def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
+    """Adjoint of the mean charge on the differentiation workload (Re_tau 180,
+    128^3, 1M particles, 500 steps, a state kept every `ckpt` steps): forward
+    and adjoint wall time, central differences with relative step h (and the
+    fraction of particles whose impact count differs between +h and -h), and
+    the mixed-precision gradients against the FP64 GPU path."""
+    c = synth.case("re180_128_adj")
+    nsteps = c.steps if steps is None else steps
+    faces, lat, P = make_inputs(c)
+    parts = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
+    base = dict(rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0)
+
+    def channel(prec):
+        real = np.float32 if prec == T.TRIBO_MIXED else np.float64
+        u = torch.from_numpy(np.ascontiguousarray(lat.astype(real))).cuda()
+        return T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, T.Params(precision=prec, **base), u,
+                         max_particles=c.n_particles)
+
+    def fresh(prec, d_scale=1.0):
+        q = dict(parts)
+        q["d"] = parts["d"] * d_scale
+        return T.Particles.from_numpy(q, prec, device="cuda")
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    mixed = channel(T.TRIBO_MIXED)
+    mixed.step(fresh(T.TRIBO_MIXED), c.dt, 20)
+    Pf = fresh(T.TRIBO_MIXED)
+    _, fwd_ms = timed(lambda: mixed.step(Pf, c.dt, nsteps))
+    mixed.adjoint(fresh(T.TRIBO_MIXED), c.dt, nsteps, ckpt)          # workspace allocation
+    Pa = fresh(T.TRIBO_MIXED)
+    (J, dU, dK, dd), adj_ms = timed(lambda: mixed.adjoint(Pa, c.dt, nsteps, ckpt))
+    dd = dd.cpu().numpy()
+    n_imp = int(Pa.to_numpy()["n_imp"].astype(np.int64).sum())
+
+    def J_of(d_scale=1.0, **kw):
+        mixed.set_params(T.Params(precision=T.TRIBO_MIXED, **{**base, **kw}))
+        Pq = fresh(T.TRIBO_MIXED, d_scale)
+        mixed.step(Pq, c.dt, nsteps)
+        out = Pq.to_numpy()
+        return float(out["q"].mean()), out["n_imp"].astype(np.int64)
+
+    def central(plus, minus, step):
+        (jp, ip), (jm, im) = plus, minus
+        return (jp - jm) / (2 * step), float(np.mean(ip != im))
+
+    fdU, flipU = central(J_of(U_c=1.0 + h), J_of(U_c=1.0 - h), h)
+    fdK, flipK = central(J_of(kappa_A=1.0 + h), J_of(kappa_A=1.0 - h), h)
+    fdD, flipD = central(J_of(d_scale=1.0 + h), J_of(d_scale=1.0 - h), h)   # d/d(log d) of all diameters
+    adjD = float(np.dot(dd, parts["d"].astype(np.float32).astype(np.float64)))
+    mixed.close()
+
+    fp64 = channel(T.TRIBO_FP64)
+    fp64.adjoint(fresh(T.TRIBO_FP64), c.dt, nsteps, ckpt)
+    P64 = fresh(T.TRIBO_FP64)
+    (J64, dU64, dK64, dd64), adj64_ms = timed(lambda: fp64.adjoint(P64, c.dt, nsteps, ckpt))
+    dd64 = dd64.cpu().numpy()
+    fp64.close()
+    rel = lambda a, b: abs(a - b) / max(abs(b), 1e-300)
+    return {
+        "workload": workload_desc(c) + f", {nsteps} steps, state kept every {ckpt}",
+        "fwd_ms": fwd_ms, "adjoint_ms": adj_ms, "adjoint_over_fwd": adj_ms / fwd_ms,
+        "J": J, "dJ_dUc": dU, "dJ_dkappaA": dK, "sum_d_dJ_dd": adjD, "impacts": n_imp,
+        "central_differences": {
+            "h_rel": h,
+            "dJ_dUc": fdU, "rel_err_Uc": rel(dU, fdU), "flip_frac_Uc": flipU,
+            "dJ_dkappaA": fdK, "rel_err_kappaA": rel(dK, fdK), "flip_frac_kappaA": flipK,
+            "dJ_dlogd": fdD, "rel_err_d": rel(adjD, fdD), "flip_frac_d": flipD},
+        "vs_fp64_gpu": {
+            "adjoint_ms_fp64": adj64_ms,
+            "rel_err_J": rel(J, J64), "rel_err_Uc": rel(dU, dU64), "rel_err_kappaA": rel(dK, dK64),
+            "rel_err_dd_max": float(np.abs(dd - dd64).max() / np.abs(dd64).max())},
+    }
+
+
 def cpu_baseline(c, faces, lat, P, n_sample):
     t_field, t_part = oracle_step_time(c, faces, lat, P, n_sample)
     t_full = t_field + t_part * (c.n_particles / n_sample)
@@ -219,6 +301,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=200_000)
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--sort-every", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -353,9 +436,11 @@ def main():
         "kernels": kern,
         "clocks": clocks,
     }
+    ch.close()
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_report(T, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, faces, lat, P, args.cpu_sample)
-    ch.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
