@@ -211,16 +211,27 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
         Pq = fresh(T.TRIBO_MIXED, d_scale)
         mixed.step(Pq, c.dt, nsteps)
         out = Pq.to_numpy()
-        return float(out["q"].mean()), out["n_imp"].astype(np.int64)
+        return out["q"].copy(), out["n_imp"].astype(np.int64)
 
-    def central(plus, minus, step):
-        (jp, ip), (jm, im) = plus, minus
-        return (jp - jm) / (2 * step), float(np.mean(ip != im))
+    n = c.n_particles
 
-    fdU, flipU = central(J_of(U_c=1.0 + h), J_of(U_c=1.0 - h), h)
-    fdK, flipK = central(J_of(kappa_A=1.0 + h), J_of(kappa_A=1.0 - h), h)
-    fdD, flipD = central(J_of(d_scale=1.0 + h), J_of(d_scale=1.0 - h), h)   # d/d(log d) of all diameters
-    adjD = float(np.dot(dd, parts["d"].astype(np.float32).astype(np.float64)))
+    def central(plus, minus, step, per_particle=None):
+        """Central difference of J; also restricted to the particles whose
+        impact count is the same at +h and -h (a flip is a jump of J, not a
+        derivative), against the adjoint's per-particle terms on that set."""
+        (qp, ip), (qm, im) = plus, minus
+        same = ip == im
+        out = {"fd": float((qp.mean() - qm.mean()) / (2 * step)), "flip_frac": float(1.0 - same.mean())}
+        if per_particle is not None:
+            out["fd_same_impacts"] = float((qp[same] - qm[same]).sum() / n / (2 * step))
+            out["adjoint_same_impacts"] = float(per_particle[same].sum())
+        return out
+
+    d32 = parts["d"].astype(np.float32).astype(np.float64)
+    cU = central(J_of(U_c=1.0 + h), J_of(U_c=1.0 - h), h)
+    cK = central(J_of(kappa_A=1.0 + h), J_of(kappa_A=1.0 - h), h)
+    cD = central(J_of(d_scale=1.0 + h), J_of(d_scale=1.0 - h), h, per_particle=dd * d32)
+    adjD = float(np.dot(dd, d32))
     mixed.close()
 
     fp64 = channel(T.TRIBO_FP64)
@@ -228,7 +239,9 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     P64 = fresh(T.TRIBO_FP64)
     (J64, dU64, dK64, dd64), adj64_ms = timed(lambda: fp64.adjoint(P64, c.dt, nsteps, ckpt))
     dd64 = dd64.cpu().numpy()
+    fin32, fin64 = Pa.to_numpy(), P64.to_numpy()
     fp64.close()
+    match = fin32["n_imp"] == fin64["n_imp"]
     rel = lambda a, b: abs(a - b) / max(abs(b), 1e-300)
     return {
         "workload": workload_desc(c) + f", {nsteps} steps, state kept every {ckpt}",
@@ -236,13 +249,19 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
         "J": J, "dJ_dUc": dU, "dJ_dkappaA": dK, "sum_d_dJ_dd": adjD, "impacts": n_imp,
         "central_differences": {
             "h_rel": h,
-            "dJ_dUc": fdU, "rel_err_Uc": rel(dU, fdU), "flip_frac_Uc": flipU,
-            "dJ_dkappaA": fdK, "rel_err_kappaA": rel(dK, fdK), "flip_frac_kappaA": flipK,
-            "dJ_dlogd": fdD, "rel_err_d": rel(adjD, fdD), "flip_frac_d": flipD},
+            "dJ_dUc": cU["fd"], "rel_err_Uc": rel(dU, cU["fd"]), "flip_frac_Uc": cU["flip_frac"],
+            "dJ_dkappaA": cK["fd"], "rel_err_kappaA": rel(dK, cK["fd"]), "flip_frac_kappaA": cK["flip_frac"],
+            "dJ_dlogd": cD["fd"], "flip_frac_d": cD["flip_frac"],
+            "dJ_dlogd_same_impacts": cD["fd_same_impacts"],
+            "adjoint_dJ_dlogd_same_impacts": cD["adjoint_same_impacts"],
+            "rel_err_d_same_impacts": rel(cD["adjoint_same_impacts"], cD["fd_same_impacts"])},
         "vs_fp64_gpu": {
             "adjoint_ms_fp64": adj64_ms,
-            "rel_err_J": rel(J, J64), "rel_err_Uc": rel(dU, dU64), "rel_err_kappaA": rel(dK, dK64),
-            "rel_err_dd_max": float(np.abs(dd - dd64).max() / np.abs(dd64).max())},
+            "impact_count_mismatch_frac": float(1.0 - match.mean()),
+            "rel_err_J": rel(J, J64),
+            "rel_err_J_matched": rel(fin32["q"][match].sum(), fin64["q"][match].sum()),
+            "rel_err_Uc": rel(dU, dU64), "rel_err_kappaA": rel(dK, dK64),
+            "rel_err_dd_matched_max": float(np.abs(dd - dd64)[match].max() / np.abs(dd64[match]).max())},
     }
 
 

@@ -283,6 +283,55 @@ def tribo_destroy(ctx: int) -> None:
     load().tribo_destroy(ctx)
 
 
+# ---------------------------------------------------------------- autograd
+
+def _mean_charge_function():
+    import torch
+
+    class MeanCharge(torch.autograd.Function):
+        """J = mean particle charge after nsteps steps, differentiable in U_c,
+        kappa_A and the diameters.  The forward pass runs tribo_adjoint, which
+        advances the particles and computes the gradients with the library's
+        reverse-mode kernels; backward scales them by the upstream gradient."""
+
+        @staticmethod
+        def forward(ctx, U_c, kappa_A, d, channel, particles, dt, nsteps, ckpt_every):
+            p = channel.params.with_(U_c=float(U_c), kappa_A=float(kappa_A))
+            channel.set_params(p)
+            particles.d.copy_(d.detach().to(particles.d.dtype))
+            dd = torch.empty(particles.n, dtype=torch.float64, device=particles.d.device)
+            J, dU, dK = tribo_adjoint(channel.ctx, particles, dt, nsteps, ckpt_every, dd)
+            ctx.save_for_backward(dd)
+            ctx.dU, ctx.dK = dU, dK
+            ctx.d_dtype = d.dtype
+            return torch.tensor(J, dtype=torch.float64, device=d.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (dd,) = ctx.saved_tensors
+            gU = gJ * ctx.dU if ctx.needs_input_grad[0] else None
+            gK = gJ * ctx.dK if ctx.needs_input_grad[1] else None
+            gd = (gJ * dd).to(ctx.d_dtype) if ctx.needs_input_grad[2] else None
+            return gU, gK, gd, None, None, None, None, None
+
+    return MeanCharge
+
+
+_MEAN_CHARGE = None
+
+
+def mean_charge(channel: "Channel", particles: Particles, dt: float, nsteps: int, U_c, kappa_A, d,
+                ckpt_every: int = 50):
+    """Differentiable mean charge after nsteps steps (torch.autograd).
+
+    U_c, kappa_A: 0-dim tensors; d: (n,) tensor of diameters on the device.
+    The particles (device arrays) are advanced nsteps steps in place."""
+    global _MEAN_CHARGE
+    if _MEAN_CHARGE is None:
+        _MEAN_CHARGE = _mean_charge_function()
+    return _MEAN_CHARGE.apply(U_c, kappa_A, d, channel, particles, dt, nsteps, ckpt_every)
+
+
 # ---------------------------------------------------------------- convenience
 
 class Channel:

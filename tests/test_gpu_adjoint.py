@@ -156,3 +156,22 @@ def test_adjoint_rejects_host_arrays():
     with pytest.raises(T.TriboError):
         T.tribo_adjoint(ch.ctx, P, c.dt, 2, 1)
     ch.close()
+
+
+def test_autograd_function_matches_oracle_gradient():
+    c, faces, lat, parts = _case(seed=12)
+    dt, nsteps = 2 * c.dt, 6
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces), oracle_params(c, U_c=2e3),
+                               oracle_state(parts), lat, dt, nsteps)
+    params = T.Params(precision=T.TRIBO_FP64, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=2e3)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(),
+                   max_particles=len(parts["x"]))
+    P = T.Particles.from_numpy(parts, T.TRIBO_FP64)
+    U = torch.tensor(2e3, dtype=torch.float64, requires_grad=True)
+    K = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    d = torch.from_numpy(parts["d"].copy()).cuda().requires_grad_(True)
+    J = T.mean_charge(ch, P, dt, nsteps, U, K, d, ckpt_every=4)
+    (3.0 * J).backward()
+    ch.close()
+    got = dict(J=float(J), dU_c=float(U.grad) / 3, dkappa_A=float(K.grad) / 3, dd=d.grad.cpu().numpy() / 3)
+    check(got, ref, 1e-9, "autograd")
