@@ -304,13 +304,15 @@ def _mean_charge_function():
             ctx.save_for_backward(dd)
             ctx.dU, ctx.dK = dU, dK
             ctx.d_dtype = d.dtype
+            dev = lambda t: t.device if isinstance(t, torch.Tensor) else None
+            ctx.devs = (dev(U_c), dev(kappa_A))
             return torch.tensor(J, dtype=torch.float64, device=d.device)
 
         @staticmethod
         def backward(ctx, gJ):
             (dd,) = ctx.saved_tensors
-            gU = gJ * ctx.dU if ctx.needs_input_grad[0] else None
-            gK = gJ * ctx.dK if ctx.needs_input_grad[1] else None
+            gU = (gJ * ctx.dU).to(ctx.devs[0]) if ctx.needs_input_grad[0] else None
+            gK = (gJ * ctx.dK).to(ctx.devs[1]) if ctx.needs_input_grad[1] else None
             gd = (gJ * dd).to(ctx.d_dtype) if ctx.needs_input_grad[2] else None
             return gU, gK, gd, None, None, None, None, None
 
