@@ -260,6 +260,43 @@ const char*  tribo_phase_name(int32_t phase);
 tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps, int32_t precision,
                                    const double* rho, double* phi, void* E, void* stream);
 
+/* Batched ensemble: many independent channels (each made by tribo_init with
+ * its own grid, gas lattice, parameters and max_particles >= its particle
+ * count) advanced together, as in the paper's sweeps over Re_tau and particle
+ * size (Sec. 4).  Every step forks one branch per channel (cell sort when
+ * due, Poisson solve and field) and joins in ONE persistent particle kernel
+ * over all channels' particles; steps are captured into a CUDA graph and
+ * replayed.  The channels must share precision and device and use frozen
+ * gas lattices (no tribo_set_modes).  While a batch exists, its channels must
+ * not be stepped on their own concurrently with it.  sort_every: re-sort each
+ * channel's particles by cell every this many batch steps (0 = never).
+ * stream: a cudaStream_t (NULL = legacy default) on which the batch joins. */
+typedef struct tribo_batch tribo_batch;
+tribo_status tribo_batch_create(tribo_batch** out, int32_t n_channels, tribo_ctx* const* channels,
+                                int32_t sort_every, void* stream);
+
+/* Time the candidate shapes of the particle kernel (threads per block,
+ * particles per tile, blocks per SM) on scratch copies of the particles and
+ * keep the fastest; choice (3 int32, may be NULL) receives it.  The particles
+ * are not changed.  tribo_batch_step tunes on its first call if this was not
+ * called.  particles: host array of n_channels pointers to ensembles of DEVICE
+ * arrays; dt: host array of n_channels step lengths.  Synchronises. */
+tribo_status tribo_batch_autotune(tribo_batch* b, tribo_particles* const* particles, const double* dt,
+                                  int32_t* choice);
+
+/* Advance every channel nsteps steps (channel i with dt[i]); arguments as for
+ * tribo_batch_autotune.  Asynchronous on the batch's stream; statistics and
+ * error words accumulate in each channel's context. */
+tribo_status tribo_batch_step(tribo_batch* b, tribo_particles* const* particles, const double* dt, int32_t nsteps);
+
+/* Wait for the batch's stream; report any channel's device error word. */
+tribo_status tribo_batch_sync(tribo_batch* b);
+
+/* Kernels the batch has executed (direct launches plus the kernels of each
+ * graph replay). */
+int64_t      tribo_batch_launch_count(const tribo_batch* b);
+void         tribo_batch_destroy(tribo_batch* b);
+
 const char*  tribo_strerror(tribo_status s);
 const char*  tribo_last_error(void);      /* thread-local detail of the last failure */
 void         tribo_destroy(tribo_ctx* ctx);

@@ -82,6 +82,15 @@ _SIGS = {
     "tribo_timing_enable": (C.c_int32, [C.c_void_p, C.c_int32]),
     "tribo_timing_read": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),
     "tribo_phase_name": (C.c_char_p, [C.c_int32]),
+    "tribo_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p), C.c_int32,
+                                       C.c_void_p]),
+    "tribo_batch_autotune": (C.c_int32, [C.c_void_p, C.POINTER(C.POINTER(tribo_particles)), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int32)]),
+    "tribo_batch_step": (C.c_int32, [C.c_void_p, C.POINTER(C.POINTER(tribo_particles)), C.POINTER(C.c_double),
+                                     C.c_int32]),
+    "tribo_batch_sync": (C.c_int32, [C.c_void_p]),
+    "tribo_batch_launch_count": (C.c_int64, [C.c_void_p]),
+    "tribo_batch_destroy": (None, [C.c_void_p]),
     "tribo_strerror": (C.c_char_p, [C.c_int32]),
     "tribo_last_error": (C.c_char_p, []),
     "tribo_destroy": (None, [C.c_void_p]),

@@ -283,6 +283,55 @@ def tribo_destroy(ctx: int) -> None:
     load().tribo_destroy(ctx)
 
 
+# ---------------------------------------------------------------- batched ensemble
+
+class Batch:
+    """Independent channels advanced together (tribo_batch_*)."""
+
+    def __init__(self, channels, sort_every: int = 0, stream=None):
+        lib = load()
+        self.channels = list(channels)
+        arr = (C.c_void_p * len(self.channels))(*[ch.ctx for ch in self.channels])
+        h = C.c_void_p()
+        sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        check(lib.tribo_batch_create(C.byref(h), len(self.channels), arr, int(sort_every), sp), "tribo_batch_create")
+        self.handle = h.value
+
+    def _args(self, particles, dt):
+        structs = [p.c_struct() for p in particles]
+        ptrs = (C.POINTER(_abi.tribo_particles) * len(structs))(*[C.pointer(s) for s in structs])
+        dts = (C.c_double * len(structs))(*[float(x) for x in dt])
+        return structs, ptrs, dts
+
+    def autotune(self, particles, dt):
+        keep, ptrs, dts = self._args(particles, dt)
+        choice = (C.c_int32 * 3)()
+        check(load().tribo_batch_autotune(self.handle, ptrs, dts, choice), "tribo_batch_autotune")
+        return dict(threads=choice[0], tile=choice[1], blocks_per_sm=choice[2])
+
+    def step(self, particles, dt, nsteps: int) -> None:
+        keep, ptrs, dts = self._args(particles, dt)
+        check(load().tribo_batch_step(self.handle, ptrs, dts, int(nsteps)), "tribo_batch_step")
+
+    def sync(self) -> None:
+        check(load().tribo_batch_sync(self.handle), "tribo_batch_sync")
+
+    @property
+    def launches(self) -> int:
+        return int(load().tribo_batch_launch_count(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            load().tribo_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------- autograd
 
 def _mean_charge_function():

@@ -41,96 +41,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_step(StepArgs<R> a, PView p, in
         for (int b = threadIdx.x; b < a.ny; b += blockDim.x) sh_hist[b] = 0u;
         __syncthreads();
     }
-    R* X = (R*)p.x; R* Y = (R*)p.y; R* Z = (R*)p.z;
-    R* VX = (R*)p.vx; R* VY = (R*)p.vy; R* VZ = (R*)p.vz;
-    const R* D = (const R*)p.d;
     unsigned int err = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride) {
-        R x = X[n], y = Y[n], z = Z[n];
-        R vx = VX[n], vy = VY[n], vz = VZ[n];
-        const R d = D[n];
-        double q = p.q[n];
-        if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
-        int j;
-        (void)cell_key<R>(x, y, z, a, &j);
-        R uf[3], Ef[3];
-        gather<R>(a, x, y, z, j, uf, Ef, a.electro != 0, &err);
-        // acceleration q E / m
-        R ax = 0, ay = 0, az = 0;
-        if (a.electro) {
-            const R qm = from_f64<R>(q) / (a.mass_coef * d * d * d);
-            ax = qm * Ef[0]; ay = qm * Ef[1]; az = qm * Ef[2];
-        }
-        R xn, yn, zn, vxn, vyn, vzn;
-        if (a.drag_law == TRIBO_DRAG_OFF) {
-            const R h = (R)0.5 * a.dt * a.dt;
-            xn = x + vx * a.dt + ax * h;
-            yn = y + vy * a.dt + ay * h;
-            zn = z + vz * a.dt + az * h;
-            vxn = vx + ax * a.dt; vyn = vy + ay * a.dt; vzn = vz + az * a.dt;
-        } else {
-            const R rx = vx - uf[0], ry = vy - uf[1], rz = vz - uf[2];
-            const R rel = rsqrt_(rx * rx + ry * ry + rz * rz);
-            const R tau_p = a.tau_coef * d * d;
-            R tau = tau_p;
-            if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN) {
-                const R re = rel * d * a.inv_nu;
-                if (re > (R)1000) tau = a.sn_coef * d / rel;
-                else tau = tau_p / ((R)1 + rpow23(re) / (R)6);
-            }
-            const R s = a.dt / tau;
-            const R phi1 = -rexpm1(-s);
-            const R phi2 = phi2_of(s, phi1);
-            const R tx = uf[0] + ax * tau, ty = uf[1] + ay * tau, tz = uf[2] + az * tau;
-            vxn = vx + (tx - vx) * phi1;
-            vyn = vy + (ty - vy) * phi1;
-            vzn = vz + (tz - vz) * phi1;
-            xn = x + tau * (vx * phi1 + tx * phi2);
-            yn = y + tau * (vy * phi1 + ty * phi2);
-            zn = z + tau * (vz * phi1 + tz * phi2);
-        }
-        // periodic wrap in x and z
-        xn = xn - a.lx * rfloor(xn / a.lx);
-        if (xn >= a.lx) xn -= a.lx;
-        zn = zn - a.lz * rfloor(zn / a.lz);
-        if (zn >= a.lz) zn -= a.lz;
-        // wall contact (hard sphere, specular)
-        const R r = (R)0.5 * d;
-        const bool lo = yn < r;
-        const bool hi = yn > a.ly - r;
-        if (lo || hi) {
-            // mirror about the contact plane; the charge transfer is FP64
-            const double rd = 0.5 * (double)d;
-            const double plane = lo ? rd : (double)a.ly - rd;
-            const double ym = 2.0 * plane - (double)yn;
-            yn = (R)ym;
-            vyn = -vyn;
-            if (yn < r || yn > a.ly - r) err |= TRIBO_DEV_ESCAPED;
-            double speed;
-            if (a.impact_vel == TRIBO_IMPACT_NORMAL) {
-                speed = fabs((double)vyn);
-            } else {
-                speed = sqrt((double)vxn * (double)vxn + (double)vyn * (double)vyn + (double)vzn * (double)vzn);
-            }
-            const double dq = impact_charge<R>(a, (double)d, speed, q);
-            q += dq;
-            p.q[n] = q;
-            p.q_wall[n] += dq;
-            p.n_imp[n] += 1u;
-            atomicAdd(&a.acc->sum_wall, dq);
-            atomicAdd(&a.acc->n_impacts, 1ull);
-        }
-        if (!(rfinite(xn) && rfinite(yn) && rfinite(zn) && rfinite(vxn) && rfinite(vyn) && rfinite(vzn)))
-            err |= TRIBO_DEV_NONFINITE;
-        X[n] = xn; Y[n] = yn; Z[n] = zn;
-        VX[n] = vxn; VY[n] = vyn; VZ[n] = vzn;
-        int jn;
-        const uint32_t key = cell_key<R>(xn, yn, zn, a, &jn);
-        if (a.Q) atomicAdd(&a.Q[key], q);
-        if (write_cell) p.cell[n] = key;
-        if (use_hist) atomicAdd(&sh_hist[jn], 1u);
-    }
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride)
+        step_one<R>(a, p, n, write_cell, sh_hist, use_hist, err);
     if (err) atomicOr(&a.acc->err, err);
     if (use_hist) {
         __syncthreads();

@@ -110,45 +110,6 @@ struct Stage {
     static size_t bytes(int64_t n, size_t rs) { return (size_t)n * (7 * rs + 2 * sizeof(double) + 3 * sizeof(uint32_t)) + 1024; }
 };
 
-PView set_view(tribo_ctx* c, void* base, int64_t n) {
-    const size_t rs = real_size(c);
-    char* b = (char*)base;
-    const size_t cap = (size_t)c->max_particles;
-    PView v{};
-    v.n = n;
-    size_t off = 0;
-    auto take = [&](size_t elem) { void* p = b + off; off += ((elem * cap + 255) / 256) * 256; return p; };
-    v.x = take(rs); v.y = take(rs); v.z = take(rs);
-    v.vx = take(rs); v.vy = take(rs); v.vz = take(rs); v.d = take(rs);
-    v.q = (double*)take(sizeof(double));
-    v.q_wall = (double*)take(sizeof(double));
-    v.n_imp = (uint32_t*)take(sizeof(uint32_t));
-    v.id = (uint32_t*)take(sizeof(uint32_t));
-    v.cell = (uint32_t*)take(sizeof(uint32_t));
-    return v;
-}
-
-PView stage_view(tribo_ctx* c, int64_t n) { return set_view(c, c->stage, n); }
-
-// copy every array of a particle set (device to device)
-tribo_status copy_view(tribo_ctx* c, const PView& dst, const PView& src) {
-    const size_t rs = real_size(c);
-    const size_t n = (size_t)src.n;
-    auto cp = [&](void* d, const void* s_, size_t elem) -> tribo_status {
-        if (!d || !s_) return TRIBO_OK;
-        TRIBO_CUDA(cudaMemcpyAsync(d, s_, elem * n, cudaMemcpyDeviceToDevice, c->stream));
-        return TRIBO_OK;
-    };
-    tribo_status st;
-    if ((st = cp(dst.x, src.x, rs)) || (st = cp(dst.y, src.y, rs)) || (st = cp(dst.z, src.z, rs)) ||
-        (st = cp(dst.vx, src.vx, rs)) || (st = cp(dst.vy, src.vy, rs)) || (st = cp(dst.vz, src.vz, rs)) ||
-        (st = cp(dst.d, src.d, rs)) || (st = cp(dst.q, src.q, sizeof(double))) ||
-        (st = cp(dst.q_wall, src.q_wall, sizeof(double))) || (st = cp(dst.n_imp, src.n_imp, sizeof(uint32_t))) ||
-        (st = cp(dst.id, src.id, sizeof(uint32_t))) || (st = cp(dst.cell, src.cell, sizeof(uint32_t))))
-        return st;
-    return TRIBO_OK;
-}
-
 tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particles* src, cudaMemcpyKind kind,
                             bool to_device) {
     const size_t rs = real_size(c);
@@ -198,6 +159,46 @@ tribo_status read_error(tribo_ctx* c, uint32_t* bits) {
 }
 
 }  // namespace
+
+PView set_view(tribo_ctx* c, void* base, int64_t n) {
+    const size_t rs = real_size(c);
+    char* b = (char*)base;
+    const size_t cap = (size_t)c->max_particles;
+    PView v{};
+    v.n = n;
+    size_t off = 0;
+    auto take = [&](size_t elem) { void* p = b + off; off += ((elem * cap + 255) / 256) * 256; return p; };
+    v.x = take(rs); v.y = take(rs); v.z = take(rs);
+    v.vx = take(rs); v.vy = take(rs); v.vz = take(rs); v.d = take(rs);
+    v.q = (double*)take(sizeof(double));
+    v.q_wall = (double*)take(sizeof(double));
+    v.n_imp = (uint32_t*)take(sizeof(uint32_t));
+    v.id = (uint32_t*)take(sizeof(uint32_t));
+    v.cell = (uint32_t*)take(sizeof(uint32_t));
+    return v;
+}
+
+PView stage_view(tribo_ctx* c, int64_t n) { return set_view(c, c->stage, n); }
+
+// copy every array of a particle set (device to device)
+tribo_status copy_view(tribo_ctx* c, const PView& dst, const PView& src) {
+    const size_t rs = real_size(c);
+    const size_t n = (size_t)src.n;
+    auto cp = [&](void* d, const void* s_, size_t elem) -> tribo_status {
+        if (!d || !s_) return TRIBO_OK;
+        TRIBO_CUDA(cudaMemcpyAsync(d, s_, elem * n, cudaMemcpyDeviceToDevice, c->stream));
+        return TRIBO_OK;
+    };
+    tribo_status st;
+    if ((st = cp(dst.x, src.x, rs)) || (st = cp(dst.y, src.y, rs)) || (st = cp(dst.z, src.z, rs)) ||
+        (st = cp(dst.vx, src.vx, rs)) || (st = cp(dst.vy, src.vy, rs)) || (st = cp(dst.vz, src.vz, rs)) ||
+        (st = cp(dst.d, src.d, rs)) || (st = cp(dst.q, src.q, sizeof(double))) ||
+        (st = cp(dst.q_wall, src.q_wall, sizeof(double))) || (st = cp(dst.n_imp, src.n_imp, sizeof(uint32_t))) ||
+        (st = cp(dst.id, src.id, sizeof(uint32_t))) || (st = cp(dst.cell, src.cell, sizeof(uint32_t))))
+        return st;
+    return TRIBO_OK;
+}
+
 }  // namespace tribo
 
 using namespace tribo;

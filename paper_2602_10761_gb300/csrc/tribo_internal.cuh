@@ -222,6 +222,11 @@ tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out);
 // dst receives src sorted by cell key (all arrays; id if present)
 tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst);
 tribo_status particles_setup(tribo_ctx* c);
+// view of n particles in a particle-set buffer of the context (stage or alt)
+PView set_view(tribo_ctx* c, void* base, int64_t n);
+PView stage_view(tribo_ctx* c, int64_t n);
+// copy every array of a particle set, device to device, on the context's stream
+tribo_status copy_view(tribo_ctx* c, const PView& dst, const PView& src);
 tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev);
 
 // synthetic mode field (fluid.cu)
