@@ -265,6 +265,67 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     }
 
 
+def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20):
+    """Batched ensemble of 64 independent channels (Re_tau in {180, 300, 395,
+    550}, grids 64^3 to 192x128x128, 50k-2M particles each, d+ in [0.5, 3]):
+    aggregate particle-steps/s of the batch (graph-captured steps, persistent
+    particle kernel over all channels, autotuned shape) against the same
+    channels stepped one after another with tribo_step."""
+    cases = synth.ensemble_cases()
+    chans, Ps, dts = [], [], []
+    for c in cases:
+        faces = synth.y_faces(c.ny, c.delta, c.gamma)
+        params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0,
+                          sort_every=sort_every)
+        ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, None, max_particles=c.n_particles)
+        Y = synth.node_y(faces)
+        ch.set_modes(synth.draw_modes(c), synth.mean_velocity(Y, c), synth.damping(Y, c))
+        T.tribo_eval_modes(ch.ctx, 0.0, None)          # frozen lattice from the device mode sum
+        ch.set_modes(None)
+        P = synth.draw_particles(c)
+        Ps.append(T.Particles.from_numpy(dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q),
+                                         T.TRIBO_MIXED, device="cuda"))
+        chans.append(ch)
+        dts.append(c.dt)
+    ntot = sum(c.n_particles for c in cases)
+    B = T.Batch(chans, sort_every=sort_every)
+    t0 = time.perf_counter()
+    shape = B.autotune(Ps, dts)
+    tune_s = time.perf_counter() - t0
+    B.step(Ps, dts, 2 * sort_every)                  # graph capture and first replay
+    B.sync()
+    torch.cuda.synchronize()
+    l0 = B.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    B.step(Ps, dts, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    B.sync()
+    batch_ms = e0.elapsed_time(e1)
+    launches = B.launches - l0
+    B.close()
+    # the same channels one after another (tribo_step per channel)
+    seq_ms = 0.0
+    for ch, P, dt in zip(chans, Ps, dts):
+        torch.cuda.synchronize()
+        e0.record()
+        ch.step(P, dt, seq_steps)
+        e1.record()
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+    for ch in chans:
+        ch.close()
+    batch_rate = ntot * steps / (batch_ms * 1e-3)
+    seq_rate = ntot * seq_steps / (seq_ms * 1e-3)
+    return {"workload": (f"64 channels (synth.ensemble_cases): Re_tau in {{180,300,395,550}}, grids 64^3 to "
+                         f"192x128x128, {ntot} particles in total, d+ in [0.5,3], sort every {sort_every}"),
+            "steps": steps, "ms_per_step": batch_ms / steps, "particle_steps_per_s": batch_rate,
+            "sequential_particle_steps_per_s": seq_rate, "sequential_steps": seq_steps,
+            "speedup_vs_sequential": batch_rate / seq_rate, "autotuned_shape": shape, "autotune_s": tune_s,
+            "kernels_per_step": launches / steps}
+
+
 def cpu_baseline(c, faces, lat, P, n_sample):
     t_field, t_part = oracle_step_time(c, faces, lat, P, n_sample)
     t_full = t_field + t_part * (c.n_particles / n_sample)
@@ -321,6 +382,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--sort-every", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -458,6 +520,8 @@ def main():
     ch.close()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(T, torch)
+    if rank == 0 and world == 1 and not args.no_batch:
+        line["batched"] = batch_report(T, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, faces, lat, P, args.cpu_sample)
     if rank == 0:
