@@ -41,6 +41,27 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device):
+    """Largest value of x over all ranks of the process group (x on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, steps, seconds_max, world):
+    """Whole-job throughput of replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank * steps / seconds_max
+
+
+def shard(items, rank, world):
+    """The share of independent work items (channels) that one rank takes."""
+    return list(items)[rank::world]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -265,13 +286,15 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     }
 
 
-def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20):
+def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world=1):
     """Batched ensemble of 64 independent channels (Re_tau in {180, 300, 395,
     550}, grids 64^3 to 192x128x128, 50k-2M particles each, d+ in [0.5, 3]):
     aggregate particle-steps/s of the batch (graph-captured steps, persistent
     particle kernel over all channels, autotuned shape) against the same
-    channels stepped one after another with tribo_step."""
-    cases = synth.ensemble_cases()
+    channels stepped one after another with tribo_step.  With several ranks the
+    channels are sharded over the ranks (independent problems, no exchange)."""
+    all_cases = synth.ensemble_cases()
+    cases = shard(all_cases, rank, world)
     chans, Ps, dts = [], [], []
     for c in cases:
         faces = synth.y_faces(c.ny, c.delta, c.gamma)
@@ -302,7 +325,7 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20):
     e1.record()
     torch.cuda.synchronize()
     B.sync()
-    batch_ms = e0.elapsed_time(e1)
+    batch_ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     launches = B.launches - l0
     B.close()
     # the same channels one after another (tribo_step per channel)
@@ -316,6 +339,8 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20):
         seq_ms += e0.elapsed_time(e1)
     for ch in chans:
         ch.close()
+    seq_ms = max_over_ranks(seq_ms, "cuda")
+    ntot = sum(c.n_particles for c in all_cases)
     batch_rate = ntot * steps / (batch_ms * 1e-3)
     seq_rate = ntot * seq_steps / (seq_ms * 1e-3)
     return {"workload": (f"64 channels (synth.ensemble_cases): Re_tau in {{180,300,395,550}}, grids 64^3 to "
@@ -438,12 +463,9 @@ def main():
     T.tribo_timing_enable(ch.ctx, False)
     launches = ch.launches - launches0
     ch.sync()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
     ms_per_step = ms / args.steps
-    value = world * c.n_particles * args.steps / (ms * 1e-3)
+    value = aggregate_rate(c.n_particles, args.steps, ms * 1e-3, world)
 
     # end to end through the public call with HOST buffers (pinned), copies inside
     host = {}
@@ -463,11 +485,8 @@ def main():
     for _ in range(args.e2e_steps):
         ch.step(Ph, c.dt, 1)          # copies in, one step, copies out, synchronises
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * c.n_particles * args.e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, "cuda")
+    e2e_value = aggregate_rate(c.n_particles, args.e2e_steps, e2e_s, world)
 
     hbm_peak, peak_kind = measured_peaks()
     kern = {}
@@ -520,8 +539,8 @@ def main():
     ch.close()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(T, torch)
-    if rank == 0 and world == 1 and not args.no_batch:
-        line["batched"] = batch_report(T, torch)
+    if not args.no_batch:
+        line["batched"] = batch_report(T, torch, rank=rank, world=world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, faces, lat, P, args.cpu_sample)
     if rank == 0:
