@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "fft.cuh"
+#include "fft_reg.cuh"
 #include "tribo_internal.cuh"
 
 namespace tribo {
@@ -35,8 +36,6 @@ using fft::pad;
 using fft::padded;
 
 constexpr int kThreads = 256;
-constexpr int kZTile = 16;      // m_x columns per forward z-transform block
-constexpr int kZTileInv = 8;    // m_x columns per inverse z-transform block (three fields)
 
 // ---------------------------------------------------------------- double-single
 struct ds {
@@ -118,32 +117,6 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(double* __restrict__ src, con
 
 // ---------------------------------------------------------------- z forward
 // Block (plane j, m_x tile): columns along k of S[k][j][m_x], in place.
-template <class R, int NZ>
-__global__ void __launch_bounds__(kThreads) k_zfwd(cplx<R>* __restrict__ S, int ny, int nxh,
-                                                   const cplx<R>* __restrict__ tw_g) {
-    constexpr int ST = padded<R, NZ>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* A = tw + NZ;
-    for (int i = threadIdx.x; i < NZ; i += blockDim.x) tw[i] = tw_g[i];
-    const int j = blockIdx.x;
-    const int mx0 = blockIdx.y * kZTile;
-    const int nt = min(kZTile, nxh - mx0);
-    // asynchronous copies straight into the transposed, padded tile
-    for (int idx = threadIdx.x; idx < NZ * kZTile; idx += kThreads) {
-        const int k = idx / kZTile;
-        const int t = idx - k * kZTile;
-        if (t < nt) fft::cp_async_elem(&A[t * ST + pad<R>(k)], &S[((size_t)k * ny + j) * nxh + mx0 + t]);
-    }
-    fft::cp_async_wait_all();
-    __syncthreads();
-    fft::transform_inplace<R, -1, NZ, kZTile, kThreads>(A, nt, tw, 1);
-    for (int idx = threadIdx.x; idx < NZ * kZTile; idx += blockDim.x) {
-        const int k = idx / kZTile;
-        const int t = idx - k * kZTile;
-        if (t < nt) S[((size_t)k * ny + j) * nxh + mx0 + t] = A[t * ST + pad<R>(k)];
-    }
-}
 
 // ---------------------------------------------------------------- y solve, FP64
 // Thread per table row (|m_z|, m_x): the pencil m_z = |m_z| and, unless it is
@@ -346,68 +319,53 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
     frow[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
 }
 
-// ---------------------------------------------------------------- z inverse
-// Block (node plane jn, m_x tile).  Interior planes: phi-hat of cell jn-1 ->
-// F0 = IFFT_z(phi-hat) and F2 = IFFT_z(-i sin(2 pi m_z/nz)/dz phi-hat); all
-// planes: F1 = IFFT_z(E_y-hat) in place.
+// ---------------------------------------------------------------- z passes (four-step)
+// Forward z transform of S in place: block (cell plane j, W columns of m_x).
 template <class R, int NZ>
-__global__ void __launch_bounds__(kThreads) k_zinv(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
-                                                   int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
-                                                   const cplx<R>* __restrict__ tw_g) {
-    constexpr int ST = padded<R, NZ>();
+__global__ void __launch_bounds__(kThreads) k_zfwd4(cplx<R>* __restrict__ S, int ny, int nxh,
+                                                    const cplx<R>* __restrict__ tw_g) {
+    using F4 = fft::FourStep<NZ, kThreads>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* A = tw + NZ;        // 3 tiles: E_y, phi, E_z
-    R* sz = reinterpret_cast<R*>(A + 3 * kZTileInv * ST);
-    for (int i = threadIdx.x; i < NZ; i += blockDim.x) {
+    cplx<R>* buf = tw + NZ;
+    for (int i = threadIdx.x; i < NZ; i += kThreads) tw[i] = tw_g[i];
+    __syncthreads();
+    const int mx0 = blockIdx.y * F4::W;
+    const int ncol = min(F4::W, nxh - mx0);
+    cplx<R>* base = S + (size_t)blockIdx.x * nxh + mx0;
+    const size_t rs = (size_t)ny * nxh;
+    fft::column_fft<R, -1, NZ, kThreads, false>(base, rs, base, rs, ncol, tw, nullptr, buf);
+}
+
+// Inverse z transforms: block (node plane jn, W columns of m_x).  All planes:
+// F1 = IFFT_z(E_y-hat) in place; interior planes: F0 = IFFT_z(phi-hat of cell
+// jn-1) and F2 = IFFT_z(-i sin(2 pi m_z/nz)/dz phi-hat).
+template <class R, int NZ>
+__global__ void __launch_bounds__(kThreads) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
+                                                    int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
+                                                    const cplx<R>* __restrict__ tw_g) {
+    using F4 = fft::FourStep<NZ, kThreads>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+    cplx<R>* buf = tw + NZ;
+    R* sz = reinterpret_cast<R*>(buf + F4::BUF);
+    for (int i = threadIdx.x; i < NZ; i += kThreads) {
         tw[i] = tw_g[i];
         sz[i] = from_f64<R>(sinz[i]);
     }
+    __syncthreads();
     const int nyn = ny + 2;
     const int jn = blockIdx.x;
-    const bool interior = jn >= 1 && jn <= ny;
-    const int mx0 = blockIdx.y * kZTileInv;
-    const int nt = min(kZTileInv, nxh - mx0);
-    const int nlines = interior ? 3 * kZTileInv : kZTileInv;   // E_y tile first when alone
-    __syncthreads();
-    cplx<R>* Fy = F + fstride;
-    for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += kThreads) {
-        const int k = idx / kZTileInv;
-        const int t = idx - k * kZTileInv;
-        if (t < nt) {
-            const int kp = pad<R>(k);
-            fft::cp_async_elem(&A[t * ST + kp], &Fy[((size_t)k * nyn + jn) * nxh + mx0 + t]);
-            if (interior)
-                fft::cp_async_elem(&A[(kZTileInv + t) * ST + kp], &S[((size_t)k * ny + (jn - 1)) * nxh + mx0 + t]);
-        }
-    }
-    fft::cp_async_wait_all();
-    __syncthreads();
-    if (interior) {
-        for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += kThreads) {
-            const int k = idx / kZTileInv;
-            const int t = idx - k * kZTileInv;
-            if (t < nt) {
-                const int kp = pad<R>(k);
-                const cplx<R> ph = A[(kZTileInv + t) * ST + kp];
-                A[(2 * kZTileInv + t) * ST + kp] = cplx<R>{sz[k] * ph.im, -sz[k] * ph.re};   // -i s phi
-            }
-        }
-        __syncthreads();
-    }
-    fft::transform_inplace<R, 1, NZ, 3 * kZTileInv, kThreads>(A, nlines, tw, 1);
-    const cplx<R>* res = A;
-    for (int idx = threadIdx.x; idx < NZ * kZTileInv; idx += blockDim.x) {
-        const int k = idx / kZTileInv;
-        const int t = idx - k * kZTileInv;
-        if (t >= nt) continue;
-        const int kp = pad<R>(k);
-        const size_t o = ((size_t)k * nyn + jn) * nxh + mx0 + t;
-        Fy[o] = res[t * ST + kp];
-        if (interior) {
-            F[o] = res[(kZTileInv + t) * ST + kp];
-            F[2 * fstride + o] = res[(2 * kZTileInv + t) * ST + kp];
-        }
+    const int mx0 = blockIdx.y * F4::W;
+    const int ncol = min(F4::W, nxh - mx0);
+    const size_t rsF = (size_t)nyn * nxh, rsS = (size_t)ny * nxh;
+    cplx<R>* Fy = F + fstride + (size_t)jn * nxh + mx0;
+    fft::column_fft<R, 1, NZ, kThreads, false>(Fy, rsF, Fy, rsF, ncol, tw, nullptr, buf);
+    if (jn >= 1 && jn <= ny) {
+        const cplx<R>* ph = S + (size_t)(jn - 1) * nxh + mx0;
+        cplx<R>* F0 = F + (size_t)jn * nxh + mx0;
+        fft::column_fft<R, 1, NZ, kThreads, false>(ph, rsS, F0, rsF, ncol, tw, nullptr, buf);
+        fft::column_fft<R, 1, NZ, kThreads, true>(ph, rsS, F0 + 2 * fstride, rsF, ncol, tw, sz, buf);
     }
 }
 
@@ -535,9 +493,9 @@ size_t xinv_smem() {
            sizeof(int) * xinv_lpb<R, M>() + 16;
 }
 template <class R, int NZ>
-size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + kZTile * padded<R, NZ>()); }
+size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>::BUF); }
 template <class R, int NZ>
-size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + 3 * kZTileInv * padded<R, NZ>()) + sizeof(R) * NZ; }
+size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>::BUF) + sizeof(R) * NZ; }
 
 template <class R, int M>
 void launch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
@@ -557,22 +515,24 @@ void launch_xinv(tribo_ctx* c, void* E, double* phi) {
 }
 template <class R, int NZ>
 void launch_zfwd(tribo_ctx* c) {
-    dim3 grid(c->ny, (c->nxh + kZTile - 1) / kZTile);
-    k_zfwd<R, NZ><<<grid, kThreads, zfwd_smem<R, NZ>(), c->stream>>>((cplx<R>*)c->S, c->ny, c->nxh,
-                                                                     (const cplx<R>*)c->d_twz);
+    constexpr int W = fft::FourStep<NZ, kThreads>::W;
+    dim3 grid(c->ny, (c->nxh + W - 1) / W);
+    k_zfwd4<R, NZ><<<grid, kThreads, zfwd_smem<R, NZ>(), c->stream>>>((cplx<R>*)c->S, c->ny, c->nxh,
+                                                                      (const cplx<R>*)c->d_twz);
 }
 template <class R, int NZ>
 void launch_zinv(tribo_ctx* c) {
-    dim3 grid(c->ny + 2, (c->nxh + kZTileInv - 1) / kZTileInv);
+    constexpr int W = fft::FourStep<NZ, kThreads>::W;
+    dim3 grid(c->ny + 2, (c->nxh + W - 1) / W);
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
-    k_zinv<R, NZ><<<grid, kThreads, zinv_smem<R, NZ>(), c->stream>>>(
+    k_zinv4<R, NZ><<<grid, kThreads, zinv_smem<R, NZ>(), c->stream>>>(
         (const cplx<R>*)c->S, (cplx<R>*)c->F, c->ny, c->nxh, fstride, c->d_sinz, (const cplx<R>*)c->d_twz);
 }
 template <class R, int NZ>
 tribo_status attr_z(int optin) {
     if (zfwd_smem<R, NZ>() > (size_t)optin || zinv_smem<R, NZ>() > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
-    TRIBO_CUDA(cudaFuncSetAttribute(k_zfwd<R, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_zinv<R, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_zfwd4<R, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_zinv4<R, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return TRIBO_OK;
 }
 template <class R, int M>
