@@ -64,54 +64,68 @@ __device__ __forceinline__ ds ds_neg(ds a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
 
 // ---------------------------------------------------------------- x forward
-// One block: LPB lines (k, j) of the charge-sum array.  z_n = x_2n + i x_2n+1,
-// Z = FFT_{nx/2}(z), X_m = (Z_m + conj Z_{M-m})/2 - (i/2) W^m (Z_m - conj Z_{M-m}).
-template <class R, int M, int LPB>
-__global__ void __launch_bounds__(kThreads) k_xfwd(double* __restrict__ src, const double* __restrict__ scale_row,
-                                                   int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
-                                                   const cplx<R>* __restrict__ tw_g) {
-    constexpr int NX = 2 * M;
-    constexpr int NXH = M + 1;
-    constexpr int ST = padded<R, M>();
+// Thread group (line, r) per line (k, j) of the charge-sum array:
+// z_n = x_2n + i x_2n+1 (scaled to -rho/eps), Z = FFT_M(z) by the register
+// four-step, X_m = (Z_m + conj Z_M-m)/2 - (i/2) W^m (Z_m - conj Z_M-m) for
+// m = 0..M.  Each thread zeroes the charge sums it has read.
+template <class R, int M>
+__global__ void __launch_bounds__(kThreads) k_xfwd4(double* __restrict__ src, const double* __restrict__ scale_row,
+                                                    int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
+                                                    const cplx<R>* __restrict__ tw_g) {
+    using F4 = fft::FourStep<M, kThreads>;
+    constexpr int N1 = F4::N1, N2 = F4::N2, TPC = F4::TPC, LPB = F4::W, CS = F4::CS;
+    constexpr int NX = 2 * M, NXH = M + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* A = tw + NX;
-    double2* stg = reinterpret_cast<double2*>(A + LPB * ST + ((LPB * ST) & 1));   // 16-byte aligned
-    R* sc = reinterpret_cast<R*>(stg + LPB * M);
-    const int line0 = blockIdx.x * LPB;
-    const int nl = min(LPB, nlines - line0);
-    for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
-    if (threadIdx.x < nl) sc[threadIdx.x] = from_f64<R>(scale_row[(line0 + threadIdx.x) % ny]);
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);   // exp(-2 pi i e / NX)
+    cplx<R>* buf = tw + NX;
+    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = tw_g[i];
     __syncthreads();
-    // stage the charge sums asynchronously; zero the source only after the
-    // copies have landed
-    const double2* src2 = reinterpret_cast<const double2*>(src) + (size_t)line0 * M;
-    for (int idx = threadIdx.x; idx < nl * M; idx += kThreads) fft::cp_async16(&stg[idx], &src2[idx]);
-    fft::cp_async_wait_all();
-    if (zero_src) {
-        double2* dst2 = reinterpret_cast<double2*>(src) + (size_t)line0 * M;
-        for (int idx = threadIdx.x; idx < nl * M; idx += kThreads) dst2[idx] = make_double2(0.0, 0.0);
+    const int r = threadIdx.x % TPC;
+    const int l = threadIdx.x / TPC;
+    const int line = blockIdx.x * LPB + l;
+    const bool live = l < LPB && line < nlines;
+    cplx<R>* lb = buf + l * CS;
+    if (live && r < N2) {
+        const R s = from_f64<R>(scale_row[line % ny]);
+        double2* row = reinterpret_cast<double2*>(src) + (size_t)line * M;
+        cplx<R> y[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) {
+            const double2 v = row[N2 * n1 + r];
+            y[n1] = cplx<R>{from_f64<R>(v.x) * s, from_f64<R>(v.y) * s};
+        }
+        if (zero_src) {
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) row[N2 * n1 + r] = make_double2(0.0, 0.0);
+        }
+        fft::reg_dft<R, -1, N1, 2 * N2>(y, tw);
+#pragma unroll
+        for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * tw[2 * r * k1];
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) lb[r * (N1 + 1) + k1] = y[k1];
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nl * M; idx += kThreads) {
-        const int l = idx / M;
-        const int n = idx - l * M;
-        const R s = sc[l];
-        const double2 v = stg[idx];
-        A[l * ST + pad<R>(n)] = cplx<R>{from_f64<R>(v.x) * s, from_f64<R>(v.y) * s};
+    cplx<R> z[N2];
+    if (live && r < N1) {
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) z[n2] = lb[n2 * (N1 + 1) + r];
+        fft::reg_dft<R, -1, N2, 2 * N1>(z, tw);
     }
     __syncthreads();
-    fft::transform_inplace<R, -1, M, LPB, kThreads>(A, nl, tw, 2);
-    const cplx<R>* Z = A;
-    for (int idx = threadIdx.x; idx < nl * NXH; idx += blockDim.x) {
-        const int l = idx / NXH;
-        const int m = idx - l * NXH;
-        const cplx<R> zm = Z[l * ST + pad<R>(m == M ? 0 : m)];
-        const cplx<R> zc = conj(Z[l * ST + pad<R>(m == 0 ? 0 : M - m)]);
-        const cplx<R> sum = zm + zc, dif = zm - zc;
-        const cplx<R> t = tw[m] * dif;
-        // X = sum/2 - (i/2) t
-        S[(size_t)(line0 + l) * NXH + m] = cplx<R>{(R)0.5 * (sum.re + t.im), (R)0.5 * (sum.im - t.re)};
+    if (live && r < N1) {
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) lb[r + N1 * k2] = z[k2];
+    }
+    __syncthreads();
+    if (live) {
+        cplx<R>* out = S + (size_t)line * NXH;
+        for (int m = r; m <= M; m += TPC) {
+            const cplx<R> zm = lb[m == M ? 0 : m];
+            const cplx<R> zc = conj(lb[m == 0 ? 0 : M - m]);
+            const cplx<R> sum = zm + zc, dif = zm - zc;
+            const cplx<R> t = tw[m] * dif;
+            out[m] = cplx<R>{(R)0.5 * (sum.re + t.im), (R)0.5 * (sum.im - t.re)};
+        }
     }
 }
 
@@ -370,127 +384,109 @@ __global__ void __launch_bounds__(kThreads) k_zinv4(const cplx<R>* __restrict__ 
 }
 
 // ---------------------------------------------------------------- x inverse
-// One block: LPB node lines (k, jn).  Fields E_x (F0 times -i sin(2 pi m/nx)/dx),
-// E_y (F1), E_z (F2), and optionally phi (F0); real inverse transform via the
-// split step Z_m = (X_m + conj X_{M-m}) + i W^-m (X_m - conj X_{M-m}) and a
-// length-M inverse FFT; x_2n = Re z_n / (nx nz), x_2n+1 = Im z_n / (nx nz).
-template <class R, int M, int LPB>
-__global__ void __launch_bounds__(kThreads) k_xinv(const cplx<R>* __restrict__ F, R* __restrict__ E,
-                                                   double* __restrict__ phi, int ny, int nz, size_t fstride,
-                                                   const double* __restrict__ sinx, const cplx<R>* __restrict__ tw_g,
-                                                   int want_phi, R norm, size_t nodes) {
-    constexpr int NX = 2 * M;
-    constexpr int NXH = M + 1;
-    constexpr int NF = 4;
-    constexpr int H = M / 2 + 1;          // pairs (m, M-m), m = 0..M/2
-    constexpr int ST = padded<R, M + 1>();   // a staged line holds X_0 .. X_M
+// Four-step variant.  Thread group (line, r) per node line (k, jn); for each
+// field the thread with n2 = r forms Z_m for its m = N2 n1 + r straight from
+// X_m and X_M-m in global memory (split step), then the register four-step
+// inverse of length M = N1 N2, and the group stores x_2n, x_2n+1 as pairs.
+// Wall lines (jn = 0, ny+1) carry E_x = E_z = 0.
+template <class R>
+__device__ __forceinline__ void store_pair(R* p, R a, R b) {
+    if constexpr (sizeof(R) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+template <class R, int M>
+__global__ void __launch_bounds__(kThreads) k_xinv4(const cplx<R>* __restrict__ F, R* __restrict__ E,
+                                                    double* __restrict__ phi, int ny, int nz, size_t fstride,
+                                                    const double* __restrict__ sinx,
+                                                    const cplx<R>* __restrict__ tw_g, int want_phi, R norm,
+                                                    size_t nodes) {
+    using F4 = fft::FourStep<M, kThreads>;
+    constexpr int N1 = F4::N1, N2 = F4::N2, TPC = F4::TPC, LPB = F4::W, CS = F4::CS;
+    constexpr int NX = 2 * M, NXH = M + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-    cplx<R>* A = tw + NX;                 // line f*LPB + l holds field f of line l
-    R* sx = reinterpret_cast<R*>(A + NF * LPB * ST);
-    int* sjn = reinterpret_cast<int*>(sx + NXH);   // node plane of each line, -1 past the end
+    cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);   // exp(-2 pi i e / NX)
+    cplx<R>* buf = tw + NX;
+    R* sx = reinterpret_cast<R*>(buf + F4::BUF);
+    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = tw_g[i];
+    for (int i = threadIdx.x; i < NXH; i += kThreads) sx[i] = from_f64<R>(sinx[i]);
+    __syncthreads();
     const int nyn = ny + 2;
-    const int nlines = nz * nyn;
-    const int line0 = blockIdx.x * LPB;
-    const int nl = min(LPB, nlines - line0);
+    const int r = threadIdx.x % TPC;
+    const int l = threadIdx.x / TPC;
+    const int line = blockIdx.x * LPB + l;
+    const bool live = l < LPB && line < nz * nyn;
+    const int jn = live ? line % nyn : 0;
+    const bool interior = jn >= 1 && jn <= ny;
     const int nf = want_phi ? 4 : 3;
-    for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = tw_g[i];
-    for (int i = threadIdx.x; i < NXH; i += blockDim.x) sx[i] = from_f64<R>(sinx[i]);
-    if (threadIdx.x < LPB) sjn[threadIdx.x] = (int)threadIdx.x < nl ? (line0 + (int)threadIdx.x) % nyn : -1;
-    __syncthreads();
-    // stage each (field, line) half spectrum into its FFT line, then the split
-    // step in place: one thread per pair (m, M-m) turns X_m, X_M-m into Z_m, Z_M-m
-    for (int idx = threadIdx.x; idx < nf * LPB * NXH; idx += kThreads) {
-        const int fl = idx / NXH;
-        const int m = idx - fl * NXH;
-        const int f = fl / LPB;
-        const int l = fl - f * LPB;
-        const int jn = sjn[l];
-        const int src_field = (f == 3) ? 0 : f;
-        cplx<R>* dst = &A[fl * ST + pad<R>(m)];
-        if (jn >= 0 && (src_field == 1 || (jn >= 1 && jn <= ny)))
-            fft::cp_async_elem(dst, &F[src_field * fstride + (size_t)(line0 + l) * NXH + m]);
-        else
-            *dst = cplx<R>{0, 0};
-    }
-    fft::cp_async_wait_all();
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nf * LPB * H; idx += kThreads) {
-        const int fl = idx / H;
-        const int m = idx - fl * H;
-        const int f = fl / LPB;
-        const int l = fl - f * LPB;
-        if (sjn[l] < 0) continue;
-        const int mb = M - m;
-        cplx<R>* zl = A + fl * ST;
-        cplx<R> xa = zl[pad<R>(m)], xb = zl[pad<R>(mb)];
-        if (f == 0) {   // E_x multiplier -i s_m
-            xa = cplx<R>{sx[m] * xa.im, -sx[m] * xa.re};
-            xb = cplx<R>{sx[mb] * xb.im, -sx[mb] * xb.re};
-        }
-        {
-            const cplx<R> cb = conj(xb);
-            const cplx<R> sum = xa + cb, dif = xa - cb;
-            const cplx<R> t = conj(tw[m]) * dif;      // W^-m (X_m - conj X_M-m)
-            zl[pad<R>(m)] = cplx<R>{sum.re - t.im, sum.im + t.re};
-        }
-        if (mb != m && mb != M) {
-            const cplx<R> ca = conj(xa);
-            const cplx<R> sum = xb + ca, dif = xb - ca;
-            const cplx<R> t = conj(tw[mb]) * dif;
-            zl[pad<R>(mb)] = cplx<R>{sum.re - t.im, sum.im + t.re};
-        }
-    }
-    __syncthreads();
-    fft::transform_inplace<R, 1, M, NF * LPB, kThreads, ST>(A, nf * LPB, tw, 2);
-    for (int idx = threadIdx.x; idx < LPB * M; idx += blockDim.x) {
-        const int l = idx / M;
-        const int n = idx - l * M;
-        if (l >= nl) continue;
-        const int np_ = pad<R>(n);
-        const cplx<R> ex = A[(0 * LPB + l) * ST + np_];
-        const cplx<R> ey_ = A[(1 * LPB + l) * ST + np_];
-        const cplx<R> ez = A[(2 * LPB + l) * ST + np_];
-        const size_t o = (size_t)(line0 + l) * NX + 2 * n;
-        E[o] = ex.re * norm;
-        E[o + 1] = ex.im * norm;
-        E[nodes + o] = ey_.re * norm;
-        E[nodes + o + 1] = ey_.im * norm;
-        E[2 * nodes + o] = ez.re * norm;
-        E[2 * nodes + o + 1] = ez.im * norm;
-        if (want_phi) {
-            const int jn = sjn[l];
-            if (jn >= 1 && jn <= ny) {
-                const int k = (line0 + l) / nyn;
-                const cplx<R> p = A[(3 * LPB + l) * ST + np_];
-                double* prow = phi + ((size_t)k * ny + (jn - 1)) * NX + 2 * n;
-                prow[0] = (double)(p.re * norm);
-                prow[1] = (double)(p.im * norm);
+    for (int f = 0; f < nf; ++f) {
+        const bool active = live && (f == 1 || interior);
+        const int src = f == 3 ? 0 : f;
+        if (active && r < N2) {
+            const cplx<R>* X = F + (size_t)src * fstride + (size_t)line * NXH;
+            cplx<R> y[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int m = N2 * n1 + r;
+                cplx<R> xa = X[m], xb = X[M - m];
+                if (f == 0) {     // E_x multiplier -i sin(2 pi m / nx) / dx
+                    xa = cplx<R>{sx[m] * xa.im, -sx[m] * xa.re};
+                    xb = cplx<R>{sx[M - m] * xb.im, -sx[M - m] * xb.re};
+                }
+                const cplx<R> cb = conj(xb);
+                const cplx<R> sum = xa + cb;
+                const cplx<R> t = conj(tw[m]) * (xa - cb);
+                y[n1] = cplx<R>{sum.re - t.im, sum.im + t.re};
             }
+            fft::reg_dft<R, 1, N1, 2 * N2>(y, tw);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * conj(tw[2 * r * k1]);
+            cplx<R>* b = buf + l * CS + r * (N1 + 1);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) b[k1] = y[k1];
+        }
+        __syncthreads();
+        if (active && r < N1) {
+            cplx<R> z[N2];
+            const cplx<R>* b = buf + l * CS + r;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) z[n2] = b[n2 * (N1 + 1)];
+            fft::reg_dft<R, 1, N2, 2 * N1>(z, tw);
+            if (f < 3) {
+                R* row = E + (size_t)f * nodes + (size_t)line * NX;
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) {
+                    const int k = r + N1 * k2;
+                    store_pair<R>(row + 2 * k, z[k2].re * norm, z[k2].im * norm);
+                }
+            } else {
+                double* prow = phi + ((size_t)(line / nyn) * ny + (jn - 1)) * NX;
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2) {
+                    const int k = r + N1 * k2;
+                    prow[2 * k] = (double)(z[k2].re * norm);
+                    prow[2 * k + 1] = (double)(z[k2].im * norm);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (live && !interior) {
+        R* ex = E + (size_t)line * NX;
+        R* ez = E + 2 * nodes + (size_t)line * NX;
+        for (int i = r; i < NX; i += TPC) {
+            ex[i] = (R)0;
+            ez[i] = (R)0;
         }
     }
 }
 
 // ---------------------------------------------------------------- dispatch
 template <class R, int M>
-constexpr int xfwd_lpb() {
-    constexpr int lines = (int)(2048 * 8 / sizeof(cplx<R>)) / M;
-    return lines > 8 ? 8 : (lines < 1 ? 1 : lines);
-}
-template <class R, int M>
-constexpr int xinv_lpb() {
-    constexpr int lines = (int)(1024 * 8 / sizeof(cplx<R>)) / M;
-    return lines > 4 ? 4 : (lines < 1 ? 1 : lines);
-}
-template <class R, int M>
-size_t xfwd_smem() {
-    return sizeof(cplx<R>) * (2 * M + xfwd_lpb<R, M>() * padded<R, M>() + 1) + sizeof(double2) * xfwd_lpb<R, M>() * M +
-           sizeof(R) * 8;
-}
+size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + fft::FourStep<M, kThreads>::BUF); }
 template <class R, int M>
 size_t xinv_smem() {
-    return sizeof(cplx<R>) * (2 * M + 4 * xinv_lpb<R, M>() * padded<R, M + 1>()) + sizeof(R) * (M + 1) +
-           sizeof(int) * xinv_lpb<R, M>() + 16;
+    return sizeof(cplx<R>) * (2 * M + fft::FourStep<M, kThreads>::BUF) + sizeof(R) * (M + 1);
 }
 template <class R, int NZ>
 size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>::BUF); }
@@ -499,17 +495,17 @@ size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>:
 
 template <class R, int M>
 void launch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
-    constexpr int LPB = xfwd_lpb<R, M>();
+    constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->ny * c->nz;
-    k_xfwd<R, M, LPB><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
+    k_xfwd4<R, M><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
         src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx);
 }
 template <class R, int M>
 void launch_xinv(tribo_ctx* c, void* E, double* phi) {
-    constexpr int LPB = xinv_lpb<R, M>();
+    constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->nz * (c->ny + 2);
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
-    k_xinv<R, M, LPB><<<(nlines + LPB - 1) / LPB, kThreads, xinv_smem<R, M>(), c->stream>>>(
+    k_xinv4<R, M><<<(nlines + LPB - 1) / LPB, kThreads, xinv_smem<R, M>(), c->stream>>>(
         (const cplx<R>*)c->F, (R*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
         phi != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)), (size_t)c->nz * (c->ny + 2) * c->nx);
 }
@@ -538,10 +534,8 @@ tribo_status attr_z(int optin) {
 template <class R, int M>
 tribo_status attr_x(int optin) {
     if (xfwd_smem<R, M>() > (size_t)optin || xinv_smem<R, M>() > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
-    TRIBO_CUDA(cudaFuncSetAttribute(k_xfwd<R, M, xfwd_lpb<R, M>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_xinv<R, M, xinv_lpb<R, M>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_xfwd4<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_xinv4<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return TRIBO_OK;
 }
 
