@@ -129,9 +129,6 @@ __global__ void __launch_bounds__(kThreads) k_xfwd4(double* __restrict__ src, co
     }
 }
 
-// ---------------------------------------------------------------- z forward
-// Block (plane j, m_x tile): columns along k of S[k][j][m_x], in place.
-
 // ---------------------------------------------------------------- y solve, FP64
 // Thread per table row (|m_z|, m_x): the pencil m_z = |m_z| and, unless it is
 // self-conjugate, m_z = nz - |m_z|.  FP64 Thomas with the precomputed
