@@ -32,9 +32,6 @@ namespace tribo {
 
 namespace {
 
-using fft::pad;
-using fft::padded;
-
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------- double-single
