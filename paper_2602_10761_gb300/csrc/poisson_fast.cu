@@ -543,6 +543,217 @@ __global__ void __launch_bounds__(256) k_ysolve_warp(cplx<float>* __restrict__ S
     }
 }
 
+// ---------------------------------------------------------------- y solve, pencil pairs with a copy ring
+// One thread per factor-table row (|m_z|, m_x): it solves the pencils m_z and
+// nz - m_z, which share the factors, in double-single.  Each thread streams
+// its rows through a private ring of kYD chunks of kYC rows in shared memory,
+// filled by asynchronous copies kYD - 1 chunks ahead of the sweep, so the
+// sequential recurrence does not wait on memory.  The forward sweep stores
+// the value entering each chunk (a checkpoint, global scratch); the backward
+// sweep walks the chunks from the top, recomputes the chunk's forward values
+// in registers from its checkpoint, substitutes back and forms E_y as the
+// chunked kernel does.
+constexpr int kYP = 64;    // threads per block
+constexpr int kYC = 8;     // rows per chunk
+constexpr int kYD = 4;     // chunks in flight
+
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+
+struct YRing {       // one slot: kYC rows x kYP threads of each stream, checkpoint pair
+    float2 t[kYC][kYP];    // 1/pivot (ds)
+    float2 c[kYC][kYP];    // c' (ds)
+    float2 a[kYC][kYP];    // pencil m_z
+    float2 b[kYC][kYP];    // pencil nz - m_z
+    float4 k[2][kYP];      // checkpoint (re hi, re lo, im hi, im lo) of both pencils
+};
+
+__device__ __forceinline__ void ds_step(ds& vr, ds& vi, ds beta, ds inv, float2 r) {
+    vr = ds_add_fast(ds_mul(beta, vr), ds_mul_f(inv, r.x));
+    vi = ds_add_fast(ds_mul(beta, vi), ds_mul_f(inv, r.y));
+}
+
+__global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
+                                                     const float2* __restrict__ tinv, const float2* __restrict__ tcp,
+                                                     const float2* __restrict__ a_ds, const float4* __restrict__ ec,
+                                                     float4* __restrict__ ck, int ny, int nz, int nxh) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    YRing* ring = reinterpret_cast<YRing*>(smem_raw);
+    float4* se = reinterpret_cast<float4*>(ring + kYD);     // ny + 1
+    float2* sa = reinterpret_cast<float2*>(se + ny + 1);     // ny
+    for (int j = threadIdx.x; j < ny; j += kYP) sa[j] = a_ds[j];
+    for (int j = threadIdx.x; j <= ny; j += kYP) se[j] = ec[j];
+    __syncthreads();
+    const int ni = (nz / 2 + 1) * nxh;
+    const int item = blockIdx.x * kYP + threadIdx.x;
+    if (item >= ni) return;                      // no block-wide barrier below
+    const int tid = threadIdx.x;
+    const int amz = item / nxh;
+    const int mx = item - amz * nxh;
+    const int mzb = nz - amz;
+    const bool pair = amz != 0 && 2 * amz != nz;
+    cplx<float>* sA = S + (size_t)amz * ny * nxh + mx;
+    cplx<float>* sB = S + (size_t)(pair ? mzb : amz) * ny * nxh + mx;
+    cplx<float>* fA = Fy + (size_t)amz * (ny + 2) * nxh + mx;
+    cplx<float>* fB = Fy + (size_t)(pair ? mzb : amz) * (ny + 2) * nxh + mx;
+    const int nch = (ny + kYC - 1) / kYC;
+    const size_t rs = (size_t)nxh;               // S row stride (pencil element j)
+    // ---------------- forward sweep
+    auto issue_fwd = [&](int c) {
+        YRing& R = ring[c % kYD];
+#pragma unroll
+        for (int i = 0; i < kYC; ++i) {
+            const int j = c * kYC + i;
+            if (j < ny) {
+                cp_async8(&R.t[i][tid], &tinv[(size_t)j * ni + item]);
+                cp_async8(&R.a[i][tid], &sA[j * rs]);
+                if (pair) cp_async8(&R.b[i][tid], &sB[j * rs]);
+            }
+        }
+    };
+#pragma unroll
+    for (int c = 0; c < kYD - 1; ++c) {
+        if (c < nch) issue_fwd(c);
+        cp_commit();
+    }
+    ds ar = {0.f, 0.f}, ai = {0.f, 0.f}, br = {0.f, 0.f}, bi = {0.f, 0.f};
+    for (int c = 0; c < nch; ++c) {
+        if (c + kYD - 1 < nch) issue_fwd(c + kYD - 1);
+        cp_commit();
+        cp_wait_group<kYD - 1>();
+        const YRing& R = ring[c % kYD];
+#pragma unroll
+        for (int i = 0; i < kYC; ++i) {
+            const int j = c * kYC + i;
+            if (j < ny) {
+                const float2 tv = R.t[i][tid];
+                const ds inv = {tv.x, tv.y};
+                const ds beta = ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv));
+                ds_step(ar, ai, beta, inv, R.a[i][tid]);
+                if (pair) ds_step(br, bi, beta, inv, R.b[i][tid]);
+            }
+        }
+        ck[((size_t)c * ni + item) * 2] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
+        ck[((size_t)c * ni + item) * 2 + 1] = make_float4(br.hi, br.lo, bi.hi, bi.lo);
+    }
+    cp_wait_group<0>();
+    // ---------------- backward sweep
+    auto issue_bwd = [&](int c) {
+        YRing& R = ring[c % kYD];
+#pragma unroll
+        for (int i = 0; i < kYC; ++i) {
+            const int j = c * kYC + i;
+            if (j < ny) {
+                cp_async8(&R.t[i][tid], &tinv[(size_t)j * ni + item]);
+                cp_async8(&R.c[i][tid], &tcp[(size_t)j * ni + item]);
+                cp_async8(&R.a[i][tid], &sA[j * rs]);
+                if (pair) cp_async8(&R.b[i][tid], &sB[j * rs]);
+            }
+        }
+        if (c > 0) {
+            cp_async16(&R.k[0][tid], &ck[((size_t)(c - 1) * ni + item) * 2]);
+            cp_async16(&R.k[1][tid], &ck[((size_t)(c - 1) * ni + item) * 2 + 1]);
+        }
+    };
+    // the forward sweep's last checkpoint writes must be visible to this
+    // thread's asynchronous reads: they come from the same thread, in order
+    __threadfence_block();
+#pragma unroll
+    for (int q = 0; q < kYD - 1; ++q) {
+        const int c = nch - 1 - q;
+        if (c >= 0) issue_bwd(c);
+        cp_commit();
+    }
+    const float4 walls = se[ny];
+    ds xa_r = {0.f, 0.f}, xa_i = {0.f, 0.f}, xb_r = {0.f, 0.f}, xb_i = {0.f, 0.f};   // x[j+1]
+    float dar = 0.f, dai = 0.f, dbr = 0.f, dbi = 0.f;                              // x[j+2] - x[j+1]
+    for (int c = nch - 1; c >= 0; --c) {
+        if (c - (kYD - 1) >= 0) issue_bwd(c - (kYD - 1));
+        cp_commit();
+        cp_wait_group<kYD - 1>();
+        const YRing& R = ring[c % kYD];
+        ds qar = {0.f, 0.f}, qai = {0.f, 0.f}, qbr = {0.f, 0.f}, qbi = {0.f, 0.f};
+        if (c > 0) {
+            const float4 ka = R.k[0][tid], kb = R.k[1][tid];
+            qar = ds{ka.x, ka.y}; qai = ds{ka.z, ka.w};
+            qbr = ds{kb.x, kb.y}; qbi = ds{kb.z, kb.w};
+        }
+        ds dA_r[kYC], dA_i[kYC], dB_r[kYC], dB_i[kYC];
+#pragma unroll
+        for (int i = 0; i < kYC; ++i) {
+            const int j = c * kYC + i;
+            if (j < ny) {
+                const float2 tv = R.t[i][tid];
+                const ds inv = {tv.x, tv.y};
+                const ds beta = ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv));
+                ds_step(qar, qai, beta, inv, R.a[i][tid]);
+                if (pair) ds_step(qbr, qbi, beta, inv, R.b[i][tid]);
+            }
+            dA_r[i] = qar; dA_i[i] = qai; dB_r[i] = qbr; dB_i[i] = qbi;
+        }
+#pragma unroll
+        for (int i = kYC - 1; i >= 0; --i) {
+            const int j = c * kYC + i;
+            if (j < ny) {
+                ds ar_ = dA_r[i], ai_ = dA_i[i], br_ = dB_r[i], bi_ = dB_i[i];
+                if (j != ny - 1) {
+                    const float2 cv = R.c[i][tid];
+                    const ds cp = {cv.x, cv.y};
+                    ar_ = ds_add_fast(ar_, ds_neg(ds_mul(cp, xa_r)));
+                    ai_ = ds_add_fast(ai_, ds_neg(ds_mul(cp, xa_i)));
+                    if (pair) {
+                        br_ = ds_add_fast(br_, ds_neg(ds_mul(cp, xb_r)));
+                        bi_ = ds_add_fast(bi_, ds_neg(ds_mul(cp, xb_i)));
+                    }
+                }
+                const float far = ds_f(ar_), fai = ds_f(ai_);
+                sA[j * rs] = cplx<float>{far, fai};
+                if (j == ny - 1) fA[(size_t)(ny + 1) * rs] = cplx<float>{walls.y * far, walls.y * fai};
+                float d0ar = 0.f, d0ai = 0.f, d0br = 0.f, d0bi = 0.f;
+                if (j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
+                    const float4 cf = se[j + 1];
+                    d0ar = ds_f(ds_add_fast(xa_r, ds_neg(ar_)));
+                    d0ai = ds_f(ds_add_fast(xa_i, ds_neg(ai_)));
+                    fA[(size_t)(j + 2) * rs] = cplx<float>{cf.x * ds_f(xa_r) + cf.y * d0ar + cf.z * dar,
+                                                           cf.x * ds_f(xa_i) + cf.y * d0ai + cf.z * dai};
+                    if (pair) {
+                        d0br = ds_f(ds_add_fast(xb_r, ds_neg(br_)));
+                        d0bi = ds_f(ds_add_fast(xb_i, ds_neg(bi_)));
+                        fB[(size_t)(j + 2) * rs] = cplx<float>{cf.x * ds_f(xb_r) + cf.y * d0br + cf.z * dbr,
+                                                               cf.x * ds_f(xb_i) + cf.y * d0bi + cf.z * dbi};
+                    }
+                }
+                if (pair) {
+                    const float fbr = ds_f(br_), fbi = ds_f(bi_);
+                    sB[j * rs] = cplx<float>{fbr, fbi};
+                    if (j == ny - 1) fB[(size_t)(ny + 1) * rs] = cplx<float>{walls.y * fbr, walls.y * fbi};
+                }
+                dar = d0ar; dai = d0ai; dbr = d0br; dbi = d0bi;
+                xa_r = ar_; xa_i = ai_; xb_r = br_; xb_i = bi_;
+            }
+        }
+    }
+    cp_wait_group<0>();
+    const float4 cf = se[0];
+    {
+        const float x0r = ds_f(xa_r), x0i = ds_f(xa_i);
+        fA[rs] = cplx<float>{cf.x * x0r + cf.z * dar, cf.x * x0i + cf.z * dai};
+        fA[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
+    }
+    if (pair) {
+        const float x0r = ds_f(xb_r), x0i = ds_f(xb_i);
+        fB[rs] = cplx<float>{cf.x * x0r + cf.z * dbr, cf.x * x0i + cf.z * dbi};
+        fB[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
+    }
+}
+
+size_t ysolve_pair_smem(int ny) { return sizeof(YRing) * kYD + sizeof(float4) * (ny + 1) + sizeof(float2) * ny; }
+
 // ---------------------------------------------------------------- z passes (four-step)
 // Forward z transform of S in place: block (cell plane j, W columns of m_x).
 template <class R, int NZ>
@@ -856,20 +1067,8 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
         cplx<float>* Fyf = (cplx<float>*)c->F + fstride;
         const float2* ads = (const float2*)c->d_yads;
         const float4* yec = (const float4*)c->d_yec;
-#define YW(RPL) k_ysolve_warp<RPL><<<wg, 256, ysolve_warp_smem<RPL>(ny), c->stream>>>(Sf, Fyf, tinv, tcp, ads, yec, ny, nz, nxh)
-        if (ny <= 32) YW(1);
-        else if (ny <= 64) YW(2);
-        else if (ny <= 128) YW(4);
-        else if (ny <= 256) YW(8);
-        else if (ny <= 512) YW(16);
-        else {
-            constexpr int CH = 8;
-            const int nch = (ny + CH - 1) / CH;
-            const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
-            k_ysolve_chunk<CH><<<(nz * nxh + 127) / 128, 128, shc, c->stream>>>(Sf, Fyf, tinv, tcp, ads, yec, ny,
-                                                                                nz, nxh);
-        }
-#undef YW
+k_ysolve_pair<<<(ni + kYP - 1) / kYP, kYP, ysolve_pair_smem(ny), c->stream>>>(
+            Sf, Fyf, tinv, tcp, ads, yec, (float4*)c->d_yck, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_INV_Z);
@@ -956,6 +1155,8 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMalloc(&c->d_yec, sizeof(float4) * (ny + 1)));
         TRIBO_CUDA(cudaMemcpy(c->d_yec, ec.data(), sizeof(float4) * (ny + 1), cudaMemcpyHostToDevice));
+        // forward-sweep checkpoints of the pencil-pair kernel: 2 float4 per (chunk, table row)
+        TRIBO_CUDA(cudaMalloc(&c->d_yck, sizeof(float4) * 2 * (size_t)((ny + kYC - 1) / kYC) * ni));
     }
     int dev = 0, optin = 0;
     TRIBO_CUDA(cudaGetDevice(&dev));
@@ -967,11 +1168,7 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_chunk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_warp<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_warp<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_warp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_warp<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return dispatch_attr<float>(nx, nz, optin);
 }
 
@@ -982,7 +1179,8 @@ void poisson_fast_free(tribo_ctx* c) {
     cudaFree(c->d_twz);
     cudaFree(c->d_yads);
     cudaFree(c->d_yec);
-    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = nullptr;
+    cudaFree(c->d_yck);
+    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = c->d_yck = nullptr;
 }
 
 tribo_status poisson_fast_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
