@@ -543,19 +543,22 @@ __global__ void __launch_bounds__(256) k_ysolve_warp(cplx<float>* __restrict__ S
     }
 }
 
-// ---------------------------------------------------------------- y solve, pencil pairs with a copy ring
-// One thread per factor-table row (|m_z|, m_x): it solves the pencils m_z and
-// nz - m_z, which share the factors, in double-single.  Each thread streams
-// its rows through a private ring of kYD chunks of kYC rows in shared memory,
-// filled by asynchronous copies kYD - 1 chunks ahead of the sweep, so the
-// sequential recurrence does not wait on memory.  The forward sweep stores
-// the value entering each chunk (a checkpoint, global scratch); the backward
-// sweep walks the chunks from the top, recomputes the chunk's forward values
-// in registers from its checkpoint, substitutes back and forms E_y as the
-// chunked kernel does.
-constexpr int kYP = 64;    // threads per block
+// ---------------------------------------------------------------- y solve, copy-ring Thomas
+// One thread per pencil, in double-single.  A block of 64 threads takes 32
+// factor-table rows (|m_z|, m_x): threads l and l + 32 solve the pencils m_z
+// and nz - m_z of row l, which share the factors (the second read of a row
+// meets it in cache).  Each thread streams its rows through a private ring
+// of kYD chunks of kYC rows in shared memory, filled by asynchronous copies
+// kYD - 1 chunks ahead of the sweep, so the sequential recurrence does not
+// wait on memory.  The forward sweep stores the value entering each chunk (a
+// checkpoint, global scratch); the backward sweep walks the chunks from the
+// top, recomputes the chunk's forward values in registers from its
+// checkpoint, substitutes back and forms E_y per cell j as
+// A_j phi_j + Bm_j (phi_j - phi_j-1) + Bp_j (phi_j+1 - phi_j), differences in
+// double-single; wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
+constexpr int kYP = 64;    // threads per block (32 table rows)
 constexpr int kYC = 8;     // rows per chunk
-constexpr int kYD = 4;     // chunks in flight
+constexpr int kYD = 3;     // chunks in flight
 
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
@@ -565,12 +568,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
 }
 
-struct YRing {       // one slot: kYC rows x kYP threads of each stream, checkpoint pair
+struct YRing {       // one slot: kYC rows of each stream per thread, and a checkpoint
     float2 t[kYC][kYP];    // 1/pivot (ds)
     float2 c[kYC][kYP];    // c' (ds)
-    float2 a[kYC][kYP];    // pencil m_z
-    float2 b[kYC][kYP];    // pencil nz - m_z
-    float4 k[2][kYP];      // checkpoint (re hi, re lo, im hi, im lo) of both pencils
+    float2 s[kYC][kYP];    // right-hand side, then phi
+    float4 k[kYP];         // checkpoint (re hi, re lo, im hi, im lo)
 };
 
 __device__ __forceinline__ void ds_step(ds& vr, ds& vi, ds beta, ds inv, float2 r) {
@@ -578,7 +580,7 @@ __device__ __forceinline__ void ds_step(ds& vr, ds& vi, ds beta, ds inv, float2 
     vi = ds_add_fast(ds_mul(beta, vi), ds_mul_f(inv, r.y));
 }
 
-__global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
+__global__ void __launch_bounds__(kYP) k_ysolve_ring(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
                                                      const float2* __restrict__ tinv, const float2* __restrict__ tcp,
                                                      const float2* __restrict__ a_ds, const float4* __restrict__ ec,
                                                      float4* __restrict__ ck, int ny, int nz, int nxh) {
@@ -590,19 +592,20 @@ __global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S
     for (int j = threadIdx.x; j <= ny; j += kYP) se[j] = ec[j];
     __syncthreads();
     const int ni = (nz / 2 + 1) * nxh;
-    const int item = blockIdx.x * kYP + threadIdx.x;
-    if (item >= ni) return;                      // no block-wide barrier below
     const int tid = threadIdx.x;
+    const int item = blockIdx.x * (kYP / 2) + (tid & (kYP / 2 - 1));
+    const int half = tid / (kYP / 2);
+    if (item >= ni) return;                      // no block-wide barrier below
     const int amz = item / nxh;
     const int mx = item - amz * nxh;
-    const int mzb = nz - amz;
-    const bool pair = amz != 0 && 2 * amz != nz;
-    cplx<float>* sA = S + (size_t)amz * ny * nxh + mx;
-    cplx<float>* sB = S + (size_t)(pair ? mzb : amz) * ny * nxh + mx;
-    cplx<float>* fA = Fy + (size_t)amz * (ny + 2) * nxh + mx;
-    cplx<float>* fB = Fy + (size_t)(pair ? mzb : amz) * (ny + 2) * nxh + mx;
+    if (half == 1 && (amz == 0 || 2 * amz == nz)) return;   // m_z is its own partner
+    const int mz = half ? nz - amz : amz;
+    cplx<float>* sp = S + (size_t)mz * ny * nxh + mx;
+    cplx<float>* fp = Fy + (size_t)mz * (ny + 2) * nxh + mx;
+    float4* ckp = ck + (size_t)half * ni + item;             // [chunk][half][item]
+    const size_t ckstride = 2 * (size_t)ni;
     const int nch = (ny + kYC - 1) / kYC;
-    const size_t rs = (size_t)nxh;               // S row stride (pencil element j)
+    const size_t rs = (size_t)nxh;
     // ---------------- forward sweep
     auto issue_fwd = [&](int c) {
         YRing& R = ring[c % kYD];
@@ -611,8 +614,7 @@ __global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S
             const int j = c * kYC + i;
             if (j < ny) {
                 cp_async8(&R.t[i][tid], &tinv[(size_t)j * ni + item]);
-                cp_async8(&R.a[i][tid], &sA[j * rs]);
-                if (pair) cp_async8(&R.b[i][tid], &sB[j * rs]);
+                cp_async8(&R.s[i][tid], &sp[j * rs]);
             }
         }
     };
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S
         if (c < nch) issue_fwd(c);
         cp_commit();
     }
-    ds ar = {0.f, 0.f}, ai = {0.f, 0.f}, br = {0.f, 0.f}, bi = {0.f, 0.f};
+    ds pr = {0.f, 0.f}, pim = {0.f, 0.f};
     for (int c = 0; c < nch; ++c) {
         if (c + kYD - 1 < nch) issue_fwd(c + kYD - 1);
         cp_commit();
@@ -633,13 +635,10 @@ __global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S
             if (j < ny) {
                 const float2 tv = R.t[i][tid];
                 const ds inv = {tv.x, tv.y};
-                const ds beta = ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv));
-                ds_step(ar, ai, beta, inv, R.a[i][tid]);
-                if (pair) ds_step(br, bi, beta, inv, R.b[i][tid]);
+                ds_step(pr, pim, ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv)), inv, R.s[i][tid]);
             }
         }
-        ck[((size_t)c * ni + item) * 2] = make_float4(ar.hi, ar.lo, ai.hi, ai.lo);
-        ck[((size_t)c * ni + item) * 2 + 1] = make_float4(br.hi, br.lo, bi.hi, bi.lo);
+        ckp[(size_t)c * ckstride] = make_float4(pr.hi, pr.lo, pim.hi, pim.lo);
     }
     cp_wait_group<0>();
     // ---------------- backward sweep
@@ -651,18 +650,11 @@ __global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S
             if (j < ny) {
                 cp_async8(&R.t[i][tid], &tinv[(size_t)j * ni + item]);
                 cp_async8(&R.c[i][tid], &tcp[(size_t)j * ni + item]);
-                cp_async8(&R.a[i][tid], &sA[j * rs]);
-                if (pair) cp_async8(&R.b[i][tid], &sB[j * rs]);
+                cp_async8(&R.s[i][tid], &sp[j * rs]);
             }
         }
-        if (c > 0) {
-            cp_async16(&R.k[0][tid], &ck[((size_t)(c - 1) * ni + item) * 2]);
-            cp_async16(&R.k[1][tid], &ck[((size_t)(c - 1) * ni + item) * 2 + 1]);
-        }
+        if (c > 0) cp_async16(&R.k[tid], &ckp[(size_t)(c - 1) * ckstride]);
     };
-    // the forward sweep's last checkpoint writes must be visible to this
-    // thread's asynchronous reads: they come from the same thread, in order
-    __threadfence_block();
 #pragma unroll
     for (int q = 0; q < kYD - 1; ++q) {
         const int c = nch - 1 - q;
@@ -670,89 +662,68 @@ __global__ void __launch_bounds__(kYP) k_ysolve_pair(cplx<float>* __restrict__ S
         cp_commit();
     }
     const float4 walls = se[ny];
-    ds xa_r = {0.f, 0.f}, xa_i = {0.f, 0.f}, xb_r = {0.f, 0.f}, xb_i = {0.f, 0.f};   // x[j+1]
-    float dar = 0.f, dai = 0.f, dbr = 0.f, dbi = 0.f;                              // x[j+2] - x[j+1]
+    ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};      // x[j+1]
+    float dnr = 0.f, dni = 0.f;                 // x[j+2] - x[j+1]
     for (int c = nch - 1; c >= 0; --c) {
         if (c - (kYD - 1) >= 0) issue_bwd(c - (kYD - 1));
         cp_commit();
         cp_wait_group<kYD - 1>();
         const YRing& R = ring[c % kYD];
-        ds qar = {0.f, 0.f}, qai = {0.f, 0.f}, qbr = {0.f, 0.f}, qbi = {0.f, 0.f};
+        ds qr = {0.f, 0.f}, qi = {0.f, 0.f};
         if (c > 0) {
-            const float4 ka = R.k[0][tid], kb = R.k[1][tid];
-            qar = ds{ka.x, ka.y}; qai = ds{ka.z, ka.w};
-            qbr = ds{kb.x, kb.y}; qbi = ds{kb.z, kb.w};
+            const float4 v = R.k[tid];
+            qr = ds{v.x, v.y};
+            qi = ds{v.z, v.w};
         }
-        ds dA_r[kYC], dA_i[kYC], dB_r[kYC], dB_i[kYC];
+        ds dr[kYC], di[kYC];
 #pragma unroll
         for (int i = 0; i < kYC; ++i) {
             const int j = c * kYC + i;
             if (j < ny) {
                 const float2 tv = R.t[i][tid];
                 const ds inv = {tv.x, tv.y};
-                const ds beta = ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv));
-                ds_step(qar, qai, beta, inv, R.a[i][tid]);
-                if (pair) ds_step(qbr, qbi, beta, inv, R.b[i][tid]);
+                ds_step(qr, qi, ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv)), inv, R.s[i][tid]);
             }
-            dA_r[i] = qar; dA_i[i] = qai; dB_r[i] = qbr; dB_i[i] = qbi;
+            dr[i] = qr;
+            di[i] = qi;
         }
 #pragma unroll
         for (int i = kYC - 1; i >= 0; --i) {
             const int j = c * kYC + i;
             if (j < ny) {
-                ds ar_ = dA_r[i], ai_ = dA_i[i], br_ = dB_r[i], bi_ = dB_i[i];
+                ds xr = dr[i], xi = di[i];
                 if (j != ny - 1) {
                     const float2 cv = R.c[i][tid];
                     const ds cp = {cv.x, cv.y};
-                    ar_ = ds_add_fast(ar_, ds_neg(ds_mul(cp, xa_r)));
-                    ai_ = ds_add_fast(ai_, ds_neg(ds_mul(cp, xa_i)));
-                    if (pair) {
-                        br_ = ds_add_fast(br_, ds_neg(ds_mul(cp, xb_r)));
-                        bi_ = ds_add_fast(bi_, ds_neg(ds_mul(cp, xb_i)));
-                    }
+                    xr = ds_add_fast(xr, ds_neg(ds_mul(cp, xr1)));
+                    xi = ds_add_fast(xi, ds_neg(ds_mul(cp, xi1)));
                 }
-                const float far = ds_f(ar_), fai = ds_f(ai_);
-                sA[j * rs] = cplx<float>{far, fai};
-                if (j == ny - 1) fA[(size_t)(ny + 1) * rs] = cplx<float>{walls.y * far, walls.y * fai};
-                float d0ar = 0.f, d0ai = 0.f, d0br = 0.f, d0bi = 0.f;
+                const float fr = ds_f(xr), fi = ds_f(xi);
+                sp[j * rs] = cplx<float>{fr, fi};
+                if (j == ny - 1) fp[(size_t)(ny + 1) * rs] = cplx<float>{walls.y * fr, walls.y * fi};
+                float d0r = 0.f, d0i = 0.f;
                 if (j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
+                    d0r = ds_f(ds_add_fast(xr1, ds_neg(xr)));
+                    d0i = ds_f(ds_add_fast(xi1, ds_neg(xi)));
                     const float4 cf = se[j + 1];
-                    d0ar = ds_f(ds_add_fast(xa_r, ds_neg(ar_)));
-                    d0ai = ds_f(ds_add_fast(xa_i, ds_neg(ai_)));
-                    fA[(size_t)(j + 2) * rs] = cplx<float>{cf.x * ds_f(xa_r) + cf.y * d0ar + cf.z * dar,
-                                                           cf.x * ds_f(xa_i) + cf.y * d0ai + cf.z * dai};
-                    if (pair) {
-                        d0br = ds_f(ds_add_fast(xb_r, ds_neg(br_)));
-                        d0bi = ds_f(ds_add_fast(xb_i, ds_neg(bi_)));
-                        fB[(size_t)(j + 2) * rs] = cplx<float>{cf.x * ds_f(xb_r) + cf.y * d0br + cf.z * dbr,
-                                                               cf.x * ds_f(xb_i) + cf.y * d0bi + cf.z * dbi};
-                    }
+                    fp[(size_t)(j + 2) * rs] = cplx<float>{cf.x * ds_f(xr1) + cf.y * d0r + cf.z * dnr,
+                                                           cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
                 }
-                if (pair) {
-                    const float fbr = ds_f(br_), fbi = ds_f(bi_);
-                    sB[j * rs] = cplx<float>{fbr, fbi};
-                    if (j == ny - 1) fB[(size_t)(ny + 1) * rs] = cplx<float>{walls.y * fbr, walls.y * fbi};
-                }
-                dar = d0ar; dai = d0ai; dbr = d0br; dbi = d0bi;
-                xa_r = ar_; xa_i = ai_; xb_r = br_; xb_i = bi_;
+                dnr = d0r;
+                dni = d0i;
+                xr1 = xr;
+                xi1 = xi;
             }
         }
     }
     cp_wait_group<0>();
     const float4 cf = se[0];
-    {
-        const float x0r = ds_f(xa_r), x0i = ds_f(xa_i);
-        fA[rs] = cplx<float>{cf.x * x0r + cf.z * dar, cf.x * x0i + cf.z * dai};
-        fA[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
-    }
-    if (pair) {
-        const float x0r = ds_f(xb_r), x0i = ds_f(xb_i);
-        fB[rs] = cplx<float>{cf.x * x0r + cf.z * dbr, cf.x * x0i + cf.z * dbi};
-        fB[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
-    }
+    const float x0r = ds_f(xr1), x0i = ds_f(xi1);
+    fp[rs] = cplx<float>{cf.x * x0r + cf.z * dnr, cf.x * x0i + cf.z * dni};
+    fp[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
 }
 
-size_t ysolve_pair_smem(int ny) { return sizeof(YRing) * kYD + sizeof(float4) * (ny + 1) + sizeof(float2) * ny; }
+size_t ysolve_ring_smem(int ny) { return sizeof(YRing) * kYD + sizeof(float4) * (ny + 1) + sizeof(float2) * ny; }
 
 // ---------------------------------------------------------------- z passes (four-step)
 // Forward z transform of S in place: block (cell plane j, W columns of m_x).
@@ -1067,7 +1038,7 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
         cplx<float>* Fyf = (cplx<float>*)c->F + fstride;
         const float2* ads = (const float2*)c->d_yads;
         const float4* yec = (const float4*)c->d_yec;
-k_ysolve_pair<<<(ni + kYP - 1) / kYP, kYP, ysolve_pair_smem(ny), c->stream>>>(
+k_ysolve_ring<<<(ni + kYP / 2 - 1) / (kYP / 2), kYP, ysolve_ring_smem(ny), c->stream>>>(
             Sf, Fyf, tinv, tcp, ads, yec, (float4*)c->d_yck, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
@@ -1155,7 +1126,7 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMalloc(&c->d_yec, sizeof(float4) * (ny + 1)));
         TRIBO_CUDA(cudaMemcpy(c->d_yec, ec.data(), sizeof(float4) * (ny + 1), cudaMemcpyHostToDevice));
-        // forward-sweep checkpoints of the pencil-pair kernel: 2 float4 per (chunk, table row)
+        // forward-sweep checkpoints of the copy-ring kernel: one float4 per (chunk, pencil)
         TRIBO_CUDA(cudaMalloc(&c->d_yck, sizeof(float4) * 2 * (size_t)((ny + kYC - 1) / kYC) * ni));
     }
     int dev = 0, optin = 0;
@@ -1168,7 +1139,7 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_chunk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_ring, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return dispatch_attr<float>(nx, nz, optin);
 }
 
