@@ -329,401 +329,6 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
     frow[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
 }
 
-// ---------------------------------------------------------------- y solve, warp-cooperative
-// Block: kYW consecutive m_x at m_z (warps 0-3) and at nz - m_z (warps 4-7),
-// which share their factor rows; one warp per pencil, lane l holding the rows
-// l*RPL .. l*RPL+RPL-1.  Both Thomas recurrences are affine in the previous
-// value, d'_j = beta_j d'_j-1 + gamma_j (beta_j = -a_j/pivot_j, gamma_j =
-// r_j/pivot_j) and x_j = -c'_j x_j+1 + d'_j, so each is a composition of the
-// lane's maps, a shuffle scan of the 32 lane maps and a local pass, all in
-// double-single.  Inputs are staged in shared memory by asynchronous copies
-// of whole rows of the block's pencils; phi and E_y leave the same way.
-// Shared rows are padded by one slot per lane group (conflict-free reads).
-constexpr int kYW = 4;
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-
-__device__ __forceinline__ ds shfl_up_ds(ds v, int s) {
-    return ds{__shfl_up_sync(0xffffffffu, v.hi, s), __shfl_up_sync(0xffffffffu, v.lo, s)};
-}
-__device__ __forceinline__ ds shfl_down_ds(ds v, int s) {
-    return ds{__shfl_down_sync(0xffffffffu, v.hi, s), __shfl_down_sync(0xffffffffu, v.lo, s)};
-}
-
-template <int RPL>
-__host__ __device__ constexpr int ywarp_rows() { return 32 * (RPL + 1); }
-
-template <int RPL>
-size_t ysolve_warp_smem(int ny) {
-    return sizeof(float4) * kYW * ywarp_rows<RPL>() + sizeof(float2) * 2 * kYW * ywarp_rows<RPL>() +
-           sizeof(float4) * (ny + 1) + sizeof(float2) * ny;
-}
-
-template <int RPL>
-__global__ void __launch_bounds__(256) k_ysolve_warp(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
-                                                     const float2* __restrict__ tinv, const float2* __restrict__ tcp,
-                                                     const float2* __restrict__ a_ds, const float4* __restrict__ ec,
-                                                     int ny, int nz, int nxh) {
-    constexpr int RS = RPL + 1;
-    constexpr int PR = ywarp_rows<RPL>();          // padded rows per pencil
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* T = reinterpret_cast<float4*>(smem_raw);           // [item][padded row] = (1/pivot, c') ds
-    float2* Sv = reinterpret_cast<float2*>(T + kYW * PR);       // [pencil][padded row]
-    float4* se = reinterpret_cast<float4*>(Sv + 2 * kYW * PR);  // ny + 1
-    float2* sa = reinterpret_cast<float2*>(se + ny + 1);         // ny
-    float2* Ev = reinterpret_cast<float2*>(T);                   // [pencil][node], after T is consumed
-    const int mz = blockIdx.x;
-    const int mz2 = nz - mz;
-    const bool pair = mz != 0 && 2 * mz != nz;
-    const int mx0 = blockIdx.y * kYW;
-    const int ni = (nz / 2 + 1) * nxh;
-    const size_t item0 = (size_t)mz * nxh + mx0;
-    auto prow = [](int j) { return (j / RPL) * RS + (j % RPL); };
-    // ---- stage
-    for (int idx = threadIdx.x; idx < ny * kYW; idx += blockDim.x) {
-        const int j = idx / kYW, t = idx - j * kYW;
-        float4* dst = &T[t * PR + prow(j)];
-        if (mx0 + t < nxh) {
-            cp_async8(dst, &tinv[(size_t)j * ni + item0 + t]);
-            cp_async8(reinterpret_cast<float2*>(dst) + 1, &tcp[(size_t)j * ni + item0 + t]);
-        }
-    }
-    for (int idx = threadIdx.x; idx < 2 * ny * kYW; idx += blockDim.x) {
-        const int h = idx / (ny * kYW);
-        const int rem = idx - h * ny * kYW;
-        const int j = rem / kYW, t = rem - j * kYW;
-        const int m = h ? mz2 : mz;
-        if (mx0 + t < nxh && (h == 0 || pair))
-            cp_async8(&Sv[(h * kYW + t) * PR + prow(j)], &S[((size_t)m * ny + j) * nxh + mx0 + t]);
-    }
-    for (int j = threadIdx.x; j < ny; j += blockDim.x) sa[j] = a_ds[j];
-    for (int j = threadIdx.x; j <= ny; j += blockDim.x) se[j] = ec[j];
-    cp_async_wait_all();
-    __syncthreads();
-    // ---- solve: one warp per pencil
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int h = w / kYW, t = w - h * kYW;
-    const bool active = mx0 + t < nxh && (h == 0 || pair);
-    const float4* Tt = T + t * PR + lane * RS;
-    float2* Sp = Sv + w * PR + lane * RS;
-    ds Xr[RPL] = {}, Xi[RPL] = {};
-    if (active) {
-        // forward: lane map, scan, local pass
-        ds B = {1.f, 0.f}, Gr = {0.f, 0.f}, Gi = {0.f, 0.f};
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            const int j = lane * RPL + i;
-            if (j < ny) {
-                const float4 tt = Tt[i];
-                const ds inv = {tt.x, tt.y};
-                const ds beta = ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv));
-                const float2 r = Sp[i];
-                Gr = ds_add_fast(ds_mul(beta, Gr), ds_mul_f(inv, r.x));
-                Gi = ds_add_fast(ds_mul(beta, Gi), ds_mul_f(inv, r.y));
-                B = ds_mul(beta, B);
-            }
-        }
-#pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            const ds Bp = shfl_up_ds(B, s), Grp = shfl_up_ds(Gr, s), Gip = shfl_up_ds(Gi, s);
-            if (lane >= s) {
-                Gr = ds_add_fast(ds_mul(B, Grp), Gr);
-                Gi = ds_add_fast(ds_mul(B, Gip), Gi);
-                B = ds_mul(B, Bp);
-            }
-        }
-        ds dr = shfl_up_ds(Gr, 1), di = shfl_up_ds(Gi, 1);
-        if (lane == 0) { dr = ds{0.f, 0.f}; di = ds{0.f, 0.f}; }
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            const int j = lane * RPL + i;
-            if (j < ny) {
-                const float4 tt = Tt[i];
-                const ds inv = {tt.x, tt.y};
-                const ds beta = ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv));
-                const float2 r = Sp[i];
-                dr = ds_add_fast(ds_mul(beta, dr), ds_mul_f(inv, r.x));
-                di = ds_add_fast(ds_mul(beta, di), ds_mul_f(inv, r.y));
-            }
-            Xr[i] = dr;
-            Xi[i] = di;
-        }
-        // backward: x_j = -c'_j x_j+1 + d'_j (c' of the last row is zero)
-        B = ds{1.f, 0.f}; Gr = ds{0.f, 0.f}; Gi = ds{0.f, 0.f};
-#pragma unroll
-        for (int i = RPL - 1; i >= 0; --i) {
-            const int j = lane * RPL + i;
-            if (j < ny) {
-                const float4 tt = Tt[i];
-                const ds c = j == ny - 1 ? ds{0.f, 0.f} : ds_neg(ds{tt.z, tt.w});
-                Gr = ds_add_fast(ds_mul(c, Gr), Xr[i]);
-                Gi = ds_add_fast(ds_mul(c, Gi), Xi[i]);
-                B = ds_mul(c, B);
-            }
-        }
-#pragma unroll
-        for (int s = 1; s < 32; s <<= 1) {
-            const ds Bn = shfl_down_ds(B, s), Grn = shfl_down_ds(Gr, s), Gin = shfl_down_ds(Gi, s);
-            if (lane + s < 32) {
-                Gr = ds_add_fast(ds_mul(B, Grn), Gr);
-                Gi = ds_add_fast(ds_mul(B, Gin), Gi);
-                B = ds_mul(B, Bn);
-            }
-        }
-        ds xr = shfl_down_ds(Gr, 1), xi = shfl_down_ds(Gi, 1);
-        if (lane == 31) { xr = ds{0.f, 0.f}; xi = ds{0.f, 0.f}; }
-#pragma unroll
-        for (int i = RPL - 1; i >= 0; --i) {
-            const int j = lane * RPL + i;
-            if (j < ny) {
-                const float4 tt = Tt[i];
-                const ds c = j == ny - 1 ? ds{0.f, 0.f} : ds_neg(ds{tt.z, tt.w});
-                xr = ds_add_fast(ds_mul(c, xr), Xr[i]);
-                xi = ds_add_fast(ds_mul(c, xi), Xi[i]);
-                Xr[i] = xr;
-                Xi[i] = xi;
-            }
-        }
-    }
-    // neighbours across the lane boundaries (all lanes take part)
-    ds lr = shfl_up_ds(Xr[RPL - 1], 1), li = shfl_up_ds(Xi[RPL - 1], 1);
-    ds rr = shfl_down_ds(Xr[0], 1), ri = shfl_down_ds(Xi[0], 1);
-    __syncthreads();                         // the factor table is consumed: Ev may overwrite it
-    if (active) {
-        float2* E = Ev + w * (ny + 2);
-        const float4 walls = se[ny];
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            const int j = lane * RPL + i;
-            if (j < ny) {
-                const ds xm_r = i > 0 ? Xr[i - 1] : lr, xm_i = i > 0 ? Xi[i - 1] : li;
-                const ds xp_r = i < RPL - 1 ? Xr[i + 1] : rr, xp_i = i < RPL - 1 ? Xi[i + 1] : ri;
-                const float fr = ds_f(Xr[i]), fi = ds_f(Xi[i]);
-                const float4 cf = se[j];
-                float er = cf.x * fr, ei = cf.x * fi;
-                if (j >= 1) {
-                    er += cf.y * ds_f(ds_add_fast(Xr[i], ds_neg(xm_r)));
-                    ei += cf.y * ds_f(ds_add_fast(Xi[i], ds_neg(xm_i)));
-                }
-                if (j <= ny - 2) {
-                    er += cf.z * ds_f(ds_add_fast(xp_r, ds_neg(Xr[i])));
-                    ei += cf.z * ds_f(ds_add_fast(xp_i, ds_neg(Xi[i])));
-                }
-                E[j + 1] = make_float2(er, ei);
-                Sp[i] = make_float2(fr, fi);
-                if (j == 0) E[0] = make_float2(walls.x * fr, walls.x * fi);
-                if (j == ny - 1) E[ny + 1] = make_float2(walls.y * fr, walls.y * fi);
-            }
-        }
-    }
-    __syncthreads();
-    // ---- write back phi (S) and the E_y spectrum (Fy), whole rows of the block's pencils
-    for (int idx = threadIdx.x; idx < 2 * ny * kYW; idx += blockDim.x) {
-        const int hh = idx / (ny * kYW);
-        const int rem = idx - hh * ny * kYW;
-        const int j = rem / kYW, tt = rem - j * kYW;
-        if (mx0 + tt < nxh && (hh == 0 || pair)) {
-            const float2 v = Sv[(hh * kYW + tt) * PR + prow(j)];
-            S[((size_t)(hh ? mz2 : mz) * ny + j) * nxh + mx0 + tt] = cplx<float>{v.x, v.y};
-        }
-    }
-    const int nyn = ny + 2;
-    for (int idx = threadIdx.x; idx < 2 * nyn * kYW; idx += blockDim.x) {
-        const int hh = idx / (nyn * kYW);
-        const int rem = idx - hh * nyn * kYW;
-        const int jn = rem / kYW, tt = rem - jn * kYW;
-        if (mx0 + tt < nxh && (hh == 0 || pair)) {
-            const float2 v = Ev[(hh * kYW + tt) * nyn + jn];
-            Fy[((size_t)(hh ? mz2 : mz) * nyn + jn) * nxh + mx0 + tt] = cplx<float>{v.x, v.y};
-        }
-    }
-}
-
-// ---------------------------------------------------------------- y solve, copy-ring Thomas
-// One thread per pencil, in double-single.  A block of 64 threads takes 32
-// factor-table rows (|m_z|, m_x): threads l and l + 32 solve the pencils m_z
-// and nz - m_z of row l, which share the factors (the second read of a row
-// meets it in cache).  Each thread streams its rows through a private ring
-// of kYD chunks of kYC rows in shared memory, filled by asynchronous copies
-// kYD - 1 chunks ahead of the sweep, so the sequential recurrence does not
-// wait on memory.  The forward sweep stores the value entering each chunk (a
-// checkpoint, global scratch); the backward sweep walks the chunks from the
-// top, recomputes the chunk's forward values in registers from its
-// checkpoint, substitutes back and forms E_y per cell j as
-// A_j phi_j + Bm_j (phi_j - phi_j-1) + Bp_j (phi_j+1 - phi_j), differences in
-// double-single; wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
-constexpr int kYP = 64;    // threads per block (32 table rows)
-constexpr int kYC = 8;     // rows per chunk
-constexpr int kYD = 3;     // chunks in flight
-
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
-}
-
-struct YRing {       // one slot: kYC rows of each stream per thread, and a checkpoint
-    float2 t[kYC][kYP];    // 1/pivot (ds)
-    float2 c[kYC][kYP];    // c' (ds)
-    float2 s[kYC][kYP];    // right-hand side, then phi
-    float4 k[kYP];         // checkpoint (re hi, re lo, im hi, im lo)
-};
-
-__device__ __forceinline__ void ds_step(ds& vr, ds& vi, ds beta, ds inv, float2 r) {
-    vr = ds_add_fast(ds_mul(beta, vr), ds_mul_f(inv, r.x));
-    vi = ds_add_fast(ds_mul(beta, vi), ds_mul_f(inv, r.y));
-}
-
-__global__ void __launch_bounds__(kYP) k_ysolve_ring(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
-                                                     const float2* __restrict__ tinv, const float2* __restrict__ tcp,
-                                                     const float2* __restrict__ a_ds, const float4* __restrict__ ec,
-                                                     float4* __restrict__ ck, int ny, int nz, int nxh) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    YRing* ring = reinterpret_cast<YRing*>(smem_raw);
-    float4* se = reinterpret_cast<float4*>(ring + kYD);     // ny + 1
-    float2* sa = reinterpret_cast<float2*>(se + ny + 1);     // ny
-    for (int j = threadIdx.x; j < ny; j += kYP) sa[j] = a_ds[j];
-    for (int j = threadIdx.x; j <= ny; j += kYP) se[j] = ec[j];
-    __syncthreads();
-    const int ni = (nz / 2 + 1) * nxh;
-    const int tid = threadIdx.x;
-    const int item = blockIdx.x * (kYP / 2) + (tid & (kYP / 2 - 1));
-    const int half = tid / (kYP / 2);
-    if (item >= ni) return;                      // no block-wide barrier below
-    const int amz = item / nxh;
-    const int mx = item - amz * nxh;
-    if (half == 1 && (amz == 0 || 2 * amz == nz)) return;   // m_z is its own partner
-    const int mz = half ? nz - amz : amz;
-    cplx<float>* sp = S + (size_t)mz * ny * nxh + mx;
-    cplx<float>* fp = Fy + (size_t)mz * (ny + 2) * nxh + mx;
-    float4* ckp = ck + (size_t)half * ni + item;             // [chunk][half][item]
-    const size_t ckstride = 2 * (size_t)ni;
-    const int nch = (ny + kYC - 1) / kYC;
-    const size_t rs = (size_t)nxh;
-    // ---------------- forward sweep
-    auto issue_fwd = [&](int c) {
-        YRing& R = ring[c % kYD];
-#pragma unroll
-        for (int i = 0; i < kYC; ++i) {
-            const int j = c * kYC + i;
-            if (j < ny) {
-                cp_async8(&R.t[i][tid], &tinv[(size_t)j * ni + item]);
-                cp_async8(&R.s[i][tid], &sp[j * rs]);
-            }
-        }
-    };
-#pragma unroll
-    for (int c = 0; c < kYD - 1; ++c) {
-        if (c < nch) issue_fwd(c);
-        cp_commit();
-    }
-    ds pr = {0.f, 0.f}, pim = {0.f, 0.f};
-    for (int c = 0; c < nch; ++c) {
-        if (c + kYD - 1 < nch) issue_fwd(c + kYD - 1);
-        cp_commit();
-        cp_wait_group<kYD - 1>();
-        const YRing& R = ring[c % kYD];
-#pragma unroll
-        for (int i = 0; i < kYC; ++i) {
-            const int j = c * kYC + i;
-            if (j < ny) {
-                const float2 tv = R.t[i][tid];
-                const ds inv = {tv.x, tv.y};
-                ds_step(pr, pim, ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv)), inv, R.s[i][tid]);
-            }
-        }
-        ckp[(size_t)c * ckstride] = make_float4(pr.hi, pr.lo, pim.hi, pim.lo);
-    }
-    cp_wait_group<0>();
-    // ---------------- backward sweep
-    auto issue_bwd = [&](int c) {
-        YRing& R = ring[c % kYD];
-#pragma unroll
-        for (int i = 0; i < kYC; ++i) {
-            const int j = c * kYC + i;
-            if (j < ny) {
-                cp_async8(&R.t[i][tid], &tinv[(size_t)j * ni + item]);
-                cp_async8(&R.c[i][tid], &tcp[(size_t)j * ni + item]);
-                cp_async8(&R.s[i][tid], &sp[j * rs]);
-            }
-        }
-        if (c > 0) cp_async16(&R.k[tid], &ckp[(size_t)(c - 1) * ckstride]);
-    };
-#pragma unroll
-    for (int q = 0; q < kYD - 1; ++q) {
-        const int c = nch - 1 - q;
-        if (c >= 0) issue_bwd(c);
-        cp_commit();
-    }
-    const float4 walls = se[ny];
-    ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};      // x[j+1]
-    float dnr = 0.f, dni = 0.f;                 // x[j+2] - x[j+1]
-    for (int c = nch - 1; c >= 0; --c) {
-        if (c - (kYD - 1) >= 0) issue_bwd(c - (kYD - 1));
-        cp_commit();
-        cp_wait_group<kYD - 1>();
-        const YRing& R = ring[c % kYD];
-        ds qr = {0.f, 0.f}, qi = {0.f, 0.f};
-        if (c > 0) {
-            const float4 v = R.k[tid];
-            qr = ds{v.x, v.y};
-            qi = ds{v.z, v.w};
-        }
-        ds dr[kYC], di[kYC];
-#pragma unroll
-        for (int i = 0; i < kYC; ++i) {
-            const int j = c * kYC + i;
-            if (j < ny) {
-                const float2 tv = R.t[i][tid];
-                const ds inv = {tv.x, tv.y};
-                ds_step(qr, qi, ds_neg(ds_mul(ds{sa[j].x, sa[j].y}, inv)), inv, R.s[i][tid]);
-            }
-            dr[i] = qr;
-            di[i] = qi;
-        }
-#pragma unroll
-        for (int i = kYC - 1; i >= 0; --i) {
-            const int j = c * kYC + i;
-            if (j < ny) {
-                ds xr = dr[i], xi = di[i];
-                if (j != ny - 1) {
-                    const float2 cv = R.c[i][tid];
-                    const ds cp = {cv.x, cv.y};
-                    xr = ds_add_fast(xr, ds_neg(ds_mul(cp, xr1)));
-                    xi = ds_add_fast(xi, ds_neg(ds_mul(cp, xi1)));
-                }
-                const float fr = ds_f(xr), fi = ds_f(xi);
-                sp[j * rs] = cplx<float>{fr, fi};
-                if (j == ny - 1) fp[(size_t)(ny + 1) * rs] = cplx<float>{walls.y * fr, walls.y * fi};
-                float d0r = 0.f, d0i = 0.f;
-                if (j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
-                    d0r = ds_f(ds_add_fast(xr1, ds_neg(xr)));
-                    d0i = ds_f(ds_add_fast(xi1, ds_neg(xi)));
-                    const float4 cf = se[j + 1];
-                    fp[(size_t)(j + 2) * rs] = cplx<float>{cf.x * ds_f(xr1) + cf.y * d0r + cf.z * dnr,
-                                                           cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
-                }
-                dnr = d0r;
-                dni = d0i;
-                xr1 = xr;
-                xi1 = xi;
-            }
-        }
-    }
-    cp_wait_group<0>();
-    const float4 cf = se[0];
-    const float x0r = ds_f(xr1), x0i = ds_f(xi1);
-    fp[rs] = cplx<float>{cf.x * x0r + cf.z * dnr, cf.x * x0i + cf.z * dni};
-    fp[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
-}
-
-size_t ysolve_ring_smem(int ny) { return sizeof(YRing) * kYD + sizeof(float4) * (ny + 1) + sizeof(float2) * ny; }
 
 // ---------------------------------------------------------------- z passes (four-step)
 // Forward z transform of S in place: block (cell plane j, W columns of m_x).
@@ -1033,13 +638,12 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
     } else {
         const float2* tinv = (const float2*)c->d_ytab;
         const float2* tcp = tinv + (size_t)ny * ni;
-        const dim3 wg(nz / 2 + 1, (nxh + kYW - 1) / kYW);
-        cplx<float>* Sf = (cplx<float>*)c->S;
-        cplx<float>* Fyf = (cplx<float>*)c->F + fstride;
-        const float2* ads = (const float2*)c->d_yads;
-        const float4* yec = (const float4*)c->d_yec;
-k_ysolve_ring<<<(ni + kYP / 2 - 1) / (kYP / 2), kYP, ysolve_ring_smem(ny), c->stream>>>(
-            Sf, Fyf, tinv, tcp, ads, yec, (float4*)c->d_yck, ny, nz, nxh);
+        constexpr int CH = 8;
+        const int nch = (ny + CH - 1) / CH;
+        const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
+        k_ysolve_chunk<CH><<<(nz * nxh + 127) / 128, 128, shc, c->stream>>>(
+            (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
+            (const float4*)c->d_yec, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_INV_Z);
@@ -1126,8 +730,6 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMalloc(&c->d_yec, sizeof(float4) * (ny + 1)));
         TRIBO_CUDA(cudaMemcpy(c->d_yec, ec.data(), sizeof(float4) * (ny + 1), cudaMemcpyHostToDevice));
-        // forward-sweep checkpoints of the copy-ring kernel: one float4 per (chunk, pencil)
-        TRIBO_CUDA(cudaMalloc(&c->d_yck, sizeof(float4) * 2 * (size_t)((ny + kYC - 1) / kYC) * ni));
     }
     int dev = 0, optin = 0;
     TRIBO_CUDA(cudaGetDevice(&dev));
@@ -1139,7 +741,6 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_chunk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_ring, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return dispatch_attr<float>(nx, nz, optin);
 }
 
@@ -1150,8 +751,7 @@ void poisson_fast_free(tribo_ctx* c) {
     cudaFree(c->d_twz);
     cudaFree(c->d_yads);
     cudaFree(c->d_yec);
-    cudaFree(c->d_yck);
-    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = c->d_yck = nullptr;
+    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = nullptr;
 }
 
 tribo_status poisson_fast_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,

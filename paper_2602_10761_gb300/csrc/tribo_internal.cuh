@@ -119,7 +119,6 @@ struct tribo_ctx {
     void* d_twz = nullptr;       // nz twiddles
     void* d_yads = nullptr;      // ny float2: y sub-diagonal in double-single (mixed mode)
     void* d_yec = nullptr;       // ny+1 float4: E_y coefficients per cell, walls (mixed mode)
-    void* d_yck = nullptr;       // forward-sweep checkpoints of the y solve (mixed mode)
 
     // synthetic mode field (fluid.cu)
     int n_modes = 0;
