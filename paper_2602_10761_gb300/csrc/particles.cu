@@ -34,7 +34,7 @@ namespace tribo {
 namespace {
 
 template <class R>
-__global__ void __launch_bounds__(kThreads, 5) k_step(StepArgs<R> a, PView p, int write_cell) {
+__global__ void __launch_bounds__(kThreads, 4) k_step(StepArgs<R> a, PView p, int write_cell) {
     extern __shared__ unsigned int sh_hist[];
     const bool use_hist = a.hist != nullptr;
     if (use_hist) {
