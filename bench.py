@@ -286,14 +286,14 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     }
 
 
-def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world=1):
+def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world=1, channels=64, scale=1.0):
     """Batched ensemble of 64 independent channels (Re_tau in {180, 300, 395,
     550}, grids 64^3 to 192x128x128, 50k-2M particles each, d+ in [0.5, 3]):
     aggregate particle-steps/s of the batch (graph-captured steps, persistent
     particle kernel over all channels, autotuned shape) against the same
     channels stepped one after another with tribo_step.  With several ranks the
     channels are sharded over the ranks (independent problems, no exchange)."""
-    all_cases = synth.ensemble_cases()
+    all_cases = synth.ensemble_cases(channels, scale=scale)
     cases = shard(all_cases, rank, world)
     chans, Ps, dts = [], [], []
     for c in cases:
@@ -343,7 +343,7 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
     ntot = sum(c.n_particles for c in all_cases)
     batch_rate = ntot * steps / (batch_ms * 1e-3)
     seq_rate = ntot * seq_steps / (seq_ms * 1e-3)
-    return {"workload": (f"64 channels (synth.ensemble_cases): Re_tau in {{180,300,395,550}}, grids 64^3 to "
+    return {"workload": (f"{channels} channels (synth.ensemble_cases): Re_tau in {{180,300,395,550}}, grids 64^3 to "
                          f"192x128x128, {ntot} particles in total, d+ in [0.5,3], sort every {sort_every}"),
             "steps": steps, "ms_per_step": batch_ms / steps, "particle_steps_per_s": batch_rate,
             "sequential_particle_steps_per_s": seq_rate, "sequential_steps": seq_steps,
@@ -408,6 +408,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--adj-steps", type=int, default=500, help="adjoint section: steps (500 = the workload)")
+    ap.add_argument("--adj-ckpt", type=int, default=50, help="adjoint section: steps between stored states")
+    ap.add_argument("--batch-steps", type=int, default=500)
+    ap.add_argument("--batch-channels", type=int, default=64)
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="batched section: particle-count factor")
     ap.add_argument("--sort-every", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -538,9 +543,10 @@ def main():
     }
     ch.close()
     if rank == 0 and world == 1 and not args.no_adjoint:
-        line["adjoint"] = adjoint_report(T, torch)
+        line["adjoint"] = adjoint_report(T, torch, steps=args.adj_steps, ckpt=args.adj_ckpt)
     if not args.no_batch:
-        line["batched"] = batch_report(T, torch, rank=rank, world=world)
+        line["batched"] = batch_report(T, torch, steps=args.batch_steps, rank=rank, world=world,
+                                       channels=args.batch_channels, scale=args.batch_scale)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(c, faces, lat, P, args.cpu_sample)
     if rank == 0:
