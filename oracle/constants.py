@@ -40,7 +40,8 @@ class Params:
     takes the gas permittivity equal to the vacuum one.
     U_c (contact potential) is not given in the paper (reading: a free
     parameter, default 1 V).  kappa_A scales the Hertz contact area (1 in the
-    paper).
+    paper).  coulomb adds the near field of the hybrid electrostatics
+    (Sec. 2.2): Coulomb's law between particles that share a cell.
     """
     mu_p: float = TABLE1["mu_p"]
     E_p: float = TABLE1["E_p"]
@@ -61,6 +62,7 @@ class Params:
     impact_vel: int = IMPACT_SPEED
     dq_t: bool = True
     electrostatics: bool = True
+    coulomb: bool = False
 
     def with_(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -123,6 +123,38 @@ def _phi12(s):
     return phi1, phi2
 
 
+def coulomb_near(g: Grid, p: Params, st: "State") -> np.ndarray:
+    """Near-field acceleration of the hybrid electrostatics (Sec. 2.2).
+
+    Coulomb's law between every pair of particles that share a grid cell,
+    F_i = q_i q_j / (4 pi eps) (s_i - s_j) / |s_i - s_j|^3 (like charges repel,
+    Newton's third law F_j = -F_i), divided by m_p as a specific force like
+    the other terms of Eq. (particle-motion).  Readings: the printed unit
+    vector and magnitude are read as the textbook Coulomb law; the far field
+    is the mesh field of all charges, unchanged.  Returns (n, 3).
+    """
+    i, j, k = locate(g, st.x, st.y, st.z)
+    key = g.cell_key(i, j, k)
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    starts = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]])
+    ends = np.r_[starts[1:], ks.shape[0]]
+    X = np.stack([st.x, st.y, st.z], axis=1)
+    coef = 1.0 / (4.0 * math.pi * p.eps)
+    mass = particle_mass(p, st.d)
+    acc = np.zeros((st.n, 3))
+    for s, e in zip(starts, ends):
+        if e - s < 2:
+            continue
+        idx = order[s:e]
+        r = X[idx][:, None, :] - X[idx][None, :, :]          # s_a - s_b
+        dist = np.linalg.norm(r, axis=2)
+        np.fill_diagonal(dist, np.inf)
+        f = coef * (st.q[idx][:, None] * st.q[idx][None, :])[:, :, None] * r / dist[:, :, None] ** 3
+        acc[idx] += f.sum(axis=1) / mass[idx][:, None]
+    return acc
+
+
 def push(p: Params, x, v, uf, acc, d, dt):
     """Advance position and velocity over dt with u, a frozen (exponential).
 
@@ -215,6 +247,8 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
             diag.update(rho=rho, phi=phi, E=E, Ep=Ep)
     else:
         acc = np.zeros((n, 3))
+    if p.electrostatics and p.coulomb:
+        acc = acc + coulomb_near(g, p, st)
     Xn, Vn, tau = push(p, X, V, uf, acc, st.d, dt)
     xn = wrap(Xn[:, 0], g.lx)
     zn = wrap(Xn[:, 2], g.lz)
