@@ -91,13 +91,18 @@ typedef struct {
  *       (Eq. precharge-surface read as contact-area fraction), 0 to omit it.
  * electrostatics: 1 to deposit, solve and apply q E / m each step, 0 for none.
  * sort_every: re-sort particles by cell every this many steps (0 = never);
- *       sorting permutes all particle arrays, including id. */
+ *       sorting permutes all particle arrays, including id.
+ * coulomb: 1 to add the near field of the hybrid electrostatics (Sec. 2.2):
+ *       Coulomb's law between particles that share a cell, on top of the mesh
+ *       field (needs electrostatics = 1 and max_particles >= n; not available
+ *       in tribo_adjoint or a batch). */
 typedef struct {
     double mu_p, E_p, phi_p, k_e, mu_w, E_w, eps_w, h, eps, eps0;
     double nu, rho, rho_p;
     double U_c, kappa_A;
     int32_t drag_law, impact_vel, dq_t, electrostatics, precision;
     int32_t sort_every;
+    int32_t coulomb;
 } tribo_params;
 
 /* Gas velocity on the wall-extended lattice (Nz, Ny+2, Nx, 3) of "real":

@@ -131,7 +131,8 @@ def coulomb_near(g: Grid, p: Params, st: "State") -> np.ndarray:
     Newton's third law F_j = -F_i), divided by m_p as a specific force like
     the other terms of Eq. (particle-motion).  Readings: the printed unit
     vector and magnitude are read as the textbook Coulomb law; the far field
-    is the mesh field of all charges, unchanged.  Returns (n, 3).
+    is the mesh field of all charges, unchanged; coincident centres exert no
+    force.  Returns (n, 3).
     """
     i, j, k = locate(g, st.x, st.y, st.z)
     key = g.cell_key(i, j, k)
@@ -149,7 +150,7 @@ def coulomb_near(g: Grid, p: Params, st: "State") -> np.ndarray:
         idx = order[s:e]
         r = X[idx][:, None, :] - X[idx][None, :, :]          # s_a - s_b
         dist = np.linalg.norm(r, axis=2)
-        np.fill_diagonal(dist, np.inf)
+        dist = np.where(dist > 0, dist, np.inf)          # self and coincident centres: no force
         f = coef * (st.q[idx][:, None] * st.q[idx][None, :])[:, :, None] * r / dist[:, :, None] ** 3
         acc[idx] += f.sum(axis=1) / mass[idx][:, None]
     return acc

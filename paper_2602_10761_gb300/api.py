@@ -43,6 +43,7 @@ class Params:
     electrostatics: int = 1
     precision: int = _abi.TRIBO_MIXED
     sort_every: int = 0
+    coulomb: int = 0          # in-cell Coulomb near field (hybrid electrostatics)
 
     def to_c(self) -> _abi.tribo_params:
         p = _abi.tribo_params()

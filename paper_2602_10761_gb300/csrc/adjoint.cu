@@ -597,6 +597,10 @@ extern "C" tribo_status tribo_adjoint(tribo_ctx* c, tribo_particles* p, double d
         set_last_error("a required particle array is NULL");
         return TRIBO_ERR_ARG;
     }
+    if (c->P.electrostatics && c->P.coulomb) {
+        set_last_error("tribo_adjoint does not differentiate the Coulomb near field");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
     if (nsteps < 0 || ckpt_every < 1 || !(dt > 0) || !std::isfinite(dt)) {
         set_last_error("need nsteps >= 0, ckpt_every >= 1 and dt > 0");
         return TRIBO_ERR_ARG;

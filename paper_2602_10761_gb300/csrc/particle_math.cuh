@@ -45,6 +45,7 @@ struct StepArgs {
     double eps_over_h;
     double inv_T_w;
     double U_c;
+    const R* acoul;                // near-field acceleration planes (x, y, z; n each), or NULL
 };
 
 template <class R> __device__ __forceinline__ R rfloor(R v);
@@ -234,6 +235,7 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     a.eps_over_h = P.eps / P.h;
     a.inv_T_w = 1.0 / (P.eps_w * P.eps0 * P.phi_p);
     a.U_c = P.U_c;
+    a.acoul = nullptr;
     return a;
 }
 
@@ -266,6 +268,9 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     if (a.electro) {
         const R qm = from_f64<R>(q) / (a.mass_coef * d * d * d);
         ax = qm * Ef[0]; ay = qm * Ef[1]; az = qm * Ef[2];
+    }
+    if (a.acoul) {
+        ax += a.acoul[n]; ay += a.acoul[p.n + n]; az += a.acoul[2 * p.n + n];
     }
     R xn, yn, zn, vxn, vyn, vzn;
     if (a.drag_law == TRIBO_DRAG_OFF) {

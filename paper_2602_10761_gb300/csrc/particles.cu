@@ -102,6 +102,7 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
     a.hist = io.stats ? c->d_hist : nullptr;
     if (io.E) a.E = (const R*)io.E;
     if (io.acc) a.acc = io.acc;
+    a.acoul = (const R*)io.acoul;
     const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
     phase_begin(c, PH_STEP);
     k_step<R><<<grid_for(p.n), kThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
@@ -241,6 +242,40 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restric
     }
 }
 
+__global__ void k_cell_members(const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ key,
+                               const uint32_t* __restrict__ rank, int64_t n, uint32_t* __restrict__ members) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        members[offsets[key[i]] + rank[i]] = (uint32_t)i;
+}
+
+// per-cell lists: key and rank of every particle, cell offsets (exclusive
+// scan of the counts) in sort_counts, members grouped by cell
+template <class R>
+tribo_status cell_lists_impl(tribo_ctx* c, const PView& p, uint32_t* members) {
+    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+    const int ntiles = (int)((ncell + kScanTile - 1) / kScanTile);
+    phase_begin(c, PH_AUX);
+    TRIBO_CUDA(cudaMemsetAsync(c->sort_counts, 0, sizeof(uint32_t) * ncell, c->stream));
+    StepArgs<R> a = make_args<R>(c, 0.0);
+    k_sort_count<R><<<grid_for(p.n), kThreads, 0, c->stream>>>(a, p, c->sort_counts, c->sort_key, c->sort_rank);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_AUX);
+    k_scan_tiles<<<ntiles, kScanThreads, 0, c->stream>>>(c->sort_counts, ncell, c->sort_tiles);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_AUX);
+    k_scan_sums<<<1, kScanThreads, 0, c->stream>>>(c->sort_tiles, ntiles);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_AUX);
+    k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(c->sort_counts, ncell, c->sort_tiles);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_AUX);
+    k_cell_members<<<grid_for(p.n), kThreads, 0, c->stream>>>(c->sort_counts, c->sort_key, c->sort_rank, p.n,
+                                                              members);
+    TRIBO_LAUNCHED(c);
+    return TRIBO_OK;
+}
+
 template <class R>
 tribo_status sort_impl(tribo_ctx* c, const PView& src, const PView& dst) {
     const size_t ncell = (size_t)c->nx * c->ny * c->nz;
@@ -274,6 +309,12 @@ tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst) {
     if (src.n == 0) return TRIBO_OK;
     if (c->prec == TRIBO_FP64) return sort_impl<double>(c, src, dst);
     return sort_impl<float>(c, src, dst);
+}
+
+tribo_status particles_cell_lists(tribo_ctx* c, const PView& p, uint32_t* members) {
+    if (p.n == 0) return TRIBO_OK;
+    if (c->prec == TRIBO_FP64) return cell_lists_impl<double>(c, p, members);
+    return cell_lists_impl<float>(c, p, members);
 }
 
 tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell,

@@ -140,6 +140,8 @@ struct tribo_ctx {
     uint32_t* sort_rank = nullptr;     // max_particles
     uint32_t* sort_tiles = nullptr;    // scan tile sums
     int64_t steps_done = 0;            // steps taken by this context (sort schedule)
+    uint32_t* nf_members = nullptr;    // near field: particle indices grouped by cell
+    void* nf_acc = nullptr;            // near field: acceleration planes (3 x max_particles real)
     void* adj = nullptr;               // adjoint workspace (checkpoints, segment states, adjoints)
     size_t adj_bytes = 0;
 
@@ -215,6 +217,7 @@ struct StepIO {               // per-call overrides of the context's buffers
     const void* E = nullptr;     // field lattice (NULL: the context's E lattice)
     Accum* acc = nullptr;        // statistics and error word (NULL: the context's)
     bool stats = true;           // add the positions to the y histogram
+    const void* acoul = nullptr; // near-field acceleration planes (x, y, z) or NULL
 };
 tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next,
                             bool write_cell, const StepIO& io = StepIO());
@@ -222,6 +225,11 @@ tribo_status particles_sum_q(tribo_ctx* c, const PView& p, double* d_out);
 // dst receives src sorted by cell key (all arrays; id if present)
 tribo_status particles_sort(tribo_ctx* c, const PView& src, const PView& dst);
 tribo_status particles_setup(tribo_ctx* c);
+// per-cell lists of p (needs max_particles >= p.n): cell offsets in sort_counts,
+// key and rank in sort_key and sort_rank, members grouped by cell
+tribo_status particles_cell_lists(tribo_ctx* c, const PView& p, uint32_t* members);
+// near-field (in-cell Coulomb) acceleration planes of p, from the cell lists (nearfield.cu)
+tribo_status particles_coulomb(tribo_ctx* c, const PView& p, const uint32_t* members, void* acoul);
 // view of n particles in a particle-set buffer of the context (stage or alt)
 PView set_view(tribo_ctx* c, void* base, int64_t n);
 PView stage_view(tribo_ctx* c, int64_t n);
