@@ -24,7 +24,7 @@ def _built():
 
 
 def _case(n=2000, seed=31):
-    return problem(8, 6, 4, n=n, q_scale=1e-12, vy_scale=0.2, near_wall=0.05, seed=seed, dplus=(0.8, 2.0))
+    return problem(8, 6, 4, n=n, q_scale=1.5e-12, vy_scale=0.2, near_wall=0.05, seed=seed, dplus=(0.8, 2.0))
 
 
 def _gpu(c, faces, lat, parts, prec, nsteps, **pkw):
