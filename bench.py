@@ -351,6 +351,46 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
             "kernels_per_step": launches / steps}
 
 
+def timevarying_report(T, torch, steps=200, sort_every=20):
+    """The 128^3 time-varying workload (Re_tau 180, 1M particles, d+ log-uniform
+    in [0.5, 2], Gaussian initial charges): the gas field is re-evaluated from
+    its 256 advected modes on the device before every step.  Reports
+    particle-steps/s of the whole step and the per-kernel split, with the field
+    evaluation (input generation) separate."""
+    c = synth.case("re180_128")
+    faces = synth.y_faces(c.ny, c.delta, c.gamma)
+    params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0,
+                      sort_every=sort_every)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, None, max_particles=c.n_particles)
+    Y = synth.node_y(faces)
+    ch.set_modes(synth.draw_modes(c), synth.mean_velocity(Y, c), synth.damping(Y, c), 0.0)
+    P = synth.draw_particles(c)
+    Pd = T.Particles.from_numpy(dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q),
+                                T.TRIBO_MIXED, device="cuda")
+    ch.step(Pd, c.dt, 5)
+    torch.cuda.synchronize()
+    T.tribo_timing_enable(ch.ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ch.step(Pd, c.dt, steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph = T.tribo_timing_read(ch.ctx)
+    T.tribo_timing_enable(ch.ctx, False)
+    ch.sync()
+    ch.close()
+    per = {k: v[0] / steps for k, v in ph.items() if v[1]}
+    field = per.get("fluid_modes", 0.0)
+    poisson = sum(v for k, v in per.items() if k.startswith("poisson"))
+    return {"workload": workload_desc(c) + ", time-varying field (256 advected modes, evaluated every step)",
+            "steps": steps, "ms_per_step": ms / steps, "particle_steps_per_s": c.n_particles * steps / (ms * 1e-3),
+            "field_ms_per_step": field, "poisson_ms_per_step": poisson,
+            "particle_step_ms": per.get("particle_step", 0.0),
+            "particle_steps_per_s_without_field": c.n_particles * steps / ((ms - field * steps) * 1e-3),
+            "poisson_solves_per_s": 1e3 / poisson if poisson > 0 else None}
+
+
 def cpu_baseline(c, faces, lat, P, n_sample):
     t_field, t_part = oracle_step_time(c, faces, lat, P, n_sample)
     t_full = t_field + t_part * (c.n_particles / n_sample)
@@ -408,6 +448,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-timevarying", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=500, help="adjoint section: steps (500 = the workload)")
     ap.add_argument("--adj-ckpt", type=int, default=50, help="adjoint section: steps between stored states")
     ap.add_argument("--batch-steps", type=int, default=500)
@@ -544,6 +585,8 @@ def main():
     ch.close()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(T, torch, steps=args.adj_steps, ckpt=args.adj_ckpt)
+    if rank == 0 and world == 1 and not args.no_timevarying:
+        line["timevarying"] = timevarying_report(T, torch)
     if not args.no_batch:
         line["batched"] = batch_report(T, torch, steps=args.batch_steps, rank=rank, world=world,
                                        channels=args.batch_channels, scale=args.batch_scale)

@@ -99,7 +99,7 @@ __device__ __forceinline__ ImpactGrad impact_grad(const StepArgs<R>& a, double k
 }
 
 template <class R>
-__global__ void __launch_bounds__(kThreads) k_adj_step(StepArgs<R> a, AdjArgs<R> g) {
+__global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs<R> g) {
     double pU = 0.0, pK = 0.0;
     unsigned int err = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -115,20 +115,39 @@ __global__ void __launch_bounds__(kThreads) k_adj_step(StepArgs<R> a, AdjArgs<R>
         (void)cell_key<R>(x, y, z, a, &j);
         Corners<R> cr;
         corners<R>(a, x, y, z, j, cr, &err);
+        // gather (the arithmetic of k_step) and, in the same pass, the
+        // trilinear Jacobians J[comp][dim] = d(field comp)/d(weight dim) of u and E
+        const R wx0 = (R)1 - cr.wx, wy0 = (R)1 - cr.wy, wz0 = (R)1 - cr.wz;
+        const R Wx[2] = {wx0, cr.wx}, Wy[2] = {wy0, cr.wy}, Wz[2] = {wz0, cr.wz};
         R uf[3] = {0, 0, 0}, Ep[3] = {0, 0, 0};
+        R Ju[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, JE[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            uf[0] += cr.w[c] * __ldg(a.u + cr.idx[c]);
-            uf[1] += cr.w[c] * __ldg(a.u + a.nodes + cr.idx[c]);
-            uf[2] += cr.w[c] * __ldg(a.u + 2 * a.nodes + cr.idx[c]);
+            const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+            const R gx = (bx ? (R)1 : (R)-1) * Wz[bz] * Wy[by];
+            const R gy = (by ? (R)1 : (R)-1) * Wz[bz] * Wx[bx];
+            const R gz = (bz ? (R)1 : (R)-1) * Wy[by] * Wx[bx];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const R v = __ldg(a.u + q * a.nodes + cr.idx[c]);
+                uf[q] += cr.w[c] * v;
+                Ju[q][0] += gx * v; Ju[q][1] += gy * v; Ju[q][2] += gz * v;
+            }
         }
         R inv_m = 0, qm = 0;
         if (a.electro) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                Ep[0] += cr.w[c] * __ldg(a.E + cr.idx[c]);
-                Ep[1] += cr.w[c] * __ldg(a.E + a.nodes + cr.idx[c]);
-                Ep[2] += cr.w[c] * __ldg(a.E + 2 * a.nodes + cr.idx[c]);
+                const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
+                const R gx = (bx ? (R)1 : (R)-1) * Wz[bz] * Wy[by];
+                const R gy = (by ? (R)1 : (R)-1) * Wz[bz] * Wx[bx];
+                const R gz = (bz ? (R)1 : (R)-1) * Wy[by] * Wx[bx];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const R v = __ldg(a.E + q * a.nodes + cr.idx[c]);
+                    Ep[q] += cr.w[c] * v;
+                    JE[q][0] += gx * v; JE[q][1] += gy * v; JE[q][2] += gz * v;
+                }
             }
             inv_m = (R)1 / (a.mass_coef * d * d * d);
             qm = from_f64<R>(q) / (a.mass_coef * d * d * d);
@@ -271,28 +290,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_step(StepArgs<R> a, AdjArgs<R>
             qb_in += (double)(aE * inv_m);
             dbar += (double)((R)-3 * aa / d);
         }
-        // gather: scatter E_p-bar, position derivative of the weights
-        R gc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            R gv = ufb[0] * __ldg(a.u + cr.idx[c]) + ufb[1] * __ldg(a.u + a.nodes + cr.idx[c]) +
-                   ufb[2] * __ldg(a.u + 2 * a.nodes + cr.idx[c]);
-            if (a.electro) {
-                gv += Epb[0] * __ldg(a.E + cr.idx[c]) + Epb[1] * __ldg(a.E + a.nodes + cr.idx[c]) +
-                      Epb[2] * __ldg(a.E + 2 * a.nodes + cr.idx[c]);
-            }
-            gc[c] = gv;
-        }
-        const R wx0 = (R)1 - cr.wx, wy0 = (R)1 - cr.wy, wz0 = (R)1 - cr.wz;
-        const R Wx[2] = {wx0, cr.wx}, Wy[2] = {wy0, cr.wy}, Wz[2] = {wz0, cr.wz};
+        // gather: position derivative through the Jacobians, then the scatter of E_p-bar
         R gx = 0, gy = 0, gz = 0;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int bx = c & 1, by = (c >> 1) & 1, bz = c >> 2;
-            const R sx_ = bx ? (R)1 : (R)-1, sy_ = by ? (R)1 : (R)-1, sz_ = bz ? (R)1 : (R)-1;
-            gx += gc[c] * sx_ * Wz[bz] * Wy[by];
-            gy += gc[c] * sy_ * Wz[bz] * Wx[bx];
-            gz += gc[c] * sz_ * Wy[by] * Wx[bx];
+        for (int q = 0; q < 3; ++q) {
+            gx += ufb[q] * Ju[q][0] + Epb[q] * JE[q][0];
+            gy += ufb[q] * Ju[q][1] + Epb[q] * JE[q][1];
+            gz += ufb[q] * Ju[q][2] + Epb[q] * JE[q][2];
         }
         xb[0] += gx * a.inv_dx;
         xb[1] += gy * cr.inv_dy;

@@ -7,7 +7,7 @@
 // Two kernels per evaluation:
 //   k_mode_phase: per (lattice y row, mode) the FP64 factor
 //                 damp(y) exp(i (ky y + phase - kx ubar t)), rounded to real;
-//   k_mode_eval:  per lattice row (k, jn) the sum over modes of
+//   k_mode_eval:  per group of kRows lattice rows (k, jn) the sum over modes of
 //                 amp_m Re(c_m Z_m(k) X_m(i)) with X_m(i) = exp(i pi nxi (2i+1)/nx)
 //                 and Z_m(k) = exp(i pi nzi (2k+1)/nz) taken from tables of
 //                 exp(i pi l / n) (exact integer index arithmetic).  Nodes i and
@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kModeChunk = 256;   // modes staged in shared memory per pass
 constexpr int kEvalThreads = 64;
+constexpr int kRows = 4;          // z rows per block: the x factor and amplitudes serve all of them
 
 template <class R>
 __global__ void k_mode_phase(int rows, int nm, const double* __restrict__ mf, const double* __restrict__ Y,
@@ -53,56 +54,71 @@ __global__ void __launch_bounds__(kEvalThreads)
 k_mode_eval(int nx, int ny2, int nz, int nm, const int2* __restrict__ ma, const double* __restrict__ mf,
             const cplx<R>* __restrict__ mc, const cplx<R>* __restrict__ tabx, const cplx<R>* __restrict__ tabz,
             const double* __restrict__ ubar, R* __restrict__ out) {
-    __shared__ cplx<R> G[kModeChunk];
-    __shared__ R A0[kModeChunk], A1[kModeChunk], A2[kModeChunk];
-    __shared__ int AX[kModeChunk];
-    const int k = blockIdx.x, jn = blockIdx.y;
+    __shared__ cplx<R> G[kRows][kModeChunk];      // c_m(jn) Z_m(k) per row of the block
+    __shared__ vec4<R> A[kModeChunk];             // amplitude vector
+    __shared__ int AX[kModeChunk];                // nxi mod 2 nx
+    const int k0 = blockIdx.x * kRows, jn = blockIdx.y;
+    const int nrow = min(kRows, nz - k0);
     const int n2x = 2 * nx, n2z = 2 * nz;
     const float inv2x = 1.0f / (float)n2x, inv2z = 1.0f / (float)n2z;
-    const int kk = 2 * k + 1;
     const int npair = nx / 2;
     const size_t plane = (size_t)nz * ny2 * nx;
-    R* row = out + ((size_t)k * ny2 + jn) * nx;
     const R ub = from_f64<R>(ubar[jn]);
     for (int p0 = 0; p0 < npair; p0 += kEvalThreads) {
         const int i = p0 + threadIdx.x;
         const int ii = 2 * i + 1;
-        R ur0 = 0, ur1 = 0, ur2 = 0, ul0 = 0, ul1 = 0, ul2 = 0;
+        R acc[kRows][6];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc[r][q] = 0;
         for (int m0 = 0; m0 < nm; m0 += kModeChunk) {
             const int cnt = min(kModeChunk, nm - m0);
             __syncthreads();
             for (int e = threadIdx.x; e < cnt; e += kEvalThreads) {
                 const int m = m0 + e;
-                const int2 a = ma[m];
-                const cplx<R> z = tabz[mod_small(a.y * kk, n2z, inv2z)];
-                G[e] = mc[(size_t)jn * nm + m] * z;
-                A0[e] = from_f64<R>(mf[6 * m + 3]);
-                A1[e] = from_f64<R>(mf[6 * m + 4]);
-                A2[e] = from_f64<R>(mf[6 * m + 5]);
-                AX[e] = a.x;
+                const int2 am = ma[m];
+                const cplx<R> cm = mc[(size_t)jn * nm + m];
+#pragma unroll
+                for (int r = 0; r < kRows; ++r)
+                    G[r][e] = r < nrow ? cm * tabz[mod_small(am.y * (2 * (k0 + r) + 1), n2z, inv2z)]
+                                       : cplx<R>{0, 0};
+                A[e] = vec4<R>{from_f64<R>(mf[6 * m + 3]), from_f64<R>(mf[6 * m + 4]), from_f64<R>(mf[6 * m + 5]),
+                               (R)0};
+                AX[e] = am.x;
             }
             __syncthreads();
             if (i < npair) {
-#pragma unroll 4
+#pragma unroll 2
                 for (int e = 0; e < cnt; ++e) {
                     const cplx<R> X = tabx[mod_small(AX[e] * ii, n2x, inv2x)];
-                    const cplx<R> g = G[e];
-                    const R p = g.re * X.re, q = g.im * X.im;
-                    const R tr = p - q;            // Re(g X): node i
-                    const R tl = p + q;            // Re(g conj X): node nx-1-i
-                    ur0 += A0[e] * tr; ur1 += A1[e] * tr; ur2 += A2[e] * tr;
-                    ul0 += A0[e] * tl; ul1 += A1[e] * tl; ul2 += A2[e] * tl;
+                    const vec4<R> av = A[e];
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r) {
+                        const cplx<R> g = G[r][e];
+                        const R p = g.re * X.re, q = g.im * X.im;
+                        const R tr = p - q;            // Re(g X): node i
+                        const R tl = p + q;            // Re(g conj X): node nx-1-i
+                        acc[r][0] += av.x * tr; acc[r][1] += av.y * tr; acc[r][2] += av.z * tr;
+                        acc[r][3] += av.x * tl; acc[r][4] += av.y * tl; acc[r][5] += av.z * tl;
+                    }
                 }
             }
         }
         if (i < npair) {
             const int il = nx - 1 - i;
-            row[i] = ur0 + ub;
-            row[il] = ul0 + ub;
-            row[plane + i] = ur1;
-            row[plane + il] = ul1;
-            row[2 * plane + i] = ur2;
-            row[2 * plane + il] = ul2;
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                if (r < nrow) {
+                    R* row = out + ((size_t)(k0 + r) * ny2 + jn) * nx;
+                    row[i] = acc[r][0] + ub;
+                    row[il] = acc[r][3] + ub;
+                    row[plane + i] = acc[r][1];
+                    row[plane + il] = acc[r][4];
+                    row[2 * plane + i] = acc[r][2];
+                    row[2 * plane + il] = acc[r][5];
+                }
+            }
         }
     }
 }
@@ -139,7 +155,7 @@ tribo_status eval_impl(tribo_ctx* c, double t, void* dst) {
         rows, nm, c->d_mode_f, c->d_Y, c->d_ubar, c->d_damp, t, (cplx<R>*)c->d_mode_c);
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_FIELD);
-    k_mode_eval<R><<<dim3(c->nz, rows), kEvalThreads, 0, c->stream>>>(
+    k_mode_eval<R><<<dim3((c->nz + kRows - 1) / kRows, rows), kEvalThreads, 0, c->stream>>>(
         c->nx, rows, c->nz, nm, c->d_mode_a, c->d_mode_f, (const cplx<R>*)c->d_mode_c,
         (const cplx<R>*)c->d_tabx, (const cplx<R>*)c->d_tabz, c->d_ubar, (R*)dst);
     TRIBO_LAUNCHED(c);
