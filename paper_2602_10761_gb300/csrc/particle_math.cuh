@@ -239,13 +239,9 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     return a;
 }
 
-// one particle per thread: blocks start in index order, so the resident blocks
-// cover one contiguous window of the (cell-sorted) particles and the lattice
-// planes they gather from stay in L2 (a grid-stride loop over a capped grid
-// spreads the resident blocks over the whole array)
 int grid_for(int64_t n) {
     int64_t b = (n + kThreads - 1) / kThreads;
-    if (b > ((int64_t)1 << 30)) b = (int64_t)1 << 30;
+    if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
     return (int)b;
 }
