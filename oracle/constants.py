@@ -42,6 +42,8 @@ class Params:
     parameter, default 1 V).  kappa_A scales the Hertz contact area (1 in the
     paper).  coulomb adds the near field of the hybrid electrostatics
     (Sec. 2.2): Coulomb's law between particles that share a cell.
+    collisions adds 4-way coupling: hard-sphere particle-particle collisions
+    (Sec. 2.2) with the condenser-model charge exchange (Sec. 2.3.1).
     """
     mu_p: float = TABLE1["mu_p"]
     E_p: float = TABLE1["E_p"]
@@ -63,6 +65,7 @@ class Params:
     dq_t: bool = True
     electrostatics: bool = True
     coulomb: bool = False
+    collisions: bool = False
 
     def with_(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -156,6 +156,88 @@ def coulomb_near(g: Grid, p: Params, st: "State") -> np.ndarray:
     return acc
 
 
+def pp_charge(p: Params, di, dj, qi, qj, speed):
+    """Charge gained by particle i in a contact with particle j (condenser
+    model, Sec. 2.3.1):
+      dq_ij = C_i C_j / (C_i + C_j) (q_j / C_j - q_i / C_i) (1 - exp(-dt_12 / T_12)),
+      C = 4 pi eps d / 2,  T_12 = C_i C_j / (C_i + C_j) (d_i + d_j) / (2 A_12) phi_p,
+      A_12 = pi d_i d_j / (2 (d_i + d_j)) alpha_12,  dt_12 = 2.94 alpha_12 / |u_12|,
+      alpha_12 = (d_i d_j / 2) (5/8 pi rho_p (1 + k_e) |u_12|^2 sqrt(d_i + d_j) / (d_i^3 + d_j^3) el)^(2/5).
+    Reading: the elastic factor el is 2 (1 - mu_p^2) / E_p (the wall formula's sum
+    of the two bodies' (1 - mu^2) / E for one material); with it and k_e = 1,
+    alpha_12 is the Hertz maximum compression of the two spheres.
+    Returns (dq_i, details); dq_j = -dq_i.  A zero speed transfers nothing.
+    """
+    di, dj = np.asarray(di, np.float64), np.asarray(dj, np.float64)
+    qi, qj = np.asarray(qi, np.float64), np.asarray(qj, np.float64)
+    speed = np.asarray(speed, np.float64)
+    Ci = 2.0 * math.pi * p.eps * di
+    Cj = 2.0 * math.pi * p.eps * dj
+    el = 2.0 * (1.0 - p.mu_p ** 2) / p.E_p
+    alpha = (di * dj / 2.0) * (0.625 * math.pi * p.rho_p * (1.0 + p.k_e) * speed ** 2
+                               * np.sqrt(di + dj) / (di ** 3 + dj ** 3) * el) ** 0.4
+    A = math.pi * di * dj / (2.0 * (di + dj)) * alpha
+    pos = speed > 0
+    dt = np.where(pos, 2.94 * alpha / np.where(pos, speed, 1.0), 0.0)
+    Cs = Ci * Cj / (Ci + Cj)
+    T = Cs * (di + dj) / (2.0 * np.where(A > 0, A, 1.0)) * p.phi_p
+    dq = np.where(pos, Cs * (qj / Cj - qi / Ci) * (-np.expm1(-dt / T)), 0.0)
+    return dq, dict(alpha=alpha, A=A, dt=dt, T=T, Cs=Cs)
+
+
+def pp_collisions(g: Grid, p: Params, x, y, z, v, q, d):
+    """Hard-sphere particle-particle collisions (4-way coupling, Sec. 2.2) with
+    the condenser charge exchange, applied to the end-of-step state.
+
+    Readings: candidates are particles of the same cell; a pair collides when
+    the spheres overlap, approach each other ((v_i - v_j).(s_i - s_j) < 0) and
+    each is the other's nearest such partner (ties to the lower index); the
+    collision is elastic along the line of centres with the particle masses
+    (for equal masses the normal components are exchanged); the charge uses
+    the relative speed before the collision.  Returns (v', q', pairs).
+    """
+    v = np.array(v, np.float64)
+    q = np.array(q, np.float64)
+    n = x.shape[0]
+    i, j, k = locate(g, x, y, z)
+    key = g.cell_key(i, j, k)
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    starts = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]]) if n else np.zeros(0, np.int64)
+    ends = np.r_[starts[1:], n] if n else np.zeros(0, np.int64)
+    S = np.stack([x, y, z], axis=1)
+    partner = np.full(n, -1, np.int64)
+    for s_, e_ in zip(starts, ends):
+        if e_ - s_ < 2:
+            continue
+        idx = np.sort(order[s_:e_])
+        r = S[idx][:, None, :] - S[idx][None, :, :]
+        dist2 = np.sum(r * r, axis=2)
+        rel = v[idx][:, None, :] - v[idx][None, :, :]
+        appr = np.sum(rel * r, axis=2) < 0
+        reach = 0.5 * (d[idx][:, None] + d[idx][None, :])
+        ok = (dist2 < reach ** 2) & appr
+        np.fill_diagonal(ok, False)
+        for a in range(idx.shape[0]):
+            if ok[a].any():
+                cand = np.flatnonzero(ok[a])
+                partner[idx[a]] = idx[cand[np.argmin(dist2[a, cand])]]
+    pairs = [(a, b) for a, b in enumerate(partner) if b > a and partner[b] == a]
+    mass = particle_mass(p, d)
+    v_new, q_new = v.copy(), q.copy()
+    for a, b in pairs:
+        nrm = S[a] - S[b]
+        nrm = nrm / np.linalg.norm(nrm)
+        vn = np.dot(v[a] - v[b], nrm)
+        ma, mb = mass[a], mass[b]
+        v_new[a] = v[a] - (2.0 * mb / (ma + mb)) * vn * nrm
+        v_new[b] = v[b] + (2.0 * ma / (ma + mb)) * vn * nrm
+        dq, _ = pp_charge(p, d[a], d[b], q[a], q[b], np.linalg.norm(v[b] - v[a]))
+        q_new[a] = q[a] + dq
+        q_new[b] = q[b] - dq
+    return v_new, q_new, pairs
+
+
 def push(p: Params, x, v, uf, acc, d, dt):
     """Advance position and velocity over dt with u, a frozen (exponential).
 
@@ -271,6 +353,11 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
         q[m] += dq
         q_wall[m] += dq
         n_imp[m] += 1
+    if p.collisions:
+        Vc, q, pairs = pp_collisions(g, p, xn, yn, zn, np.stack([vxn, vyn, vzn], axis=1), q, st.d)
+        vxn, vyn, vzn = Vc[:, 0], Vc[:, 1], Vc[:, 2]
+        if diag is not None:
+            diag.update(pairs=pairs)
     if diag is not None:
         diag.update(uf=uf, hit=hit, tau=tau)
     return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall)
