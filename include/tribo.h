@@ -95,7 +95,13 @@ typedef struct {
  * coulomb: 1 to add the near field of the hybrid electrostatics (Sec. 2.2):
  *       Coulomb's law between particles that share a cell, on top of the mesh
  *       field (needs electrostatics = 1 and max_particles >= n; not available
- *       in tribo_adjoint or a batch). */
+ *       in tribo_adjoint or a batch).
+ * collisions: 1 for 4-way coupling: hard-sphere particle-particle collisions
+ *       (Sec. 2.2) of particles that share a cell at the end of a step, with
+ *       the condenser-model charge exchange of the contact (Sec. 2.3.1); a
+ *       pair collides when the spheres overlap, approach each other and each
+ *       is the other's nearest such partner (needs max_particles >= n; not
+ *       available in tribo_adjoint or a batch). */
 typedef struct {
     double mu_p, E_p, phi_p, k_e, mu_w, E_w, eps_w, h, eps, eps0;
     double nu, rho, rho_p;
@@ -103,6 +109,7 @@ typedef struct {
     int32_t drag_law, impact_vel, dq_t, electrostatics, precision;
     int32_t sort_every;
     int32_t coulomb;
+    int32_t collisions;
 } tribo_params;
 
 /* Gas velocity on the wall-extended lattice (Nz, Ny+2, Nx, 3) of "real":

@@ -38,7 +38,7 @@ class tribo_params(C.Structure):
                 ("mu_p", "E_p", "phi_p", "k_e", "mu_w", "E_w", "eps_w", "h", "eps", "eps0",
                  "nu", "rho", "rho_p", "U_c", "kappa_A")] + \
                [(n, C.c_int32) for n in
-                ("drag_law", "impact_vel", "dq_t", "electrostatics", "precision", "sort_every", "coulomb")]
+                ("drag_law", "impact_vel", "dq_t", "electrostatics", "precision", "sort_every", "coulomb", "collisions")]
 
 
 class tribo_fluid(C.Structure):

@@ -44,6 +44,7 @@ class Params:
     precision: int = _abi.TRIBO_MIXED
     sort_every: int = 0
     coulomb: int = 0          # in-cell Coulomb near field (hybrid electrostatics)
+    collisions: int = 0       # 4-way coupling: particle-particle collisions with charge exchange
 
     def to_c(self) -> _abi.tribo_params:
         p = _abi.tribo_params()

@@ -61,6 +61,10 @@ tribo_status check_params(const tribo_params* p) {
     }
     if (p->sort_every < 0) { set_last_error("sort_every must be >= 0"); return TRIBO_ERR_ARG; }
     if (p->coulomb != 0 && p->coulomb != 1) { set_last_error("coulomb must be 0 or 1"); return TRIBO_ERR_ARG; }
+    if (p->collisions != 0 && p->collisions != 1) {
+        set_last_error("collisions must be 0 or 1");
+        return TRIBO_ERR_ARG;
+    }
     return TRIBO_OK;
 }
 
@@ -217,7 +221,7 @@ void free_ctx(tribo_ctx* c) {
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
-                    c->sort_tiles, c->adj, c->nf_members, c->nf_acc};
+                    c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -420,15 +424,23 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     // the sort writes the other particle set; the sets swap after each sort
     // and the caller's arrays receive the data back at the end if needed
     const bool near = electro && c->P.coulomb;
-    if (near) {
+    const bool collide = c->P.collisions != 0;
+    if (near || collide) {
         if (p->n > c->max_particles) {
-            set_last_error("the Coulomb near field needs max_particles >= n");
+            set_last_error("the Coulomb near field and particle collisions need max_particles >= n");
             return TRIBO_ERR_CAPACITY;
         }
         if (!c->nf_members) {
             TRIBO_CUDA(cudaStreamSynchronize(c->stream));
             TRIBO_CUDA(cudaMalloc((void**)&c->nf_members, sizeof(uint32_t) * c->max_particles));
+        }
+        if (near && !c->nf_acc) {
+            TRIBO_CUDA(cudaStreamSynchronize(c->stream));
             TRIBO_CUDA(cudaMalloc(&c->nf_acc, 3 * real_size(c) * c->max_particles));
+        }
+        if (collide && !c->pp_partner) {
+            TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+            TRIBO_CUDA(cudaMalloc((void**)&c->pp_partner, sizeof(uint32_t) * c->max_particles));
         }
     }
     StepIO io;
@@ -458,6 +470,11 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                 return st;
         }
         if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last, io))) return st;
+        if (collide) {
+            if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
+                (st = particles_collide(c, cur, c->nf_members, c->pp_partner)))
+                return st;
+        }
         c->steps_done++;
         c->time += dt;
     }

@@ -142,6 +142,7 @@ struct tribo_ctx {
     int64_t steps_done = 0;            // steps taken by this context (sort schedule)
     uint32_t* nf_members = nullptr;    // near field: particle indices grouped by cell
     void* nf_acc = nullptr;            // near field: acceleration planes (3 x max_particles real)
+    uint32_t* pp_partner = nullptr;    // particle-particle collisions: nearest partner per particle
     void* adj = nullptr;               // adjoint workspace (checkpoints, segment states, adjoints)
     size_t adj_bytes = 0;
 
@@ -230,6 +231,8 @@ tribo_status particles_setup(tribo_ctx* c);
 tribo_status particles_cell_lists(tribo_ctx* c, const PView& p, uint32_t* members);
 // near-field (in-cell Coulomb) acceleration planes of p, from the cell lists (nearfield.cu)
 tribo_status particles_coulomb(tribo_ctx* c, const PView& p, const uint32_t* members, void* acoul);
+// particle-particle collisions of the end-of-step state p from its cell lists (collide.cu)
+tribo_status particles_collide(tribo_ctx* c, const PView& p, const uint32_t* members, uint32_t* partner);
 // view of n particles in a particle-set buffer of the context (stage or alt)
 PView set_view(tribo_ctx* c, void* base, int64_t n);
 PView stage_view(tribo_ctx* c, int64_t n);

@@ -56,7 +56,7 @@ int main(void) {
   printf("tribo_particles %zu\n", sizeof(tribo_particles));
   printf("tribo_modes %zu\n", sizeof(tribo_modes));
   P(tribo_grid, lx) P(tribo_grid, y_faces)
-  P(tribo_params, kappa_A) P(tribo_params, drag_law) P(tribo_params, sort_every) P(tribo_params, coulomb)
+  P(tribo_params, kappa_A) P(tribo_params, drag_law) P(tribo_params, sort_every) P(tribo_params, coulomb) P(tribo_params, collisions)
   P(tribo_particles, x) P(tribo_particles, q) P(tribo_particles, cell) P(tribo_particles, on_host)
   P(tribo_modes, nxi) P(tribo_modes, damp) P(tribo_modes, t0)
   return 0;
