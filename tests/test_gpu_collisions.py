@@ -1,13 +1,23 @@
 """4-way coupling on the GPU against the oracle: clustered large particles
 (d+ 10-20, about fifteen per cell) collide with one another (about a hundred
-pairs in ten steps) and exchange charge in each contact; FP64 to 1e-12 and
-mixed to 1e-5 per particle, impact counts exact, with and without re-sorting
-and together with the Coulomb near field."""
+pairs in ten steps) and exchange charge in each contact; FP64 to 1e-12 per
+particle, impact counts exact, with and without re-sorting and together with
+the Coulomb near field.
+
+Mixed precision: the collision normal is the direction between two centres
+about d_min = 1.1 mm apart, while FP32 positions in a channel of height
+L_y = 40 mm carry a rounding of eps_32 L_y; each collision's velocity change
+therefore carries a relative error up to eps_32 L_y / d_min = 2.2e-6, and a
+particle colliding a few times in ten steps accumulates ~1e-5.  The bar for
+this coupling in mixed precision is 5e-5 (the FP64 runs check the arithmetic
+at 1e-12)."""
 import numpy as np
 import pytest
 
 import oracle
-from _problems import TOL_FP64, TOL_MIXED, compare_states, oracle_params, oracle_state, problem
+from _problems import TOL_FP64, compare_states, oracle_params, oracle_state, problem
+
+TOL_COLL_MIXED = 5e-5
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,7 +69,7 @@ def test_collisions_match_oracle(prec, variant):
         npairs += len(diag.get("pairs", []))
     assert npairs > 50
     got = _gpu(c, faces, lat_r, pr, prec, 10, U_c=100.0, collisions=1, **variant)
-    tol = TOL_FP64 if prec == T.TRIBO_FP64 else TOL_MIXED
+    tol = TOL_FP64 if prec == T.TRIBO_FP64 else TOL_COLL_MIXED
     compare_states(g, got, st, tol, label=f"collisions prec={prec} {variant}")
     assert np.array_equal(got["n_imp"].astype(np.int64), st.n_imp)
     # particle-particle exchanges conserve the total charge up to the wall transfers
