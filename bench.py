@@ -393,6 +393,35 @@ def timevarying_report(T, torch, steps=200, sort_every=20):
             "poisson_solves_per_s": 1e3 / poisson if poisson > 0 else None}
 
 
+def interactions_report(T, torch, steps=100, sort_every=20):
+    """Cost of the particle-particle interactions (the in-cell Coulomb near
+    field and the 4-way collisions) on the 128^3 workload with 1M particles:
+    ms per step with each switch against the plain coupled step."""
+    c = synth.case("re180_128")
+    faces, lat, P = make_inputs(c)
+    parts = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
+    u = torch.from_numpy(lat).cuda()
+    out = {"workload": workload_desc(c) + ", frozen field"}
+    for name, kw in (("plain", {}), ("coulomb", dict(coulomb=1)), ("collisions", dict(collisions=1)),
+                     ("coulomb_and_collisions", dict(coulomb=1, collisions=1))):
+        params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0,
+                          sort_every=sort_every, **kw)
+        ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, u, max_particles=c.n_particles)
+        Pd = T.Particles.from_numpy(parts, T.TRIBO_MIXED, device="cuda")
+        ch.step(Pd, c.dt, 5)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ch.step(Pd, c.dt, steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ch.sync()
+        ch.close()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": c.n_particles / (ms * 1e-3)}
+    return out
+
+
 def cpu_baseline(c, faces, lat, P, n_sample):
     t_field, t_part = oracle_step_time(c, faces, lat, P, n_sample)
     t_full = t_field + t_part * (c.n_particles / n_sample)
@@ -451,6 +480,7 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-timevarying", action="store_true")
+    ap.add_argument("--no-interactions", action="store_true")
     ap.add_argument("--adj-steps", type=int, default=500, help="adjoint section: steps (500 = the workload)")
     ap.add_argument("--adj-ckpt", type=int, default=50, help="adjoint section: steps between stored states")
     ap.add_argument("--batch-steps", type=int, default=500)
@@ -587,6 +617,8 @@ def main():
     ch.close()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(T, torch, steps=args.adj_steps, ckpt=args.adj_ckpt)
+    if rank == 0 and world == 1 and not args.no_interactions:
+        line["interactions"] = interactions_report(T, torch)
     if rank == 0 and world == 1 and not args.no_timevarying:
         line["timevarying"] = timevarying_report(T, torch)
     if not args.no_batch:
