@@ -19,7 +19,9 @@
 // Both particles of a pair share a cell, so the cell's deposited charge sum
 // is unchanged.  Decisions and updates are formed in FP64 from the stored
 // values (same-cell position differences of FP32 numbers are exact), so the
-// choice of pairs does not depend on the precision of the state.
+// choice of pairs does not depend on the precision of the state; pairs
+// clearly apart are rejected first in the real type (with a 1e-4 relative
+// margin on the squared contact distance, far above its rounding).
 #include <cmath>
 
 #include "particle_math.cuh"
@@ -47,9 +49,14 @@ __global__ void __launch_bounds__(kThreads) k_pp_partner(PView p, const uint32_t
             const double xi = X[n], yi = Y[n], zi = Z[n];
             const double ui = VX[n], vi = VY[n], wi = VZ[n], di = D[n];
             double bd = 0.0;
+            const R xr = X[n], yr = Y[n], zr = Z[n], dr = D[n];
             for (uint32_t m = b; m < e; ++m) {
                 const uint32_t j = members[m];
                 if (j == (uint32_t)n) continue;
+                // cheap rejection in the real type, with a margin far above its rounding
+                const R fx = xr - X[j], fy = yr - Y[j], fz = zr - Z[j];
+                const R freach = (R)0.5 * (dr + D[j]);
+                if (fx * fx + fy * fy + fz * fz > freach * freach * (R)1.0001) continue;
                 const double rx = xi - (double)X[j], ry = yi - (double)Y[j], rz = zi - (double)Z[j];
                 const double d2 = rx * rx + ry * ry + rz * rz;
                 const double reach = 0.5 * (di + (double)D[j]);
