@@ -44,6 +44,8 @@ class Params:
     (Sec. 2.2): Coulomb's law between particles that share a cell.
     collisions adds 4-way coupling: hard-sphere particle-particle collisions
     (Sec. 2.2) with the condenser-model charge exchange (Sec. 2.3.1).
+    ssm (an oracle.ssm.SSM) replaces the condenser model of wall impacts by
+    the stochastic scaling model (Sec. 2.3.2).
     """
     mu_p: float = TABLE1["mu_p"]
     E_p: float = TABLE1["E_p"]
@@ -66,6 +68,7 @@ class Params:
     electrostatics: bool = True
     coulomb: bool = False
     collisions: bool = False
+    ssm: object = None          # oracle.ssm.SSM: wall impacts charge by the SSM instead
 
     def with_(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -62,14 +62,20 @@ class State:
     d: np.ndarray
     n_imp: np.ndarray
     q_wall: np.ndarray
+    id: np.ndarray = None       # particle identities (random-number counters of the SSM)
+
+    def __post_init__(self):
+        if self.id is None:
+            self.id = np.arange(self.x.shape[0], dtype=np.int64)
 
     @staticmethod
-    def from_arrays(x, y, z, vx, vy, vz, q, d, n_imp=None, q_wall=None) -> "State":
+    def from_arrays(x, y, z, vx, vy, vz, q, d, n_imp=None, q_wall=None, ids=None) -> "State":
         n = np.asarray(x).shape[0]
         f = lambda a: np.array(a, dtype=np.float64)
         return State(f(x), f(y), f(z), f(vx), f(vy), f(vz), f(q), f(d),
                      np.zeros(n, np.int64) if n_imp is None else np.array(n_imp, np.int64),
-                     np.zeros(n) if q_wall is None else f(q_wall))
+                     np.zeros(n) if q_wall is None else f(q_wall),
+                     np.arange(n, dtype=np.int64) if ids is None else np.array(ids, np.int64))
 
     def copy(self) -> "State":
         return State(*(np.array(getattr(self, f.name)) for f in dataclasses.fields(self)))
@@ -348,8 +354,12 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
             speed = np.abs(Vn[m, 1])
         else:
             speed = np.linalg.norm(Vn[m], axis=1)
-        dq_c, dq_t, _ = condenser_wall(p, st.d[m], speed, q[m])
-        dq = dq_c + dq_t
+        if p.ssm is not None:
+            from .ssm import ssm_wall_charge
+            dq, _ = ssm_wall_charge(p, p.ssm, st.d[m], speed, q[m], st.id[m], n_imp[m])
+        else:
+            dq_c, dq_t, _ = condenser_wall(p, st.d[m], speed, q[m])
+            dq = dq_c + dq_t
         q[m] += dq
         q_wall[m] += dq
         n_imp[m] += 1
@@ -360,7 +370,7 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
             diag.update(pairs=pairs)
     if diag is not None:
         diag.update(uf=uf, hit=hit, tau=tau)
-    return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall)
+    return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall, st.id.copy())
 
 
 def run(g: Grid, p: Params, st: State, u_lat, dt: float, nsteps: int,

@@ -1,0 +1,106 @@
+"""Pins of the oracle's stochastic scaling model of wall-impact charging
+(Sec. 2.3.2, reference parameters of Sec. 3.1) and of its random numbers."""
+import math
+import os
+
+import numpy as np
+
+import oracle
+from oracle.ssm import SSM, hertz_area, normals, philox4x32_10, saturation_charge, skew_normal_params, \
+    ssm_wall_charge
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+
+
+def _moments(x):
+    m = x.mean()
+    s = x.std()
+    return m, s, np.mean(((x - m) / s) ** 3)
+
+
+def test_philox_known_answer_vectors():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        w = [int(v, 16) for v in r]
+        ctr = [np.array([v], np.uint64) for v in w[:4]]
+        out = [int(x[0]) for x in philox4x32_10(ctr, (w[4], w[5]))]
+        assert out == w[6:10]
+
+
+def test_box_muller_normals():
+    n = 400_000
+    z0, z1 = normals(np.arange(n), np.zeros(n, np.int64), seed=12345)
+    for z in (z0, z1):
+        m, s, g = _moments(z)
+        assert abs(m) < 0.01 and abs(s - 1) < 0.01 and abs(g) < 0.02
+    assert abs(np.corrcoef(z0, z1)[0, 1]) < 0.01
+    # the counter decides the draw: another count gives independent normals
+    y0, _ = normals(np.arange(n), np.ones(n, np.int64), seed=12345)
+    assert abs(np.corrcoef(z0, y0)[0, 1]) < 0.01
+
+
+def test_skew_normal_sampler_moments():
+    n = 400_000
+    z0, z1 = normals(np.arange(n), np.full(n, 7, np.int64), seed=3)
+    for mean, sd, skew in ((1.0, 2.0, 0.5), (-3.0, 0.5, -0.8), (0.0, 1.0, 0.0), (2.0, 0.1, 0.99)):
+        xi, om, de = skew_normal_params(mean, sd, skew)
+        x = xi + om * (de * np.abs(z0) + np.sqrt(1 - de ** 2) * z1)
+        m, s, g = _moments(x)
+        assert abs(m - mean) < 0.01 * sd and abs(s / sd - 1) < 0.01 and abs(g - skew) < 0.03, (mean, sd, skew)
+
+
+def test_reference_impact_reproduces_reference_statistics():
+    p = oracle.Params(rho_p=1150.0)
+    s = SSM(seed=99)
+    n = 400_000
+    d = np.full(n, 2 * s.r0)
+    dq, det = ssm_wall_charge(p, s, d, np.full(n, s.un0), np.zeros(n), np.arange(n), np.zeros(n, np.int64))
+    assert np.allclose(det["area_ratio"], 1.0, rtol=1e-14)
+    m, sd, g = _moments(dq)
+    assert abs(m - s.mu0) < 4 * s.sigma0 / math.sqrt(n)
+    assert abs(sd / s.sigma0 - 1) < 0.01
+    assert abs(g - s.gamma0) < 0.03
+
+
+def test_saturation_charges_printed_in_the_paper():
+    s = SSM()
+    assert abs(saturation_charge(s, 50e-6) / 3.13e-13 - 1) < 2e-3          # Sec. 3.1
+    assert abs(saturation_charge(s, 100e-6) / 1.25e-12 - 1) < 2e-3         # Sec. 3.1
+    # the paper prints 7.81e-15 C for 25 um; the formula gives ten times that
+    assert abs(saturation_charge(s, 25e-6) / 7.81e-14 - 1) < 2e-3
+    # at q = -q_sat (dq0_min < 0) the wall's active sites are exhausted
+    p = oracle.Params()
+    d = np.array([50e-6])
+    _, det = ssm_wall_charge(p, s, d, [0.3], -saturation_charge(s, d), [0], [0])
+    assert det["chi_w"][0] == 0.0 and det["mu_w"][0] == 0.0
+
+
+def test_deterministic_limit_scales_with_the_hertz_area():
+    """sigma_0 = gamma_0 = 0, q = 0: dq = mu_0 A / A_0 = mu_0 (d/d_0)^2 (u/u_0)^(4/5)."""
+    p = oracle.Params(rho_p=1150.0)
+    s = SSM(sigma0=0.0, gamma0=0.0)
+    d = np.array([50e-6, 91e-6, 400e-6])
+    u = np.array([0.01, 0.3, 0.925])
+    dq, _ = ssm_wall_charge(p, s, d, u, np.zeros(3), np.arange(3), np.zeros(3, np.int64))
+    ref = s.mu0 * (d / (2 * s.r0)) ** 2 * (u / s.un0) ** 0.8
+    assert np.allclose(dq, ref, rtol=1e-12, atol=0)
+
+
+def test_step_uses_the_ssm_with_the_impact_counter():
+    g = oracle.Grid(4, 4, 2 * math.pi * 0.02, math.pi * 0.02, np.linspace(0, 0.04, 5))
+    lat = np.zeros((4, 6, 4, 3))
+    n = 6
+    d = np.full(n, 1e-4)
+    st = oracle.State.from_arrays(np.linspace(0.001, 0.1, n), np.full(n, 0.5e-4 + 1e-6), np.full(n, 0.01),
+                                  np.zeros(n), np.full(n, -0.5), np.zeros(n), np.zeros(n), d,
+                                  n_imp=np.arange(n), ids=np.arange(n) + 100)
+    p = oracle.Params(drag_law=2, electrostatics=False, ssm=SSM(seed=5))
+    out = oracle.step(g, p, st, lat, 1e-5)
+    assert np.all(out.n_imp == st.n_imp + 1)
+    speed = np.abs(out.vy)
+    dq, _ = ssm_wall_charge(p, p.ssm, d, speed, np.zeros(n), st.id, st.n_imp)
+    assert np.array_equal(out.q, dq)
+    assert np.array_equal(out.q_wall, dq)
+    other = oracle.step(g, p.with_(ssm=SSM(seed=6)), st, lat, 1e-5)
+    assert not np.array_equal(other.q, out.q)
