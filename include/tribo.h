@@ -188,6 +188,29 @@ tribo_status tribo_set_modes(tribo_ctx* ctx, const tribo_modes* modes);
  * Asynchronous. */
 tribo_status tribo_eval_modes(tribo_ctx* ctx, double t, void* u_out);
 
+/* Stochastic scaling model (SSM) of wall-impact charging (Sec. 2.3.2), with
+ * the reference impact of Sec. 3.1 (r0 = 2e-4 m, un0 = 0.925 m/s,
+ * mu0 = -4.12e-15 C, sigma0 = 6.49e-15 C, gamma0 = -0.191,
+ * dq0_min = -2.19e-14 C; c_sat = C_sat = 5e-4 C/m^2).  An impact gives
+ * dq = mu_w - Y with mu_w = dq0_min (A/A0) chi_w and Y skew-normal with mean
+ * (dq0_min - mu0)(A/A0) chi_i, deviation sigma0 sqrt((A/A0) chi_i) and
+ * skewness -gamma0 / ((A/A0) chi_i) (clipped to the family's range), where
+ * A, A0 are the Hertz contact areas of the impact and of the reference
+ * impact and chi_w = 1 - sgn(dq0_min) 4 q/(c_sat d^2),
+ * chi_i = 1 + sgn(dq0_min - mu0) 4 q/(c_sat d^2), both clipped to [0, 1];
+ * the charging-site density ratio is taken as 1.  The random numbers are
+ * Philox4x32-10 with counter (particle id, impact count before the impact,
+ * 0, 0) and key (seed low word, seed high word): results do not depend on
+ * the particle order.  Needs the particles' id arrays in tribo_step; not
+ * available in tribo_adjoint or a batch.  ssm NULL: back to the condenser
+ * model. */
+typedef struct {
+    double r0, un0, mu0, sigma0, gamma0, dq0_min, c_sat;
+    uint64_t seed;
+} tribo_ssm;
+
+tribo_status tribo_set_ssm(tribo_ctx* ctx, const tribo_ssm* ssm);
+
 /* Replace the physical parameters and switches (precision must not change). */
 tribo_status tribo_set_params(tribo_ctx* ctx, const tribo_params* params);
 

@@ -51,6 +51,11 @@ class tribo_modes(C.Structure):
                 ("t0", C.c_double)]
 
 
+class tribo_ssm(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("r0", "un0", "mu0", "sigma0", "gamma0", "dq0_min", "c_sat")] + \
+               [("seed", C.c_uint64)]
+
+
 class tribo_particles(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(n, C.c_void_p) for n in ("x", "y", "z", "vx", "vy", "vz", "d")] + \
                [("q", C.c_void_p), ("q_wall", C.c_void_p), ("n_imp", C.c_void_p), ("id", C.c_void_p),
@@ -63,6 +68,7 @@ _SIGS = {
     "tribo_set_fluid": (C.c_int32, [C.c_void_p, C.POINTER(tribo_fluid)]),
     "tribo_set_params": (C.c_int32, [C.c_void_p, C.POINTER(tribo_params)]),
     "tribo_set_modes": (C.c_int32, [C.c_void_p, C.POINTER(tribo_modes)]),
+    "tribo_set_ssm": (C.c_int32, [C.c_void_p, C.POINTER(tribo_ssm)]),
     "tribo_eval_modes": (C.c_int32, [C.c_void_p, C.c_double, C.c_void_p]),
     "tribo_step": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.c_double, C.c_int32]),
     "tribo_poisson": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

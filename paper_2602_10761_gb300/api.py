@@ -187,6 +187,17 @@ def tribo_set_modes(ctx: int, modes, ubar, damp, t0: float = 0.0) -> None:
     check(load().tribo_set_modes(ctx, C.byref(m)), "tribo_set_modes")
 
 
+def tribo_set_ssm(ctx: int, ssm) -> None:
+    """Stochastic scaling model of wall impacts (None: condenser model).  ssm:
+    object with r0, un0, mu0, sigma0, gamma0, dq0_min, c_sat, seed."""
+    if ssm is None:
+        check(load().tribo_set_ssm(ctx, None), "tribo_set_ssm")
+        return
+    s = _abi.tribo_ssm(*(float(getattr(ssm, k)) for k in ("r0", "un0", "mu0", "sigma0", "gamma0", "dq0_min",
+                                                          "c_sat")), int(ssm.seed))
+    check(load().tribo_set_ssm(ctx, C.byref(s)), "tribo_set_ssm")
+
+
 def tribo_eval_modes(ctx: int, t: float, u_out=None) -> None:
     check(load().tribo_eval_modes(ctx, float(t), _ptr(u_out)), "tribo_eval_modes")
 
@@ -421,6 +432,9 @@ class Channel:
         u = torch.empty((3, self.nz, self.ny + 2, self.nx), dtype=rdt, device="cuda")
         tribo_eval_modes(self.ctx, t, u)
         return u
+
+    def set_ssm(self, ssm) -> None:
+        tribo_set_ssm(self.ctx, ssm)
 
     def set_params(self, params: Params) -> None:
         tribo_set_params(self.ctx, params)

@@ -601,8 +601,8 @@ extern "C" tribo_status tribo_adjoint(tribo_ctx* c, tribo_particles* p, double d
         set_last_error("a required particle array is NULL");
         return TRIBO_ERR_ARG;
     }
-    if ((c->P.electrostatics && c->P.coulomb) || c->P.collisions) {
-        set_last_error("tribo_adjoint does not differentiate the Coulomb near field or particle collisions");
+    if ((c->P.electrostatics && c->P.coulomb) || c->P.collisions || c->ssm_on) {
+        set_last_error("tribo_adjoint does not differentiate the Coulomb near field, particle collisions or the SSM");
         return TRIBO_ERR_UNSUPPORTED;
     }
     if (nsteps < 0 || ckpt_every < 1 || !(dt > 0) || !std::isfinite(dt)) {

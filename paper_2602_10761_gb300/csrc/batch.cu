@@ -443,8 +443,8 @@ tribo_status tribo_batch_create(tribo_batch** out, int32_t n_channels, tribo_ctx
             return TRIBO_ERR_UNSUPPORTED;
         }
         if (!c->alt) { set_last_error("batch channels need max_particles > 0"); return TRIBO_ERR_ARG; }
-        if ((c->P.electrostatics && c->P.coulomb) || c->P.collisions) {
-            set_last_error("the Coulomb near field and particle collisions are not available in a batch");
+        if ((c->P.electrostatics && c->P.coulomb) || c->P.collisions || c->ssm_on) {
+            set_last_error("the Coulomb near field, particle collisions and the SSM are not available in a batch");
             return TRIBO_ERR_UNSUPPORTED;
         }
         for (int k = 0; k < i; ++k)

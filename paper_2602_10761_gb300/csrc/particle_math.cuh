@@ -46,6 +46,10 @@ struct StepArgs {
     double inv_T_w;
     double U_c;
     const R* acoul;                // near-field acceleration planes (x, y, z; n each), or NULL
+    // stochastic scaling model of wall impacts (ssm = 0: condenser model)
+    int ssm;
+    unsigned int ssm_key0, ssm_key1;
+    double ssm_inv_A0, ssm_mu0, ssm_sigma0, ssm_gamma0, ssm_dq0min, ssm_xcoef;
 };
 
 template <class R> __device__ __forceinline__ R rfloor(R v);
@@ -209,6 +213,60 @@ __device__ __forceinline__ double impact_charge(const StepArgs<R>& a, double d, 
     return dq;
 }
 
+// ---- stochastic scaling model (Sec. 2.3.2) of one wall impact, FP64
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32 x 32 -> 64-bit
+// multiplications with the Weyl-sequence key schedule
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned int hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned int hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// dq = mu_w - Y, Y skew-normal with mean mu_i, deviation sigma_i, skewness
+// gamma_i; the sample from two Box-Muller normals of the words of the
+// counter (particle id, impact count)
+template <class R>
+__device__ __noinline__ double ssm_charge(const StepArgs<R>& a, double d, double speed, double q, unsigned int id,
+                                          unsigned int count) {
+    const double r = 0.5 * d;
+    const double A = M_PI * r * r * pow(a.alpha_coef * speed * speed, 0.4);
+    const double area = A * a.ssm_inv_A0;
+    const double x = a.ssm_xcoef * q / (d * d);
+    const double sw = a.ssm_dq0min > 0.0 ? 1.0 : (a.ssm_dq0min < 0.0 ? -1.0 : 0.0);
+    const double di = a.ssm_dq0min - a.ssm_mu0;
+    const double si = di > 0.0 ? 1.0 : (di < 0.0 ? -1.0 : 0.0);
+    const double chi_w = fmin(fmax(1.0 - sw * x, 0.0), 1.0);
+    const double chi_i = fmin(fmax(1.0 + si * x, 0.0), 1.0);
+    const double ni = area * chi_i;
+    const double mu_w = a.ssm_dq0min * area * chi_w;
+    const double mu_i = di * ni;
+    const double sigma_i = a.ssm_sigma0 * sqrt(ni);
+    double g = ni > 0.0 ? -a.ssm_gamma0 / ni : 0.0;
+    g = fmin(fmax(g, -0.9952717464311565), 0.9952717464311565);
+    // skew-normal (xi, omega, delta) from the mean, deviation and skewness
+    const double b = 0.7978845608028654;          // sqrt(2 / pi)
+    const double ag = pow(fabs(g), 2.0 / 3.0);
+    const double t = ag / (pow(0.5 * (4.0 - M_PI), 2.0 / 3.0) + ag);
+    const double delta = (g > 0.0 ? 1.0 : (g < 0.0 ? -1.0 : 0.0)) * sqrt(t) / b;
+    const double omega = sigma_i / sqrt(1.0 - 2.0 * delta * delta / M_PI);
+    const double xi = mu_i - omega * delta * b;
+    const uint4 w = philox4x32_10(make_uint4(id, count, 0u, 0u), make_uint2(a.ssm_key0, a.ssm_key1));
+    const double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;   // 2^-32
+    const double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+    const double rad = sqrt(-2.0 * log(u0));
+    double sn, cs;
+    sincos(2.0 * M_PI * u1, &sn, &cs);
+    const double z0 = rad * cs, z1 = rad * sn;
+    const double y = xi + omega * (delta * fabs(z0) + sqrt(1.0 - delta * delta) * z1);
+    return mu_w - y;
+}
+
 template <class R>
 StepArgs<R> make_args(tribo_ctx* c, double dt) {
     StepArgs<R> a{};
@@ -236,6 +294,17 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     a.inv_T_w = 1.0 / (P.eps_w * P.eps0 * P.phi_p);
     a.U_c = P.U_c;
     a.acoul = nullptr;
+    a.ssm = c->ssm_on ? 1 : 0;
+    if (c->ssm_on) {
+        a.ssm_key0 = (unsigned int)(c->ssm.seed & 0xffffffffu);
+        a.ssm_key1 = (unsigned int)(c->ssm.seed >> 32);
+        a.ssm_inv_A0 = 1.0 / c->ssm_A0;
+        a.ssm_mu0 = c->ssm.mu0;
+        a.ssm_sigma0 = c->ssm.sigma0;
+        a.ssm_gamma0 = c->ssm.gamma0;
+        a.ssm_dq0min = c->ssm.dq0_min;
+        a.ssm_xcoef = 4.0 / c->ssm.c_sat;
+    }
     return a;
 }
 
@@ -323,7 +392,9 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
         } else {
             speed = sqrt((double)vxn * (double)vxn + (double)vyn * (double)vyn + (double)vzn * (double)vzn);
         }
-        const double dq = impact_charge<R>(a, (double)d, speed, q);
+        const double dq = a.ssm && speed > 0.0
+                              ? ssm_charge<R>(a, (double)d, speed, q, p.id[n], p.n_imp[n])
+                              : impact_charge<R>(a, (double)d, speed, q);
         q += dq;
         p.q[n] = q;
         p.q_wall[n] += dq;

@@ -379,6 +379,25 @@ tribo_status tribo_eval_modes(tribo_ctx* c, double t, void* u_out) {
     return modes_eval(c, t, u_out);
 }
 
+tribo_status tribo_set_ssm(tribo_ctx* c, const tribo_ssm* m) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    if (!m) { c->ssm_on = false; return TRIBO_OK; }
+    if (!(m->r0 > 0 && m->un0 > 0 && m->c_sat > 0 && m->sigma0 >= 0 && std::isfinite(m->mu0) &&
+          std::isfinite(m->gamma0) && std::isfinite(m->dq0_min))) {
+        set_last_error("SSM reference parameters must be finite with r0, un0, c_sat > 0 and sigma0 >= 0");
+        return TRIBO_ERR_ARG;
+    }
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    c->ssm = *m;
+    // Hertz contact area pi r alpha of the reference impact (diameter 2 r0, speed un0)
+    const tribo_params& P = c->P;
+    const double elastic = (1.0 - P.mu_p * P.mu_p) / P.E_p + (1.0 - P.mu_w * P.mu_w) / P.E_w;
+    const double coef = 0.625 * M_PI * P.rho_p * (1.0 + P.k_e) * elastic;
+    c->ssm_A0 = M_PI * m->r0 * m->r0 * std::pow(coef * m->un0 * m->un0, 0.4);
+    c->ssm_on = true;
+    return TRIBO_OK;
+}
+
 tribo_status tribo_set_params(tribo_ctx* c, const tribo_params* params) {
     if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
     tribo_status st = check_params(params);
@@ -416,6 +435,10 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     }
     const bool electro = c->P.electrostatics != 0;
     const bool want_cell = v.cell != nullptr;
+    if (c->ssm_on && !p->id) {
+        set_last_error("the SSM needs the particles' id arrays (its random-number counters)");
+        return TRIBO_ERR_ARG;
+    }
     const int S = c->P.sort_every;
     if (S > 0 && p->n > c->max_particles) {
         set_last_error("sorting needs max_particles >= n");

@@ -143,6 +143,9 @@ struct tribo_ctx {
     uint32_t* nf_members = nullptr;    // near field: particle indices grouped by cell
     void* nf_acc = nullptr;            // near field: acceleration planes (3 x max_particles real)
     uint32_t* pp_partner = nullptr;    // particle-particle collisions: nearest partner per particle
+    bool ssm_on = false;               // wall impacts charge by the stochastic scaling model
+    tribo_ssm ssm{};
+    double ssm_A0 = 0.0;               // Hertz contact area of the SSM reference impact
     void* adj = nullptr;               // adjoint workspace (checkpoints, segment states, adjoints)
     size_t adj_bytes = 0;
 

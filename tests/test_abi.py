@@ -55,10 +55,12 @@ int main(void) {
   printf("tribo_fluid %zu\n", sizeof(tribo_fluid));
   printf("tribo_particles %zu\n", sizeof(tribo_particles));
   printf("tribo_modes %zu\n", sizeof(tribo_modes));
+  printf("tribo_ssm %zu\n", sizeof(tribo_ssm));
   P(tribo_grid, lx) P(tribo_grid, y_faces)
   P(tribo_params, kappa_A) P(tribo_params, drag_law) P(tribo_params, sort_every) P(tribo_params, coulomb) P(tribo_params, collisions)
   P(tribo_particles, x) P(tribo_particles, q) P(tribo_particles, cell) P(tribo_particles, on_host)
   P(tribo_modes, nxi) P(tribo_modes, damp) P(tribo_modes, t0)
+  P(tribo_ssm, c_sat) P(tribo_ssm, seed)
   return 0;
 }
 ''')
@@ -71,6 +73,7 @@ int main(void) {
     assert int(out["tribo_fluid"]) == C.sizeof(_abi.tribo_fluid)
     assert int(out["tribo_particles"]) == C.sizeof(_abi.tribo_particles)
     assert int(out["tribo_modes"]) == C.sizeof(_abi.tribo_modes)
+    assert int(out["tribo_ssm"]) == C.sizeof(_abi.tribo_ssm)
     for key, val in out.items():
         if "." in key:
             st, f = key.split(".")
