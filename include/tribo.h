@@ -194,7 +194,7 @@ tribo_status tribo_eval_modes(tribo_ctx* ctx, double t, void* u_out);
  * dq0_min = -2.19e-14 C; c_sat = C_sat = 5e-4 C/m^2).  An impact gives
  * dq = mu_w - Y with mu_w = dq0_min (A/A0) chi_w and Y skew-normal with mean
  * (dq0_min - mu0)(A/A0) chi_i, deviation sigma0 sqrt((A/A0) chi_i) and
- * skewness -gamma0 / ((A/A0) chi_i) (clipped to the family's range), where
+ * skewness -gamma0 / ((A/A0) chi_i) (clipped to [-0.99, 0.99]), where
  * A, A0 are the Hertz contact areas of the impact and of the reference
  * impact and chi_w = 1 - sgn(dq0_min) 4 q/(c_sat d^2),
  * chi_i = 1 + sgn(dq0_min - mu0) 4 q/(c_sat d^2), both clipped to [0, 1];

@@ -20,8 +20,9 @@ Readings:
 * the charge of one impact is dq = mu_w - Y with Y ~ G(mu_i, sigma_i, gamma_i)
   (at the reference impact its mean is mu_0 and, Y being a sum of
   same-signed site transfers, its bound is dq0_min);
-* gamma_i as printed (-gamma_0 N_0 / N_i), clipped to the skew-normal's range
-  |gamma| < 0.9952717;
+* gamma_i as printed (-gamma_0 N_0 / N_i), clipped to |gamma| <= 0.99, inside
+  the skew-normal family's range (|gamma| < 0.99527), where the sample stays
+  well conditioned;
 * the site density c / c_0 is 1 (the history term is not tracked; the paper
   notes it matters only after about 1e4 impacts, never reached in its runs);
 * A and A_0 are the Hertz contact areas pi (d/2) alpha without kappa_A;
@@ -41,7 +42,9 @@ import numpy as np
 
 from .constants import Params
 
-GAMMA_MAX = 0.9952717464311565      # sup of |skewness| of the skew-normal family
+# |skewness| is clipped below the skew-normal family's supremum 0.99527, where
+# delta -> 1 and sqrt(1 - delta^2) would be the root of rounding noise
+GAMMA_MAX = 0.99
 
 
 @dataclasses.dataclass
@@ -132,7 +135,7 @@ def ssm_wall_charge(p: Params, s: SSM, d, speed, q, ids, counts):
     gamma_i = np.where(ni > 0, -s.gamma0 / np.where(ni > 0, ni, 1.0), 0.0)
     xi, omega, delta = skew_normal_params(mu_i, sigma_i, gamma_i)
     z0, z1 = normals(ids, counts, s.seed)
-    y = xi + omega * (delta * np.abs(z0) + np.sqrt(1.0 - delta ** 2) * z1)
+    y = xi + omega * (delta * np.abs(z0) + np.sqrt(np.maximum(1.0 - delta ** 2, 0.0)) * z1)
     dq = mu_w - y
     return dq, dict(area_ratio=area, chi_w=chi_w, chi_i=chi_i, mu_w=mu_w, mu_i=mu_i, sigma_i=sigma_i,
                     gamma_i=gamma_i)

@@ -248,7 +248,7 @@ __device__ __noinline__ double ssm_charge(const StepArgs<R>& a, double d, double
     const double mu_i = di * ni;
     const double sigma_i = a.ssm_sigma0 * sqrt(ni);
     double g = ni > 0.0 ? -a.ssm_gamma0 / ni : 0.0;
-    g = fmin(fmax(g, -0.9952717464311565), 0.9952717464311565);
+    g = fmin(fmax(g, -0.99), 0.99);               // inside the family's range, well conditioned
     // skew-normal (xi, omega, delta) from the mean, deviation and skewness
     const double b = 0.7978845608028654;          // sqrt(2 / pi)
     const double ag = pow(fabs(g), 2.0 / 3.0);
@@ -263,7 +263,7 @@ __device__ __noinline__ double ssm_charge(const StepArgs<R>& a, double d, double
     double sn, cs;
     sincos(2.0 * M_PI * u1, &sn, &cs);
     const double z0 = rad * cs, z1 = rad * sn;
-    const double y = xi + omega * (delta * fabs(z0) + sqrt(1.0 - delta * delta) * z1);
+    const double y = xi + omega * (delta * fabs(z0) + sqrt(fmax(1.0 - delta * delta, 0.0)) * z1);
     return mu_w - y;
 }
 
