@@ -187,9 +187,26 @@ def tribo_set_modes(ctx: int, modes, ubar, damp, t0: float = 0.0) -> None:
     check(load().tribo_set_modes(ctx, C.byref(m)), "tribo_set_modes")
 
 
+@dataclasses.dataclass
+class SSMParams:
+    """Stochastic scaling model of wall-impact charging (Sec. 2.3.2): the
+    reference impact (radius r0, normal speed un0) with its charge statistics
+    and C_sat, as given for the paper's particles in Sec. 3.1, and the seed of
+    the Philox4x32-10 stream.  sigma0 = gamma0 = 0 makes the model
+    deterministic."""
+    r0: float = 2e-4          # reference particle radius [m]
+    un0: float = 0.925        # reference normal impact speed [m/s]
+    mu0: float = -4.12e-15    # mean charge of the reference impact [C]
+    sigma0: float = 6.49e-15  # its standard deviation [C]
+    gamma0: float = -0.191    # its skewness
+    dq0_min: float = -2.19e-14   # minimum charge of the reference impact [C]
+    c_sat: float = 500e-6     # saturation surface charge density C_sat [C/m^2]
+    seed: int = 0
+
+
 def tribo_set_ssm(ctx: int, ssm) -> None:
     """Stochastic scaling model of wall impacts (None: condenser model).  ssm:
-    object with r0, un0, mu0, sigma0, gamma0, dq0_min, c_sat, seed."""
+    an SSMParams, or any object with its fields."""
     if ssm is None:
         check(load().tribo_set_ssm(ctx, None), "tribo_set_ssm")
         return

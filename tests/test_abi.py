@@ -87,3 +87,12 @@ def test_error_strings(lib):
     lib.tribo_init.restype = C.c_int32
     # a NULL output pointer is an argument error, reported without touching a GPU
     assert lib.tribo_init(None, None, None, None, C.c_int64(0), None) == _abi.TRIBO_ERR_ARG
+
+
+def test_ssm_defaults_are_the_reference_impact_of_sec_3_1():
+    """The binding's SSM defaults equal the oracle's (both restate Sec. 3.1)."""
+    import dataclasses
+
+    import paper_2602_10761_gb300 as T
+    from oracle.ssm import SSM
+    assert dataclasses.asdict(T.SSMParams()) == dataclasses.asdict(SSM())

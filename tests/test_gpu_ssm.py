@@ -3,6 +3,8 @@ near-wall particles impacting over ten steps, each impact's charge drawn
 from Philox4x32-10 with counter (particle id, impact count), so the result
 must not depend on the particle order (re-sorting on and off); FP64 to 1e-12
 and mixed to 1e-5 per particle, impact counts exact."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -30,7 +32,7 @@ def _gpu(c, faces, lat, parts, prec, nsteps, ssm, **pkw):
     params = T.Params(precision=prec, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, **pkw)
     ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params,
                    torch.from_numpy(np.ascontiguousarray(lat.astype(real))).cuda(), max_particles=len(parts["x"]))
-    ch.set_ssm(ssm)
+    ch.set_ssm(T.SSMParams(**dataclasses.asdict(ssm)))
     P = T.Particles.from_numpy(parts, prec, device="cuda")
     ch.step(P, c.dt, nsteps)
     ch.sync()
@@ -68,7 +70,7 @@ def test_ssm_needs_particle_ids():
     c, faces, lat, parts = problem(12, 8, 6, n=20, seed=2)
     ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, T.Params(precision=T.TRIBO_FP64),
                    torch.from_numpy(lat).cuda(), max_particles=20)
-    ch.set_ssm(SSM())
+    ch.set_ssm(T.SSMParams())
     P = T.Particles.from_numpy(parts, T.TRIBO_FP64, with_id=False)
     with pytest.raises(T.TriboError):
         ch.step(P, c.dt, 1)

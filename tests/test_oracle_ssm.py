@@ -87,6 +87,25 @@ def test_deterministic_limit_scales_with_the_hertz_area():
     assert np.allclose(dq, ref, rtol=1e-12, atol=0)
 
 
+def test_deterministic_limit_matched_to_the_condenser_model():
+    """Sec. 3.1: with sigma_0 = gamma_0 = 0 and mu_0 = dq0_min = mu_condenser the SSM
+    stands in for the condenser model.  Matched at the reference impact, the two
+    agree there; elsewhere their ratio is the closed form of the two scalings:
+    the condenser charge C U_c dt_w / T_w (dt_w / T_w ~ 1e-8) goes as d^3 u^(3/5),
+    the SSM's mu_0 A / A_0 as d^2 u^(4/5), so SSM / condenser = (d_0 / d)(u / u_0)^(1/5)."""
+    p = oracle.Params(rho_p=1150.0, U_c=5.0)
+    s0 = SSM()
+    mu_c, _, _ = oracle.condenser_wall(p, np.array([2 * s0.r0]), np.array([s0.un0]), np.zeros(1))
+    s = SSM(sigma0=0.0, gamma0=0.0, mu0=float(mu_c[0]), dq0_min=float(mu_c[0]))
+    d = np.array([2 * s0.r0, 50e-6, 91e-6, 400e-6, 1e-3])
+    u = np.array([s0.un0, 0.01, 0.3, 0.925, 2.0])
+    dq, _ = ssm_wall_charge(p, s, d, u, np.zeros(5), np.arange(5), np.zeros(5, np.int64))
+    cond, _, _ = oracle.condenser_wall(p, d, u, np.zeros(5))
+    assert abs(dq[0] / cond[0] - 1) < 1e-13
+    ratio = (2 * s0.r0 / d) * (u / s0.un0) ** 0.2
+    assert np.allclose(dq / cond, ratio, rtol=1e-7, atol=0)
+
+
 def test_step_uses_the_ssm_with_the_impact_counter():
     g = oracle.Grid(4, 4, 2 * math.pi * 0.02, math.pi * 0.02, np.linspace(0, 0.04, 5))
     lat = np.zeros((4, 6, 4, 3))
