@@ -23,6 +23,6 @@ from .constants import Params, TABLE1  # noqa: F401
 from .grid import Grid, locate, trilinear  # noqa: F401
 from .poisson import deposit, poisson, efield, fv_apply, dense_poisson  # noqa: F401
 from .particles import (  # noqa: F401
-    State, relaxation_time, push, wrap, wall_impacts, condenser_wall, step, run,
+    State, relaxation_time, push, wrap, wall_impacts, condenser_wall, step, run, momentum_source,
     ystats, particle_mass, coulomb_near, pp_charge, pp_collisions,
 )

@@ -265,6 +265,31 @@ def push(p: Params, x, v, uf, acc, d, dt):
     return xn, vn, tau
 
 
+def momentum_source(g: Grid, p: Params, st: "State", uf, acc, tau, dt):
+    """F_s of the gas momentum equation (Eq. ns): the particles' aerodynamic
+    forces summed over each control volume, per unit gas mass.
+
+    Reading: the drag force of a particle over the step is its drag impulse
+    under the integrator of push() divided by dt; with u, a and tau frozen,
+    dv/dt = (u - v)/tau + a integrates to a drag impulse
+      dv_drag = (u - v) phi1 - a tau phi2,
+    and F_s[c] = -(1 / (rho V_c)) sum_{p in c} m_p dv_drag,p / dt over the
+    particles whose start position lies in cell c (where u was gathered).
+    Returns planes (3, nz, ny, nx).
+    """
+    fs = np.zeros((3, g.nz, g.ny, g.nx))
+    if p.drag_law == DRAG_OFF or st.n == 0:
+        return fs
+    V = np.stack([st.vx, st.vy, st.vz], axis=1)
+    phi1, phi2 = _phi12(dt / tau)
+    dv = (uf - V) * phi1[:, None] - acc * (tau * phi2)[:, None]
+    i, j, k = locate(g, st.x, st.y, st.z)
+    w = -particle_mass(p, st.d) / (p.rho * dt)
+    for c in range(3):
+        np.add.at(fs[c], (k, j, i), w * dv[:, c])
+    return fs / g.vol_y[None, None, :, None]
+
+
 def wrap(s, length):
     """Periodic wrap into [0, L); a result equal to L (rounding) becomes 0."""
     w = s - length * np.floor(s / length)
@@ -369,19 +394,26 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
         if diag is not None:
             diag.update(pairs=pairs)
     if diag is not None:
-        diag.update(uf=uf, hit=hit, tau=tau)
+        diag.update(uf=uf, hit=hit, tau=tau, acc=acc, F_s=momentum_source(g, p, st, uf, acc, tau, dt))
     return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall, st.id.copy())
 
 
 def run(g: Grid, p: Params, st: State, u_lat, dt: float, nsteps: int,
-        hist: np.ndarray | None = None) -> State:
-    """nsteps coupled steps; optionally accumulate the y-cell histogram.
+        hist: np.ndarray | None = None, fs: np.ndarray | None = None) -> State:
+    """nsteps coupled steps; optionally accumulate the y-cell histogram and
+    the mean momentum source over the steps (fs, planes (3, nz, ny, nx),
+    overwritten).
 
     u_lat may be an array or a callable t -> lattice (time-varying gas field).
     """
+    if fs is not None:
+        fs[...] = 0.0
     for n in range(nsteps):
         lat = u_lat(n * dt) if callable(u_lat) else u_lat
-        st = step(g, p, st, lat, dt)
+        diag = {} if fs is not None else None
+        st = step(g, p, st, lat, dt, diag=diag)
+        if fs is not None:
+            fs += diag["F_s"] / nsteps
         if hist is not None:
             hist += ystats(g, st)
     return st
