@@ -211,6 +211,26 @@ typedef struct {
 
 tribo_status tribo_set_ssm(tribo_ctx* ctx, const tribo_ssm* ssm);
 
+/* Momentum source of the particles on the gas, F_s of the momentum equation
+ * (Eq. ns, Sec. 2.1): the aerodynamic forces of the particles of a control
+ * volume summed, per unit gas mass,
+ *   F_s[c] = -(1 / (rho V_c)) sum_{p in c} m_p dv_p / dt,
+ * where dv_p = (u - v) phi1 - a tau phi2 is the velocity change the drag
+ * gives the particle over the step under the exponential integrator (u, the
+ * electric acceleration a and tau frozen; phi1 = 1 - e^-s, phi2 = s - phi1,
+ * s = dt / tau), and c is the particle's cell at the start of the step (where
+ * u was gathered).  Wall and particle-particle impulses are not aerodynamic
+ * and are not included; drag off gives zero.
+ * F_s: device (3, Nz, Ny, Nx) "real" planes F_x, F_y, F_z in m/s^2 (cell
+ * key (k Ny + j) Nx + i within a plane), aligned to the real type,
+ * caller-owned and borrowed until replaced; NULL switches the source off.
+ * Every tribo_step with nsteps >= 1 overwrites it with the mean of F_s over
+ * its steps (stream-ordered; zero when there are no particles), so a gas
+ * solver stepping once per call receives the source of that step.
+ * tribo_adjoint and batches do not write it.  TRIBO_ERR_ARG for a misaligned
+ * pointer. */
+tribo_status tribo_set_momentum_source(tribo_ctx* ctx, void* F_s);
+
 /* Replace the physical parameters and switches (precision must not change). */
 tribo_status tribo_set_params(tribo_ctx* ctx, const tribo_params* params);
 

@@ -219,6 +219,13 @@ def tribo_eval_modes(ctx: int, t: float, u_out=None) -> None:
     check(load().tribo_eval_modes(ctx, float(t), _ptr(u_out)), "tribo_eval_modes")
 
 
+def tribo_set_momentum_source(ctx: int, F_s=None) -> None:
+    """Momentum source of the particles on the gas (Eq. ns): device planes
+    (3, Nz, Ny, Nx) of the real type, overwritten by every tribo_step with
+    the mean over its steps; None switches it off."""
+    check(load().tribo_set_momentum_source(ctx, _ptr(F_s)), "tribo_set_momentum_source")
+
+
 def tribo_set_params(ctx: int, params: Params) -> None:
     p = params.to_c()
     check(load().tribo_set_params(ctx, C.byref(p)), "tribo_set_params")
@@ -452,6 +459,20 @@ class Channel:
 
     def set_ssm(self, ssm) -> None:
         tribo_set_ssm(self.ctx, ssm)
+
+    def momentum_source(self, on: bool = True):
+        """Allocate (or drop, on=False) the planes F_s (3, Nz, Ny, Nx) of the
+        particles' momentum source on the gas; every step() overwrites them
+        with the mean over its steps.  Returns the tensor (or None)."""
+        import torch
+        if not on:
+            tribo_set_momentum_source(self.ctx, None)
+            self.F_s = None
+            return None
+        rdt = torch.float64 if self.params.precision == _abi.TRIBO_FP64 else torch.float32
+        self.F_s = torch.zeros((3, self.nz, self.ny, self.nx), dtype=rdt, device="cuda")
+        tribo_set_momentum_source(self.ctx, self.F_s)
+        return self.F_s
 
     def set_params(self, params: Params) -> None:
         tribo_set_params(self.ctx, params)

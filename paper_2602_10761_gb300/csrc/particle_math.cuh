@@ -46,6 +46,10 @@ struct StepArgs {
     double inv_T_w;
     double U_c;
     const R* acoul;                // near-field acceleration planes (x, y, z; n each), or NULL
+    R* fs;                         // momentum source planes (x, y, z; ncell each), or NULL
+    const R* fs_inv_vol;           // 1 / V_c per y cell
+    R fs_coef;                     // -1 / (rho dt nsteps)
+    size_t ncell;
     // stochastic scaling model of wall impacts (ssm = 0: condenser model)
     int ssm;
     unsigned int ssm_key0, ssm_key1;
@@ -294,6 +298,10 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     a.inv_T_w = 1.0 / (P.eps_w * P.eps0 * P.phi_p);
     a.U_c = P.U_c;
     a.acoul = nullptr;
+    a.fs = nullptr;
+    a.fs_inv_vol = (const R*)c->d_inv_vol;
+    a.fs_coef = 0;
+    a.ncell = (size_t)c->nx * c->ny * c->nz;
     a.ssm = c->ssm_on ? 1 : 0;
     if (c->ssm_on) {
         a.ssm_key0 = (unsigned int)(c->ssm.seed & 0xffffffffu);
@@ -329,7 +337,7 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     double q = p.q[n];
     if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
     int j;
-    (void)cell_key<R>(x, y, z, a, &j);
+    const uint32_t key0 = cell_key<R>(x, y, z, a, &j);
     R uf[3], Ef[3];
     gather<R>(a, x, y, z, j, uf, Ef, a.electro != 0, &err);
     // acceleration q E / m
@@ -368,6 +376,14 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
         xn = x + tau * (vx * phi1 + tx * phi2);
         yn = y + tau * (vy * phi1 + ty * phi2);
         zn = z + tau * (vz * phi1 + tz * phi2);
+        if (a.fs) {
+            // drag impulse of the step, (u - v) phi1 - a tau phi2, on the gas of the start cell
+            const R w = a.fs_coef * a.fs_inv_vol[j] * (a.mass_coef * d * d * d);
+            const R tp = tau * phi2;
+            atomicAdd(&a.fs[key0], w * ((uf[0] - vx) * phi1 - ax * tp));
+            atomicAdd(&a.fs[a.ncell + key0], w * ((uf[1] - vy) * phi1 - ay * tp));
+            atomicAdd(&a.fs[2 * a.ncell + key0], w * ((uf[2] - vz) * phi1 - az * tp));
+        }
     }
     // periodic wrap in x and z
     xn = xn - a.lx * rfloor(xn / a.lx);

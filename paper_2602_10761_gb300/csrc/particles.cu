@@ -103,6 +103,8 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
     if (io.E) a.E = (const R*)io.E;
     if (io.acc) a.acc = io.acc;
     a.acoul = (const R*)io.acoul;
+    a.fs = (R*)io.fs;
+    a.fs_coef = (R)io.fs_coef;
     const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
     phase_begin(c, PH_STEP);
     k_step<R><<<grid_for(p.n), kThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);

@@ -97,15 +97,20 @@ tribo_status build_tables(tribo_ctx* c) {
     const size_t rs = real_size(c);
     std::vector<double> Yd = c->Y, inv(ny + 1);
     for (int jn = 0; jn <= ny; ++jn) inv[jn] = 1.0 / (c->Y[jn + 1] - c->Y[jn]);
+    std::vector<double> ivol(ny);
+    for (int j = 0; j < ny; ++j) ivol[j] = 1.0 / (c->dx * c->dy[j] * c->dz);
     TRIBO_CUDA(cudaMalloc(&c->d_Yr, rs * (ny + 2)));
     TRIBO_CUDA(cudaMalloc(&c->d_invdY, rs * (ny + 1)));
+    TRIBO_CUDA(cudaMalloc(&c->d_inv_vol, rs * ny));
     if (c->prec == TRIBO_FP64) {
         TRIBO_CUDA(cudaMemcpy(c->d_Yr, Yd.data(), rs * (ny + 2), cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMemcpy(c->d_invdY, inv.data(), rs * (ny + 1), cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMemcpy(c->d_inv_vol, ivol.data(), rs * ny, cudaMemcpyHostToDevice));
     } else {
-        std::vector<float> Yf(Yd.begin(), Yd.end()), invf(inv.begin(), inv.end());
+        std::vector<float> Yf(Yd.begin(), Yd.end()), invf(inv.begin(), inv.end()), ivf(ivol.begin(), ivol.end());
         TRIBO_CUDA(cudaMemcpy(c->d_Yr, Yf.data(), rs * (ny + 2), cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMemcpy(c->d_invdY, invf.data(), rs * (ny + 1), cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMemcpy(c->d_inv_vol, ivf.data(), rs * ny, cudaMemcpyHostToDevice));
     }
     return TRIBO_OK;
 }
@@ -221,7 +226,7 @@ void free_ctx(tribo_ctx* c) {
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
-                    c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner};
+                    c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner, c->d_inv_vol};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -398,6 +403,14 @@ tribo_status tribo_set_ssm(tribo_ctx* c, const tribo_ssm* m) {
     return TRIBO_OK;
 }
 
+tribo_status tribo_set_momentum_source(tribo_ctx* c, void* F_s) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    if ((uintptr_t)F_s % real_size(c)) { set_last_error("F_s must be aligned to its real type"); return TRIBO_ERR_ARG; }
+    TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+    c->fs = F_s;
+    return TRIBO_OK;
+}
+
 tribo_status tribo_set_params(tribo_ctx* c, const tribo_params* params) {
     if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
     tribo_status st = check_params(params);
@@ -423,6 +436,8 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     tribo_status st = check_particles(c, p);
     if (st) return st;
     if (nsteps < 0 || !(dt > 0) || !std::isfinite(dt)) { set_last_error("need nsteps >= 0 and dt > 0"); return TRIBO_ERR_ARG; }
+    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+    if (c->fs && nsteps > 0) TRIBO_CUDA(cudaMemsetAsync(c->fs, 0, 3 * ncell * real_size(c), c->stream));
     if (nsteps == 0 || p->n == 0) {
         c->n_samples += nsteps;
         return TRIBO_OK;
@@ -468,6 +483,10 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     }
     StepIO io;
     if (near) io.acoul = c->nf_acc;
+    if (c->fs && c->P.drag_law != TRIBO_DRAG_OFF) {
+        io.fs = c->fs;
+        io.fs_coef = -1.0 / (c->P.rho * dt * nsteps);
+    }
     PView home = v, cur = v, other = S > 0 ? set_view(c, c->alt, p->n) : v;
     if (!v.id) other.id = nullptr;
     if (!v.cell) other.cell = nullptr;

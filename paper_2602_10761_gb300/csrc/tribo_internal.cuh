@@ -146,6 +146,8 @@ struct tribo_ctx {
     bool ssm_on = false;               // wall impacts charge by the stochastic scaling model
     tribo_ssm ssm{};
     double ssm_A0 = 0.0;               // Hertz contact area of the SSM reference impact
+    void* fs = nullptr;                // momentum source planes F_x, F_y, F_z (borrowed) or NULL
+    void* d_inv_vol = nullptr;         // 1 / (dx dy_j dz) per y cell, real type
     void* adj = nullptr;               // adjoint workspace (checkpoints, segment states, adjoints)
     size_t adj_bytes = 0;
 
@@ -222,6 +224,8 @@ struct StepIO {               // per-call overrides of the context's buffers
     Accum* acc = nullptr;        // statistics and error word (NULL: the context's)
     bool stats = true;           // add the positions to the y histogram
     const void* acoul = nullptr; // near-field acceleration planes (x, y, z) or NULL
+    void* fs = nullptr;          // momentum source planes to add this step's drag to, or NULL
+    double fs_coef = 0.0;        // -1 / (rho dt nsteps): the mean over the call's steps
 };
 tribo_status particles_step(tribo_ctx* c, const PView& p, double dt, bool deposit_next,
                             bool write_cell, const StepIO& io = StepIO());

@@ -1,0 +1,164 @@
+"""Momentum source of the particles on the gas (F_s of Eq. ns) on the GPU
+against the oracle, through the C ABI (tribo_set_momentum_source).
+
+Per cell, |F_s,gpu - F_s,oracle| <= tol * S_c, where S_c is the cell's sum
+of the magnitudes of its terms, (m_p / (rho V_c dt)) ((|u| + |v|) phi1 +
+|a| tau phi2), averaged over the steps: the rounding bound of a sum whose
+terms may cancel.  FP64: ten steps (after a three-step call, so the source is
+overwritten, not accumulated), tol 1e-12, with and without re-sorting.
+Mixed: one step from the same rounded state (the cells are the same by
+construction), tol 1e-5 (FP32 arithmetic, a few roundings per term and
+float atomics: about 10 eps_32 = 6e-7); over ten mixed steps near-face
+particles may change cells, so there the cell sums of V_c F_s (the total
+momentum) are compared, to 1e-4 of their bound.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _problems import TOL_FP64, compare_states, oracle_params, problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2602_10761_gb300 as T  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_10761_gb300 import build
+    build.build()
+    T.load()
+
+
+def _case(real, seed=61, n=4000, shape=(32, 24, 16)):
+    c, faces, lat, parts = problem(*shape, n=n, q_scale=2e-13, vy_scale=0.4, near_wall=0.2, seed=seed,
+                                   dplus=(0.8, 2.5))
+    pr = {k: (v if k == "q" else np.asarray(v).astype(real).astype(np.float64)) for k, v in parts.items()}
+    return c, faces, lat.astype(real).astype(np.float64), pr
+
+
+def _oracle(c, faces, lat, parts, nsteps, warm=0, **pkw):
+    """Oracle state, mean F_s over nsteps (after warm steps) and its bound S_c."""
+    g = oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces)
+    p = oracle_params(c, U_c=2e3, **pkw)
+    st = oracle.State.from_arrays(parts["x"], parts["y"], parts["z"], parts["vx"], parts["vy"], parts["vz"],
+                                  parts["q"], parts["d"])
+    st = oracle.run(g, p, st, lat, c.dt, warm)
+    fs = np.zeros((3, g.nz, g.ny, g.nx))
+    bound = np.zeros_like(fs)
+    for _ in range(nsteps):
+        diag = {}
+        V = np.stack([st.vx, st.vy, st.vz], axis=1)
+        i, j, k = oracle.locate(g, st.x, st.y, st.z)
+        key = g.cell_key(i, j, k)
+        pre = st
+        st = oracle.step(g, p, st, lat, c.dt, diag=diag)
+        fs += diag["F_s"] / nsteps
+        s = c.dt / diag["tau"]
+        phi1 = -np.expm1(-s)
+        w = oracle.particle_mass(p, pre.d) / (p.rho * c.dt)
+        for comp in range(3):
+            t = w * ((np.abs(diag["uf"][:, comp]) + np.abs(V[:, comp])) * phi1 +
+                     np.abs(diag["acc"][:, comp]) * diag["tau"] * (s - phi1))
+            b = np.bincount(key, weights=t, minlength=g.ncells).reshape(g.nz, g.ny, g.nx)
+            bound[comp] += b / (g.vol_y[None, :, None] * nsteps)
+    return g, st, fs, bound
+
+
+def _gpu(c, faces, lat, parts, prec, nsteps, warm=0, **pkw):
+    real = np.float64 if prec == T.TRIBO_FP64 else np.float32
+    params = T.Params(precision=prec, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=2e3, **pkw)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params,
+                   torch.from_numpy(np.ascontiguousarray(lat.astype(real))).cuda(), max_particles=len(parts["x"]))
+    F = ch.momentum_source()
+    P = T.Particles.from_numpy(parts, prec, device="cuda")
+    if warm:
+        ch.step(P, c.dt, warm)
+    ch.step(P, c.dt, nsteps)
+    ch.sync()
+    fs = F.cpu().numpy().astype(np.float64)
+    out = P.to_numpy()
+    ch.close()
+    order = np.argsort(out["id"])
+    return {k: np.asarray(v)[order].astype(np.float64) for k, v in out.items()}, fs
+
+
+def _check(fs, ref, bound, tol, label):
+    assert np.any(ref != 0)
+    err = np.abs(fs - ref)
+    worst = (err / np.where(bound > 0, bound, 1.0)).max()
+    assert np.all(err <= tol * bound), f"{label}: worst error / bound {worst}"
+    return worst
+
+
+@pytest.mark.parametrize("sort_every", [0, 3])
+def test_momentum_source_fp64_matches_oracle(sort_every):
+    c, faces, lat, parts = _case(np.float64)
+    g, ref_st, ref, bound = _oracle(c, faces, lat, parts, 10, warm=3)
+    got, fs = _gpu(c, faces, lat, parts, T.TRIBO_FP64, 10, warm=3, sort_every=sort_every)
+    compare_states(g, got, ref_st, TOL_FP64, label="two-way fp64")
+    _check(fs, ref, bound, 1e-12, f"fp64 sort={sort_every}")
+
+
+@pytest.mark.parametrize("drag", [T.TRIBO_DRAG_STOKES, T.TRIBO_DRAG_SCHILLER_NAUMANN])
+@pytest.mark.parametrize("sort_every", [0, 1])
+def test_momentum_source_mixed_one_step(sort_every, drag):
+    c, faces, lat, parts = _case(np.float32, seed=62)
+    _, _, ref, bound = _oracle(c, faces, lat, parts, 1, drag_law=drag)
+    _, fs = _gpu(c, faces, lat, parts, T.TRIBO_MIXED, 1, sort_every=sort_every, drag_law=drag)
+    _check(fs, ref, bound, 1e-5, f"mixed drag={drag} sort={sort_every}")
+
+
+def test_momentum_source_mixed_ten_steps_total():
+    c, faces, lat, parts = _case(np.float32, seed=63)
+    g, _, ref, bound = _oracle(c, faces, lat, parts, 10)
+    _, fs = _gpu(c, faces, lat, parts, T.TRIBO_MIXED, 10, sort_every=4)
+    vol = g.vol_y[None, None, :, None]
+    tot, tot_ref, tot_bound = (fs * vol).sum(axis=(1, 2, 3)), (ref * vol).sum(axis=(1, 2, 3)), \
+        (bound * vol).sum(axis=(1, 2, 3))
+    assert np.all(np.abs(tot - tot_ref) <= 1e-4 * tot_bound), (tot, tot_ref, tot_bound)
+
+
+def test_momentum_source_is_overwritten_and_switched_off():
+    c, faces, lat, parts = _case(np.float64, seed=64, n=500, shape=(16, 12, 8))
+    params = T.Params(precision=T.TRIBO_FP64, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(), max_particles=500)
+    F = ch.momentum_source()
+    P = T.Particles.from_numpy(parts, T.TRIBO_FP64)
+    ch.step(P, c.dt, 2)
+    ch.sync()
+    assert torch.count_nonzero(F).item() > 0
+    # drag off: no source; the previous call's values are gone
+    ch.set_params(params.with_(drag_law=T.TRIBO_DRAG_OFF))
+    ch.step(P, c.dt, 1)
+    ch.sync()
+    assert torch.count_nonzero(F).item() == 0
+    # switched off: the buffer is left alone
+    ch.set_params(params)
+    F.fill_(7.0)
+    ch.momentum_source(False)
+    ch.step(P, c.dt, 1)
+    ch.sync()
+    assert bool((F == 7.0).all())
+    # no particles: zero
+    F2 = ch.momentum_source()
+    F2.fill_(7.0)
+    E = T.Particles.from_numpy({k: v[:0] for k, v in parts.items()}, T.TRIBO_FP64)
+    ch.step(E, c.dt, 1)
+    ch.sync()
+    assert torch.count_nonzero(F2).item() == 0
+    ch.close()
+
+
+def test_momentum_source_rejects_misaligned_buffer():
+    c, faces, lat, _ = _case(np.float64, seed=65, n=10, shape=(16, 12, 8))
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, T.Params(precision=T.TRIBO_FP64),
+                   torch.from_numpy(lat).cuda(), max_particles=10)
+    # FP64 planes must be 8-byte aligned: a float32 view one element in is not
+    buf = torch.zeros(6 * c.nx * c.ny * c.nz + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(T.TriboError):
+        T.tribo_set_momentum_source(ch.ctx, buf[1:])
+    ch.close()
