@@ -395,18 +395,24 @@ def timevarying_report(T, torch, steps=200, sort_every=20):
 
 def interactions_report(T, torch, steps=100, sort_every=20):
     """Cost of the particle-particle interactions (the in-cell Coulomb near
-    field and the 4-way collisions) on the 128^3 workload with 1M particles:
-    ms per step with each switch against the plain coupled step."""
+    field and the 4-way collisions), of the stochastic scaling model of wall
+    charging and of the momentum source on the gas (2-way coupling) on the
+    128^3 workload with 1M particles: ms per step with each switch against
+    the plain coupled step."""
     c = synth.case("re180_128")
     faces, lat, P = make_inputs(c)
     parts = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
     u = torch.from_numpy(lat).cuda()
     out = {"workload": workload_desc(c) + ", frozen field"}
     for name, kw in (("plain", {}), ("coulomb", dict(coulomb=1)), ("collisions", dict(collisions=1)),
-                     ("coulomb_and_collisions", dict(coulomb=1, collisions=1))):
+                     ("coulomb_and_collisions", dict(coulomb=1, collisions=1)), ("ssm", {}), ("two_way", {})):
         params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0,
                           sort_every=sort_every, **kw)
         ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, u, max_particles=c.n_particles)
+        if name == "ssm":
+            ch.set_ssm(T.SSMParams(seed=1))
+        if name == "two_way":
+            ch.momentum_source()
         Pd = T.Particles.from_numpy(parts, T.TRIBO_MIXED, device="cuda")
         ch.step(Pd, c.dt, 5)
         torch.cuda.synchronize()
