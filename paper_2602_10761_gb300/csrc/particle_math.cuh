@@ -337,7 +337,7 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     double q = p.q[n];
     if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
     int j;
-    const uint32_t key0 = cell_key<R>(x, y, z, a, &j);
+    (void)cell_key<R>(x, y, z, a, &j);
     R uf[3], Ef[3];
     gather<R>(a, x, y, z, j, uf, Ef, a.electro != 0, &err);
     // acceleration q E / m
@@ -378,6 +378,9 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
         zn = z + tau * (vz * phi1 + tz * phi2);
         if (a.fs) {
             // drag impulse of the step, (u - v) phi1 - a tau phi2, on the gas of the start cell
+            // (its key is formed only here: the plain step needs the y index alone)
+            int j0;
+            const uint32_t key0 = cell_key<R>(x, y, z, a, &j0);
             const R w = a.fs_coef * a.fs_inv_vol[j] * (a.mass_coef * d * d * d);
             const R tp = tau * phi2;
             atomicAdd(&a.fs[key0], w * ((uf[0] - vx) * phi1 - ax * tp));
