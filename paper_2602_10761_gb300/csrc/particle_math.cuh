@@ -18,6 +18,7 @@ template <class R>
 struct StepArgs {
     int nx, ny, nz, nyn;
     R lx, ly, lz, inv_dx, inv_dz, dt;
+    R inv_lx, inv_lz;
     double dx, dz;                 // FP64 cell sizes (exact locate in FP64 mode)
     const double* yf;              // ny+1 FP64 faces
     const float* yf_up;            // ny+1 rounded-up float faces
@@ -122,7 +123,7 @@ __device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a
 // coordinates (wx, wy, wz are the upper-node fractions)
 template <class R>
 struct Corners {
-    size_t idx[8];
+    uint32_t idx[8];               // node indices within one lattice plane (planes hold < 2^32 nodes)
     R w[8];
     R wx, wy, wz;
     R inv_dy;                      // 1 / (Y[jn0+1] - Y[jn0])
@@ -151,10 +152,10 @@ __device__ __forceinline__ void corners(const StepArgs<R>& a, R x, R y, R z, int
     cr.inv_dy = a.invdY[jn0];
     const R wy = (y - a.Yr[jn0]) * cr.inv_dy;
     const R wx0 = (R)1 - wx, wy0 = (R)1 - wy, wz0 = (R)1 - wz;
-    const size_t r00 = ((size_t)k0 * a.nyn + jn0) * a.nx;
-    const size_t r01 = ((size_t)k0 * a.nyn + jn0 + 1) * a.nx;
-    const size_t r10 = ((size_t)k1 * a.nyn + jn0) * a.nx;
-    const size_t r11 = ((size_t)k1 * a.nyn + jn0 + 1) * a.nx;
+    const uint32_t r00 = ((uint32_t)k0 * (uint32_t)a.nyn + (uint32_t)jn0) * (uint32_t)a.nx;
+    const uint32_t r01 = r00 + (uint32_t)a.nx;
+    const uint32_t r10 = ((uint32_t)k1 * (uint32_t)a.nyn + (uint32_t)jn0) * (uint32_t)a.nx;
+    const uint32_t r11 = r10 + (uint32_t)a.nx;
     cr.idx[0] = r00 + i0; cr.idx[1] = r00 + i1; cr.idx[2] = r01 + i0; cr.idx[3] = r01 + i1;
     cr.idx[4] = r10 + i0; cr.idx[5] = r10 + i1; cr.idx[6] = r11 + i0; cr.idx[7] = r11 + i1;
     cr.w[0] = wz0 * wy0 * wx0; cr.w[1] = wz0 * wy0 * wx; cr.w[2] = wz0 * wy * wx0; cr.w[3] = wz0 * wy * wx;
@@ -169,36 +170,56 @@ __device__ __forceinline__ void gather(const StepArgs<R>& a, R x, R y, R z, int 
     Corners<R> cr;
     corners<R>(a, x, y, z, j, cr, err);
     R u0 = 0, u1 = 0, u2 = 0, e0 = 0, e1 = 0, e2 = 0;
+    // one base pointer per plane: each load is base + 32-bit index
+    const R* __restrict__ U0 = a.u;
+    const R* __restrict__ U1 = a.u + a.nodes;
+    const R* __restrict__ U2 = a.u + 2 * a.nodes;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        u0 += cr.w[c] * __ldg(a.u + cr.idx[c]);
-        u1 += cr.w[c] * __ldg(a.u + a.nodes + cr.idx[c]);
-        u2 += cr.w[c] * __ldg(a.u + 2 * a.nodes + cr.idx[c]);
+        u0 += cr.w[c] * __ldg(U0 + cr.idx[c]);
+        u1 += cr.w[c] * __ldg(U1 + cr.idx[c]);
+        u2 += cr.w[c] * __ldg(U2 + cr.idx[c]);
     }
     if (withE) {
+        const R* __restrict__ E0 = a.E;
+        const R* __restrict__ E1 = a.E + a.nodes;
+        const R* __restrict__ E2 = a.E + 2 * a.nodes;
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            e0 += cr.w[c] * __ldg(a.E + cr.idx[c]);
-            e1 += cr.w[c] * __ldg(a.E + a.nodes + cr.idx[c]);
-            e2 += cr.w[c] * __ldg(a.E + 2 * a.nodes + cr.idx[c]);
+            e0 += cr.w[c] * __ldg(E0 + cr.idx[c]);
+            e1 += cr.w[c] * __ldg(E1 + cr.idx[c]);
+            e2 += cr.w[c] * __ldg(E2 + cr.idx[c]);
         }
     }
     uf[0] = u0; uf[1] = u1; uf[2] = u2;
     Ef[0] = e0; Ef[1] = e1; Ef[2] = e2;
 }
 
+// coefficients (-1)^k / (k+2)! of phi2(s) / s^2, k = 0..K, formed at compile time
+template <int K>
+struct Phi2Series {
+    double c[K + 1];
+    constexpr Phi2Series() : c() {
+        double f = 2.0;                       // (k+2)!
+        for (int k = 0; k <= K; ++k) {
+            c[k] = (k % 2 ? -1.0 : 1.0) / f;
+            f *= (double)(k + 3);
+        }
+    }
+};
+
 template <class R>
 __device__ __forceinline__ R phi2_of(R s, R phi1) {
     if (s < (R)0.5) {
-        // sum_{n>=2} (-1)^n s^n / n!, truncated below the precision's epsilon
-        const int nt = sizeof(R) == 8 ? 18 : 10;
-        R term = s * s * (R)0.5;
-        R sum = term;
-        for (int n = 3; n <= nt; ++n) {
-            term = -term * s / (R)n;
-            sum += term;
-        }
-        return sum;
+        // sum_{n=2}^{N} (-1)^n s^n / n! = s^2 sum_k (-1)^k s^k / (k+2)!, by Horner with the
+        // coefficients as constants; N = 18 (FP64) or 10 (FP32) leaves the truncation below
+        // the precision's epsilon for s < 1/2
+        constexpr int K = sizeof(R) == 8 ? 16 : 8;
+        constexpr Phi2Series<K> S{};
+        R p = (R)S.c[K];
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) p = (R)S.c[k] + s * p;
+        return s * s * p;
     }
     return s - phi1;
 }
@@ -277,6 +298,7 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     a.nx = c->nx; a.ny = c->ny; a.nz = c->nz; a.nyn = c->ny + 2;
     a.lx = (R)c->lx; a.ly = (R)c->ly; a.lz = (R)c->lz;
     a.inv_dx = (R)(1.0 / c->dx); a.inv_dz = (R)(1.0 / c->dz);
+    a.inv_lx = (R)(1.0 / c->lx); a.inv_lz = (R)(1.0 / c->lz);
     a.dt = (R)dt;
     a.dx = c->dx; a.dz = c->dz;
     a.yf = c->d_yf; a.yf_up = c->d_yf_up; a.xf_up = c->d_xf_up; a.zf_up = c->d_zf_up;
@@ -388,11 +410,21 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
             atomicAdd(&a.fs[2 * a.ncell + key0], w * ((uf[2] - vz) * phi1 - az * tp));
         }
     }
-    // periodic wrap in x and z
-    xn = xn - a.lx * rfloor(xn / a.lx);
-    if (xn >= a.lx) xn -= a.lx;
-    zn = zn - a.lz * rfloor(zn / a.lz);
-    if (zn >= a.lz) zn -= a.lz;
+    // periodic wrap in x and z (FP64: the oracle's own operations, so cells stay bit-exact;
+    // FP32: the reciprocal, with both ends corrected)
+    if constexpr (sizeof(R) == 8) {
+        xn = xn - a.lx * rfloor(xn / a.lx);
+        if (xn >= a.lx) xn -= a.lx;
+        zn = zn - a.lz * rfloor(zn / a.lz);
+        if (zn >= a.lz) zn -= a.lz;
+    } else {
+        xn = xn - a.lx * rfloor(xn * a.inv_lx);
+        if (xn < (R)0) xn += a.lx;
+        if (xn >= a.lx) xn -= a.lx;
+        zn = zn - a.lz * rfloor(zn * a.inv_lz);
+        if (zn < (R)0) zn += a.lz;
+        if (zn >= a.lz) zn -= a.lz;
+    }
     // wall contact (hard sphere, specular)
     const R r = (R)0.5 * d;
     const bool lo = yn < r;

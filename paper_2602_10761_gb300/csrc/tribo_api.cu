@@ -293,7 +293,10 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
     }
     if (ny < 2 || ny > 1024) { set_last_error("ny must be in [2, 1024]"); return TRIBO_ERR_UNSUPPORTED; }
     if (!(grid->lx > 0 && grid->lz > 0)) { set_last_error("lx, lz must be positive"); return TRIBO_ERR_ARG; }
-    if ((int64_t)nx * ny * nz >= (int64_t)1 << 32) { set_last_error("too many cells"); return TRIBO_ERR_UNSUPPORTED; }
+    if ((int64_t)nx * (ny + 2) * nz >= (int64_t)1 << 32) {
+        set_last_error("too many cells (the lattice planes index their nodes in 32 bits)");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
     if (grid->y_faces[0] != 0.0) { set_last_error("y_faces[0] must be 0"); return TRIBO_ERR_ARG; }
     for (int j = 0; j < ny; ++j)
         if (!(grid->y_faces[j + 1] > grid->y_faces[j])) {
