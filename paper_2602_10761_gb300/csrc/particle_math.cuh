@@ -13,6 +13,15 @@ namespace tribo {
 namespace {
 
 constexpr int kThreads = 256;
+// block shape of the fused particle step (threads, resident blocks per SM for the register budget)
+#ifndef TRIBO_KSTEP_THREADS
+#define TRIBO_KSTEP_THREADS 256
+#endif
+#ifndef TRIBO_KSTEP_MINB
+#define TRIBO_KSTEP_MINB 4
+#endif
+constexpr int kStepThreads = TRIBO_KSTEP_THREADS;
+constexpr int kStepMinBlocks = TRIBO_KSTEP_MINB;
 
 template <class R>
 struct StepArgs {
@@ -338,9 +347,11 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     return a;
 }
 
-int grid_for(int64_t n) {
-    int64_t b = (n + kThreads - 1) / kThreads;
-    if (b > 152 * 16) b = 152 * 16;
+// blocks for a grid-stride loop over n items: at most 152 x 16 blocks of 256 threads
+int grid_for(int64_t n, int threads = kThreads) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)152 * 16 * kThreads / threads;
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -34,7 +34,7 @@ namespace tribo {
 namespace {
 
 template <class R>
-__global__ void __launch_bounds__(kThreads, 4) k_step(StepArgs<R> a, PView p, int write_cell) {
+__global__ void __launch_bounds__(kStepThreads, kStepMinBlocks) k_step(StepArgs<R> a, PView p, int write_cell) {
     extern __shared__ unsigned int sh_hist[];
     const bool use_hist = a.hist != nullptr;
     if (use_hist) {
@@ -107,7 +107,7 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
     a.fs_coef = (R)io.fs_coef;
     const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
     phase_begin(c, PH_STEP);
-    k_step<R><<<grid_for(p.n), kThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
+    k_step<R><<<grid_for(p.n, kStepThreads), kStepThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }
