@@ -358,36 +358,16 @@ int grid_for(int64_t n, int threads = kThreads) {
 
 // one particle of the coupled step (the body of k_step): gather, push,
 // wrap, wall impact with the condenser charge, deposit for the next step
-// the inputs of one particle's step
-template <class R>
-struct PIn {
-    R x, y, z, vx, vy, vz, d;
-    double q;
-};
-
-template <class R>
-__device__ __forceinline__ void step_core(const StepArgs<R>& a, const PView& p, int64_t n, const PIn<R>& in,
-                                          int write_cell, unsigned int* sh_hist, bool use_hist, unsigned int& err);
-
 template <class R>
 __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, int64_t n, int write_cell,
                                          unsigned int* sh_hist, bool use_hist, unsigned int& err) {
-    const PIn<R> in{((const R*)p.x)[n], ((const R*)p.y)[n], ((const R*)p.z)[n], ((const R*)p.vx)[n],
-                    ((const R*)p.vy)[n], ((const R*)p.vz)[n], ((const R*)p.d)[n], p.q[n]};
-    step_core<R>(a, p, n, in, write_cell, sh_hist, use_hist, err);
-}
-
-// the step of particle n from its inputs: gather, push, wrap, wall impact, the
-// stores, the deposit for the next step
-template <class R>
-__device__ __forceinline__ void step_core(const StepArgs<R>& a, const PView& p, int64_t n, const PIn<R>& in,
-                                          int write_cell, unsigned int* sh_hist, bool use_hist, unsigned int& err) {
     R* X = (R*)p.x; R* Y = (R*)p.y; R* Z = (R*)p.z;
     R* VX = (R*)p.vx; R* VY = (R*)p.vy; R* VZ = (R*)p.vz;
-    R x = in.x, y = in.y, z = in.z;
-    R vx = in.vx, vy = in.vy, vz = in.vz;
-    const R d = in.d;
-    double q = in.q;
+    const R* D = (const R*)p.d;
+    R x = X[n], y = Y[n], z = Z[n];
+    R vx = VX[n], vy = VY[n], vz = VZ[n];
+    const R d = D[n];
+    double q = p.q[n];
     if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
     int j;
     (void)cell_key<R>(x, y, z, a, &j);

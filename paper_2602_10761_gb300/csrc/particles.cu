@@ -27,7 +27,6 @@
 // smallest float not below each FP64 face.
 #include <cmath>
 
-#include "async_copy.cuh"
 #include "particle_math.cuh"
 
 namespace tribo {
@@ -46,95 +45,6 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks) k_step(StepArgs<
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride)
         step_one<R>(a, p, n, write_cell, sh_hist, use_hist, err);
-    if (err) atomicOr(&a.acc->err, err);
-    if (use_hist) {
-        __syncthreads();
-        for (int b = threadIdx.x; b < a.ny; b += blockDim.x) {
-            const unsigned int v = sh_hist[b];
-            if (v) atomicAdd(&a.hist[b], (unsigned long long)v);
-        }
-    }
-}
-
-// The fused step with the particle stream staged in shared memory: the
-// block's tiles of kStepThreads particles (x, y, z, vx, vy, vz, d, q) arrive
-// by bulk asynchronous copies, one tile ahead of the one being computed, so
-// the gather of a tile overlaps the DRAM latency of the next.  Tiles
-// [0, ntiles) are whole; the particles after them take the plain loads.  All
-// arrays must be 16-byte aligned.  Every wait is bounded: a wait that runs
-// out sets TRIBO_DEV_TIMEOUT, waits (bounded) for the block's copies still in
-// flight and leaves the rest of the block's tiles unstepped.
-constexpr uint32_t kWaitPolls = 1u << 22;
-
-template <class R>
-__global__ void __launch_bounds__(kStepThreads, kStepMinBlocks) k_step_staged(StepArgs<R> a, PView p,
-                                                                              int write_cell, int64_t ntiles) {
-    constexpr int T = kStepThreads;
-    constexpr uint32_t STAGE = 7 * T * sizeof(R) + T * sizeof(double);
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + 2 * STAGE);
-    unsigned int* sh_hist = reinterpret_cast<unsigned int*>(bar + 2);
-    const bool use_hist = a.hist != nullptr;
-    if (use_hist)
-        for (int b = threadIdx.x; b < a.ny; b += blockDim.x) sh_hist[b] = 0u;
-    if (threadIdx.x == 0) {
-        ac::mbar_init(&bar[0], 1);
-        ac::mbar_init(&bar[1], 1);
-        ac::fence_mbar_init();
-    }
-    __syncthreads();
-    bool issued[2] = {false, false};               // thread 0: a copy into the stage is in flight
-    auto issue = [&](int st, int64_t tile) {
-        const int64_t n0 = tile * T;
-        unsigned char* dst = smem_raw + (size_t)st * STAGE;
-        ac::mbar_expect_tx(&bar[st], STAGE);
-        const void* src[7] = {p.x, p.y, p.z, p.vx, p.vy, p.vz, p.d};
-#pragma unroll
-        for (int k = 0; k < 7; ++k)
-            ac::bulk_g2s(dst + (size_t)k * T * sizeof(R), (const R*)src[k] + n0, T * sizeof(R), &bar[st]);
-        ac::bulk_g2s(dst + 7 * T * sizeof(R), p.q + n0, T * sizeof(double), &bar[st]);
-        issued[st] = true;
-    };
-    unsigned int err = 0;
-    uint32_t parity[2] = {0u, 0u};
-    int st = 0;
-    int64_t tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < ntiles) issue(0, tile);
-    bool failed = false;
-    for (; tile < ntiles; tile += gridDim.x) {
-        const bool ok = ac::mbar_wait(&bar[st], parity[st], kWaitPolls);
-        // block-wide: every thread also finished the previous tile (its stage is free)
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        if (threadIdx.x == 0) {
-            issued[st] = false;
-            if (tile + gridDim.x < ntiles) {
-                ac::fence_proxy_async();
-                issue(st ^ 1, tile + gridDim.x);
-            }
-        }
-        parity[st] ^= 1u;
-        const R* sv = reinterpret_cast<const R*>(smem_raw + (size_t)st * STAGE);
-        const double* sq = reinterpret_cast<const double*>(smem_raw + (size_t)st * STAGE + 7 * T * sizeof(R));
-        const int t = threadIdx.x;
-        const PIn<R> in{sv[t], sv[T + t], sv[2 * T + t], sv[3 * T + t], sv[4 * T + t], sv[5 * T + t],
-                        sv[6 * T + t], sq[t]};
-        step_core<R>(a, p, tile * T + t, in, write_cell, sh_hist, use_hist, err);
-        st ^= 1;
-    }
-    if (failed) {
-        err |= TRIBO_DEV_TIMEOUT;
-        if (threadIdx.x == 0) {
-            // the copies still in flight must land before the block's shared memory is released
-            for (int k = 0; k < 2; ++k)
-                if (issued[k]) (void)ac::mbar_wait(&bar[k], parity[k], kWaitPolls);
-        }
-    } else {
-        for (int64_t n = ntiles * T + (int64_t)blockIdx.x * T + threadIdx.x; n < p.n; n += (int64_t)gridDim.x * T)
-            step_one<R>(a, p, n, write_cell, sh_hist, use_hist, err);
-    }
     if (err) atomicOr(&a.acc->err, err);
     if (use_hist) {
         __syncthreads();
@@ -196,19 +106,8 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
     a.fs = (R*)io.fs;
     a.fs_coef = (R)io.fs_coef;
     const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
-    const uintptr_t al = (uintptr_t)p.x | (uintptr_t)p.y | (uintptr_t)p.z | (uintptr_t)p.vx | (uintptr_t)p.vy |
-                         (uintptr_t)p.vz | (uintptr_t)p.d | (uintptr_t)p.q;
-    const int64_t ntiles = p.n / kStepThreads;
     phase_begin(c, PH_STEP);
-    if (al % 16 == 0 && ntiles > 0) {
-        // one resident wave of persistent blocks, each walking its tiles
-        const int blocks = (int)std::min<int64_t>(ntiles, (int64_t)152 * kStepMinBlocks);
-        const size_t shs = 2 * (7 * kStepThreads * sizeof(R) + kStepThreads * sizeof(double)) +
-                           2 * sizeof(uint64_t) + sh;
-        k_step_staged<R><<<blocks, kStepThreads, shs, c->stream>>>(a, p, write_cell ? 1 : 0, ntiles);
-    } else {
-        k_step<R><<<grid_for(p.n, kStepThreads), kStepThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
-    }
+    k_step<R><<<grid_for(p.n, kStepThreads), kStepThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }
@@ -459,12 +358,6 @@ tribo_status lattice_from_aos3(tribo_ctx* c, const void* src_dev) {
 tribo_status particles_setup(tribo_ctx* c) {
     TRIBO_CUDA(cudaFuncSetAttribute(k_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 1024 * 4));
     TRIBO_CUDA(cudaFuncSetAttribute(k_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 1024 * 4));
-    // two stages of particle tiles, two barriers, the y histogram
-    TRIBO_CUDA(cudaFuncSetAttribute(k_step_staged<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(2 * (7 * kStepThreads * sizeof(float) + kStepThreads * sizeof(double)) +
-                                          16 + 4 * 1024 * 4)));
-    TRIBO_CUDA(cudaFuncSetAttribute(k_step_staged<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(2 * (8 * kStepThreads * sizeof(double)) + 16 + 4 * 1024 * 4)));
     return TRIBO_OK;
 }
 
