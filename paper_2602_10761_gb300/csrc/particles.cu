@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks) k_step(StepArgs<
         __syncthreads();
     }
     unsigned int err = 0;
+    // one resident wave of blocks walks the particles in windows of gridDim.x * blockDim.x: the
+    // particles are ordered by cell, so the lattice the wave gathers from stays small in L2
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride)
         step_one<R>(a, p, n, write_cell, sh_hist, use_hist, err);
@@ -107,7 +109,10 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
     a.fs_coef = (R)io.fs_coef;
     const size_t sh = sizeof(unsigned int) * (size_t)c->ny;
     phase_begin(c, PH_STEP);
-    k_step<R><<<grid_for(p.n, kStepThreads), kStepThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
+    // one resident wave (a grid of several waves measured 6% slower)
+    const int kblocks = (int)std::min<int64_t>((p.n + kStepThreads - 1) / kStepThreads,
+                                               (int64_t)c->num_sms * kStepMinBlocks);
+    k_step<R><<<kblocks, kStepThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }

@@ -308,6 +308,8 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
     tribo_ctx* c = new (std::nothrow) tribo_ctx();
     if (!c) { set_last_error("host allocation failed"); return TRIBO_ERR_OOM; }
     cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (c->num_sms < 1) c->num_sms = 1;
     c->stream = (cudaStream_t)stream;
     c->prec = params->precision;
     c->P = *params;

@@ -74,6 +74,7 @@ struct Accum {                // device-side statistics accumulators
 
 struct tribo_ctx {
     int device = 0;
+    int num_sms = 152;                 // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
     int prec = TRIBO_FP64;
     tribo_params P{};
