@@ -562,7 +562,9 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             }
             AdjArgs<R> ga{L.seg[i], (const R*)P.d, L.lam, db, L.Eb, L.pacc, n, c->P.kappa_A};
             phase_begin(c, PH_ADJOINT);
-            k_adj_step<R><<<grid_for(n), kThreads, 0, c->stream>>>(a, ga);
+            // one resident wave (two blocks per SM), as for the forward step
+            const int ab = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)c->num_sms * 2);
+            k_adj_step<R><<<ab, kThreads, 0, c->stream>>>(a, ga);
             TRIBO_LAUNCHED(c);
             if (!electro) continue;
             const int gb = (int)std::min<size_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
