@@ -332,8 +332,22 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
 
 // ---------------------------------------------------------------- z passes (four-step)
 // Forward z transform of S in place: block (cell plane j, W columns of m_x).
+// one tile (cell plane j, W columns of m_x) of the forward z transform; out of line so
+// that each tile starts from a fresh register allocation
 template <class R, int NZ>
-__global__ void __launch_bounds__(kThreads) k_zfwd4(cplx<R>* __restrict__ S, int ny, int nxh,
+__device__ __noinline__ void zfwd_tile(cplx<R>* __restrict__ S, int ny, int nxh, int ntx, int t,
+                                       const cplx<R>* __restrict__ tw, cplx<R>* buf) {
+    using F4 = fft::FourStep<NZ, kThreads>;
+    const int j = t / ntx;
+    const int mx0 = (t - j * ntx) * F4::W;
+    const int ncol = min(F4::W, nxh - mx0);
+    cplx<R>* base = S + (size_t)j * nxh + mx0;
+    const size_t rs = (size_t)ny * nxh;
+    fft::column_fft<R, -1, NZ, kThreads, false>(base, rs, base, rs, ncol, tw, nullptr, buf);
+}
+
+template <class R, int NZ>
+__global__ void __launch_bounds__(kThreads, 4) k_zfwd4(cplx<R>* __restrict__ S, int ny, int nxh,
                                                     const cplx<R>* __restrict__ tw_g) {
     using F4 = fft::FourStep<NZ, kThreads>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -341,18 +355,36 @@ __global__ void __launch_bounds__(kThreads) k_zfwd4(cplx<R>* __restrict__ S, int
     cplx<R>* buf = tw + NZ;
     for (int i = threadIdx.x; i < NZ; i += kThreads) tw[i] = tw_g[i];
     __syncthreads();
-    const int mx0 = blockIdx.y * F4::W;
-    const int ncol = min(F4::W, nxh - mx0);
-    cplx<R>* base = S + (size_t)blockIdx.x * nxh + mx0;
-    const size_t rs = (size_t)ny * nxh;
-    fft::column_fft<R, -1, NZ, kThreads, false>(base, rs, base, rs, ncol, tw, nullptr, buf);
+    const int ntx = (nxh + F4::W - 1) / F4::W;
+    for (int t = blockIdx.x; t < ny * ntx; t += gridDim.x) zfwd_tile<R, NZ>(S, ny, nxh, ntx, t, tw, buf);
 }
 
 // Inverse z transforms: block (node plane jn, W columns of m_x).  All planes:
 // F1 = IFFT_z(E_y-hat) in place; interior planes: F0 = IFFT_z(phi-hat of cell
 // jn-1) and F2 = IFFT_z(-i sin(2 pi m_z/nz)/dz phi-hat).
+// one tile (node plane jn, W columns of m_x) of the inverse z transforms, out of line
 template <class R, int NZ>
-__global__ void __launch_bounds__(kThreads) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
+__device__ __noinline__ void zinv_tile(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F, int ny, int nxh,
+                                       int ntx, int t, size_t fstride, const cplx<R>* __restrict__ tw,
+                                       const R* __restrict__ sz, cplx<R>* buf) {
+    using F4 = fft::FourStep<NZ, kThreads>;
+    const int nyn = ny + 2;
+    const size_t rsF = (size_t)nyn * nxh, rsS = (size_t)ny * nxh;
+    const int jn = t / ntx;
+    const int mx0 = (t - jn * ntx) * F4::W;
+    const int ncol = min(F4::W, nxh - mx0);
+    cplx<R>* Fy = F + fstride + (size_t)jn * nxh + mx0;
+    fft::column_fft<R, 1, NZ, kThreads, false>(Fy, rsF, Fy, rsF, ncol, tw, nullptr, buf);
+    if (jn >= 1 && jn <= ny) {
+        const cplx<R>* ph = S + (size_t)(jn - 1) * nxh + mx0;
+        cplx<R>* F0 = F + (size_t)jn * nxh + mx0;
+        fft::column_fft<R, 1, NZ, kThreads, false>(ph, rsS, F0, rsF, ncol, tw, nullptr, buf);
+        fft::column_fft<R, 1, NZ, kThreads, true>(ph, rsS, F0 + 2 * fstride, rsF, ncol, tw, sz, buf);
+    }
+}
+
+template <class R, int NZ>
+__global__ void __launch_bounds__(kThreads, 3) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
                                                     int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
                                                     const cplx<R>* __restrict__ tw_g) {
     using F4 = fft::FourStep<NZ, kThreads>;
@@ -365,19 +397,9 @@ __global__ void __launch_bounds__(kThreads) k_zinv4(const cplx<R>* __restrict__ 
         sz[i] = from_f64<R>(sinz[i]);
     }
     __syncthreads();
-    const int nyn = ny + 2;
-    const int jn = blockIdx.x;
-    const int mx0 = blockIdx.y * F4::W;
-    const int ncol = min(F4::W, nxh - mx0);
-    const size_t rsF = (size_t)nyn * nxh, rsS = (size_t)ny * nxh;
-    cplx<R>* Fy = F + fstride + (size_t)jn * nxh + mx0;
-    fft::column_fft<R, 1, NZ, kThreads, false>(Fy, rsF, Fy, rsF, ncol, tw, nullptr, buf);
-    if (jn >= 1 && jn <= ny) {
-        const cplx<R>* ph = S + (size_t)(jn - 1) * nxh + mx0;
-        cplx<R>* F0 = F + (size_t)jn * nxh + mx0;
-        fft::column_fft<R, 1, NZ, kThreads, false>(ph, rsS, F0, rsF, ncol, tw, nullptr, buf);
-        fft::column_fft<R, 1, NZ, kThreads, true>(ph, rsS, F0 + 2 * fstride, rsF, ncol, tw, sz, buf);
-    }
+    const int ntx = (nxh + F4::W - 1) / F4::W;
+    for (int t = blockIdx.x; t < (ny + 2) * ntx; t += gridDim.x)
+        zinv_tile<R, NZ>(S, F, ny, nxh, ntx, t, fstride, tw, sz, buf);
 }
 
 // ---------------------------------------------------------------- x inverse
@@ -393,7 +415,7 @@ __device__ __forceinline__ void store_pair(R* p, R a, R b) {
 }
 
 template <class R, int M>
-__global__ void __launch_bounds__(kThreads) k_xinv4(const cplx<R>* __restrict__ F, R* __restrict__ E,
+__global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict__ F, R* __restrict__ E,
                                                     double* __restrict__ phi, int ny, int nz, size_t fstride,
                                                     const double* __restrict__ sinx,
                                                     const cplx<R>* __restrict__ tw_g, int want_phi, R norm,
@@ -411,7 +433,9 @@ __global__ void __launch_bounds__(kThreads) k_xinv4(const cplx<R>* __restrict__ 
     const int nyn = ny + 2;
     const int r = threadIdx.x % TPC;
     const int l = threadIdx.x / TPC;
-    const int line = blockIdx.x * LPB + l;
+    const int ntb = (nz * nyn + LPB - 1) / LPB;
+    for (int tb = blockIdx.x; tb < ntb; tb += gridDim.x) {
+    const int line = tb * LPB + l;
     const bool live = l < LPB && line < nz * nyn;
     const int jn = live ? line % nyn : 0;
     const bool interior = jn >= 1 && jn <= ny;
@@ -476,6 +500,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv4(const cplx<R>* __restrict__ 
             ez[i] = (R)0;
         }
     }
+    }
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -490,6 +515,18 @@ size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>:
 template <class R, int NZ>
 size_t zinv_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>::BUF) + sizeof(R) * NZ; }
 
+// blocks of one resident wave of `kernel` (its occupancy is queried once per instantiation),
+// at most `tiles`
+template <class K>
+int wave_blocks(K kernel, size_t smem, int num_sms, int64_t tiles, int* cache) {
+    if (*cache == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, smem) != cudaSuccess || b < 1) b = 1;
+        *cache = b;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)*cache * num_sms));
+}
+
 template <class R, int M>
 void launch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
     constexpr int LPB = fft::FourStep<M, kThreads>::W;
@@ -502,21 +539,27 @@ void launch_xinv(tribo_ctx* c, void* E, double* phi) {
     constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->nz * (c->ny + 2);
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
-    k_xinv4<R, M><<<(nlines + LPB - 1) / LPB, kThreads, xinv_smem<R, M>(), c->stream>>>(
+    static int occ = 0;
+    const int g = wave_blocks(k_xinv4<R, M>, xinv_smem<R, M>(), c->num_sms, (nlines + LPB - 1) / LPB, &occ);
+    k_xinv4<R, M><<<g, kThreads, xinv_smem<R, M>(), c->stream>>>(
         (const cplx<R>*)c->F, (R*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
         phi != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)), (size_t)c->nz * (c->ny + 2) * c->nx);
 }
 template <class R, int NZ>
 void launch_zfwd(tribo_ctx* c) {
     constexpr int W = fft::FourStep<NZ, kThreads>::W;
-    dim3 grid(c->ny, (c->nxh + W - 1) / W);
+    static int occ = 0;
+    const int grid = wave_blocks(k_zfwd4<R, NZ>, zfwd_smem<R, NZ>(), c->num_sms,
+                                 (int64_t)c->ny * ((c->nxh + W - 1) / W), &occ);
     k_zfwd4<R, NZ><<<grid, kThreads, zfwd_smem<R, NZ>(), c->stream>>>((cplx<R>*)c->S, c->ny, c->nxh,
                                                                       (const cplx<R>*)c->d_twz);
 }
 template <class R, int NZ>
 void launch_zinv(tribo_ctx* c) {
     constexpr int W = fft::FourStep<NZ, kThreads>::W;
-    dim3 grid(c->ny + 2, (c->nxh + W - 1) / W);
+    static int occ = 0;
+    const int grid = wave_blocks(k_zinv4<R, NZ>, zinv_smem<R, NZ>(), c->num_sms,
+                                 (int64_t)(c->ny + 2) * ((c->nxh + W - 1) / W), &occ);
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
     k_zinv4<R, NZ><<<grid, kThreads, zinv_smem<R, NZ>(), c->stream>>>(
         (const cplx<R>*)c->S, (cplx<R>*)c->F, c->ny, c->nxh, fstride, c->d_sinz, (const cplx<R>*)c->d_twz);
