@@ -292,7 +292,7 @@ int64_t      tribo_launch_count(const tribo_ctx* ctx);
  * for phases 0..nphases-1, the summed device time [ms] and the launch count
  * since the last enable (ms, counts: host arrays of nphases entries).
  * tribo_phase_name gives the phase's kernel name (NULL past the last). */
-#define TRIBO_NPHASES 13
+#define TRIBO_NPHASES 12
 tribo_status tribo_timing_enable(tribo_ctx* ctx, int32_t on);
 tribo_status tribo_timing_read(tribo_ctx* ctx, double* ms, int64_t* counts, int32_t nphases);
 const char*  tribo_phase_name(int32_t phase);

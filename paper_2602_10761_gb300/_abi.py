@@ -25,7 +25,7 @@ TRIBO_DRAG_SCHILLER_NAUMANN = 1
 TRIBO_DRAG_OFF = 2
 TRIBO_IMPACT_SPEED = 0
 TRIBO_IMPACT_NORMAL = 1
-TRIBO_NPHASES = 13
+TRIBO_NPHASES = 12
 
 
 class tribo_grid(C.Structure):

@@ -90,15 +90,14 @@ struct FourStep {
     static constexpr int BUF = W * CS;                      // complex elements of the transpose buffer
 };
 
-// Transform W columns: column `col` of the block starts at src + col and its
-// element n sits n * rs_src further; output element n of column col is handed
-// to store(col, n, value).  MUL: multiply the input element n by -i mul[n]
-// first (spectral derivative).  All threads of the block call this; it
-// synchronises twice.
-template <class R, int SIGN, int N, int NT, bool MUL, class Store>
-__device__ __forceinline__ void column_fft_to(const cplx<R>* src, size_t rs_src, int ncol,
-                                              const cplx<R>* __restrict__ tw, const R* __restrict__ mul,
-                                              cplx<R>* buf, Store store) {
+// Transform W columns: column `col` of the block starts at src + col (dst +
+// col) and its element n sits n * rs_src (rs_dst) further.  MUL: multiply the
+// input element n by -i mul[n] first (spectral derivative).  All threads of
+// the block call this; it synchronises twice.
+template <class R, int SIGN, int N, int NT, bool MUL>
+__device__ __forceinline__ void column_fft(const cplx<R>* src, size_t rs_src, cplx<R>* dst, size_t rs_dst,
+                                           int ncol, const cplx<R>* __restrict__ tw, const R* __restrict__ mul,
+                                           cplx<R>* buf) {
     using F = FourStep<N, NT>;
     constexpr int N1 = F::N1, N2 = F::N2;
     const int col = threadIdx.x % F::W;
@@ -134,19 +133,9 @@ __device__ __forceinline__ void column_fft_to(const cplx<R>* src, size_t rs_src,
         for (int n2 = 0; n2 < N2; ++n2) z[n2] = b[n2 * (N1 + 1)];
         reg_dft<R, SIGN, N2, N1>(z, tw);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) store(col, r + N1 * k2, z[k2]);
+        for (int k2 = 0; k2 < N2; ++k2) dst[col + (size_t)(r + N1 * k2) * rs_dst] = z[k2];
     }
     __syncthreads();
-}
-
-// column_fft_to writing element n of column col at dst + col + n * rs_dst
-template <class R, int SIGN, int N, int NT, bool MUL>
-__device__ __forceinline__ void column_fft(const cplx<R>* src, size_t rs_src, cplx<R>* dst, size_t rs_dst,
-                                           int ncol, const cplx<R>* __restrict__ tw, const R* __restrict__ mul,
-                                           cplx<R>* buf) {
-    column_fft_to<R, SIGN, N, NT, MUL>(src, rs_src, ncol, tw, mul, buf, [=](int col, int n, const cplx<R>& v) {
-        dst[col + (size_t)n * rs_dst] = v;
-    });
 }
 
 }  // namespace fft

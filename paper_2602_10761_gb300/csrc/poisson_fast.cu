@@ -23,7 +23,6 @@
 //    element passes through shared memory once, in one transpose.
 // Passes: xfwd (zeroes the charge buffer), zfwd, ysolve, zinv, xinv.
 #include <algorithm>
-#include <cooperative_groups.h>
 #include <cmath>
 #include <vector>
 
@@ -504,183 +503,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
     }
 }
 
-// ---------------------------------------------------------------- fused inverse z + x
-// Both inverse transforms of one node plane jn by a cluster of kZX CTAs,
-// exchanging through distributed shared memory instead of global memory:
-//  z stage  CTA c takes the m_x columns [c CPC, (c+1) CPC): the inverse z
-//           transforms of the E_y spectrum and, on interior planes, of
-//           phi-hat (plain, for E_x) and of -i sin(2 pi m_z / nz)/dz phi-hat
-//           (E_z), as in k_zinv4; element z of each result goes straight into
-//           the receive buffer of the CTA that owns row z (rows [c RPC,
-//           (c+1) RPC) belong to CTA c);
-//  barrier  one cluster barrier (release/acquire) publishes the exchange;
-//  x stage  each CTA does the real inverse x transforms of its rows, as
-//           k_xinv4 (E_x multiplier -i sin(2 pi m / nx)/dx), and stores the
-//           E rows; wall planes carry E_x = E_z = 0.
-// The intermediate fields never reach global memory: per plane the solve
-// reads the two spectra and writes E once.
-constexpr int kZX = 8;
-
-template <int NZ, int M>
-struct ZXShape {
-    static constexpr int NX = 2 * M, NXH = M + 1;
-    static constexpr int RPC = NZ / kZX;                     // z rows per CTA
-    static constexpr int CPC = (NXH + kZX - 1) / kZX;        // m_x columns per CTA
-    static constexpr int BUFZ = fft::FourStep<NZ, kThreads>::BUF;
-    static constexpr int BUFX = fft::FourStep<M, kThreads>::BUF;
-    static constexpr int BUF = BUFZ > BUFX ? BUFZ : BUFX;
-    static constexpr size_t RECV = 3 * (size_t)RPC * NXH;    // complex elements, fields x rows x m_x
-    static constexpr size_t SMEM = sizeof(cplx<float>) * (NZ + NX + BUF + RECV) + sizeof(float) * (NZ + M + 1);
-};
-
-template <int NZ, int M>
-__global__ void __cluster_dims__(kZX, 1, 1) __launch_bounds__(kThreads, 1)
-    k_zxinv(const cplx<float>* __restrict__ S, const cplx<float>* __restrict__ Fy, float* __restrict__ E, int ny,
-            const double* __restrict__ sinz_g, const double* __restrict__ sinx_g,
-            const cplx<float>* __restrict__ twz_g, const cplx<float>* __restrict__ twx_g, float norm, size_t nodes) {
-    using Z = ZXShape<NZ, M>;
-    using FX = fft::FourStep<M, kThreads>;
-    constexpr int NX = Z::NX, NXH = Z::NXH, RPC = Z::RPC, CPC = Z::CPC;
-    constexpr int N1 = FX::N1, N2 = FX::N2, TPC = FX::TPC, LPB = FX::W, CS = FX::CS;
-    constexpr int WZ = fft::FourStep<NZ, kThreads>::W;
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
-    const int jn = blockIdx.x / kZX;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<float>* twz = reinterpret_cast<cplx<float>*>(smem_raw);
-    cplx<float>* twx = twz + NZ;
-    cplx<float>* buf = twx + NX;
-    cplx<float>* recv = buf + Z::BUF;
-    float* sz = reinterpret_cast<float*>(recv + Z::RECV);
-    float* sx = sz + NZ;
-    for (int i = threadIdx.x; i < NZ; i += kThreads) {
-        twz[i] = twz_g[i];
-        sz[i] = (float)sinz_g[i];
-    }
-    for (int i = threadIdx.x; i < NX; i += kThreads) twx[i] = twx_g[i];
-    for (int i = threadIdx.x; i <= M; i += kThreads) sx[i] = (float)sinx_g[i];
-    __syncthreads();
-    const int nyn = ny + 2;
-    const bool interior = jn >= 1 && jn <= ny;
-    // ---- z stage
-    const int kx0 = rank * CPC;
-    const int ncols = max(0, min(CPC, NXH - kx0));
-    for (int c0 = 0; c0 < ncols; c0 += WZ) {
-        const int nc = min(WZ, ncols - c0);
-        auto to_owner = [&](int f) {
-            return [=, &cluster](int col, int n, const cplx<float>& v) {
-                cplx<float>* local = recv + ((size_t)f * RPC + n % RPC) * NXH + kx0 + c0 + col;
-                *cluster.map_shared_rank(local, (unsigned)(n / RPC)) = v;
-            };
-        };
-        fft::column_fft_to<float, 1, NZ, kThreads, false>(Fy + (size_t)jn * NXH + kx0 + c0, (size_t)nyn * NXH, nc,
-                                                          twz, nullptr, buf, to_owner(1));
-        if (interior) {
-            const cplx<float>* ph = S + (size_t)(jn - 1) * NXH + kx0 + c0;
-            fft::column_fft_to<float, 1, NZ, kThreads, false>(ph, (size_t)ny * NXH, nc, twz, nullptr, buf,
-                                                              to_owner(0));
-            fft::column_fft_to<float, 1, NZ, kThreads, true>(ph, (size_t)ny * NXH, nc, twz, sz, buf, to_owner(2));
-        }
-    }
-    cluster.sync();
-    // ---- x stage: lines (field, row) of this CTA
-    const int r = threadIdx.x % TPC;
-    const int l = threadIdx.x / TPC;
-    const int nlines = (interior ? 3 : 1) * RPC;
-    for (int p0 = 0; p0 < nlines; p0 += LPB) {
-        const int li = p0 + l;
-        const bool live = l < LPB && li < nlines;
-        const int f = interior ? li / RPC : 1;
-        const int row = li % RPC;
-        const cplx<float>* X = recv + ((size_t)f * RPC + row) * NXH;
-        if (live && r < N2) {
-            cplx<float> y[N1];
-#pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) {
-                const int m = N2 * n1 + r;
-                cplx<float> xa = X[m], xb = X[M - m];
-                if (f == 0) {
-                    xa = cplx<float>{sx[m] * xa.im, -sx[m] * xa.re};
-                    xb = cplx<float>{sx[M - m] * xb.im, -sx[M - m] * xb.re};
-                }
-                const cplx<float> cb = conj(xb);
-                const cplx<float> sum = xa + cb;
-                const cplx<float> t = conj(twx[m]) * (xa - cb);
-                y[n1] = cplx<float>{sum.re - t.im, sum.im + t.re};
-            }
-            fft::reg_dft<float, 1, N1, 2 * N2>(y, twx);
-#pragma unroll
-            for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * conj(twx[2 * r * k1]);
-            cplx<float>* b = buf + l * CS + r * (N1 + 1);
-#pragma unroll
-            for (int k1 = 0; k1 < N1; ++k1) b[k1] = y[k1];
-        }
-        __syncthreads();
-        if (live && r < N1) {
-            cplx<float> z[N2];
-            const cplx<float>* b = buf + l * CS + r;
-#pragma unroll
-            for (int n2 = 0; n2 < N2; ++n2) z[n2] = b[n2 * (N1 + 1)];
-            fft::reg_dft<float, 1, N2, 2 * N1>(z, twx);
-            const int zrow = rank * RPC + row;
-            float* out = E + (size_t)f * nodes + ((size_t)zrow * nyn + jn) * NX;
-#pragma unroll
-            for (int k2 = 0; k2 < N2; ++k2) {
-                const int k = r + N1 * k2;
-                store_pair<float>(out + 2 * k, z[k2].re * norm, z[k2].im * norm);
-            }
-        }
-        __syncthreads();
-    }
-    if (!interior) {
-        for (int row = 0; row < RPC; ++row) {
-            const size_t off = ((size_t)(rank * RPC + row) * nyn + jn) * NX;
-            for (int i = threadIdx.x; i < NX; i += kThreads) {
-                E[off + i] = 0.f;
-                E[2 * nodes + off + i] = 0.f;
-            }
-        }
-    }
-}
-
-template <int NZ, int M>
-bool launch_zxinv_sized(tribo_ctx* c, void* E) {
-    using Z = ZXShape<NZ, M>;
-    static int ok = -1;          // the cluster shape fits this device (checked once)
-    if (ok < 0) {
-        ok = 0;
-        if (Z::SMEM <= (size_t)227 * 1024 &&
-            cudaFuncSetAttribute(k_zxinv<NZ, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Z::SMEM) ==
-                cudaSuccess) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(kZX * (c->ny + 2));
-            cfg.blockDim = dim3(kThreads);
-            cfg.dynamicSmemBytes = Z::SMEM;
-            int clusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&clusters, k_zxinv<NZ, M>, &cfg) == cudaSuccess && clusters > 0) ok = 1;
-        }
-        (void)cudaGetLastError();
-    }
-    if (!ok) return false;
-    const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
-    k_zxinv<NZ, M><<<kZX * (c->ny + 2), kThreads, Z::SMEM, c->stream>>>(
-        (const cplx<float>*)c->S, (const cplx<float>*)c->F + fstride, (float*)E, c->ny, c->d_sinz, c->d_sinx,
-        (const cplx<float>*)c->d_twz, (const cplx<float>*)c->d_twx, (float)(1.0 / ((double)c->nx * (double)c->nz)),
-        (size_t)c->nz * (c->ny + 2) * c->nx);
-    return true;
-}
-
-// the fused inverse for the sizes it covers (FP32, nz a multiple of kZX, shared memory permitting)
-bool launch_zxinv(tribo_ctx* c, void* E) {
-    if (c->nz == 256 && c->nx == 384) return launch_zxinv_sized<256, 192>(c, E);
-    if (c->nz == 128 && c->nx == 128) return launch_zxinv_sized<128, 64>(c, E);
-    if (c->nz == 64 && c->nx == 64) return launch_zxinv_sized<64, 32>(c, E);
-    if (c->nz == 16 && c->nx == 32) return launch_zxinv_sized<16, 16>(c, E);
-    if (c->nz == 16 && c->nx == 24) return launch_zxinv_sized<16, 12>(c, E);
-    return false;
-}
-
 // ---------------------------------------------------------------- dispatch
 template <class R, int M>
 size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + fft::FourStep<M, kThreads>::BUF); }
@@ -867,14 +689,6 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
             (const float4*)c->d_yec, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
-    if constexpr (sizeof(R) == 4) {
-        // one fused pass when the shape allows it (the E lattice only; phi needs the split passes)
-        phase_begin(c, PH_INV_ZX);
-        if (!phi && launch_zxinv(c, E)) {
-            TRIBO_LAUNCHED(c);
-            return TRIBO_OK;
-        }
-    }
     phase_begin(c, PH_INV_Z);
     dispatch_zinv<R>(c);
     TRIBO_LAUNCHED(c);

@@ -632,7 +632,7 @@ namespace tribo {
 
 static const char* kPhaseNames[TRIBO_NPHASES] = {
     "particle_step", "deposit", "poisson_fwd_x", "poisson_fwd_z", "poisson_solve_y",
-    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux", "fluid_modes", "adjoint", "poisson_inv_zx"};
+    "poisson_inv_z", "poisson_inv_x", "sort", "misc", "aux", "fluid_modes", "adjoint"};
 
 static void flush_timing(tribo_ctx* c) {
     if (c->ev_used == 0) return;

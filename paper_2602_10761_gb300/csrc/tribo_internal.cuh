@@ -173,7 +173,7 @@ namespace tribo {
 
 // kernel phases for timing
 enum Phase { PH_STEP = 0, PH_DEPOSIT, PH_FWD_X, PH_FWD_Z, PH_SOLVE_Y, PH_INV_Z, PH_INV_X, PH_SORT, PH_MISC,
-             PH_AUX, PH_FIELD, PH_ADJOINT, PH_INV_ZX };
+             PH_AUX, PH_FIELD, PH_ADJOINT };
 void phase_begin(tribo_ctx* c, int phase);
 void phase_end(tribo_ctx* c);
 
