@@ -120,28 +120,39 @@ struct Stage {
     static size_t bytes(int64_t n, size_t rs) { return (size_t)n * (7 * rs + 2 * sizeof(double) + 3 * sizeof(uint32_t)) + 1024; }
 };
 
+// Host <-> device copies of a particle set on `stream`.  to_device: group 1 is
+// what the deposit needs (x, y, z, q), group 2 the rest, 3 both; the ids are
+// copied only when `with_id`.  Back to the host: every state array, the ids
+// when `with_id`.
 tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particles* src, cudaMemcpyKind kind,
-                            bool to_device) {
+                            bool to_device, int groups, bool with_id, cudaStream_t stream) {
     const size_t rs = real_size(c);
     const size_t n = (size_t)src->n;
     auto cp = [&](void* dev, void* host, size_t elem) -> tribo_status {
         if (!host) return TRIBO_OK;
-        if (to_device) TRIBO_CUDA(cudaMemcpyAsync(dev, host, elem * n, kind, c->stream));
-        else TRIBO_CUDA(cudaMemcpyAsync(host, dev, elem * n, kind, c->stream));
+        if (to_device) TRIBO_CUDA(cudaMemcpyAsync(dev, host, elem * n, kind, stream));
+        else TRIBO_CUDA(cudaMemcpyAsync(host, dev, elem * n, kind, stream));
         return TRIBO_OK;
     };
     tribo_status st;
+    if (to_device) {
+        if ((groups & 1) && ((st = cp(dst.x, src->x, rs)) || (st = cp(dst.y, src->y, rs)) ||
+                             (st = cp(dst.z, src->z, rs)) || (st = cp(dst.q, src->q, sizeof(double)))))
+            return st;
+        if ((groups & 2) &&
+            ((st = cp(dst.vx, src->vx, rs)) || (st = cp(dst.vy, src->vy, rs)) || (st = cp(dst.vz, src->vz, rs)) ||
+             (st = cp(dst.d, src->d, rs)) || (st = cp(dst.q_wall, src->q_wall, sizeof(double))) ||
+             (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) ||
+             (with_id && (st = cp(dst.id, src->id, sizeof(uint32_t))))))
+            return st;
+        return TRIBO_OK;
+    }
     if ((st = cp(dst.x, src->x, rs)) || (st = cp(dst.y, src->y, rs)) || (st = cp(dst.z, src->z, rs)) ||
         (st = cp(dst.vx, src->vx, rs)) || (st = cp(dst.vy, src->vy, rs)) || (st = cp(dst.vz, src->vz, rs)) ||
         (st = cp(dst.q, src->q, sizeof(double))) || (st = cp(dst.q_wall, src->q_wall, sizeof(double))) ||
-        (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))))
+        (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) ||
+        (with_id && (st = cp(dst.id, src->id, sizeof(uint32_t)))) || (st = cp(dst.cell, src->cell, sizeof(uint32_t))))
         return st;
-    if (to_device) {
-        if ((st = cp(dst.d, src->d, rs)) || (st = cp(dst.id, src->id, sizeof(uint32_t)))) return st;
-    } else {
-        if ((st = cp(dst.id, src->id, sizeof(uint32_t))) || (st = cp(dst.cell, src->cell, sizeof(uint32_t))))
-            return st;
-    }
     return TRIBO_OK;
 }
 
@@ -230,6 +241,8 @@ void free_ctx(tribo_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->copy_done) cudaEventDestroy(c->copy_done);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaSetDevice(prev);
     delete c;
 }
@@ -447,19 +460,42 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         c->n_samples += nsteps;
         return TRIBO_OK;
     }
-    PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
-    if (p->on_host) {
-        if (!p->id) v.id = nullptr;
-        if (!p->cell) v.cell = nullptr;
-        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true))) return st;
-    }
-    const bool electro = c->P.electrostatics != 0;
-    const bool want_cell = v.cell != nullptr;
     if (c->ssm_on && !p->id) {
         set_last_error("the SSM needs the particles' id arrays (its random-number counters)");
         return TRIBO_ERR_ARG;
     }
     const int S = c->P.sort_every;
+    // does a sort fall into this call (the first step s with (steps_done + s) % S == 0)?
+    const bool sorts = S > 0 && (int64_t)((S - c->steps_done % S) % S) < nsteps;
+    PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
+    bool rest_pending = false;       // host call: the arrays the solve does not need are still in flight
+    if (p->on_host) {
+        // the ids travel only when a sort permutes them or the SSM reads them
+        const bool ids = p->id && (sorts || c->ssm_on);
+        if (!ids) v.id = nullptr;
+        if (!p->cell) v.cell = nullptr;
+        if (!c->copy_stream) {
+            TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+            TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+        }
+        // what the deposit needs first, on the compute stream; the rest beside it on the copy
+        // stream (after the work already queued on the compute stream), awaited before its first use
+        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 1, ids, c->stream))) return st;
+        TRIBO_CUDA(cudaEventRecord(c->copy_done, c->stream));
+        TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_done, 0));
+        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) return st;
+        TRIBO_CUDA(cudaEventRecord(c->copy_done, c->copy_stream));
+        rest_pending = true;
+    }
+    auto await_rest = [&]() -> tribo_status {
+        if (rest_pending) {
+            TRIBO_CUDA(cudaStreamWaitEvent(c->stream, c->copy_done, 0));
+            rest_pending = false;
+        }
+        return TRIBO_OK;
+    };
+    const bool electro = c->P.electrostatics != 0;
+    const bool want_cell = v.cell != nullptr;
     if (S > 0 && p->n > c->max_particles) {
         set_last_error("sorting needs max_particles >= n");
         return TRIBO_ERR_CAPACITY;
@@ -502,7 +538,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     for (int s = 0; s < nsteps; ++s) {
         const bool last = s == nsteps - 1;
         if (S > 0 && c->steps_done % S == 0) {
-            if ((st = particles_sort(c, cur, other))) return st;
+            if ((st = await_rest()) || (st = particles_sort(c, cur, other))) return st;
             std::swap(cur, other);
         }
         if (c->n_modes) {
@@ -511,6 +547,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         if (electro) {
             if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
         }
+        if ((st = await_rest())) return st;
         if (near) {
             if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
                 (st = particles_coulomb(c, cur, c->nf_members, c->nf_acc)))
@@ -530,7 +567,9 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     }
     c->n_samples += nsteps;
     if (p->on_host) {
-        if ((st = copy_particles(c, v, p, cudaMemcpyDeviceToHost, false))) return st;
+        // ids come back only if a sort permuted them
+        if ((st = copy_particles(c, v, p, cudaMemcpyDeviceToHost, false, 3, sorts && v.id != nullptr, c->stream)))
+            return st;
         return sync_and_check(c);
     }
     return TRIBO_OK;

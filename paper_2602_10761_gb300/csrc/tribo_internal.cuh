@@ -76,6 +76,8 @@ struct tribo_ctx {
     int device = 0;
     int num_sms = 152;                 // streaming multiprocessors of the device
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // host-pointer calls: the particle arrays the solve does not need
+    cudaEvent_t copy_done = nullptr;     // ... recorded when they have landed
     int prec = TRIBO_FP64;
     tribo_params P{};
     int nx = 0, ny = 0, nz = 0, nxh = 0;

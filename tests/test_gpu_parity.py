@@ -180,6 +180,42 @@ def test_host_pointer_call_matches_device_call():
     assert sa["n_impacts"] == sb["n_impacts"]
 
 
+@pytest.mark.parametrize("ssm", [False, True])
+def test_host_pointer_single_steps_match_device_call(ssm):
+    """Seven one-step host-pointer calls (the arrays the solve does not need
+    copied beside it, the ids only in the calls that sort or when the SSM reads
+    them) against one seven-step device call: the same FP64 oracle path, so
+    the states agree to FP32 rounding (the call-start deposit sums in another
+    order) and the impact counts and ids exactly."""
+    c, faces, lat, parts = problem(32, 24, 16, n=2000, q_scale=1e-13, vy_scale=0.4, near_wall=0.2, seed=23)
+    lat_r, parts_r = round_inputs(lat, parts, np.float32)
+    params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1e3, sort_every=3)
+    out = []
+    for host in (False, True):
+        ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat_r.astype(np.float32)).cuda(),
+                       max_particles=2000)
+        if ssm:
+            ch.set_ssm(T.SSMParams(seed=3))
+        P = T.Particles.from_numpy(parts_r, T.TRIBO_MIXED, device=None if host else "cuda")
+        if host:
+            for _ in range(7):
+                ch.step(P, c.dt, 1)
+        else:
+            ch.step(P, c.dt, 7)
+        ch.sync()
+        o = P.to_numpy()
+        ch.close()
+        order = np.argsort(o["id"])
+        out.append({k: np.asarray(v)[order] for k, v in o.items()})
+    a, b = out
+    assert np.array_equal(np.sort(b["id"]), np.arange(2000))
+    for k in ("x", "y", "z", "vx", "vy", "vz", "q", "q_wall"):
+        s = max(np.abs(a[k]).max(), 1e-30)
+        assert np.abs(a[k].astype(np.float64) - b[k].astype(np.float64)).max() <= 1e-5 * s, k
+    assert np.array_equal(a["n_imp"], b["n_imp"])
+    assert a["n_imp"].sum() > 50
+
+
 @pytest.mark.parametrize("n", [0, 1, 33, 257])
 def test_small_and_ragged_ensembles(n):
     c, faces, lat, parts = problem(12, 8, 6, n=n, q_scale=1e-12, vy_scale=0.3, near_wall=0.3, seed=n + 1)
