@@ -551,14 +551,12 @@ def main():
     ms_per_step = ms / args.steps
     value = aggregate_rate(c.n_particles, args.steps, ms * 1e-3, world)
 
-    # end to end through the public call with HOST buffers (pinned), copies inside
+    # end to end through the public call with HOST buffers (pinned), copies inside: the same
+    # simulation continued, its state (cell-ordered by the last sort) held on the host
     host = {}
-    for k in ("x", "y", "z", "vx", "vy", "vz", "d"):
-        host[k] = torch.from_numpy(np.asarray(getattr(P, k), np.float32)).pin_memory().numpy()
-    host["q"] = torch.from_numpy(np.asarray(P.q, np.float64)).pin_memory().numpy()
-    host["q_wall"] = torch.zeros(c.n_particles, dtype=torch.float64).pin_memory().numpy()
-    host["n_imp"] = torch.zeros(c.n_particles, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
-    host["id"] = torch.arange(c.n_particles, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+    for k in ("x", "y", "z", "vx", "vy", "vz", "d", "q", "q_wall", "n_imp", "id"):
+        v = getattr(Pd, k).cpu().pin_memory().numpy()
+        host[k] = v.view(np.uint32) if k in ("n_imp", "id") else v
     Ph = T.Particles(**host)
     # the ids move only in the calls that sort (the step count before the call a multiple of
     # sort_every); the average over the timed calls is reported
