@@ -156,6 +156,42 @@ tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particle
     return TRIBO_OK;
 }
 
+// particles [a0, a0 + n) of a set
+PView sub_view(const tribo_ctx* c, const PView& v, int64_t a0, int64_t n) {
+    const size_t rs = real_size(c);
+    auto at = [&](void* base, size_t elem) -> void* { return base ? (char*)base + (size_t)a0 * elem : nullptr; };
+    PView s = v;
+    s.n = n;
+    s.x = at(v.x, rs); s.y = at(v.y, rs); s.z = at(v.z, rs);
+    s.vx = at(v.vx, rs); s.vy = at(v.vy, rs); s.vz = at(v.vz, rs); s.d = at(v.d, rs);
+    s.q = (double*)at(v.q, sizeof(double));
+    s.q_wall = (double*)at(v.q_wall, sizeof(double));
+    s.n_imp = (uint32_t*)at(v.n_imp, sizeof(uint32_t));
+    s.id = (uint32_t*)at(v.id, sizeof(uint32_t));
+    s.cell = (uint32_t*)at(v.cell, sizeof(uint32_t));
+    return s;
+}
+
+// the state arrays of device particles `part` back into the caller's host arrays at a0
+tribo_status copy_back_range(tribo_ctx* c, const PView& part, const tribo_particles* host, int64_t a0, bool with_id,
+                             cudaStream_t stream) {
+    const size_t rs = real_size(c);
+    const size_t n = (size_t)part.n;
+    auto cp = [&](void* h, const void* d, size_t elem) -> tribo_status {
+        if (!h || !d) return TRIBO_OK;
+        TRIBO_CUDA(cudaMemcpyAsync((char*)h + (size_t)a0 * elem, d, elem * n, cudaMemcpyDeviceToHost, stream));
+        return TRIBO_OK;
+    };
+    tribo_status st;
+    if ((st = cp(host->x, part.x, rs)) || (st = cp(host->y, part.y, rs)) || (st = cp(host->z, part.z, rs)) ||
+        (st = cp(host->vx, part.vx, rs)) || (st = cp(host->vy, part.vy, rs)) || (st = cp(host->vz, part.vz, rs)) ||
+        (st = cp(host->q, part.q, sizeof(double))) || (st = cp(host->q_wall, part.q_wall, sizeof(double))) ||
+        (st = cp(host->n_imp, part.n_imp, sizeof(uint32_t))) ||
+        (with_id && (st = cp(host->id, part.id, sizeof(uint32_t)))) || (st = cp(host->cell, part.cell, sizeof(uint32_t))))
+        return st;
+    return TRIBO_OK;
+}
+
 tribo_status check_particles(const tribo_ctx* c, const tribo_particles* p) {
     if (!p) { set_last_error("particles is NULL"); return TRIBO_ERR_ARG; }
     if (p->n < 0) { set_last_error("negative particle count"); return TRIBO_ERR_ARG; }
@@ -242,6 +278,8 @@ void free_ctx(tribo_ctx* c) {
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->copy_done) cudaEventDestroy(c->copy_done);
+    for (cudaEvent_t e : c->chunk_done)
+        if (e) cudaEventDestroy(e);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaSetDevice(prev);
     delete c;
@@ -477,6 +515,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         if (!c->copy_stream) {
             TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
             TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+            for (cudaEvent_t& e : c->chunk_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
         // what the deposit needs first, on the compute stream; the rest beside it on the copy
         // stream (after the work already queued on the compute stream), awaited before its first use
@@ -487,6 +526,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         TRIBO_CUDA(cudaEventRecord(c->copy_done, c->copy_stream));
         rest_pending = true;
     }
+    bool sent_back = false;          // host call: the results already went back chunk by chunk
     auto await_rest = [&]() -> tribo_status {
         if (rest_pending) {
             TRIBO_CUDA(cudaStreamWaitEvent(c->stream, c->copy_done, 0));
@@ -553,7 +593,24 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                 (st = particles_coulomb(c, cur, c->nf_members, c->nf_acc)))
                 return st;
         }
-        if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last, io))) return st;
+        // host call, last step, no pair interactions (they need every particle): the step in
+        // chunks, each chunk's arrays sent back on the copy stream while the next one runs
+        const bool chunked = p->on_host && last && !near && !collide;
+        if (chunked) {
+            constexpr int K = 4;
+            for (int ci = 0; ci < K; ++ci) {
+                const int64_t a0 = cur.n * ci / K, a1 = cur.n * (ci + 1) / K;
+                if (a1 <= a0) continue;
+                const PView part = sub_view(c, cur, a0, a1 - a0);
+                if ((st = particles_step(c, part, dt, false, want_cell, io))) return st;
+                TRIBO_CUDA(cudaEventRecord(c->chunk_done[ci], c->stream));
+                TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->chunk_done[ci], 0));
+                if ((st = copy_back_range(c, part, p, a0, sorts && part.id != nullptr, c->copy_stream))) return st;
+            }
+            sent_back = true;
+        } else if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last, io))) {
+            return st;
+        }
         if (collide) {
             if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
                 (st = particles_collide(c, cur, c->nf_members, c->pp_partner)))
@@ -562,10 +619,15 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         c->steps_done++;
         c->time += dt;
     }
+    c->n_samples += nsteps;
+    if (sent_back) {
+        // the arrays went back from the set that holds them, chunk by chunk
+        TRIBO_CUDA(cudaStreamSynchronize(c->copy_stream));
+        return sync_and_check(c);
+    }
     if (cur.x != home.x) {
         if ((st = copy_view(c, home, cur))) return st;
     }
-    c->n_samples += nsteps;
     if (p->on_host) {
         // ids come back only if a sort permuted them
         if ((st = copy_particles(c, v, p, cudaMemcpyDeviceToHost, false, 3, sorts && v.id != nullptr, c->stream)))

@@ -78,6 +78,7 @@ struct tribo_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t copy_stream = nullptr;  // host-pointer calls: the particle arrays the solve does not need
     cudaEvent_t copy_done = nullptr;     // ... recorded when they have landed
+    cudaEvent_t chunk_done[4] = {};      // host calls: chunks of the last step, sent back as they finish
     int prec = TRIBO_FP64;
     tribo_params P{};
     int nx = 0, ny = 0, nz = 0, nxh = 0;
