@@ -43,10 +43,12 @@ __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks) k_step(StepArgs<
     }
     unsigned int err = 0;
     // one resident wave of blocks walks the particles in windows of gridDim.x * blockDim.x: the
-    // particles are ordered by cell, so the lattice the wave gathers from stays small in L2
+    // particles are ordered by cell, so the lattice the wave gathers from stays small in L2.  The
+    // walk runs from the last cell plane down: the field pass wrote those planes last (they are
+    // still in L2), and the charge sums deposited last are the ones the next solve reads first
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < p.n; n += stride)
-        step_one<R>(a, p, n, write_cell, sh_hist, use_hist, err);
+    for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < p.n; m += stride)
+        step_one<R>(a, p, p.n - 1 - m, write_cell, sh_hist, use_hist, err);
     if (err) atomicOr(&a.acc->err, err);
     if (use_hist) {
         __syncthreads();
