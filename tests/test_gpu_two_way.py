@@ -196,3 +196,24 @@ def test_momentum_source_rejects_misaligned_buffer():
     with pytest.raises(T.TriboError):
         T.tribo_set_momentum_source(ch.ctx, buf[1:])
     ch.close()
+
+
+def test_momentum_source_of_a_host_pointer_call():
+    """A host-pointer call (its last step in chunks, each sent back while the next
+    runs) gives the momentum source of the same call on device arrays, up to the
+    order of the float atomic sums."""
+    c, faces, lat, parts = _case(np.float32, seed=66)
+    out = []
+    for host in (False, True):
+        params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=2e3, sort_every=2)
+        ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params,
+                       torch.from_numpy(lat.astype(np.float32)).cuda(), max_particles=len(parts["x"]))
+        F = ch.momentum_source()
+        P = T.Particles.from_numpy(parts, T.TRIBO_MIXED, device=None if host else "cuda")
+        ch.step(P, c.dt, 3)
+        ch.sync()
+        out.append(F.cpu().numpy().astype(np.float64))
+        ch.close()
+    a, b = out
+    assert np.any(a != 0)
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
