@@ -7,8 +7,9 @@
 //   fork   one branch per channel (its own stream): the cell sort when due,
 //          then the channel's Poisson solve and field (Sec. 2.2);
 //   join   one persistent particle kernel for ALL channels' particles:
-//          a fixed grid walks a global tile space (tile = a run of one
-//          channel's particles); each block loads its channel's step
+//          a fixed grid walks a global tile space in order, block b taking
+//          tiles b, b + G, ... (tile = a run of one channel's particles);
+//          each block loads its channel's step
 //          arguments into shared memory and runs the same per-particle step
 //          as the single-channel kernel (step_one), depositing the charge for
 //          the next step.
@@ -42,11 +43,13 @@ k_step_batch(const BatchChan<R>* __restrict__ chans, const int64_t* __restrict__
     __shared__ __align__(16) unsigned char raw[sizeof(BatchChan<R>)];
     BatchChan<R>& sc = *reinterpret_cast<BatchChan<R>*>(raw);
     extern __shared__ unsigned int sh_hist[];
-    const int64_t t0 = (int64_t)blockIdx.x * tiles_per_block;
-    const int64_t t1 = min(t0 + tiles_per_block, ntiles);
+    // the resident wave walks the tile space in order (block b takes tiles b, b + G, ...): the
+    // particles of a channel are cell-ordered, so the lattice the wave gathers from stays
+    // small in L2 (contiguous ranges per block spread the wave over every channel at once)
+    (void)tiles_per_block;
     int cur = -1;
     unsigned int err = 0;
-    for (int64_t t = t0; t < t1; ++t) {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         // channel of tile t: the last c with tstart[c] <= t
         int lo = 0, hi = nch - 1;
         while (lo < hi) {
