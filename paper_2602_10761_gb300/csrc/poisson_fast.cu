@@ -384,7 +384,7 @@ __device__ __noinline__ void zinv_tile(const cplx<R>* __restrict__ S, cplx<R>* _
 }
 
 template <class R, int NZ>
-__global__ void __launch_bounds__(kThreads, 3) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
+__global__ void __launch_bounds__(kThreads, 4) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
                                                     int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
                                                     const cplx<R>* __restrict__ tw_g) {
     using F4 = fft::FourStep<NZ, kThreads>;
