@@ -685,12 +685,10 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
         // at 249 registers: 264 us, at 384x256x256)
         constexpr int CH = 12;
         const int nch = (ny + CH - 1) / CH;
-        // the chunk checkpoints of a block (one float4 per chunk and thread) must fit in shared memory
-        int bt = 128;
-        auto shc_for = [&](int t) { return sizeof(float4) * ((size_t)nch * t + ny + 1) + sizeof(float2) * ny; };
-        if (shc_for(bt) > (size_t)c->smem_optin) bt = 64;
-        const size_t shc = shc_for(bt);
-        k_ysolve_chunk<CH><<<(nz * nxh + bt - 1) / bt, bt, shc, c->stream>>>(
+        // the chunk checkpoints of a block, one float4 per chunk and thread: at ny = 1024 (the
+        // largest grid) 196 KB, inside the opt-in shared memory per block
+        const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
+        k_ysolve_chunk<CH><<<(nz * nxh + 127) / 128, 128, shc, c->stream>>>(
             (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
             (const float4*)c->d_yec, ny, nz, nxh);
     }
@@ -790,7 +788,6 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_chunk<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    c->smem_optin = optin;
     return dispatch_attr<float>(nx, nz, optin);
 }
 
