@@ -505,37 +505,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     const int S = c->P.sort_every;
     // does a sort fall into this call (the first step s with (steps_done + s) % S == 0)?
     const bool sorts = S > 0 && (int64_t)((S - c->steps_done % S) % S) < nsteps;
-    PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
-    bool rest_pending = false;       // host call: the arrays the solve does not need are still in flight
-    if (p->on_host) {
-        // the ids travel only when a sort permutes them or the SSM reads them
-        const bool ids = p->id && (sorts || c->ssm_on);
-        if (!ids) v.id = nullptr;
-        if (!p->cell) v.cell = nullptr;
-        if (!c->copy_stream) {
-            TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-            TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
-            for (cudaEvent_t& e : c->chunk_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        }
-        // what the deposit needs first, on the compute stream; the rest beside it on the copy
-        // stream (after the work already queued on the compute stream), awaited before its first use
-        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 1, ids, c->stream))) return st;
-        TRIBO_CUDA(cudaEventRecord(c->copy_done, c->stream));
-        TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_done, 0));
-        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) return st;
-        TRIBO_CUDA(cudaEventRecord(c->copy_done, c->copy_stream));
-        rest_pending = true;
-    }
-    bool sent_back = false;          // host call: the results already went back chunk by chunk
-    auto await_rest = [&]() -> tribo_status {
-        if (rest_pending) {
-            TRIBO_CUDA(cudaStreamWaitEvent(c->stream, c->copy_done, 0));
-            rest_pending = false;
-        }
-        return TRIBO_OK;
-    };
     const bool electro = c->P.electrostatics != 0;
-    const bool want_cell = v.cell != nullptr;
     if (S > 0 && p->n > c->max_particles) {
         set_last_error("sorting needs max_particles >= n");
         return TRIBO_ERR_CAPACITY;
@@ -562,79 +532,126 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             TRIBO_CUDA(cudaMalloc((void**)&c->pp_partner, sizeof(uint32_t) * c->max_particles));
         }
     }
-    StepIO io;
-    if (near) io.acoul = c->nf_acc;
-    if (c->fs && c->P.drag_law != TRIBO_DRAG_OFF) {
-        io.fs = c->fs;
-        io.fs_coef = -1.0 / (c->P.rho * dt * nsteps);
-    }
-    PView home = v, cur = v, other = S > 0 ? set_view(c, c->alt, p->n) : v;
-    if (!v.id) other.id = nullptr;
-    if (!v.cell) other.cell = nullptr;
-    if (electro) {
-        TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
-        if ((st = particles_deposit(c, cur))) return st;
-    }
-    for (int s = 0; s < nsteps; ++s) {
-        const bool last = s == nsteps - 1;
-        if (S > 0 && c->steps_done % S == 0) {
-            if ((st = await_rest()) || (st = particles_sort(c, cur, other))) return st;
-            std::swap(cur, other);
-        }
-        if (c->n_modes) {
-            if ((st = modes_eval(c, c->time, c->u_lat))) return st;
-        }
-        if (electro) {
-            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
-        }
-        if ((st = await_rest())) return st;
-        if (near) {
-            if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
-                (st = particles_coulomb(c, cur, c->nf_members, c->nf_acc)))
-                return st;
-        }
-        // host call, last step, no pair interactions (they need every particle): the step in
-        // chunks, each chunk's arrays sent back on the copy stream while the next one runs
-        const bool chunked = p->on_host && last && !near && !collide;
-        if (chunked) {
-            constexpr int K = 4;
-            for (int ci = 0; ci < K; ++ci) {
-                const int64_t a0 = cur.n * ci / K, a1 = cur.n * (ci + 1) / K;
-                if (a1 <= a0) continue;
-                const PView part = sub_view(c, cur, a0, a1 - a0);
-                if ((st = particles_step(c, part, dt, false, want_cell, io))) return st;
-                TRIBO_CUDA(cudaEventRecord(c->chunk_done[ci], c->stream));
-                TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->chunk_done[ci], 0));
-                if ((st = copy_back_range(c, part, p, a0, sorts && part.id != nullptr, c->copy_stream))) return st;
-            }
-            sent_back = true;
-        } else if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last, io))) {
-            return st;
-        }
-        if (collide) {
-            if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
-                (st = particles_collide(c, cur, c->nf_members, c->pp_partner)))
-                return st;
-        }
-        c->steps_done++;
-        c->time += dt;
-    }
-    c->n_samples += nsteps;
-    if (sent_back) {
-        // the arrays went back from the set that holds them, chunk by chunk
-        TRIBO_CUDA(cudaStreamSynchronize(c->copy_stream));
-        return sync_and_check(c);
-    }
-    if (cur.x != home.x) {
-        if ((st = copy_view(c, home, cur))) return st;
-    }
+    PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
+    bool rest_pending = false;       // host call: the arrays the solve does not need are still in flight
     if (p->on_host) {
-        // ids come back only if a sort permuted them
-        if ((st = copy_particles(c, v, p, cudaMemcpyDeviceToHost, false, 3, sorts && v.id != nullptr, c->stream)))
+        // the ids travel only when a sort permutes them or the SSM reads them
+        const bool ids = p->id && (sorts || c->ssm_on);
+        if (!ids) v.id = nullptr;
+        if (!p->cell) v.cell = nullptr;
+        if (!c->copy_stream) {
+            TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+            TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+            for (cudaEvent_t& e : c->chunk_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        }
+        // what the deposit needs first, on the compute stream; the rest beside it on the copy
+        // stream (after the work already queued on the compute stream), awaited before its first use
+        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 1, ids, c->stream))) {
+            cudaStreamSynchronize(c->stream);
             return st;
-        return sync_and_check(c);
+        }
+        TRIBO_CUDA(cudaEventRecord(c->copy_done, c->stream));
+        TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_done, 0));
+        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) {
+            cudaStreamSynchronize(c->copy_stream);
+            cudaStreamSynchronize(c->stream);
+            return st;
+        }
+        TRIBO_CUDA(cudaEventRecord(c->copy_done, c->copy_stream));
+        rest_pending = true;
     }
-    return TRIBO_OK;
+    // everything after the copies: on an error of a host call, the copies in flight are awaited
+    // before the caller gets its arrays back
+    auto run = [&]() -> tribo_status {
+        const bool want_cell = v.cell != nullptr;
+        bool sent_back = false;          // host call: the results already went back chunk by chunk
+        auto await_rest = [&]() -> tribo_status {
+            if (rest_pending) {
+                TRIBO_CUDA(cudaStreamWaitEvent(c->stream, c->copy_done, 0));
+                rest_pending = false;
+            }
+            return TRIBO_OK;
+        };
+        StepIO io;
+        if (near) io.acoul = c->nf_acc;
+        if (c->fs && c->P.drag_law != TRIBO_DRAG_OFF) {
+            io.fs = c->fs;
+            io.fs_coef = -1.0 / (c->P.rho * dt * nsteps);
+        }
+        PView home = v, cur = v, other = S > 0 ? set_view(c, c->alt, p->n) : v;
+        if (!v.id) other.id = nullptr;
+        if (!v.cell) other.cell = nullptr;
+        if (electro) {
+            TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
+            if ((st = particles_deposit(c, cur))) return st;
+        }
+        for (int s = 0; s < nsteps; ++s) {
+            const bool last = s == nsteps - 1;
+            if (S > 0 && c->steps_done % S == 0) {
+                if ((st = await_rest()) || (st = particles_sort(c, cur, other))) return st;
+                std::swap(cur, other);
+            }
+            if (c->n_modes) {
+                if ((st = modes_eval(c, c->time, c->u_lat))) return st;
+            }
+            if (electro) {
+                if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
+            }
+            if ((st = await_rest())) return st;
+            if (near) {
+                if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
+                    (st = particles_coulomb(c, cur, c->nf_members, c->nf_acc)))
+                    return st;
+            }
+            // host call, last step, no pair interactions (they need every particle): the step in
+            // chunks, each chunk's arrays sent back on the copy stream while the next one runs
+            const bool chunked = p->on_host && last && !near && !collide;
+            if (chunked) {
+                constexpr int K = 4;
+                for (int ci = 0; ci < K; ++ci) {
+                    const int64_t a0 = cur.n * ci / K, a1 = cur.n * (ci + 1) / K;
+                    if (a1 <= a0) continue;
+                    const PView part = sub_view(c, cur, a0, a1 - a0);
+                    if ((st = particles_step(c, part, dt, false, want_cell, io))) return st;
+                    TRIBO_CUDA(cudaEventRecord(c->chunk_done[ci], c->stream));
+                    TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->chunk_done[ci], 0));
+                    if ((st = copy_back_range(c, part, p, a0, sorts && part.id != nullptr, c->copy_stream))) return st;
+                }
+                sent_back = true;
+            } else if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last, io))) {
+                return st;
+            }
+            if (collide) {
+                if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
+                    (st = particles_collide(c, cur, c->nf_members, c->pp_partner)))
+                    return st;
+            }
+            c->steps_done++;
+            c->time += dt;
+        }
+        c->n_samples += nsteps;
+        if (sent_back) {
+            // the arrays went back from the set that holds them, chunk by chunk
+            TRIBO_CUDA(cudaStreamSynchronize(c->copy_stream));
+            return sync_and_check(c);
+        }
+        if (cur.x != home.x) {
+            if ((st = copy_view(c, home, cur))) return st;
+        }
+        if (p->on_host) {
+            // ids come back only if a sort permuted them
+            if ((st = copy_particles(c, v, p, cudaMemcpyDeviceToHost, false, 3, sorts && v.id != nullptr, c->stream)))
+                return st;
+            return sync_and_check(c);
+        }
+        return TRIBO_OK;
+    };
+    st = run();
+    if (st && p->on_host && c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    return st;
 }
 
 tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E) {
