@@ -585,11 +585,15 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
             if ((st = particles_deposit(c, cur))) return st;
         }
+        // the cell lists the collisions built at the end of a step serve the next step's near
+        // field (the collisions move no particle) unless a sort reorders the particles between
+        bool lists_fresh = false;
         for (int s = 0; s < nsteps; ++s) {
             const bool last = s == nsteps - 1;
             if (S > 0 && c->steps_done % S == 0) {
                 if ((st = await_rest()) || (st = particles_sort(c, cur, other))) return st;
                 std::swap(cur, other);
+                lists_fresh = false;
             }
             if (c->n_modes) {
                 if ((st = modes_eval(c, c->time, c->u_lat))) return st;
@@ -599,10 +603,11 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             }
             if ((st = await_rest())) return st;
             if (near) {
-                if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
+                if ((!lists_fresh && (st = particles_cell_lists(c, cur, c->nf_members))) ||
                     (st = particles_coulomb(c, cur, c->nf_members, c->nf_acc)))
                     return st;
             }
+            lists_fresh = false;     // the step moves the particles
             // host call, last step, no pair interactions (they need every particle): the step in
             // chunks, each chunk's arrays sent back on the copy stream while the next one runs
             const bool chunked = p->on_host && last && !near && !collide;
@@ -625,6 +630,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                 if ((st = particles_cell_lists(c, cur, c->nf_members)) ||
                     (st = particles_collide(c, cur, c->nf_members, c->pp_partner)))
                     return st;
+                lists_fresh = true;
             }
             c->steps_done++;
             c->time += dt;

@@ -52,7 +52,8 @@ def _gpu(c, faces, lat, parts, prec, nsteps, **pkw):
     return {k: np.asarray(v)[order].astype(np.float64) for k, v in out.items()}
 
 
-@pytest.mark.parametrize("variant", [dict(sort_every=0), dict(sort_every=3), dict(sort_every=0, coulomb=1)])
+@pytest.mark.parametrize("variant", [dict(sort_every=0), dict(sort_every=3), dict(sort_every=0, coulomb=1),
+                                     dict(sort_every=3, coulomb=1)])
 @pytest.mark.parametrize("prec", [T.TRIBO_FP64, T.TRIBO_MIXED])
 def test_collisions_match_oracle(prec, variant):
     c, faces, lat, parts = _case()
