@@ -242,14 +242,16 @@ tribo_status issue_steps(tribo_batch* b, const std::vector<PView>& home, int cou
 
 template <class R>
 tribo_status autotune_impl(tribo_batch* b, const std::vector<PView>& home, const double* dt, int32_t* choice) {
-    // scratch copies of the particles in the contexts' second sets
+    // scratch copies of the particles in the contexts' second sets; a channel that sorts is
+    // timed on a cell-sorted copy, the order it steps in (unsorted particles favour other shapes)
     std::vector<PView> scratch(b->n);
     for (int i = 0; i < b->n; ++i) {
         tribo_ctx* c = b->ch[i];
         scratch[i] = alt_of(c, home[i]);
         cudaStream_t keep = c->stream;
         c->stream = b->stream;
-        tribo_status st = copy_view(c, scratch[i], home[i]);
+        tribo_status st = c->P.sort_every > 0 && home[i].n > 0 ? particles_sort(c, home[i], scratch[i])
+                                                               : copy_view(c, scratch[i], home[i]);
         c->stream = keep;
         if (st) return st;
     }
