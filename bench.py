@@ -197,6 +197,13 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     nsteps = c.steps if steps is None else steps
     faces, lat, P = make_inputs(c)
     parts = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
+    # the ensemble in cell order, as a simulation that sorts its particles holds it (neither the
+    # forward call nor the adjoint re-sorts here)
+    ix = np.floor(np.asarray(P.x) / (c.lx / c.nx)).astype(np.int64) % c.nx
+    iz = np.floor(np.asarray(P.z) / (c.lz / c.nz)).astype(np.int64) % c.nz
+    jy = np.clip(np.searchsorted(faces, np.asarray(P.y), side="right") - 1, 0, c.ny - 1)
+    order = np.argsort((iz * c.ny + jy) * c.nx + ix, kind="stable")
+    parts = {k: np.asarray(v)[order] for k, v in parts.items()}
     base = dict(rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0)
 
     def channel(prec):
