@@ -685,14 +685,10 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
         // at 249 registers: 264 us, at 384x256x256)
         constexpr int CH = 12;
         const int nch = (ny + CH - 1) / CH;
-        // one pencil per thread: on small grids the pencils are few, so the blocks shrink until
-        // every SM holds at least two (128x128x128: 8320 pencils, 65 blocks of 128 threads)
-        int bt = 128;
-        while (bt > 32 && (int64_t)((nz * nxh + bt - 1) / bt) < 2 * (int64_t)c->num_sms) bt /= 2;
         // the chunk checkpoints of a block, one float4 per chunk and thread: at ny = 1024 (the
-        // largest grid) and 128 threads 196 KB, inside the opt-in shared memory per block
-        const size_t shc = sizeof(float4) * ((size_t)nch * bt + ny + 1) + sizeof(float2) * ny;
-        k_ysolve_chunk<CH><<<(nz * nxh + bt - 1) / bt, bt, shc, c->stream>>>(
+        // largest grid) 196 KB, inside the opt-in shared memory per block
+        const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
+        k_ysolve_chunk<CH><<<(nz * nxh + 127) / 128, 128, shc, c->stream>>>(
             (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
             (const float4*)c->d_yec, ny, nz, nxh);
     }
