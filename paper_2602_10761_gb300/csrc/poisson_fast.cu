@@ -213,7 +213,7 @@ __device__ __forceinline__ ds ds_mul_f(ds a, float b) {
     return fast_two_sum(p, e);
 }
 
-template <int C>
+template <int C, bool PF>
 __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
                                                       const float2* __restrict__ tinv,
                                                       const float2* __restrict__ tcp,
@@ -238,15 +238,39 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
     const int tid = threadIdx.x;
     // forward sweep, checkpoints at the end of each chunk
     ds pr = {0.f, 0.f}, pim = {0.f, 0.f};
+    float2 tvn[C];                  // prefetch buffers (PF): the next chunk's loads
+    cplx<float> rvn[C];
+    if constexpr (PF) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            if (i < ny) {
+                tvn[i] = tinv[(size_t)i * ni + item];
+                rvn[i] = srow[(size_t)i * nxh];
+            }
+        }
+    }
     for (int c = 0; c < nch; ++c) {
         float2 tv[C];
         cplx<float> rv[C];
+        if constexpr (PF) {
 #pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const int j = c * C + i;
-            if (j < ny) {
-                tv[i] = tinv[(size_t)j * ni + item];
-                rv[i] = srow[(size_t)j * nxh];
+            for (int i = 0; i < C; ++i) { tv[i] = tvn[i]; rv[i] = rvn[i]; }
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const int j = (c + 1) * C + i;
+                if (j < ny) {
+                    tvn[i] = tinv[(size_t)j * ni + item];
+                    rvn[i] = srow[(size_t)j * nxh];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const int j = c * C + i;
+                if (j < ny) {
+                    tv[i] = tinv[(size_t)j * ni + item];
+                    rv[i] = srow[(size_t)j * nxh];
+                }
             }
         }
 #pragma unroll
@@ -264,6 +288,19 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
     const float4 walls = se[ny];
     ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};      // x[j+1]
     float dnr = 0.f, dni = 0.f;                 // x[j+2] - x[j+1]
+    float2 tvb[C], cvb[C];          // prefetch buffers (PF): the previous chunk's loads
+    cplx<float> rvb[C];
+    if constexpr (PF) {
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const int j = (nch - 1) * C + i;
+            if (j < ny) {
+                tvb[i] = tinv[(size_t)j * ni + item];
+                cvb[i] = tcp[(size_t)j * ni + item];
+                rvb[i] = srow[(size_t)j * nxh];
+            }
+        }
+    }
     for (int c = nch - 1; c >= 0; --c) {
         ds qr = {0.f, 0.f}, qi = {0.f, 0.f};
         if (c > 0) {
@@ -273,13 +310,27 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
         }
         float2 tv[C], cv[C];
         cplx<float> rv[C];
+        if constexpr (PF) {
 #pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const int j = c * C + i;
-            if (j < ny) {
-                tv[i] = tinv[(size_t)j * ni + item];
-                cv[i] = tcp[(size_t)j * ni + item];
-                rv[i] = srow[(size_t)j * nxh];
+            for (int i = 0; i < C; ++i) { tv[i] = tvb[i]; cv[i] = cvb[i]; rv[i] = rvb[i]; }
+            if (c > 0) {
+#pragma unroll
+                for (int i = 0; i < C; ++i) {
+                    const int j = (c - 1) * C + i;
+                    tvb[i] = tinv[(size_t)j * ni + item];
+                    cvb[i] = tcp[(size_t)j * ni + item];
+                    rvb[i] = srow[(size_t)j * nxh];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const int j = c * C + i;
+                if (j < ny) {
+                    tv[i] = tinv[(size_t)j * ni + item];
+                    cv[i] = tcp[(size_t)j * ni + item];
+                    rv[i] = srow[(size_t)j * nxh];
+                }
             }
         }
         ds dr[C], di[C];
@@ -314,7 +365,7 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
                     d0i = ds_f(ds_add_fast(xi1, ds_neg(xi)));
                     const float4 cf = se[j + 1];
                     frow[(size_t)(j + 2) * nxh] = cplx<float>{cf.x * ds_f(xr1) + cf.y * d0r + cf.z * dnr,
-                                                              cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
+                        cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
                 }
                 dnr = d0r;
                 dni = d0i;
@@ -681,16 +732,29 @@ tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zer
     } else {
         const float2* tinv = (const float2*)c->d_ytab;
         const float2* tcp = tinv + (size_t)ny * ni;
-        // 12-row chunks: 168 registers, three blocks per SM (8 rows: 204 us, 12: 180 us, 16 rows
-        // at 249 registers: 264 us, at 384x256x256)
-        constexpr int CH = 12;
-        const int nch = (ny + CH - 1) / CH;
+        // Many pencils (384x256x256: 386 blocks): 12-row chunks, 168 registers, three blocks per
+        // SM (8 rows: 204 us, 12: 180 us, 16 rows at 249 registers: 264 us).  Few pencils (fewer
+        // than two blocks per SM, e.g. 128^3): 8-row chunks with the next chunk's loads issued
+        // before the current one is computed (a 128^3 solve 130 -> 113 us; at 384x256x256 the
+        // prefetch costs occupancy: 209 us).
+        const int64_t nblk = ((int64_t)nz * nxh + 127) / 128;
+        const bool few = nblk < 2 * (int64_t)c->num_sms;
+        const int ch = few ? 8 : 12;
+        const int nch = (ny + ch - 1) / ch;
         // the chunk checkpoints of a block, one float4 per chunk and thread: at ny = 1024 (the
-        // largest grid) 196 KB, inside the opt-in shared memory per block
+        // largest grid) 264 KB with 8-row chunks, 196 KB with 12; the prefetching kernel runs
+        // only where the checkpoints fit
         const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
-        k_ysolve_chunk<CH><<<(nz * nxh + 127) / 128, 128, shc, c->stream>>>(
-            (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
-            (const float4*)c->d_yec, ny, nz, nxh);
+        const size_t sh12 = sizeof(float4) * ((size_t)((ny + 11) / 12) * 128 + ny + 1) + sizeof(float2) * ny;
+        if (few && shc <= (size_t)c->smem_optin) {
+            k_ysolve_chunk<8, true><<<(unsigned)nblk, 128, shc, c->stream>>>(
+                (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
+                (const float4*)c->d_yec, ny, nz, nxh);
+        } else {
+            k_ysolve_chunk<12, false><<<(unsigned)nblk, 128, sh12, c->stream>>>(
+                (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
+                (const float4*)c->d_yec, ny, nz, nxh);
+        }
     }
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_INV_Z);
@@ -787,7 +851,9 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         return dispatch_attr<double>(nx, nz, optin);
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
-    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_chunk<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<12, false>), cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<8, true>), cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    c->smem_optin = optin;
     return dispatch_attr<float>(nx, nz, optin);
 }
 

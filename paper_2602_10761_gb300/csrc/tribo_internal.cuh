@@ -75,6 +75,7 @@ struct Accum {                // device-side statistics accumulators
 struct tribo_ctx {
     int device = 0;
     int num_sms = 152;                 // streaming multiprocessors of the device
+    int smem_optin = 48 * 1024;        // opt-in shared memory per block
     cudaStream_t stream = nullptr;
     cudaStream_t copy_stream = nullptr;  // host-pointer calls: the particle arrays the solve does not need
     cudaEvent_t copy_done = nullptr;     // ... recorded when they have landed
