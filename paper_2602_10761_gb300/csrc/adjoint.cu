@@ -505,6 +505,32 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     const double t_start = c->time;
     const size_t qbytes = ncell * sizeof(double);
 
+    // the field of every forward step kept in HBM when it fits in half of the free memory: the
+    // recomputed segments then take it instead of depositing and solving again
+    const size_t ebytes = 3 * nodes * sizeof(R);
+    bool keepE = false;
+    if (electro && nsteps > 0) {
+        const size_t need = ebytes * (size_t)nsteps;
+        if (need <= c->adj_E_bytes) {
+            keepE = true;
+        } else {
+            size_t freeb = 0, total = 0;
+            if (cudaMemGetInfo(&freeb, &total) == cudaSuccess && need + c->adj_E_bytes <= freeb / 2) {
+                TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+                if (c->adj_E) cudaFree(c->adj_E);
+                c->adj_E = nullptr;
+                c->adj_E_bytes = 0;
+                if (cudaMalloc(&c->adj_E, need) == cudaSuccess) {
+                    c->adj_E_bytes = need;
+                    keepE = true;
+                } else {
+                    (void)cudaGetLastError();
+                }
+            }
+        }
+    }
+    auto E_of_step = [&](int s) -> R* { return (R*)((char*)c->adj_E + ebytes * (size_t)s); };
+
     // ---- forward pass on the caller's particles, with checkpoints
     if (electro && nsteps > 0) {
         TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, qbytes, c->stream));
@@ -513,8 +539,13 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     for (int s = 0; s < nsteps; ++s) {
         if (s % C == 0 && (st = copy_state<R>(c, L.ckpt[s / C], state_of<R>(P), n))) return st;
         if (c->n_modes && (st = modes_eval(c, t_start + s * dt, c->u_lat))) return st;
-        if (electro && (st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
-        if ((st = particles_step(c, P, dt, electro && s < nsteps - 1, P.cell != nullptr && s == nsteps - 1)))
+        StepIO fio;
+        if (electro) {
+            void* Es = keepE ? (void*)E_of_step(s) : c->E_lat;
+            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, Es))) return st;
+            fio.E = Es;
+        }
+        if ((st = particles_step(c, P, dt, electro && s < nsteps - 1, P.cell != nullptr && s == nsteps - 1, fio)))
             return st;
         c->steps_done++;
     }
@@ -540,24 +571,27 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
         const int s0 = g * C;
         const int len = std::min(C, nsteps - s0);
         if ((st = copy_state<R>(c, L.W, L.ckpt[g], n))) return st;
-        if (electro) {
+        // the field of step s0 + i: kept from the forward pass, or solved again from the
+        // recomputed charges
+        auto segE = [&](int i) -> R* { return keepE ? E_of_step(s0 + i) : L.segE[i]; };
+        if (electro && !keepE) {
             TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, qbytes, c->stream));
             if ((st = particles_deposit(c, Wp))) return st;
         }
         for (int i = 0; i < len; ++i) {
             if ((st = copy_state<R>(c, L.seg[i], L.W, n))) return st;
             if (c->n_modes && (st = modes_eval(c, t_start + (s0 + i) * dt, c->u_lat))) return st;
-            if (electro && (st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, L.segE[i]))) return st;
+            if (electro && !keepE && (st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, L.segE[i]))) return st;
             if (i < len - 1) {
-                io.E = electro ? (const void*)L.segE[i] : nullptr;
-                if ((st = particles_step(c, Wp, dt, electro, false, io))) return st;
+                io.E = electro ? (const void*)segE(i) : nullptr;
+                if ((st = particles_step(c, Wp, dt, electro && !keepE, false, io))) return st;
             }
         }
         for (int i = len - 1; i >= 0; --i) {
             if (c->n_modes && i < len - 1 && (st = modes_eval(c, t_start + (s0 + i) * dt, c->u_lat))) return st;
             StepArgs<R> a = make_args<R>(c, dt);
             if (electro) {
-                a.E = L.segE[i];
+                a.E = segE(i);
                 TRIBO_CUDA(cudaMemsetAsync(L.Eb, 0, 3 * nodes * sizeof(R), c->stream));
             }
             AdjArgs<R> ga{L.seg[i], (const R*)P.d, L.lam, db, L.Eb, L.pacc, n, c->P.kappa_A};

@@ -273,7 +273,8 @@ void free_ctx(tribo_ctx* c) {
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
-                    c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner, c->d_inv_vol};
+                    c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner, c->d_inv_vol,
+                    c->adj_E};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);

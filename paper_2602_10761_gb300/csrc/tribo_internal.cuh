@@ -155,6 +155,8 @@ struct tribo_ctx {
     void* d_inv_vol = nullptr;         // 1 / (dx dy_j dz) per y cell, real type
     void* adj = nullptr;               // adjoint workspace (checkpoints, segment states, adjoints)
     size_t adj_bytes = 0;
+    void* adj_E = nullptr;             // adjoint: the field of every forward step, when it fits
+    size_t adj_E_bytes = 0;
 
     // statistics
     tribo::Accum* d_acc = nullptr;
