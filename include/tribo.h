@@ -261,12 +261,22 @@ tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void*
  *   ckpt_every >= 1: the forward pass stores the state every ckpt_every
  *      steps; the backward pass recomputes each segment from its stored
  *      state, keeping that segment's states (and field lattices) in a
- *      workspace the context owns and keeps for later calls.
+ *      workspace the context owns and keeps for later calls.  The field
+ *      lattice of every forward step is also kept when it fits in the budget
+ *      of tribo_set_adjoint_memory; the recomputed segments then take it
+ *      instead of solving again.
  *   J, dJ_dUc, dJ_dkappaA: HOST doubles, each may be NULL.
  *   dJ_dd: DEVICE array of n doubles (dJ/dd_p), may be NULL.
  * Synchronises; TRIBO_ERR_OOM if the workspace cannot be allocated. */
 tribo_status tribo_adjoint(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t nsteps, int32_t ckpt_every,
                            double* J, double* dJ_dUc, double* dJ_dkappaA, double* dJ_dd);
+
+/* Device memory the adjoint may take for the field lattices of every forward
+ * step (nsteps x 3 x Nz x (Ny+2) x Nx reals): max_bytes < 0 (the default)
+ * half of the free device memory at the call, 0 never (each recomputed
+ * segment solves its fields again), > 0 at most that many bytes.  The results
+ * do not depend on it beyond rounding. */
+tribo_status tribo_set_adjoint_memory(tribo_ctx* ctx, int64_t max_bytes);
 
 /* Statistics since the last tribo_reset_stats (Sec. 4.1): sum of the current
  * particle charges of p (may be NULL: sum_q is then not written), total wall

@@ -226,6 +226,12 @@ def tribo_set_momentum_source(ctx: int, F_s=None) -> None:
     check(load().tribo_set_momentum_source(ctx, _ptr(F_s)), "tribo_set_momentum_source")
 
 
+def tribo_set_adjoint_memory(ctx: int, max_bytes: int = -1) -> None:
+    """Budget of the adjoint's kept forward fields: < 0 half of the free device
+    memory (default), 0 never keep them, > 0 at most that many bytes."""
+    check(load().tribo_set_adjoint_memory(ctx, int(max_bytes)), "tribo_set_adjoint_memory")
+
+
 def tribo_set_params(ctx: int, params: Params) -> None:
     p = params.to_c()
     check(load().tribo_set_params(ctx, C.byref(p)), "tribo_set_params")

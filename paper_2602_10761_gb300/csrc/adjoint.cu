@@ -511,11 +511,15 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     bool keepE = false;
     if (electro && nsteps > 0) {
         const size_t need = ebytes * (size_t)nsteps;
-        if (need <= c->adj_E_bytes) {
+        if (c->adj_E_limit >= 0 && need > (size_t)c->adj_E_limit) {
+            keepE = false;
+        } else if (need <= c->adj_E_bytes) {
             keepE = true;
         } else {
             size_t freeb = 0, total = 0;
-            if (cudaMemGetInfo(&freeb, &total) == cudaSuccess && need + c->adj_E_bytes <= freeb / 2) {
+            const bool room = c->adj_E_limit >= 0 ||
+                              (cudaMemGetInfo(&freeb, &total) == cudaSuccess && need + c->adj_E_bytes <= freeb / 2);
+            if (room) {
                 TRIBO_CUDA(cudaStreamSynchronize(c->stream));
                 if (c->adj_E) cudaFree(c->adj_E);
                 c->adj_E = nullptr;
@@ -626,6 +630,12 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
 }  // namespace tribo
 
 using namespace tribo;
+
+extern "C" tribo_status tribo_set_adjoint_memory(tribo_ctx* c, int64_t max_bytes) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    c->adj_E_limit = max_bytes < 0 ? -1 : max_bytes;
+    return TRIBO_OK;
+}
 
 extern "C" tribo_status tribo_adjoint(tribo_ctx* c, tribo_particles* p, double dt, int32_t nsteps,
                                       int32_t ckpt_every, double* J, double* dJ_dUc, double* dJ_dkappaA,

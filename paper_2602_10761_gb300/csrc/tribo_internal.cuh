@@ -157,6 +157,7 @@ struct tribo_ctx {
     size_t adj_bytes = 0;
     void* adj_E = nullptr;             // adjoint: the field of every forward step, when it fits
     size_t adj_E_bytes = 0;
+    int64_t adj_E_limit = -1;          // its budget: < 0 half of the free memory, else bytes
 
     // statistics
     tribo::Accum* d_acc = nullptr;

@@ -175,3 +175,28 @@ def test_autograd_function_matches_oracle_gradient():
     ch.close()
     got = dict(J=float(J), dU_c=float(U.grad) / 3, dkappa_A=float(K.grad) / 3, dd=d.grad.cpu().numpy() / 3)
     check(got, ref, 1e-9, "autograd")
+
+
+def test_adjoint_with_and_without_the_kept_forward_fields():
+    """The recomputed segments take the forward's fields when they are kept
+    (default budget) or solve them again (budget 0): both match the oracle
+    gradient and each other to rounding."""
+    c, faces, lat, parts = _case(seed=13)
+    dt, nsteps = 2 * c.dt, 7
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces), oracle_params(c, U_c=2e3),
+                               oracle_state(parts), lat, dt, nsteps)
+    got = []
+    for budget in (-1, 0):
+        params = T.Params(precision=T.TRIBO_FP64, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=2e3)
+        ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(),
+                       max_particles=len(parts["x"]))
+        T.tribo_set_adjoint_memory(ch.ctx, budget)
+        P = T.Particles.from_numpy(parts, T.TRIBO_FP64)
+        J, dU, dK, dd = ch.adjoint(P, dt, nsteps, 3)
+        ch.close()
+        g = dict(J=J, dU_c=dU, dkappa_A=dK, dd=dd.cpu().numpy())
+        check(g, ref, 1e-9, f"budget {budget}")
+        got.append(g)
+    a, b = got
+    assert abs(a["J"] - b["J"]) <= 1e-12 * abs(a["J"])
+    assert np.abs(a["dd"] - b["dd"]).max() <= 1e-11 * np.abs(a["dd"]).max()
