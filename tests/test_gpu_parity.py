@@ -169,13 +169,15 @@ def test_schiller_naumann_high_reynolds_branch():
     compare_states(g, got, ref, TOL_FP64, label="SN high Re")
 
 
-def test_host_pointer_call_matches_device_call():
+@pytest.mark.parametrize("prec", [T.TRIBO_MIXED, T.TRIBO_FP64])
+def test_host_pointer_call_matches_device_call(prec):
     c, faces, lat, parts = problem(32, 24, 16, n=1500, q_scale=1e-12, vy_scale=0.3, near_wall=0.05, seed=9)
-    lat_r, parts_r = round_inputs(lat, parts, np.float32)
-    a, sa = run_gpu(c, faces, lat_r, parts_r, T.TRIBO_MIXED, 5, U_c=1e3, sort_every=2)
-    b, sb = run_gpu(c, faces, lat_r, parts_r, T.TRIBO_MIXED, 5, U_c=1e3, host=True, sort_every=2)
+    lat_r, parts_r = round_inputs(lat, parts, _real(prec))
+    a, sa = run_gpu(c, faces, lat_r, parts_r, prec, 5, U_c=1e3, sort_every=2)
+    b, sb = run_gpu(c, faces, lat_r, parts_r, prec, 5, U_c=1e3, host=True, sort_every=2)
+    rtol = 1e-6 if prec == T.TRIBO_MIXED else 1e-12
     for k in ("x", "y", "z", "vx", "vy", "vz"):
-        assert np.allclose(a[k], b[k], rtol=1e-6, atol=1e-9), k
+        assert np.allclose(a[k], b[k], rtol=rtol, atol=rtol * np.abs(a[k]).max()), k
     assert np.array_equal(a["n_imp"], b["n_imp"])
     assert np.array_equal(a["cell"], b["cell"])
     assert sa["n_impacts"] == sb["n_impacts"]
