@@ -33,7 +33,7 @@ WORKLOAD = "re550_384"
 # algorithmic bytes of the particle kernel per launch (mixed precision):
 PARTICLE_BYTES = 72      # per particle: state read (7 x f32 + q f64), state write (6 x f32), deposit
 NODE_BYTES = 24          # per lattice node the gather touches: u (3 x f32) + E (3 x f32)
-CELL_BYTES = 8           # per cell: the FP64 charge sum the deposit reads and writes back
+CELL_BYTES = 4           # per cell: the FP32 charge sum the deposit reads and writes back
 
 
 def dist_env():
@@ -598,7 +598,7 @@ def main():
     nodes_all = c.nx * (c.ny + 2) * c.nz
     alg = {
         "particle_step": c.n_particles * PARTICLE_BYTES + nodes * NODE_BYTES + cells * CELL_BYTES,
-        "poisson": cells * 8 + nodes_all * 12,
+        "poisson": cells * CELL_BYTES + nodes_all * 12,
     }
     dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
     step_ms = phases["particle_step"][0] / max(phases["particle_step"][1], 1)

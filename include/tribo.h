@@ -59,9 +59,11 @@ typedef int32_t tribo_status;
 #define TRIBO_DEV_OUTSIDE   0x4u /* a particle position was outside the channel before a step */
 
 #define TRIBO_FP64  0   /* everything in FP64 */
-#define TRIBO_MIXED 1   /* FP32 particle state, interpolation, force math, FFT and
-                           fields; FP64 y-tridiagonal solve, wall-impact charge and
-                           time of flight, per-particle and cell charge accumulators */
+#define TRIBO_MIXED 1   /* FP32 particle state, interpolation, force math, cell
+                           charge sums, FFT and fields; FP64-class y-tridiagonal
+                           solve (FP64 factors, double-single sweeps); FP64
+                           wall-impact charge, time of flight and per-particle
+                           charges */
 
 #define TRIBO_DRAG_STOKES           0
 #define TRIBO_DRAG_SCHILLER_NAUMANN 1
@@ -244,7 +246,9 @@ tribo_status tribo_step(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t n
  * double, may be NULL.  E: device (3, Nz, Ny+2, Nx) "real", the planes
  * E_x, E_y, E_z on the wall-extended lattice; the wall nodes hold E_x = E_z = 0
  * and the one-sided E_y.  rho and phi must be 16-byte aligned and E aligned
- * to its real type; TRIBO_ERR_ARG otherwise.  Asynchronous. */
+ * to its real type; TRIBO_ERR_ARG otherwise.  In TRIBO_MIXED the transforms
+ * are FP32: rho is first rounded to FP32 into the context's cell-sum array
+ * (work space that tribo_step refills at its start).  Asynchronous. */
 tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void* E);
 
 /* Reverse-mode derivative of the mean particle charge after nsteps coupled

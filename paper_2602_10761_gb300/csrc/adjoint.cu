@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
 // cyp[j] E_y-bar[node j+2] (node j is the bottom wall node for j = 0, node
 // j+2 the top wall node for j = ny-1).
 template <class R>
-__global__ void k_adj_grad(const R* __restrict__ Eb, const double* __restrict__ cy, double* __restrict__ out,
+__global__ void k_adj_grad(const R* __restrict__ Eb, const double* __restrict__ cy, R* __restrict__ out,
                            int nx, int ny, int nz, double cx, double cz) {
     const size_t ncell = (size_t)nx * ny * nz;
     const size_t nodes = (size_t)nz * (ny + 2) * nx;
@@ -356,7 +356,7 @@ __global__ void k_adj_grad(const R* __restrict__ Eb, const double* __restrict__ 
         const R* Ey = Eb + nodes;
         v += cy[3 * j] * (double)Ey[row - nx + i] + cy[3 * j + 1] * (double)Ey[row + i] +
              cy[3 * j + 2] * (double)Ey[row + nx + i];
-        out[e] = v;
+        out[e] = (R)v;
     }
 }
 
@@ -503,7 +503,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     TRIBO_CUDA(cudaMemsetAsync(L.acc, 0, sizeof(Accum), c->stream));
     tribo_status st;
     const double t_start = c->time;
-    const size_t qbytes = ncell * sizeof(double);
+    const size_t qbytes = ncell * sizeof(R);
 
     // the field of every forward step kept in HBM when it fits in half of the free memory: the
     // recomputed segments then take it instead of depositing and solving again
@@ -607,7 +607,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             if (!electro) continue;
             const int gb = (int)std::min<size_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
             phase_begin(c, PH_ADJOINT);
-            k_adj_grad<R><<<gb, kThreads, 0, c->stream>>>(L.Eb, L.cy, c->Q, c->nx, c->ny, c->nz,
+            k_adj_grad<R><<<gb, kThreads, 0, c->stream>>>(L.Eb, L.cy, (R*)c->Q, c->nx, c->ny, c->nz,
                                                           0.5 / c->dx, 0.5 / c->dz);
             TRIBO_LAUNCHED(c);
             if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, L.psi, c->E_lat))) return st;

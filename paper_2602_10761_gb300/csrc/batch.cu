@@ -171,7 +171,7 @@ tribo_status upload_chans(tribo_batch* b, int slot, const std::vector<PView>& vi
     for (int i = 0; i < b->n; ++i) {
         tribo_ctx* c = b->ch[i];
         StepArgs<R> a = make_args<R>(c, dt[i]);
-        a.Q = c->P.electrostatics ? c->Q : nullptr;
+        a.Q = c->P.electrostatics ? (R*)c->Q : nullptr;
         a.hist = scratch ? nullptr : c->d_hist;
         a.acc = scratch ? b->d_scratch : c->d_acc;
         h[i].a = a;
@@ -324,7 +324,7 @@ tribo_status step_impl(tribo_batch* b, const std::vector<PView>& home, const dou
         if (!c->P.electrostatics || home[i].n == 0) continue;
         cudaStream_t keep = c->stream;
         c->stream = b->stream;
-        cudaError_t e = cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, b->stream);
+        cudaError_t e = cudaMemsetAsync(c->Q, 0, real_bytes(c->prec) * (size_t)c->nx * c->ny * c->nz, b->stream);
         st = e == cudaSuccess ? particles_deposit(c, home[i]) : cuda_fail(e, "batch deposit");
         c->stream = keep;
         if (st) return st;

@@ -41,7 +41,7 @@ struct StepArgs {
     const R* u;                    // planes u_x, u_y, u_z, each `nodes` long
     const R* E;                    // planes E_x, E_y, E_z, each `nodes` long
     size_t nodes;
-    double* Q;                     // cell charge sums for the next step (may be NULL)
+    R* Q;                          // cell charge sums for the next step (may be NULL)
     unsigned long long* hist;      // ny (may be NULL)
     Accum* acc;
     // physics
@@ -470,7 +470,7 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     VX[n] = vxn; VY[n] = vyn; VZ[n] = vzn;
     int jn;
     const uint32_t key = cell_key<R>(xn, yn, zn, a, &jn);
-    if (a.Q) atomicAdd(&a.Q[key], q);
+    if (a.Q) atomicAdd(&a.Q[key], (R)q);
     if (write_cell) p.cell[n] = key;
     if (use_hist) atomicAdd(&sh_hist[jn], 1u);
 }

@@ -125,8 +125,9 @@ __device__ cplx<R>* fft_smem(cplx<R>* A, cplx<R>* B, const FftPlan& plan, int nl
 }
 
 // ---------------------------------------------------------------- fwd_x
-template <class R>
-__global__ void k_fwd_x(double* __restrict__ src, const double* __restrict__ scale_row, int zero_src,
+// src holds QT: the context's charge sums (QT = R) or a caller's FP64 density.
+template <class R, class QT>
+__global__ void k_fwd_x(QT* __restrict__ src, const double* __restrict__ scale_row, int zero_src,
                         cplx<R>* __restrict__ S, int nx, int ny, int nlines, int nxh, FftPlan plan,
                         int lpb) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -139,8 +140,8 @@ __global__ void k_fwd_x(double* __restrict__ src, const double* __restrict__ sca
         const int i = idx - (idx / nx) * nx;
         const int j = line % ny;
         const size_t g = (size_t)line * nx + i;
-        const double v = src[g];
-        if (zero_src) src[g] = 0.0;
+        const QT v = src[g];
+        if (zero_src) src[g] = (QT)0;
         A[idx] = cplx<R>{(R)v * (R)scale_row[j], (R)0};
     }
     __syncthreads();
@@ -312,14 +313,14 @@ tribo_status setup_kernels(tribo_ctx* c) {
         set_last_error("grid needs more shared memory per block than the device offers");
         return TRIBO_ERR_UNSUPPORTED;
     }
-    TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_inv_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_fft_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return TRIBO_OK;
 }
 
 template <class R>
-tribo_status solve_impl(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+tribo_status solve_impl(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
                         void* Evoid) {
     const int nx = c->nx, ny = c->ny, nz = c->nz, nxh = c->nxh;
     cplx<R>* S = (cplx<R>*)c->S;
@@ -330,8 +331,8 @@ tribo_status solve_impl(tribo_ctx* c, double* src, const double* scale, bool zer
         const int nlines = ny * nz;
         dim3 grid((nlines + lpb - 1) / lpb);
         phase_begin(c, PH_FWD_X);
-        k_fwd_x<R><<<grid, kThreads, smem_fwd_x<R>(nx, lpb), c->stream>>>(
-            src, scale, zero_src ? 1 : 0, S, nx, ny, nlines, nxh, c->plan_x, lpb);
+        k_fwd_x<R, R><<<grid, kThreads, smem_fwd_x<R>(nx, lpb), c->stream>>>(
+            (R*)src, scale, zero_src ? 1 : 0, S, nx, ny, nlines, nxh, c->plan_x, lpb);
         TRIBO_LAUNCHED(c);
     }
     {
@@ -473,7 +474,7 @@ tribo_status poisson_free(tribo_ctx* c) {
     return TRIBO_OK;
 }
 
-tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
                            void* E) {
     if (c->fast) return poisson_fast_solve(c, src, scale, zero_src, phi, E);
     if (c->prec == TRIBO_FP64) return solve_impl<double>(c, src, scale, zero_src, phi, E);
@@ -645,7 +646,7 @@ tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, d
     const int want_phi = phi != nullptr ? 1 : 0;
     const int nf = 3 + want_phi;
     const int nlines = ny * nz;
-    k_fwd_x<R><<<(nlines + lpb - 1) / lpb, kThreads, smem_fwd_x<R>(nx, lpb), stream>>>(
+    k_fwd_x<R, double><<<(nlines + lpb - 1) / lpb, kThreads, smem_fwd_x<R>(nx, lpb), stream>>>(
         const_cast<double*>(rho), d_scale, 0, S, nx, ny, nlines, nxh, px, lpb);
     k_fft_z<R><<<dim3(ny, (nxh + mt - 1) / mt, 1), kThreads, sizeof(cplx<R>) * 2 * mt * nz, stream>>>(
         S, nz, ny, nxh, mt, pz, (R)-1, 0);
@@ -682,8 +683,9 @@ tribo_status noalloc_device(int dev, unsigned char** base) {
         int optin = 0;
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: device attribute");
-        const void* fns[] = {(const void*)k_fwd_x<float>, (const void*)k_inv_x<float>, (const void*)k_fft_z<float>,
-                             (const void*)k_fwd_x<double>, (const void*)k_inv_x<double>,
+        const void* fns[] = {(const void*)k_fwd_x<float, double>, (const void*)k_inv_x<float>,
+                             (const void*)k_fft_z<float>, (const void*)k_fwd_x<double, double>,
+                             (const void*)k_inv_x<double>,
                              (const void*)k_fft_z<double>};
         for (const void* f : fns) {
             e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);

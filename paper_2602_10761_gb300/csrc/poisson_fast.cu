@@ -24,6 +24,7 @@
 // Passes: xfwd (zeroes the charge buffer), zfwd, ysolve, zinv, xinv.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "fft.cuh"
@@ -66,9 +67,10 @@ __device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
 // Thread group (line, r) per line (k, j) of the charge-sum array:
 // z_n = x_2n + i x_2n+1 (scaled to -rho/eps), Z = FFT_M(z) by the register
 // four-step, X_m = (Z_m + conj Z_M-m)/2 - (i/2) W^m (Z_m - conj Z_M-m) for
-// m = 0..M.  Each thread zeroes the charge sums it has read.
+// m = 0..M.  Each thread zeroes the charge sums it has read.  The sums have
+// the real type R (a caller's FP64 density is rounded to R beforehand).
 template <class R, int M>
-__global__ void __launch_bounds__(kThreads) k_xfwd4(double* __restrict__ src, const double* __restrict__ scale_row,
+__global__ void __launch_bounds__(kThreads) k_xfwd4(R* __restrict__ src, const double* __restrict__ scale_row,
                                                     int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
                                                     const cplx<R>* __restrict__ tw_g) {
     using F4 = fft::FourStep<M, kThreads>;
@@ -86,16 +88,20 @@ __global__ void __launch_bounds__(kThreads) k_xfwd4(double* __restrict__ src, co
     cplx<R>* lb = buf + l * CS;
     if (live && r < N2) {
         const R s = from_f64<R>(scale_row[line % ny]);
-        double2* row = reinterpret_cast<double2*>(src) + (size_t)line * M;
+        using V2 = std::conditional_t<sizeof(R) == 8, double2, float2>;   // (x_2n, x_2n+1)
+        V2* row = reinterpret_cast<V2*>(src) + (size_t)line * M;
         cplx<R> y[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
-            const double2 v = row[N2 * n1 + r];
-            y[n1] = cplx<R>{from_f64<R>(v.x) * s, from_f64<R>(v.y) * s};
+            const V2 v = row[N2 * n1 + r];
+            y[n1] = cplx<R>{v.x * s, v.y * s};
         }
         if (zero_src) {
+            V2 zero;
+            zero.x = (R)0;
+            zero.y = (R)0;
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) row[N2 * n1 + r] = make_double2(0.0, 0.0);
+            for (int n1 = 0; n1 < N1; ++n1) row[N2 * n1 + r] = zero;
         }
         fft::reg_dft<R, -1, N1, 2 * N2>(y, tw);
 #pragma unroll
@@ -579,7 +585,7 @@ int wave_blocks(K kernel, size_t smem, int num_sms, int64_t tiles, int* cache) {
 }
 
 template <class R, int M>
-void launch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
+void launch_xfwd(tribo_ctx* c, R* src, const double* scale, bool zero) {
     constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->ny * c->nz;
     k_xfwd4<R, M><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
@@ -643,7 +649,7 @@ bool fast_len(int n) {
 }
 
 template <class R>
-bool dispatch_xfwd(tribo_ctx* c, double* src, const double* scale, bool zero) {
+bool dispatch_xfwd(tribo_ctx* c, R* src, const double* scale, bool zero) {
     switch (c->nx / 2) {
 #define CASE(N) case N: launch_xfwd<R, N>(c, src, scale, zero); return true;
         TRIBO_FAST_SIZES(CASE)
@@ -714,7 +720,7 @@ void split_ds(double v, float* hi, float* lo) {
 }
 
 template <class R>
-tribo_status solve_fast(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi, void* E) {
+tribo_status solve_fast(tribo_ctx* c, R* src, const double* scale, bool zero_src, double* phi, void* E) {
     const int ny = c->ny, nz = c->nz, nxh = c->nxh;
     phase_begin(c, PH_FWD_X);
     dispatch_xfwd<R>(c, src, scale, zero_src);
@@ -867,10 +873,10 @@ void poisson_fast_free(tribo_ctx* c) {
     c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = nullptr;
 }
 
-tribo_status poisson_fast_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+tribo_status poisson_fast_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
                                 void* E) {
-    if (c->prec == TRIBO_FP64) return solve_fast<double>(c, src, scale, zero_src, phi, E);
-    return solve_fast<float>(c, src, scale, zero_src, phi, E);
+    if (c->prec == TRIBO_FP64) return solve_fast<double>(c, (double*)src, scale, zero_src, phi, E);
+    return solve_fast<float>(c, (float*)src, scale, zero_src, phi, E);
 }
 
 }  // namespace tribo

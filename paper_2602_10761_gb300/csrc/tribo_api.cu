@@ -22,6 +22,11 @@ tribo_status cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
+__global__ void k_round_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
 bool is_2a3b(int n) {
     if (n < 1) return false;
     while (n % 2 == 0) n /= 2;
@@ -583,7 +588,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         if (!v.id) other.id = nullptr;
         if (!v.cell) other.cell = nullptr;
         if (electro) {
-            TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
+            TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, real_size(c) * (size_t)c->nx * c->ny * c->nz, c->stream));
             if ((st = particles_deposit(c, cur))) return st;
         }
         // the cell lists the collisions built at the end of a step serve the next step's near
@@ -667,7 +672,14 @@ tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E
         set_last_error("rho and phi must be 16-byte aligned, E aligned to its real type");
         return TRIBO_ERR_ARG;
     }
-    return poisson_solve(c, const_cast<double*>(rho), c->d_scale_rho, false, phi, E);
+    if (c->prec == TRIBO_FP64) return poisson_solve(c, const_cast<double*>(rho), c->d_scale_rho, false, phi, E);
+    // mixed: the solve reads FP32 sources; round the density into the charge-sum
+    // array (scratch between calls: every step call deposits afresh)
+    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
+    k_round_to_float<<<(unsigned)std::min<size_t>((ncell + 255) / 256, 4096), 256, 0, c->stream>>>(
+        rho, (float*)c->Q, ncell);
+    TRIBO_LAUNCHED(c);
+    return poisson_solve(c, c->Q, c->d_scale_rho, false, phi, E);
 }
 
 tribo_status tribo_stats(tribo_ctx* c, const tribo_particles* p, double* sum_q, uint64_t* n_impacts,

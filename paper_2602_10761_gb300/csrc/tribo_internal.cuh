@@ -111,7 +111,7 @@ struct tribo_ctx {
     // fields
     void* u_lat = nullptr;       // (3, nz, ny+2, nx) real: u_x, u_y, u_z planes
     void* E_lat = nullptr;       // (3, nz, ny+2, nx) real: E_x, E_y, E_z planes
-    double* Q = nullptr;         // (nz, ny, nx) cell charge sums
+    void* Q = nullptr;           // (nz, ny, nx) cell charge sums, real type (room for doubles)
     void* S = nullptr;           // (nz, ny, nxh) cplx<real> spectrum
     void* F = nullptr;           // (4, nz, ny+2, nxh) cplx<real> field spectra
     void* W = nullptr;           // (ny, nz*nxh) cplx<double> Thomas scratch (generic path)
@@ -203,17 +203,18 @@ tribo_status cuda_fail(cudaError_t e, const char* what);
 // Poisson (poisson.cu)
 tribo_status poisson_setup(tribo_ctx* c);
 tribo_status poisson_free(tribo_ctx* c);
-// src: device (nz, ny, nx) double; scale: device ny per-row factor giving the
-// RHS -rho/eps; zero_src: write zeros back into src after reading.
-// phi may be NULL.  E: (3, nz, ny+2, nx) real (E_x, E_y, E_z).
-tribo_status poisson_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src,
+// src: device (nz, ny, nx) of the real type (charge sums or a density);
+// scale: device ny per-row factor giving the RHS -rho/eps; zero_src: write
+// zeros back into src after reading.  phi may be NULL.  E: (3, nz, ny+2, nx)
+// real (E_x, E_y, E_z).
+tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src,
                            double* phi, void* E);
 
 // compile-time-length Poisson path (poisson_fast.cu)
 bool poisson_fast_supported(int nx, int nz);
 tribo_status poisson_fast_setup(tribo_ctx* c);
 void poisson_fast_free(tribo_ctx* c);
-tribo_status poisson_fast_solve(tribo_ctx* c, double* src, const double* scale, bool zero_src, double* phi,
+tribo_status poisson_fast_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
                                 void* E);
 
 // particles (particles.cu)
