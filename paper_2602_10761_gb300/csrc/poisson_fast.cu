@@ -205,19 +205,32 @@ __global__ void __launch_bounds__(128) k_ysolve64(cplx<double>* __restrict__ S, 
 // the chunks from the top, recomputes each chunk's forward values into
 // registers from its checkpoint and substitutes back.  E_y per cell j is
 // A_j phi_j + Bm_j (phi_j - phi_j-1) + Bp_j (phi_j+1 - phi_j), the
-// differences taken in double-single, written one row behind the backward
-// sweep; wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
-__device__ __forceinline__ ds ds_add_fast(ds a, ds b) {   // one two-sum on the high parts
-    ds s = two_sum(a.hi, b.hi);
-    s.lo += a.lo + b.lo;
+// differences formed from the double-single values, written one row behind
+// the backward sweep; wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
+// a r - b c with one normalisation: the two products' high parts are combined
+// by a two-sum and their error terms (each exact to FP32 rounding of an
+// O(u) correction) are added to the low part.
+__device__ __forceinline__ ds ds_fms(ds a, float r, ds b, ds c) {
+    const float h1 = a.hi * r;
+    const float e1 = fmaf(a.lo, r, fmaf(a.hi, r, -h1));
+    const float h2 = b.hi * c.hi;
+    const float e2 = fmaf(b.lo, c.hi, fmaf(b.hi, c.lo, fmaf(b.hi, c.hi, -h2)));
+    ds s = two_sum(h1, -h2);
+    s.lo += e1 - e2;
     return fast_two_sum(s.hi, s.lo);
 }
-__device__ __forceinline__ ds ds_mul_f(ds a, float b) {
-    const float p = a.hi * b;
-    float e = fmaf(a.hi, b, -p);
-    e = fmaf(a.lo, b, e);
-    return fast_two_sum(p, e);
+// d - b c in the same way
+__device__ __forceinline__ ds ds_sub_mul(ds d, ds b, ds c) {
+    const float h = b.hi * c.hi;
+    const float e = fmaf(b.lo, c.hi, fmaf(b.hi, c.lo, fmaf(b.hi, c.hi, -h)));
+    ds s = two_sum(d.hi, -h);
+    s.lo += d.lo - e;
+    return fast_two_sum(s.hi, s.lo);
 }
+// a - b rounded to FP32: the high parts' difference is exact when they are
+// within a factor two of each other (Sterbenz) and has no cancellation
+// otherwise, so the result is within a few roundings of the difference
+__device__ __forceinline__ float ds_diff_f(ds a, ds b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
 template <int C, bool PF>
 __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
@@ -285,8 +298,8 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
             if (j < ny) {
                 const ds inv = {tv[i].x, tv[i].y};
                 const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
-                pr = ds_add_fast(ds_mul_f(inv, rv[i].re), ds_neg(ds_mul(at, pr)));
-                pim = ds_add_fast(ds_mul_f(inv, rv[i].im), ds_neg(ds_mul(at, pim)));
+                pr = ds_fms(inv, rv[i].re, at, pr);
+                pim = ds_fms(inv, rv[i].im, at, pim);
             }
         }
         ck[(size_t)c * blockDim.x + tid] = make_float4(pr.hi, pr.lo, pim.hi, pim.lo);
@@ -346,8 +359,8 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
             if (j < ny) {
                 const ds inv = {tv[i].x, tv[i].y};
                 const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
-                qr = ds_add_fast(ds_mul_f(inv, rv[i].re), ds_neg(ds_mul(at, qr)));
-                qi = ds_add_fast(ds_mul_f(inv, rv[i].im), ds_neg(ds_mul(at, qi)));
+                qr = ds_fms(inv, rv[i].re, at, qr);
+                qi = ds_fms(inv, rv[i].im, at, qi);
                 dr[i] = qr;
                 di[i] = qi;
             }
@@ -359,16 +372,16 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
                 ds xr = dr[i], xi = di[i];
                 if (j != ny - 1) {
                     const ds cp = {cv[i].x, cv[i].y};
-                    xr = ds_add_fast(xr, ds_neg(ds_mul(cp, xr1)));
-                    xi = ds_add_fast(xi, ds_neg(ds_mul(cp, xi1)));
+                    xr = ds_sub_mul(xr, cp, xr1);
+                    xi = ds_sub_mul(xi, cp, xi1);
                 }
                 const float fr = ds_f(xr), fi = ds_f(xi);
                 srow[(size_t)j * nxh] = cplx<float>{fr, fi};
                 if (j == ny - 1) frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * fr, walls.y * fi};
                 float d0r = 0.f, d0i = 0.f;
                 if (j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
-                    d0r = ds_f(ds_add_fast(xr1, ds_neg(xr)));
-                    d0i = ds_f(ds_add_fast(xi1, ds_neg(xi)));
+                    d0r = ds_diff_f(xr1, xr);
+                    d0i = ds_diff_f(xi1, xi);
                     const float4 cf = se[j + 1];
                     frow[(size_t)(j + 2) * nxh] = cplx<float>{cf.x * ds_f(xr1) + cf.y * d0r + cf.z * dnr,
                         cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
@@ -739,10 +752,11 @@ tribo_status solve_fast(tribo_ctx* c, R* src, const double* scale, bool zero_src
         const float2* tinv = (const float2*)c->d_ytab;
         const float2* tcp = tinv + (size_t)ny * ni;
         // Many pencils (384x256x256: 386 blocks): 12-row chunks, 168 registers, three blocks per
-        // SM (8 rows: 204 us, 12: 180 us, 16 rows at 249 registers: 264 us).  Few pencils (fewer
-        // than two blocks per SM, e.g. 128^3): 8-row chunks with the next chunk's loads issued
-        // before the current one is computed (a 128^3 solve 130 -> 113 us; at 384x256x256 the
-        // prefetch costs occupancy: 209 us).
+        // SM (160 us; 10 rows at 176 registers, two blocks per SM: 250 us; 16 rows at 249
+        // registers: 264 us).  Few pencils (fewer than two blocks per SM, e.g. 128^3): 8-row
+        // chunks with the next chunk's loads issued before the current one is computed (a 128^3
+        // solve 130 -> 113 us).  At 384x256x256 the prefetch loses although 8 rows (164
+        // registers) keep three blocks per SM: 201 us, 6 rows 215 us.
         const int64_t nblk = ((int64_t)nz * nxh + 127) / 128;
         const bool few = nblk < 2 * (int64_t)c->num_sms;
         const int ch = few ? 8 : 12;
