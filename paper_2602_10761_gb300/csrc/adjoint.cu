@@ -58,7 +58,8 @@ struct AdjArgs {
     const R* d;            // diameters
     SView<R> b;            // in: adjoint of state n+1; out: adjoint of state n
     double* db;            // accumulated d-bar per particle
-    R* Eb;                 // field-lattice adjoint (3 planes), NULL without electrostatics
+    R* Eb;                 // field-lattice adjoint, NULL without electrostatics: FP64 three planes,
+                           // FP32 node-major float4 (x, y, z, 0)
     double* pacc;          // [0] U_c-bar, [1] kappa_A-bar
     int64_t n;
     double kappa_A;
@@ -192,7 +193,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
         R vb[3] = {g.b.vx[n], g.b.vy[n], g.b.vz[n]};
         const double qb = g.b.q[n];
         double qb_in = qb;
-        double dbar = 0.0;
+        double dbar = 0.0;                        // the impact's FP64 term
+        R dbar_r = 0;                             // the terms formed in the real type
         if (hit) {
             const R vyh = -vn[1];                 // v_y after the reflection
             double speed;
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
                 }
             }
             // y'' = 2 plane - y' with plane = r (bottom) or ly - r (top)
-            dbar += (double)(lo ? xb[1] : -xb[1]);
+            dbar_r += lo ? xb[1] : -xb[1];
             xb[1] = -xb[1];
             vb[1] = -vb[1];
         }
@@ -254,18 +256,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
             // tau(d, rel)
             R relb = 0;
             if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN && re > (R)1000) {
-                dbar += (double)(taub * tau / d);
+                dbar_r += taub * tau / d;
                 relb = -taub * tau / rel;
             } else if (a.drag_law == TRIBO_DRAG_SCHILLER_NAUMANN) {
-                dbar += (double)(taub * (R)2 * tau / d);
+                dbar_r += taub * (R)2 * tau / d;
                 if (re > (R)0) {
                     const R f = (R)1 + rpow23(re) / (R)6;
                     const R reb = -taub * tau / f * rpow23(re) / ((R)9 * re);
-                    dbar += (double)(reb * rel * a.inv_nu);
+                    dbar_r += reb * rel * a.inv_nu;
                     relb = reb * d * a.inv_nu;
                 }
             } else {
-                dbar += (double)(taub * (R)2 * tau / d);
+                dbar_r += taub * (R)2 * tau / d;
             }
             if (rel > (R)0 && relb != (R)0) {
                 const R k = relb / rel;
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
                 aa += ab[c] * acc[c];
             }
             qb_in += (double)(aE * inv_m);
-            dbar += (double)((R)-3 * aa / d);
+            dbar_r += (R)-3 * aa / d;
         }
         // gather: position derivative through the Jacobians, then the scatter of E_p-bar
         R gx = 0, gy = 0, gz = 0;
@@ -302,17 +304,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
         xb[1] += gy * cr.inv_dy;
         xb[2] += gz * a.inv_dz;
         if (a.electro && (Epb[0] != (R)0 || Epb[1] != (R)0 || Epb[2] != (R)0)) {
+            if constexpr (sizeof(R) == 4) {      // node-major (x, y, z, 0): one vector atomic a corner
+                float4* E4 = reinterpret_cast<float4*>(g.Eb);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                atomic_add_r<R>(g.Eb + cr.idx[c], cr.w[c] * Epb[0]);
-                atomic_add_r<R>(g.Eb + a.nodes + cr.idx[c], cr.w[c] * Epb[1]);
-                atomic_add_r<R>(g.Eb + 2 * a.nodes + cr.idx[c], cr.w[c] * Epb[2]);
+                for (int c = 0; c < 8; ++c)
+                    atomicAdd(E4 + cr.idx[c], make_float4(cr.w[c] * Epb[0], cr.w[c] * Epb[1], cr.w[c] * Epb[2], 0.f));
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    atomic_add_r<R>(g.Eb + cr.idx[c], cr.w[c] * Epb[0]);
+                    atomic_add_r<R>(g.Eb + a.nodes + cr.idx[c], cr.w[c] * Epb[1]);
+                    atomic_add_r<R>(g.Eb + 2 * a.nodes + cr.idx[c], cr.w[c] * Epb[2]);
+                }
             }
         }
         g.b.x[n] = xb[0]; g.b.y[n] = xb[1]; g.b.z[n] = xb[2];
         g.b.vx[n] = vb[0]; g.b.vy[n] = vb[1]; g.b.vz[n] = vb[2];
         g.b.q[n] = qb_in;
-        g.db[n] += dbar;
+        g.db[n] += dbar + (double)dbar_r;
     }
     // parameter sums: warp reduction, one atomic per warp with a contribution
 #pragma unroll
@@ -336,27 +345,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
 // cyp[j] E_y-bar[node j+2] (node j is the bottom wall node for j = 0, node
 // j+2 the top wall node for j = ny-1).
 template <class R>
-__global__ void k_adj_grad(const R* __restrict__ Eb, const double* __restrict__ cy, R* __restrict__ out,
-                           int nx, int ny, int nz, double cx, double cz) {
-    const size_t ncell = (size_t)nx * ny * nz;
+__global__ void k_adj_grad(const R* __restrict__ Eb, const R* __restrict__ cy, R* __restrict__ out,
+                           int nx, int ny, int nz, R cx, R cz) {
     const size_t nodes = (size_t)nz * (ny + 2) * nx;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < ncell; e += stride) {
-        const int i = (int)(e % nx);
-        const size_t kj = e / nx;
-        const int j = (int)(kj % ny);
-        const int k = (int)(kj / ny);
-        const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+    const R* Ey = Eb + nodes;
+    const R* Ez = Eb + 2 * nodes;
+    for (int row = blockIdx.x; row < nz * ny; row += gridDim.x) {      // cell row (k, j)
+        const int k = row / ny;
+        const int j = row - k * ny;
         const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
-        const size_t row = ((size_t)k * (ny + 2) + j + 1) * nx;
-        double v = cx * ((double)Eb[row + ip] - (double)Eb[row + im]);
-        const size_t rkp = ((size_t)kp * (ny + 2) + j + 1) * nx + i;
-        const size_t rkm = ((size_t)km * (ny + 2) + j + 1) * nx + i;
-        v += cz * ((double)Eb[2 * nodes + rkp] - (double)Eb[2 * nodes + rkm]);
-        const R* Ey = Eb + nodes;
-        v += cy[3 * j] * (double)Ey[row - nx + i] + cy[3 * j + 1] * (double)Ey[row + i] +
-             cy[3 * j + 2] * (double)Ey[row + nx + i];
-        out[e] = (R)v;
+        const R c0 = cy[3 * j], c1 = cy[3 * j + 1], c2 = cy[3 * j + 2];
+        const size_t nr = ((size_t)k * (ny + 2) + j + 1) * nx;         // node row of the cells
+        const size_t nkp = ((size_t)kp * (ny + 2) + j + 1) * nx, nkm = ((size_t)km * (ny + 2) + j + 1) * nx;
+        R* o = out + (size_t)row * nx;
+        for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+            const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+            R v;
+            if constexpr (sizeof(R) == 4) {
+                const float4* E4 = reinterpret_cast<const float4*>(Eb);
+                v = cx * (E4[nr + ip].x - E4[nr + im].x);
+                v += cz * (E4[nkp + i].z - E4[nkm + i].z);
+                v += c0 * E4[nr - nx + i].y + c1 * E4[nr + i].y + c2 * E4[nr + nx + i].y;
+            } else {
+                v = cx * (Eb[nr + ip] - Eb[nr + im]);
+                v += cz * (Ez[nkp + i] - Ez[nkm + i]);
+                v += c0 * Ey[nr - nx + i] + c1 * Ey[nr + i] + c2 * Ey[nr + nx + i];
+            }
+            o[i] = v;
+        }
     }
 }
 
@@ -412,11 +428,15 @@ struct AdjLayout {
     uint32_t* Wni;
     R* Eb;
     double* psi;
-    double* cy;
+    R* cy;
     double* pacc;
     double* db;
     Accum* acc;
 };
+
+// reals per node of E-bar: three planes in FP64, float4 per node in FP32
+template <class R>
+constexpr size_t eb_reals() { return sizeof(R) == 4 ? 4 : 3; }
 
 // carve the workspace (base NULL: only count the bytes)
 template <class R>
@@ -434,9 +454,9 @@ size_t layout(AdjLayout<R>& L, char* base, int64_t n, int nseg, int C, bool elec
     L.Wqw = (double*)cv.take(n * sizeof(double));
     L.Wni = (uint32_t*)cv.take(n * sizeof(uint32_t));
     L.lam = take_state<R>(cv, n);
-    L.Eb = electro ? (R*)cv.take(3 * nodes * sizeof(R)) : nullptr;
+    L.Eb = electro ? (R*)cv.take(eb_reals<R>() * nodes * sizeof(R)) : nullptr;
     L.psi = electro ? (double*)cv.take(ncell * sizeof(double)) : nullptr;
-    L.cy = (double*)cv.take(3 * (size_t)ny * sizeof(double));
+    L.cy = (R*)cv.take(3 * (size_t)ny * sizeof(R));
     L.pacc = (double*)cv.take(2 * sizeof(double));
     L.db = (double*)cv.take(n * sizeof(double));
     L.acc = (Accum*)cv.take(sizeof(Accum));
@@ -495,9 +515,10 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     }
     layout<R>(L, (char*)c->adj, n, nseg, Cs, electro, nodes, ncell, c->ny);
     double* db = dd ? dd : L.db;
-    const std::vector<double> cy = grad_transpose_y(c);
+    const std::vector<double> cy64 = grad_transpose_y(c);
+    const std::vector<R> cy(cy64.begin(), cy64.end());
     TRIBO_CUDA(cudaStreamSynchronize(c->stream));
-    TRIBO_CUDA(cudaMemcpy(L.cy, cy.data(), sizeof(double) * cy.size(), cudaMemcpyHostToDevice));
+    TRIBO_CUDA(cudaMemcpy(L.cy, cy.data(), sizeof(R) * cy.size(), cudaMemcpyHostToDevice));
     TRIBO_CUDA(cudaMemsetAsync(db, 0, n * sizeof(double), c->stream));
     TRIBO_CUDA(cudaMemsetAsync(L.pacc, 0, 2 * sizeof(double), c->stream));
     TRIBO_CUDA(cudaMemsetAsync(L.acc, 0, sizeof(Accum), c->stream));
@@ -596,7 +617,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             StepArgs<R> a = make_args<R>(c, dt);
             if (electro) {
                 a.E = segE(i);
-                TRIBO_CUDA(cudaMemsetAsync(L.Eb, 0, 3 * nodes * sizeof(R), c->stream));
+                TRIBO_CUDA(cudaMemsetAsync(L.Eb, 0, eb_reals<R>() * nodes * sizeof(R), c->stream));
             }
             AdjArgs<R> ga{L.seg[i], (const R*)P.d, L.lam, db, L.Eb, L.pacc, n, c->P.kappa_A};
             phase_begin(c, PH_ADJOINT);
@@ -605,12 +626,12 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             k_adj_step<R><<<ab, kThreads, 0, c->stream>>>(a, ga);
             TRIBO_LAUNCHED(c);
             if (!electro) continue;
-            const int gb = (int)std::min<size_t>((ncell + kThreads - 1) / kThreads, 152 * 16);
+            const int gb = (int)std::min<int64_t>((int64_t)c->nz * c->ny, (int64_t)c->num_sms * 16);
             phase_begin(c, PH_ADJOINT);
-            k_adj_grad<R><<<gb, kThreads, 0, c->stream>>>(L.Eb, L.cy, (R*)c->Q, c->nx, c->ny, c->nz,
-                                                          0.5 / c->dx, 0.5 / c->dz);
+            k_adj_grad<R><<<gb, 128, 0, c->stream>>>(L.Eb, L.cy, (R*)c->Q, c->nx, c->ny, c->nz,
+                                                     (R)(0.5 / c->dx), (R)(0.5 / c->dz));
             TRIBO_LAUNCHED(c);
-            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, L.psi, c->E_lat))) return st;
+            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, L.psi, nullptr))) return st;
             phase_begin(c, PH_ADJOINT);
             k_adj_deposit<R><<<grid_for(n), kThreads, 0, c->stream>>>(a, L.seg[i], n, L.psi, L.lam.q);
             TRIBO_LAUNCHED(c);

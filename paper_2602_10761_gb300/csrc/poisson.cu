@@ -477,6 +477,7 @@ tribo_status poisson_free(tribo_ctx* c) {
 tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
                            void* E) {
     if (c->fast) return poisson_fast_solve(c, src, scale, zero_src, phi, E);
+    if (!E) E = c->E_lat;       // the generic passes always form the field
     if (c->prec == TRIBO_FP64) return solve_impl<double>(c, src, scale, zero_src, phi, E);
     return solve_impl<float>(c, src, scale, zero_src, phi, E);
 }

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd4(R* __restrict__ src, const d
 __global__ void __launch_bounds__(128) k_ysolve64(cplx<double>* __restrict__ S, cplx<double>* __restrict__ Fy,
                                                   const double2* __restrict__ tab, double2* __restrict__ W,
                                                   const double* __restrict__ ycoef, const double* __restrict__ ey,
-                                                  int ny, int nz, int nxh) {
+                                                  int ny, int nz, int nxh, int want_ey) {
     const int ni = (nz / 2 + 1) * nxh;
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     if (item >= ni) return;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(128) k_ysolve64(cplx<double>* __restrict__ S, 
             }
             srow[(size_t)j * nxh] = cplx<double>{x.x, x.y};
             const int jn = j + 2;
-            if (jn <= ny + 1) {
+            if (want_ey && jn <= ny + 1) {
                 const double cm = ey[3 * jn], c0 = ey[3 * jn + 1], cq = ey[3 * jn + 2];
                 frow[(size_t)jn * nxh] = cplx<double>{cm * x.x + c0 * x1.x + cq * x2.x,
                                                       cm * x.y + c0 * x1.y + cq * x2.y};
@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(128) k_ysolve64(cplx<double>* __restrict__ S, 
             x2 = x1;
             x1 = x;
         }
+        if (!want_ey) continue;
         const double c0 = ey[3 * 1 + 1], cq = ey[3 * 1 + 2];
         frow[(size_t)1 * nxh] = cplx<double>{c0 * x1.x + cq * x2.x, c0 * x1.y + cq * x2.y};
         const double cw = ey[3 * 0 + 2];
@@ -232,7 +233,7 @@ __device__ __forceinline__ ds ds_sub_mul(ds d, ds b, ds c) {
 // otherwise, so the result is within a few roundings of the difference
 __device__ __forceinline__ float ds_diff_f(ds a, ds b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
-template <int C, bool PF>
+template <int C, bool PF, bool EY = true>
 __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
                                                       const float2* __restrict__ tinv,
                                                       const float2* __restrict__ tcp,
@@ -377,9 +378,9 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
                 }
                 const float fr = ds_f(xr), fi = ds_f(xi);
                 srow[(size_t)j * nxh] = cplx<float>{fr, fi};
-                if (j == ny - 1) frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * fr, walls.y * fi};
+                if (EY && j == ny - 1) frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * fr, walls.y * fi};
                 float d0r = 0.f, d0i = 0.f;
-                if (j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
+                if (EY && j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
                     d0r = ds_diff_f(xr1, xr);
                     d0i = ds_diff_f(xi1, xi);
                     const float4 cf = se[j + 1];
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
             }
         }
     }
+    if (!EY) return;
     const float4 cf = se[0];
     const float x0r = ds_f(xr1), x0i = ds_f(xi1);
     frow[(size_t)1 * nxh] = cplx<float>{cf.x * x0r + cf.z * dnr, cf.x * x0i + cf.z * dni};
@@ -452,11 +454,24 @@ __device__ __noinline__ void zinv_tile(const cplx<R>* __restrict__ S, cplx<R>* _
         fft::column_fft<R, 1, NZ, kThreads, true>(ph, rsS, F0 + 2 * fstride, rsF, ncol, tw, sz, buf);
     }
 }
+// the potential alone: only phi-hat's transform, on the interior node rows
+template <class R, int NZ>
+__device__ __noinline__ void zinv_tile_phi(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F, int ny,
+                                           int nxh, int ntx, int t, const cplx<R>* __restrict__ tw, cplx<R>* buf) {
+    using F4 = fft::FourStep<NZ, kThreads>;
+    const size_t rsF = (size_t)(ny + 2) * nxh, rsS = (size_t)ny * nxh;
+    const int jn = t / ntx;
+    const int mx0 = (t - jn * ntx) * F4::W;
+    const int ncol = min(F4::W, nxh - mx0);
+    if (jn < 1 || jn > ny) return;
+    fft::column_fft<R, 1, NZ, kThreads, false>(S + (size_t)(jn - 1) * nxh + mx0, rsS, F + (size_t)jn * nxh + mx0,
+                                               rsF, ncol, tw, nullptr, buf);
+}
 
 template <class R, int NZ>
 __global__ void __launch_bounds__(kThreads, 4) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
                                                     int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
-                                                    const cplx<R>* __restrict__ tw_g) {
+                                                    const cplx<R>* __restrict__ tw_g, int phi_only) {
     using F4 = fft::FourStep<NZ, kThreads>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
@@ -469,7 +484,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_zinv4(const cplx<R>* __restrict
     __syncthreads();
     const int ntx = (nxh + F4::W - 1) / F4::W;
     for (int t = blockIdx.x; t < (ny + 2) * ntx; t += gridDim.x)
-        zinv_tile<R, NZ>(S, F, ny, nxh, ntx, t, fstride, tw, sz, buf);
+        if (phi_only) zinv_tile_phi<R, NZ>(S, F, ny, nxh, ntx, t, tw, buf);
+        else zinv_tile<R, NZ>(S, F, ny, nxh, ntx, t, fstride, tw, sz, buf);
 }
 
 // ---------------------------------------------------------------- x inverse
@@ -488,8 +504,8 @@ template <class R, int M>
 __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict__ F, R* __restrict__ E,
                                                     double* __restrict__ phi, int ny, int nz, size_t fstride,
                                                     const double* __restrict__ sinx,
-                                                    const cplx<R>* __restrict__ tw_g, int want_phi, R norm,
-                                                    size_t nodes) {
+                                                    const cplx<R>* __restrict__ tw_g, int want_phi, int want_e,
+                                                    R norm, size_t nodes) {
     using F4 = fft::FourStep<M, kThreads>;
     constexpr int N1 = F4::N1, N2 = F4::N2, TPC = F4::TPC, LPB = F4::W, CS = F4::CS;
     constexpr int NX = 2 * M, NXH = M + 1;
@@ -510,7 +526,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
     const int jn = live ? line % nyn : 0;
     const bool interior = jn >= 1 && jn <= ny;
     const int nf = want_phi ? 4 : 3;
-    for (int f = 0; f < nf; ++f) {
+    for (int f = want_e ? 0 : 3; f < nf; ++f) {
         const bool active = live && (f == 1 || interior);
         const int src = f == 3 ? 0 : f;
         if (active && r < N2) {
@@ -562,7 +578,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
         }
         __syncthreads();
     }
-    if (live && !interior) {
+    if (want_e && live && !interior) {
         R* ex = E + (size_t)line * NX;
         R* ez = E + 2 * nodes + (size_t)line * NX;
         for (int i = r; i < NX; i += TPC) {
@@ -613,7 +629,8 @@ void launch_xinv(tribo_ctx* c, void* E, double* phi) {
     const int g = wave_blocks(k_xinv4<R, M>, xinv_smem<R, M>(), c->num_sms, (nlines + LPB - 1) / LPB, &occ);
     k_xinv4<R, M><<<g, kThreads, xinv_smem<R, M>(), c->stream>>>(
         (const cplx<R>*)c->F, (R*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
-        phi != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)), (size_t)c->nz * (c->ny + 2) * c->nx);
+        phi != nullptr ? 1 : 0, E != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)),
+        (size_t)c->nz * (c->ny + 2) * c->nx);
 }
 template <class R, int NZ>
 void launch_zfwd(tribo_ctx* c) {
@@ -625,14 +642,15 @@ void launch_zfwd(tribo_ctx* c) {
                                                                       (const cplx<R>*)c->d_twz);
 }
 template <class R, int NZ>
-void launch_zinv(tribo_ctx* c) {
+void launch_zinv(tribo_ctx* c, bool phi_only) {
     constexpr int W = fft::FourStep<NZ, kThreads>::W;
     static int occ = 0;
     const int grid = wave_blocks(k_zinv4<R, NZ>, zinv_smem<R, NZ>(), c->num_sms,
                                  (int64_t)(c->ny + 2) * ((c->nxh + W - 1) / W), &occ);
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
     k_zinv4<R, NZ><<<grid, kThreads, zinv_smem<R, NZ>(), c->stream>>>(
-        (const cplx<R>*)c->S, (cplx<R>*)c->F, c->ny, c->nxh, fstride, c->d_sinz, (const cplx<R>*)c->d_twz);
+        (const cplx<R>*)c->S, (cplx<R>*)c->F, c->ny, c->nxh, fstride, c->d_sinz, (const cplx<R>*)c->d_twz,
+        phi_only ? 1 : 0);
 }
 template <class R, int NZ>
 tribo_status attr_z(int optin) {
@@ -689,9 +707,9 @@ bool dispatch_zfwd(tribo_ctx* c) {
     }
 }
 template <class R>
-bool dispatch_zinv(tribo_ctx* c) {
+bool dispatch_zinv(tribo_ctx* c, bool phi_only) {
     switch (c->nz) {
-#define CASE(N) case N: launch_zinv<R, N>(c); return true;
+#define CASE(N) case N: launch_zinv<R, N>(c, phi_only); return true;
         TRIBO_FAST_SIZES(CASE)
 #undef CASE
         default: return false;
@@ -747,7 +765,7 @@ tribo_status solve_fast(tribo_ctx* c, R* src, const double* scale, bool zero_src
     if constexpr (sizeof(R) == 8) {
         k_ysolve64<<<(ni + 127) / 128, 128, 0, c->stream>>>((cplx<double>*)c->S, (cplx<double>*)c->F + fstride,
                                                             (const double2*)c->d_ytab, (double2*)c->W2,
-                                                            c->d_ycoef, c->d_ey, ny, nz, nxh);
+                                                            c->d_ycoef, c->d_ey, ny, nz, nxh, E != nullptr ? 1 : 0);
     } else {
         const float2* tinv = (const float2*)c->d_ytab;
         const float2* tcp = tinv + (size_t)ny * ni;
@@ -766,19 +784,17 @@ tribo_status solve_fast(tribo_ctx* c, R* src, const double* scale, bool zero_src
         // only where the checkpoints fit
         const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
         const size_t sh12 = sizeof(float4) * ((size_t)((ny + 11) / 12) * 128 + ny + 1) + sizeof(float2) * ny;
-        if (few && shc <= (size_t)c->smem_optin) {
-            k_ysolve_chunk<8, true><<<(unsigned)nblk, 128, shc, c->stream>>>(
-                (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
-                (const float4*)c->d_yec, ny, nz, nxh);
-        } else {
-            k_ysolve_chunk<12, false><<<(unsigned)nblk, 128, sh12, c->stream>>>(
-                (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
-                (const float4*)c->d_yec, ny, nz, nxh);
-        }
+        // without E (the adjoint's potential-only solves) the E_y spectrum is not written
+        auto* ys = few && shc <= (size_t)c->smem_optin
+                       ? (E ? k_ysolve_chunk<8, true> : k_ysolve_chunk<8, true, false>)
+                       : (E ? k_ysolve_chunk<12, false> : k_ysolve_chunk<12, false, false>);
+        ys<<<(unsigned)nblk, 128, few && shc <= (size_t)c->smem_optin ? shc : sh12, c->stream>>>(
+            (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
+            (const float4*)c->d_yec, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_INV_Z);
-    dispatch_zinv<R>(c);
+    dispatch_zinv<R>(c, E == nullptr);
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_INV_X);
     dispatch_xinv<R>(c, E, phi);
@@ -873,6 +889,10 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
     TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<12, false>), cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<8, true>), cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<12, false, false>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin));
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<8, true, false>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    optin));
     c->smem_optin = optin;
     return dispatch_attr<float>(nx, nz, optin);
 }

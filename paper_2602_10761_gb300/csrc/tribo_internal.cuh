@@ -206,7 +206,8 @@ tribo_status poisson_free(tribo_ctx* c);
 // src: device (nz, ny, nx) of the real type (charge sums or a density);
 // scale: device ny per-row factor giving the RHS -rho/eps; zero_src: write
 // zeros back into src after reading.  phi may be NULL.  E: (3, nz, ny+2, nx)
-// real (E_x, E_y, E_z).
+// real (E_x, E_y, E_z), or NULL for the potential alone (phi then non-NULL;
+// the generic-length passes still form the field, into the context's E_lat).
 tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src,
                            double* phi, void* E);
 
