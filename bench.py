@@ -295,6 +295,64 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     }
 
 
+def fp64_report(T, torch, c, faces, lat, P, steps=10, sort_every=20):
+    """The mixed-precision path against the plain FP64 GPU path on the full
+    workload: both start from the same state (the FP32-rounded inputs, which
+    FP64 holds exactly) and take `steps` coupled steps.  Per quantity, the
+    largest difference over all particles (matched by id; x and z modulo the
+    box) relative to the quantity's largest FP64 magnitude; the charge over
+    the particles whose impact counts agree; the fractions of particles whose
+    cell or impact count differ; the FP64 path's time per step."""
+    parts = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
+    out, ms = {}, {}
+    for prec in (T.TRIBO_MIXED, T.TRIBO_FP64):
+        real = np.float32 if prec == T.TRIBO_MIXED else np.float64
+        params = T.Params(precision=prec, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0, sort_every=sort_every)
+        ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat.astype(real)).cuda(),
+                       max_particles=c.n_particles)
+        src = {k: (v if k == "q" else np.asarray(v).astype(np.float32).astype(real)) for k, v in parts.items()}
+        Pd = T.Particles.from_numpy(src, prec, device="cuda", with_cell=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ch.step(Pd, c.dt, steps)
+        e1.record()
+        ch.sync()
+        torch.cuda.synchronize()
+        ms[prec] = e0.elapsed_time(e1) / steps
+        o = Pd.to_numpy()
+        ch.close()
+        del Pd
+        order = np.argsort(o["id"])
+        out[prec] = {k: np.asarray(v)[order] for k, v in o.items()}
+    a, b = out[T.TRIBO_MIXED], out[T.TRIBO_FP64]
+    same = a["n_imp"] == b["n_imp"]
+
+    def rel(k, period=None, sel=None):
+        d = a[k].astype(np.float64) - b[k]
+        if period:
+            d = (d + 0.5 * period) % period - 0.5 * period
+        ref = b[k] if sel is None else b[k][sel]
+        d = d if sel is None else d[sel]
+        return float(np.abs(d).max() / max(np.abs(ref).max(), 1e-300)) if d.size else 0.0
+
+    dv = np.sqrt(sum((a[k].astype(np.float64) - b[k]) ** 2 for k in ("vx", "vy", "vz")))
+    sp = np.sqrt(sum(b[k] ** 2 for k in ("vx", "vy", "vz")))
+    return {"steps": steps, "particles": int(len(b["x"])), "fp64_ms_per_step": ms[T.TRIBO_FP64],
+            "mixed_ms_per_step": ms[T.TRIBO_MIXED],
+            "rel_err": {"x": rel("x", c.lx), "y": rel("y"), "z": rel("z", c.lz), "vx": rel("vx"), "vy": rel("vy"),
+                        "vz": rel("vz"), "q_same_impacts": rel("q", sel=same)},
+            "velocity_rel_err_per_particle_max": float((dv / np.maximum(sp, 1e-300)).max()),
+            "max_abs_fp64": {k: float(np.abs(b[k]).max()) for k in ("vx", "vy", "vz")},
+            "note": ("positions against the box, each velocity component and the charge against its largest FP64 "
+                     "magnitude; v_y and v_z start at 0 (the particles leave at the local mean gas velocity) and "
+                     "stay small against v_x over 10 steps (max_abs_fp64), so their errors show the FP32 position "
+                     "resolution (u_R x/dx, 2.3e-5 of a cell at x = L_x) rather than the step's arithmetic"),
+            "impact_mismatch_frac": float(1.0 - same.mean()),
+            "cell_mismatch_frac": float((a["cell"] != b["cell"]).mean()),
+            "impacts_fp64": int(b["n_imp"].sum())}
+
+
 def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world=1, channels=64, scale=1.0):
     """Batched ensemble of 64 independent channels (Re_tau in {180, 300, 395,
     550}, grids 64^3 to 192x128x128, 50k-2M particles each, d+ in [0.5, 3]):
@@ -349,6 +407,7 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
     for ch in chans:
         ch.close()
     seq_ms = max_over_ranks(seq_ms, "cuda")
+    check = batch_vs_fp64(T, torch, sorted(cases, key=lambda c: c.n_particles)[:2]) if rank == 0 else None
     ntot = sum(c.n_particles for c in all_cases)
     batch_rate = ntot * steps / (batch_ms * 1e-3)
     seq_rate = ntot * seq_steps / (seq_ms * 1e-3)
@@ -357,7 +416,57 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
             "steps": steps, "ms_per_step": batch_ms / steps, "particle_steps_per_s": batch_rate,
             "sequential_particle_steps_per_s": seq_rate, "sequential_steps": seq_steps,
             "speedup_vs_sequential": batch_rate / seq_rate, "autotuned_shape": shape, "autotune_s": tune_s,
-            "kernels_per_step": launches / steps}
+            "kernels_per_step": launches / steps, "vs_fp64_gpu": check}
+
+
+def batch_vs_fp64(T, torch, cases, steps=10, sort_every=5):
+    """Channels stepped together as one mixed-precision batch against each
+    stepped alone on the plain FP64 GPU path, from the same FP32-rounded state:
+    the largest position and velocity differences relative to each quantity's
+    largest FP64 magnitude, and the fraction of particles whose impact count
+    differs, over all the channels' particles."""
+    res = {"channels": [c.name for c in cases], "steps": steps}
+    err = {k: 0.0 for k in ("x", "y", "z", "vx", "vy", "vz")}
+    mism = n = 0
+    outs = {T.TRIBO_MIXED: [], T.TRIBO_FP64: []}
+    for prec in (T.TRIBO_MIXED, T.TRIBO_FP64):
+        real = np.float32 if prec == T.TRIBO_MIXED else np.float64
+        chans, Ps = [], []
+        for c in cases:
+            faces = synth.y_faces(c.ny, c.delta, c.gamma)
+            lat = synth.fluid_lattice(c, faces=faces).astype(np.float32).astype(real)
+            params = T.Params(precision=prec, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0, sort_every=sort_every)
+            chans.append(T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(),
+                                   max_particles=c.n_particles))
+            P = synth.draw_particles(c)
+            src = dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q)
+            Ps.append(T.Particles.from_numpy({k: (v if k == "q" else np.asarray(v).astype(np.float32).astype(real))
+                                              for k, v in src.items()}, prec, device="cuda"))
+        if prec == T.TRIBO_MIXED:
+            B = T.Batch(chans, sort_every=sort_every)
+            B.step(Ps, [c.dt for c in cases], steps)
+            B.sync()
+            B.close()
+        else:
+            for ch, P, c in zip(chans, Ps, cases):
+                ch.step(P, c.dt, steps)
+                ch.sync()
+        for ch, P in zip(chans, Ps):
+            o = P.to_numpy()
+            order = np.argsort(o["id"])
+            outs[prec].append({k: np.asarray(v)[order] for k, v in o.items()})
+            ch.close()
+    for c, a, b in zip(cases, outs[T.TRIBO_MIXED], outs[T.TRIBO_FP64]):
+        for k in err:
+            d = a[k].astype(np.float64) - b[k]
+            if k in ("x", "z"):
+                L = c.lx if k == "x" else c.lz
+                d = (d + 0.5 * L) % L - 0.5 * L
+            err[k] = max(err[k], float(np.abs(d).max() / max(np.abs(b[k]).max(), 1e-300)))
+        mism += int((a["n_imp"] != b["n_imp"]).sum())
+        n += len(b["x"])
+    res.update(rel_err=err, impact_mismatch_frac=mism / max(n, 1), particles=n)
+    return res
 
 
 def timevarying_report(T, torch, steps=200, sort_every=20):
@@ -491,6 +600,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=100_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the mixed vs FP64 GPU comparison")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-timevarying", action="store_true")
     ap.add_argument("--no-interactions", action="store_true")
@@ -633,6 +743,9 @@ def main():
         "clocks": clocks,
     }
     ch.close()
+    del Pd
+    if rank == 0 and world == 1 and not args.no_fp64:
+        line["vs_fp64_gpu"] = fp64_report(T, torch, c, faces, lat, P, sort_every=args.sort_every)
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_report(T, torch, steps=args.adj_steps, ckpt=args.adj_ckpt)
     if rank == 0 and world == 1 and not args.no_interactions:
