@@ -512,8 +512,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);   // exp(-2 pi i e / NX)
     cplx<R>* buf = tw + NX;
-    R* sx = reinterpret_cast<R*>(buf + F4::BUF);
+    cplx<R>* t2 = buf + F4::BUF;    // t2[k1 N2 + r] = W_M^(r k1): consecutive in r, no bank conflicts
+    R* sx = reinterpret_cast<R*>(t2 + N1 * N2);
     for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = tw_g[i];
+    for (int i = threadIdx.x; i < N1 * N2; i += kThreads) t2[i] = tw_g[2 * (i % N2) * (i / N2)];
     for (int i = threadIdx.x; i < NXH; i += kThreads) sx[i] = from_f64<R>(sinx[i]);
     __syncthreads();
     const int nyn = ny + 2;
@@ -547,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
             }
             fft::reg_dft<R, 1, N1, 2 * N2>(y, tw);
 #pragma unroll
-            for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * conj(tw[2 * r * k1]);
+            for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * conj(t2[k1 * N2 + r]);
             cplx<R>* b = buf + l * CS + r * (N1 + 1);
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) b[k1] = y[k1];
@@ -594,7 +596,8 @@ template <class R, int M>
 size_t xfwd_smem() { return sizeof(cplx<R>) * (2 * M + fft::FourStep<M, kThreads>::BUF); }
 template <class R, int M>
 size_t xinv_smem() {
-    return sizeof(cplx<R>) * (2 * M + fft::FourStep<M, kThreads>::BUF) + sizeof(R) * (M + 1);
+    using F4 = fft::FourStep<M, kThreads>;
+    return sizeof(cplx<R>) * (2 * M + F4::BUF + F4::N1 * F4::N2) + sizeof(R) * (M + 1);
 }
 template <class R, int NZ>
 size_t zfwd_smem() { return sizeof(cplx<R>) * (NZ + fft::FourStep<NZ, kThreads>::BUF); }
