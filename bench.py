@@ -675,22 +675,21 @@ def main():
         v = getattr(Pd, k).cpu().pin_memory().numpy()
         host[k] = v.view(np.uint32) if k in ("n_imp", "id") else v
     Ph = T.Particles(**host)
-    # the ids move only in the calls that sort (the step count before the call a multiple of
-    # sort_every); the average over the timed calls is reported
-    done = args.warmup + args.steps + 1
-    sorting = sum(1 for i in range(args.e2e_steps)
-                  if args.sort_every > 0 and (done + i) % args.sort_every == 0) / max(args.e2e_steps, 1)
-    h2d = sum(host[k].nbytes for k in ("x", "y", "z", "vx", "vy", "vz", "d", "q", "q_wall", "n_imp"))
-    d2h = sum(host[k].nbytes for k in ("x", "y", "z", "vx", "vy", "vz", "q", "q_wall", "n_imp"))
-    h2d += int(host["id"].nbytes * sorting)
-    d2h += int(host["id"].nbytes * sorting)
+    # the bytes moved are the library's own count of the copies it issued (tribo_transfer_bytes):
+    # every state array in; positions and velocities out, with q, q_wall, n_imp only of the
+    # particles an impact changed, except in the call that sorts (the ids move then, and every
+    # array comes back); the average over the timed calls is reported
     ch.step(Ph, c.dt, 1)
     if world > 1:
         dist.barrier()
+    b0 = T.tribo_transfer_bytes(ch.ctx)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         ch.step(Ph, c.dt, 1)          # copies in, one step, copies out, synchronises
     e2e_s = time.perf_counter() - t0
+    b1 = T.tribo_transfer_bytes(ch.ctx)
+    h2d = (b1[0] - b0[0]) // max(args.e2e_steps, 1)
+    d2h = (b1[1] - b0[1]) // max(args.e2e_steps, 1)
     e2e_s = max_over_ranks(e2e_s, "cuda")
     e2e_value = aggregate_rate(c.n_particles, args.e2e_steps, e2e_s, world)
 

@@ -238,8 +238,17 @@ tribo_status tribo_set_params(tribo_ctx* ctx, const tribo_params* params);
 
 /* Advance the particles nsteps coupled steps of length dt [s].  Device
  * pointers: asynchronous on the context's stream.  Host pointers: copies in,
- * steps, copies out and synchronises before returning. */
+ * steps, copies out and synchronises before returning; every host array then
+ * holds the new state.  A host call that does not re-sort (and has no pair
+ * interactions) sends back the positions and velocities of all particles
+ * and q, q_wall, n_imp only of those whose impact count changed: the others'
+ * values are unchanged, and the caller's arrays already hold them. */
 tribo_status tribo_step(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t nsteps);
+
+/* Bytes the host-pointer calls of this context have moved across the host
+ * link since tribo_init: host to device and device to host (the sum of the
+ * copies issued).  Either pointer may be NULL. */
+tribo_status tribo_transfer_bytes(tribo_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
 
 /* Standalone Poisson solve and field (step 2 above).  rho: device
  * (Nz, Ny, Nx) double charge density [C/m^3].  phi: device (Nz, Ny, Nx)

@@ -71,6 +71,7 @@ _SIGS = {
     "tribo_set_ssm": (C.c_int32, [C.c_void_p, C.POINTER(tribo_ssm)]),
     "tribo_set_momentum_source": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "tribo_set_adjoint_memory": (C.c_int32, [C.c_void_p, C.c_int64]),
+    "tribo_transfer_bytes": (C.c_int32, [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "tribo_eval_modes": (C.c_int32, [C.c_void_p, C.c_double, C.c_void_p]),
     "tribo_step": (C.c_int32, [C.c_void_p, C.POINTER(tribo_particles), C.c_double, C.c_int32]),
     "tribo_poisson": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),

@@ -232,6 +232,14 @@ def tribo_set_adjoint_memory(ctx: int, max_bytes: int = -1) -> None:
     check(load().tribo_set_adjoint_memory(ctx, int(max_bytes)), "tribo_set_adjoint_memory")
 
 
+def tribo_transfer_bytes(ctx: int) -> tuple:
+    """(host to device, device to host) bytes the context's host-pointer calls
+    have moved since tribo_init."""
+    h2d, d2h = C.c_uint64(0), C.c_uint64(0)
+    check(load().tribo_transfer_bytes(ctx, C.byref(h2d), C.byref(d2h)), "tribo_transfer_bytes")
+    return int(h2d.value), int(d2h.value)
+
+
 def tribo_set_params(ctx: int, params: Params) -> None:
     p = params.to_c()
     check(load().tribo_set_params(ctx, C.byref(p)), "tribo_set_params")

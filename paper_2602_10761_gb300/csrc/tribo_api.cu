@@ -27,6 +27,31 @@ __global__ void k_round_to_float(const double* __restrict__ src, float* __restri
         dst[i] = (float)src[i];
 }
 
+// A host call's list of the particles whose impact count changed (their q,
+// q_wall, n_imp are the only ones of those arrays that moved): a 16-byte
+// header holding the count, then the entries.
+struct PatchEntry {
+    uint32_t i, n_imp;
+    double q, q_wall;
+};
+constexpr size_t kPatchHeader = 16;
+constexpr int64_t kPatchHost = 4096;       // entries sent back with the count in one copy
+constexpr int kChunks = 4;                 // a host call's last step runs in this many particle ranges
+
+__global__ void k_patch(const uint32_t* __restrict__ n_imp, const uint32_t* __restrict__ n_imp0,
+                        const double* __restrict__ q, const double* __restrict__ q_wall, int64_t n,
+                        unsigned char* __restrict__ list, unsigned int cap) {
+    unsigned int* count = reinterpret_cast<unsigned int*>(list);
+    PatchEntry* out = reinterpret_cast<PatchEntry*>(list + kPatchHeader);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t m = n_imp[i];
+        if (m != n_imp0[i]) {
+            const unsigned int k = atomicAdd(count, 1u);
+            if (k < cap) out[k] = PatchEntry{(uint32_t)i, m, q[i], q_wall[i]};
+        }
+    }
+}
+
 bool is_2a3b(int n) {
     if (n < 1) return false;
     while (n % 2 == 0) n /= 2;
@@ -137,6 +162,7 @@ tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particle
         if (!host) return TRIBO_OK;
         if (to_device) TRIBO_CUDA(cudaMemcpyAsync(dev, host, elem * n, kind, stream));
         else TRIBO_CUDA(cudaMemcpyAsync(host, dev, elem * n, kind, stream));
+        (to_device ? c->h2d_bytes : c->d2h_bytes) += elem * n;
         return TRIBO_OK;
     };
     tribo_status st;
@@ -178,22 +204,76 @@ PView sub_view(const tribo_ctx* c, const PView& v, int64_t a0, int64_t n) {
 }
 
 // the state arrays of device particles `part` back into the caller's host arrays at a0
+// (states_only: positions, velocities and cells, not q, q_wall, n_imp)
 tribo_status copy_back_range(tribo_ctx* c, const PView& part, const tribo_particles* host, int64_t a0, bool with_id,
-                             cudaStream_t stream) {
+                             bool states_only, cudaStream_t stream) {
     const size_t rs = real_size(c);
     const size_t n = (size_t)part.n;
     auto cp = [&](void* h, const void* d, size_t elem) -> tribo_status {
         if (!h || !d) return TRIBO_OK;
         TRIBO_CUDA(cudaMemcpyAsync((char*)h + (size_t)a0 * elem, d, elem * n, cudaMemcpyDeviceToHost, stream));
+        c->d2h_bytes += elem * n;
         return TRIBO_OK;
     };
     tribo_status st;
     if ((st = cp(host->x, part.x, rs)) || (st = cp(host->y, part.y, rs)) || (st = cp(host->z, part.z, rs)) ||
         (st = cp(host->vx, part.vx, rs)) || (st = cp(host->vy, part.vy, rs)) || (st = cp(host->vz, part.vz, rs)) ||
-        (st = cp(host->q, part.q, sizeof(double))) || (st = cp(host->q_wall, part.q_wall, sizeof(double))) ||
-        (st = cp(host->n_imp, part.n_imp, sizeof(uint32_t))) ||
+        (!states_only && ((st = cp(host->q, part.q, sizeof(double))) ||
+                          (st = cp(host->q_wall, part.q_wall, sizeof(double))) ||
+                          (st = cp(host->n_imp, part.n_imp, sizeof(uint32_t))))) ||
         (with_id && (st = cp(host->id, part.id, sizeof(uint32_t)))) || (st = cp(host->cell, part.cell, sizeof(uint32_t))))
         return st;
+    return TRIBO_OK;
+}
+
+// the arrays of the caller's particles [a0, a0 + part.n) that the deposit does not need
+// (group 2 of copy_particles) into device particles `part`
+tribo_status copy_rest_range(tribo_ctx* c, const PView& part, const tribo_particles* host, int64_t a0, bool with_id,
+                             cudaStream_t stream) {
+    const size_t rs = real_size(c);
+    const size_t n = (size_t)part.n;
+    auto cp = [&](void* d, const void* h, size_t elem) -> tribo_status {
+        if (!h || !d) return TRIBO_OK;
+        TRIBO_CUDA(cudaMemcpyAsync(d, (const char*)h + (size_t)a0 * elem, elem * n, cudaMemcpyHostToDevice, stream));
+        c->h2d_bytes += elem * n;
+        return TRIBO_OK;
+    };
+    tribo_status st;
+    if ((st = cp(part.vx, host->vx, rs)) || (st = cp(part.vy, host->vy, rs)) || (st = cp(part.vz, host->vz, rs)) ||
+        (st = cp(part.d, host->d, rs)) || (st = cp(part.q_wall, host->q_wall, sizeof(double))) ||
+        (st = cp(part.n_imp, host->n_imp, sizeof(uint32_t))) ||
+        (with_id && (st = cp(part.id, host->id, sizeof(uint32_t)))))
+        return st;
+    return TRIBO_OK;
+}
+
+// After a host call in patch mode (stream idle): write the listed particles'
+// q, q_wall, n_imp into the caller's arrays; a list longer than its capacity
+// gives way to copying the three arrays whole.
+tribo_status apply_patch(tribo_ctx* c, const PView& dev, const tribo_particles* host) {
+    const int64_t cnt = *static_cast<const unsigned int*>(c->patch_host);
+    const int64_t hn = std::min<int64_t>(c->patch_cap, kPatchHost);
+    const size_t n = (size_t)dev.n;
+    if (cnt > c->patch_cap) {
+        TRIBO_CUDA(cudaMemcpy(host->q, dev.q, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        TRIBO_CUDA(cudaMemcpy(host->q_wall, dev.q_wall, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        TRIBO_CUDA(cudaMemcpy(host->n_imp, dev.n_imp, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+        c->d2h_bytes += (2 * sizeof(double) + sizeof(uint32_t)) * n;
+        return TRIBO_OK;
+    }
+    unsigned char* hl = static_cast<unsigned char*>(c->patch_host) + kPatchHeader;
+    if (cnt > hn) {
+        const size_t off = sizeof(PatchEntry) * (size_t)hn, len = sizeof(PatchEntry) * (size_t)(cnt - hn);
+        TRIBO_CUDA(cudaMemcpy(hl + off, static_cast<unsigned char*>(c->patch) + kPatchHeader + off, len,
+                              cudaMemcpyDeviceToHost));
+        c->d2h_bytes += len;
+    }
+    const PatchEntry* e = reinterpret_cast<const PatchEntry*>(hl);
+    for (int64_t k = 0; k < cnt; ++k) {
+        host->q[e[k].i] = e[k].q;
+        host->q_wall[e[k].i] = e[k].q_wall;
+        host->n_imp[e[k].i] = e[k].n_imp;
+    }
     return TRIBO_OK;
 }
 
@@ -279,14 +359,18 @@ void free_ctx(tribo_ctx* c) {
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
                     c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner, c->d_inv_vol,
-                    c->adj_E};
+                    c->adj_E, c->n_imp0, c->patch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->copy_done) cudaEventDestroy(c->copy_done);
     for (cudaEvent_t e : c->chunk_done)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->rest_done)
+        if (e) cudaEventDestroy(e);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->back_stream) cudaStreamDestroy(c->back_stream);
+    if (c->patch_host) cudaFreeHost(c->patch_host);
     cudaSetDevice(prev);
     delete c;
 }
@@ -538,6 +622,21 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             TRIBO_CUDA(cudaMalloc((void**)&c->pp_partner, sizeof(uint32_t) * c->max_particles));
         }
     }
+    // host call without a re-sort or pair interactions: q, q_wall and n_imp come back only for
+    // the particles an impact changed (the caller's arrays hold the others already)
+    const bool patch = p->on_host && !sorts && !near && !collide;
+    // ... and when that call's one step is also its last, it runs in chunks that each wait only
+    // for their own particles' arrays, so the copies back overlap the copies in
+    const bool one_chunked = patch && nsteps == 1;
+    if (patch && !c->n_imp0) {
+        TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+        const int64_t cap = std::max<int64_t>(1024, c->max_particles / 8);
+        const size_t bytes = kPatchHeader + sizeof(PatchEntry) * (size_t)cap;
+        TRIBO_CUDA(cudaMalloc((void**)&c->n_imp0, sizeof(uint32_t) * c->max_particles));
+        TRIBO_CUDA(cudaMalloc(&c->patch, bytes));
+        TRIBO_CUDA(cudaHostAlloc(&c->patch_host, bytes, cudaHostAllocDefault));
+        c->patch_cap = cap;
+    }
     PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
     bool rest_pending = false;       // host call: the arrays the solve does not need are still in flight
     if (p->on_host) {
@@ -547,8 +646,10 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         if (!p->cell) v.cell = nullptr;
         if (!c->copy_stream) {
             TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+            TRIBO_CUDA(cudaStreamCreateWithFlags(&c->back_stream, cudaStreamNonBlocking));
             TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
             for (cudaEvent_t& e : c->chunk_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            for (cudaEvent_t& e : c->rest_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         }
         // what the deposit needs first, on the compute stream; the rest beside it on the copy
         // stream (after the work already queued on the compute stream), awaited before its first use
@@ -558,11 +659,25 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         }
         TRIBO_CUDA(cudaEventRecord(c->copy_done, c->stream));
         TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_done, 0));
-        if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) {
+        if (one_chunked) {
+            // in the ranges the step's chunks take, each recorded as it lands
+            for (int ci = 0; ci < kChunks; ++ci) {
+                const int64_t a0 = p->n * ci / kChunks, a1 = p->n * (ci + 1) / kChunks;
+                if (a1 > a0 && (st = copy_rest_range(c, sub_view(c, v, a0, a1 - a0), p, a0, ids, c->copy_stream))) {
+                    cudaStreamSynchronize(c->copy_stream);
+                    cudaStreamSynchronize(c->stream);
+                    return st;
+                }
+                TRIBO_CUDA(cudaEventRecord(c->rest_done[ci], c->copy_stream));
+            }
+        } else if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) {
             cudaStreamSynchronize(c->copy_stream);
             cudaStreamSynchronize(c->stream);
             return st;
         }
+        if (patch)
+            TRIBO_CUDA(cudaMemcpyAsync(c->n_imp0, v.n_imp, sizeof(uint32_t) * (size_t)p->n, cudaMemcpyDeviceToDevice,
+                                       c->copy_stream));
         TRIBO_CUDA(cudaEventRecord(c->copy_done, c->copy_stream));
         rest_pending = true;
     }
@@ -607,7 +722,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             if (electro) {
                 if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
             }
-            if ((st = await_rest())) return st;
+            if (!one_chunked && (st = await_rest())) return st;
             if (near) {
                 if ((!lists_fresh && (st = particles_cell_lists(c, cur, c->nf_members))) ||
                     (st = particles_coulomb(c, cur, c->nf_members, c->nf_acc)))
@@ -618,15 +733,29 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             // chunks, each chunk's arrays sent back on the copy stream while the next one runs
             const bool chunked = p->on_host && last && !near && !collide;
             if (chunked) {
-                constexpr int K = 4;
-                for (int ci = 0; ci < K; ++ci) {
-                    const int64_t a0 = cur.n * ci / K, a1 = cur.n * (ci + 1) / K;
+                for (int ci = 0; ci < kChunks; ++ci) {
+                    const int64_t a0 = cur.n * ci / kChunks, a1 = cur.n * (ci + 1) / kChunks;
+                    if (one_chunked) TRIBO_CUDA(cudaStreamWaitEvent(c->stream, c->rest_done[ci], 0));
                     if (a1 <= a0) continue;
                     const PView part = sub_view(c, cur, a0, a1 - a0);
                     if ((st = particles_step(c, part, dt, false, want_cell, io))) return st;
                     TRIBO_CUDA(cudaEventRecord(c->chunk_done[ci], c->stream));
-                    TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->chunk_done[ci], 0));
-                    if ((st = copy_back_range(c, part, p, a0, sorts && part.id != nullptr, c->copy_stream))) return st;
+                    TRIBO_CUDA(cudaStreamWaitEvent(c->back_stream, c->chunk_done[ci], 0));
+                    if ((st = copy_back_range(c, part, p, a0, sorts && part.id != nullptr, patch, c->back_stream)))
+                        return st;
+                }
+                if (patch) {
+                    if ((st = await_rest())) return st;     // n_imp as it arrived
+                    // the changed particles' list, its count and first entries in one copy
+                    TRIBO_CUDA(cudaMemsetAsync(c->patch, 0, kPatchHeader, c->stream));
+                    const int blocks = (int)std::min<int64_t>((cur.n + 255) / 256, (int64_t)c->num_sms * 8);
+                    k_patch<<<blocks, 256, 0, c->stream>>>(cur.n_imp, c->n_imp0, cur.q, cur.q_wall, cur.n,
+                                                           (unsigned char*)c->patch, (unsigned int)c->patch_cap);
+                    TRIBO_LAUNCHED(c);
+                    const size_t hb = kPatchHeader + sizeof(PatchEntry) * (size_t)std::min<int64_t>(c->patch_cap,
+                                                                                                    kPatchHost);
+                    TRIBO_CUDA(cudaMemcpyAsync(c->patch_host, c->patch, hb, cudaMemcpyDeviceToHost, c->stream));
+                    c->d2h_bytes += hb;
                 }
                 sent_back = true;
             } else if ((st = particles_step(c, cur, dt, electro && !last, want_cell && last, io))) {
@@ -644,7 +773,12 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         c->n_samples += nsteps;
         if (sent_back) {
             // the arrays went back from the set that holds them, chunk by chunk
+            TRIBO_CUDA(cudaStreamSynchronize(c->back_stream));
             TRIBO_CUDA(cudaStreamSynchronize(c->copy_stream));
+            if (patch) {
+                TRIBO_CUDA(cudaStreamSynchronize(c->stream));
+                if ((st = apply_patch(c, cur, p))) return st;
+            }
             return sync_and_check(c);
         }
         if (cur.x != home.x) {
@@ -661,9 +795,17 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     st = run();
     if (st && p->on_host && c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
+        cudaStreamSynchronize(c->back_stream);
         cudaStreamSynchronize(c->stream);
     }
     return st;
+}
+
+tribo_status tribo_transfer_bytes(tribo_ctx* c, uint64_t* h2d, uint64_t* d2h) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    if (h2d) *h2d = c->h2d_bytes;
+    if (d2h) *d2h = c->d2h_bytes;
+    return TRIBO_OK;
 }
 
 tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E) {

@@ -80,6 +80,15 @@ struct tribo_ctx {
     cudaStream_t copy_stream = nullptr;  // host-pointer calls: the particle arrays the solve does not need
     cudaEvent_t copy_done = nullptr;     // ... recorded when they have landed
     cudaEvent_t chunk_done[4] = {};      // host calls: chunks of the last step, sent back as they finish
+    cudaEvent_t rest_done[4] = {};       // ... the rest of their arrays landed, chunk by chunk
+    cudaStream_t back_stream = nullptr;  // ... the copies back (beside the copies in: both directions)
+    // host calls that do not re-sort: n_imp as it arrived, and the list of the particles whose
+    // impact count changed (16-byte count header, then entries; device and pinned host copies)
+    uint32_t* n_imp0 = nullptr;
+    void* patch = nullptr;
+    void* patch_host = nullptr;
+    int64_t patch_cap = 0;
+    uint64_t h2d_bytes = 0, d2h_bytes = 0;   // host-call traffic across the host link
     int prec = TRIBO_FP64;
     tribo_params P{};
     int nx = 0, ny = 0, nz = 0, nxh = 0;
