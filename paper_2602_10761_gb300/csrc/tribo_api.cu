@@ -661,6 +661,8 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         TRIBO_CUDA(cudaStreamWaitEvent(c->copy_stream, c->copy_done, 0));
         if (one_chunked) {
             // in the ranges the step's chunks take, each recorded as it lands
+            // (n_imp as it arrived is copied with each range, before the range's chunk of the step
+            // may run and count impacts)
             for (int ci = 0; ci < kChunks; ++ci) {
                 const int64_t a0 = p->n * ci / kChunks, a1 = p->n * (ci + 1) / kChunks;
                 if (a1 > a0 && (st = copy_rest_range(c, sub_view(c, v, a0, a1 - a0), p, a0, ids, c->copy_stream))) {
@@ -668,16 +670,22 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                     cudaStreamSynchronize(c->stream);
                     return st;
                 }
+                if (a1 > a0)
+                    TRIBO_CUDA(cudaMemcpyAsync(c->n_imp0 + a0, v.n_imp + a0, sizeof(uint32_t) * (size_t)(a1 - a0),
+                                               cudaMemcpyDeviceToDevice, c->copy_stream));
                 TRIBO_CUDA(cudaEventRecord(c->rest_done[ci], c->copy_stream));
             }
-        } else if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) {
-            cudaStreamSynchronize(c->copy_stream);
-            cudaStreamSynchronize(c->stream);
-            return st;
+        } else {
+            if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) {
+                cudaStreamSynchronize(c->copy_stream);
+                cudaStreamSynchronize(c->stream);
+                return st;
+            }
+            // the first step waits for copy_done, recorded after this copy
+            if (patch)
+                TRIBO_CUDA(cudaMemcpyAsync(c->n_imp0, v.n_imp, sizeof(uint32_t) * (size_t)p->n,
+                                           cudaMemcpyDeviceToDevice, c->copy_stream));
         }
-        if (patch)
-            TRIBO_CUDA(cudaMemcpyAsync(c->n_imp0, v.n_imp, sizeof(uint32_t) * (size_t)p->n, cudaMemcpyDeviceToDevice,
-                                       c->copy_stream));
         TRIBO_CUDA(cudaEventRecord(c->copy_done, c->copy_stream));
         rest_pending = true;
     }

@@ -89,3 +89,35 @@ def test_transfer_bytes_of_host_calls():
     # device arrays: nothing crosses
     _, nb, _ = _run(c, faces, lat, parts, T.TRIBO_MIXED, host=False, calls=1)
     assert nb == (0, 0)
+
+
+def test_pinned_host_call_with_slow_copies_keeps_every_impact():
+    """Pinned host arrays (the copies run asynchronously) and a tiny grid (the
+    field solve ends long before the last range of the arrays has landed): the
+    first ranges' chunks of the step run while later ranges are still being
+    copied, and the impact counts they add must all come back."""
+    n = 4_000_000
+    c, faces, lat, parts = problem(16, 12, 8, n=n, q_scale=1e-13, vy_scale=0.2, near_wall=0.01, seed=34)
+    a, _, changed = _run(c, faces, lat, parts, T.TRIBO_MIXED, host=False, calls=1)
+    params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1e3, sort_every=0)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat.astype(np.float32)).cuda(),
+                   max_particles=n)
+    Pd = T.Particles.from_numpy(parts, T.TRIBO_MIXED, device="cuda")
+    host = {}
+    for k in ("x", "y", "z", "vx", "vy", "vz", "d", "q", "q_wall", "n_imp", "id"):
+        v = getattr(Pd, k).cpu().pin_memory().numpy()
+        host[k] = v.view(np.uint32) if k in ("n_imp", "id") else v
+    del Pd
+    Ph = T.Particles(**host)
+    ch.step(Ph, c.dt, 1)
+    ch.sync()
+    ch.close()
+    order = np.argsort(host["id"])
+    b = {k: np.asarray(v)[order] for k, v in host.items()}
+    assert changed[0] > 20000                     # impacts in every range, the first included
+    first = np.arange(n) < n // 4
+    assert (a["n_imp"][first] > 0).sum() > 1000
+    assert np.array_equal(a["n_imp"], b["n_imp"])
+    for k in ("q", "q_wall"):
+        s = max(np.abs(a[k]).max(), 1e-300)
+        assert np.abs(a[k] - b[k]).max() <= 1e-5 * s, k
