@@ -346,7 +346,8 @@ tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps, int32_t p
  * over all channels' particles; steps are captured into a CUDA graph and
  * replayed.  The channels must share precision and device and use frozen
  * gas lattices (no tribo_set_modes).  While a batch exists, its channels must
- * not be stepped on their own concurrently with it.  sort_every: re-sort each
+ * not be stepped or solved (tribo_step, tribo_poisson, tribo_adjoint) on their
+ * own concurrently with it: they share the channel's work arrays.  sort_every: re-sort each
  * channel's particles by cell every this many batch steps (0 = never).
  * stream: a cudaStream_t (NULL = legacy default) on which the batch joins. */
 typedef struct tribo_batch tribo_batch;
