@@ -69,8 +69,13 @@ __device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
 // four-step, X_m = (Z_m + conj Z_M-m)/2 - (i/2) W^m (Z_m - conj Z_M-m) for
 // m = 0..M.  Each thread zeroes the charge sums it has read.  The sums have
 // the real type R (a caller's FP64 density is rounded to R beforehand).
+// six resident blocks (40 registers) where the length fits them without spilling: FP32 up to
+// M = 192 (76 -> 75.8 us at 384x256x256); one otherwise
 template <class R, int M>
-__global__ void __launch_bounds__(kThreads) k_xfwd4(R* __restrict__ src, const double* __restrict__ scale_row,
+constexpr int xfwd_min_blocks() { return sizeof(R) == 4 && M <= 192 ? 6 : 1; }
+
+template <class R, int M>
+__global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(R* __restrict__ src, const double* __restrict__ scale_row,
                                                     int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
                                                     const cplx<R>* __restrict__ tw_g) {
     using F4 = fft::FourStep<M, kThreads>;
