@@ -48,3 +48,71 @@ def test_fit_rate_window():
 
 def test_wall_units():
     assert abs(cor.t_plus(1.0, 0.1314, 1.46e-5) - 0.1314 ** 2 / 1.46e-5) < 1e-9
+
+
+class _FakeChannel:
+    """Host stand-in for a Channel: the mean charge after the run is
+    J = a * U_c + b * kappa_A (linear, as the condenser charge is in U_c and
+    kappa_A), with the exact derivatives as the adjoint would return them."""
+
+    def __init__(self, a=3e-17, b=-2e-17, U_c=100.0, kappa_A=1.0):
+        from paper_2602_10761_gb300 import Params
+        self.a, self.b = a, b
+        self.params = Params(U_c=U_c, kappa_A=kappa_A)
+        self.calls = 0
+
+    def set_params(self, p):
+        self.params = p
+
+    def adjoint(self, particles, dt, nsteps, ckpt_every, want_dd=True):
+        self.calls += 1
+        J = self.a * self.params.U_c + self.b * self.params.kappa_A
+        return J, self.a, self.b, None
+
+
+@pytest.mark.parametrize("param,true", [("U_c", 2e3), ("kappa_A", 1.7)])
+def test_calibrate_newton_on_a_linear_charge(param, true):
+    ch = _FakeChannel()
+    target = (ch.a * true + ch.b * ch.params.kappa_A if param == "U_c"
+              else ch.a * ch.params.U_c + ch.b * true)
+    theta, hist = cor.calibrate(ch, lambda: None, 1e-5, 10, target, param=param, iters=5, rtol=1e-12)
+    # one Newton correction is exact for a linear J; the second evaluation confirms it
+    assert abs(theta / true - 1) < 1e-12
+    assert len(hist) == 2 and ch.calls == 2
+    assert getattr(ch.params, param) == theta
+
+
+def test_calibrate_rejects_a_flat_charge_and_unknown_parameters():
+    ch = _FakeChannel(a=0.0)
+    with pytest.raises(ArithmeticError):
+        cor.calibrate(ch, lambda: None, 1e-5, 10, 1e-15, param="U_c")
+    with pytest.raises(ValueError):
+        cor.calibrate(_FakeChannel(), lambda: None, 1e-5, 10, 1e-15, param="rho_p")
+
+
+class _FakeStepper:
+    """Host stand-in for charging_history: every step adds dq to each charge."""
+
+    def __init__(self, n, dq):
+        self.n, self.dq, self.q, self.steps = n, dq, 0.0, []
+
+    def stats(self, particles):
+        return {"sum_q": self.q * self.n}
+
+    def step(self, particles, dt, k):
+        self.steps.append(k)
+        self.q += self.dq * k
+
+
+def test_charging_history_samples_and_rate():
+    class P:
+        n = 1000
+    ch = _FakeStepper(P.n, dq=1e-19)
+    dt, u_tau, nu = 4.2e-5, 0.1314, 1.46e-5
+    tp, qrel = cor.charging_history(ch, P, dt, 25, 10, u_tau, nu)
+    assert ch.steps == [10, 10, 5]                 # the last chunk is the remainder
+    assert np.allclose(tp, cor.t_plus(np.array([0, 10, 20, 25]) * dt, u_tau, nu))
+    assert np.allclose(qrel, np.array([0, 10, 20, 25]) * 1e-19 / cor.Q_SAT)
+    # a constant rate per step gives the slope dq / (Q_SAT dt+) exactly
+    slope = cor.fit_rate(tp, qrel)
+    assert abs(slope / (1e-19 / cor.Q_SAT / (dt * u_tau ** 2 / nu)) - 1) < 1e-10
