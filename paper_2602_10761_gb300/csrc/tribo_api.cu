@@ -628,13 +628,14 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     // ... and when that call's one step is also its last, it runs in chunks that each wait only
     // for their own particles' arrays, so the copies back overlap the copies in
     const bool one_chunked = patch && nsteps == 1;
-    if (patch && !c->n_imp0) {
+    if (patch && !(c->n_imp0 && c->patch && c->patch_host)) {
+        // each buffer on its own, so that a failed allocation is retried by the next call
         TRIBO_CUDA(cudaStreamSynchronize(c->stream));
         const int64_t cap = std::max<int64_t>(1024, c->max_particles / 8);
         const size_t bytes = kPatchHeader + sizeof(PatchEntry) * (size_t)cap;
-        TRIBO_CUDA(cudaMalloc((void**)&c->n_imp0, sizeof(uint32_t) * c->max_particles));
-        TRIBO_CUDA(cudaMalloc(&c->patch, bytes));
-        TRIBO_CUDA(cudaHostAlloc(&c->patch_host, bytes, cudaHostAllocDefault));
+        if (!c->n_imp0) TRIBO_CUDA(cudaMalloc((void**)&c->n_imp0, sizeof(uint32_t) * c->max_particles));
+        if (!c->patch) TRIBO_CUDA(cudaMalloc(&c->patch, bytes));
+        if (!c->patch_host) TRIBO_CUDA(cudaHostAlloc(&c->patch_host, bytes, cudaHostAllocDefault));
         c->patch_cap = cap;
     }
     PView v = p->on_host ? stage_view(c, p->n) : device_view(p);
@@ -644,13 +645,14 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         const bool ids = p->id && (sorts || c->ssm_on);
         if (!ids) v.id = nullptr;
         if (!p->cell) v.cell = nullptr;
-        if (!c->copy_stream) {
-            TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
-            TRIBO_CUDA(cudaStreamCreateWithFlags(&c->back_stream, cudaStreamNonBlocking));
-            TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
-            for (cudaEvent_t& e : c->chunk_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-            for (cudaEvent_t& e : c->rest_done) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        }
+        // each stream and event on its own, so that a failed creation is retried by the next call
+        if (!c->copy_stream) TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        if (!c->back_stream) TRIBO_CUDA(cudaStreamCreateWithFlags(&c->back_stream, cudaStreamNonBlocking));
+        if (!c->copy_done) TRIBO_CUDA(cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming));
+        for (cudaEvent_t& e : c->chunk_done)
+            if (!e) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (cudaEvent_t& e : c->rest_done)
+            if (!e) TRIBO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         // what the deposit needs first, on the compute stream; the rest beside it on the copy
         // stream (after the work already queued on the compute stream), awaited before its first use
         if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 1, ids, c->stream))) {
@@ -803,7 +805,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     st = run();
     if (st && p->on_host && c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
-        cudaStreamSynchronize(c->back_stream);
+        if (c->back_stream) cudaStreamSynchronize(c->back_stream);
         cudaStreamSynchronize(c->stream);
     }
     return st;
