@@ -466,3 +466,34 @@ def test_mirror_and_shift_symmetry():
     assert np.max(per(s.z, a.z + sz * g.dz, g.lz)) < 1e-15
     assert np.allclose(s.vx, a.vx, rtol=1e-9, atol=1e-14)
     assert np.allclose(s.q, a.q, rtol=1e-9, atol=1e-30)
+
+
+# ---------------------------------------------------------------- C_rel statistics (Sec. 4.1)
+
+def test_row_counts_by_brute_force():
+    g = small_grid(ny=9)
+    rng = np.random.default_rng(19)
+    n = 500
+    x, z = rng.uniform(0, g.lx, n), rng.uniform(0, g.lz, n)
+    y = rng.uniform(g.yf[0], g.yf[-1], n)
+    st = oracle.State.from_arrays(x, y, z, np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n), np.full(n, 1e-5))
+    counts = oracle.particles.ystats(g, st)
+    brute = np.zeros(g.ny)
+    for yy in y:                       # the row whose faces bracket y (a face belongs to the upper row)
+        for j in range(g.ny):
+            if g.yf[j] <= yy < g.yf[j + 1] or (j == g.ny - 1 and yy == g.yf[-1]):
+                brute[j] += 1
+                break
+    assert np.array_equal(counts, brute) and counts.sum() == n
+
+
+def test_relative_concentration_of_a_uniform_suspension_is_one():
+    g = small_grid(ny=9)
+    # counts in proportion to the rows' volumes: a uniform suspension
+    counts = 1000.0 * g.vol_y * g.nx * g.nz / (g.lx * g.ly * g.lz)
+    assert np.allclose(oracle.particles.c_rel(g, counts), 1.0, rtol=1e-13)
+    # any counts: the volume-weighted mean of C_rel is one
+    rng = np.random.default_rng(20)
+    counts = rng.integers(0, 50, g.ny).astype(float)
+    cr = oracle.particles.c_rel(g, counts)
+    assert abs((cr * g.vol_y * g.nx * g.nz).sum() / (g.lx * g.ly * g.lz) - 1.0) < 1e-13
