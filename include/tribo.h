@@ -247,7 +247,8 @@ tribo_status tribo_step(tribo_ctx* ctx, tribo_particles* p, double dt, int32_t n
 
 /* Bytes the host-pointer calls of this context have moved across the host
  * link since tribo_init: host to device and device to host (the sum of the
- * copies issued).  Either pointer may be NULL. */
+ * copies issued).  Either pointer may be NULL; TRIBO_ERR_ARG if ctx is NULL.
+ * The paper has no counterpart: it measures the interface, not the method. */
 tribo_status tribo_transfer_bytes(tribo_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
 
 /* Standalone Poisson solve and field (step 2 above).  rho: device
