@@ -133,7 +133,13 @@ typedef struct {
  *   id                     : n uint32, optional (NULL): permuted with the
  *                            particles when they are re-sorted
  *   cell                   : n uint32, optional (NULL) output: cell key
- *                            (k * ny + j) * nx + i of each final position */
+ *                            (k * ny + j) * nx + i of each final position
+ *   site                   : n double, optional (NULL): the charging-site
+ *                            density c/c0 in [0, 1] of the stochastic scaling
+ *                            model (Sec. 2.3.2), updated by each wall impact
+ *                            while the SSM is set (tribo_set_ssm) and
+ *                            permuted with the particles by a sort; NULL
+ *                            holds c/c0 = 1 */
 typedef struct {
     int64_t n;
     void *x, *y, *z, *vx, *vy, *vz, *d;
@@ -143,6 +149,7 @@ typedef struct {
     uint32_t* id;
     uint32_t* cell;
     int32_t on_host;          /* 1: all pointers are host pointers */
+    double* site;
 } tribo_particles;
 
 /* Create a context on the current device.  stream: a cudaStream_t to order
@@ -199,8 +206,13 @@ tribo_status tribo_eval_modes(tribo_ctx* ctx, double t, void* u_out);
  * skewness -gamma0 / ((A/A0) chi_i) (clipped to [-0.99, 0.99]), where
  * A, A0 are the Hertz contact areas of the impact and of the reference
  * impact and chi_w = 1 - sgn(dq0_min) 4 q/(c_sat d^2),
- * chi_i = 1 + sgn(dq0_min - mu0) 4 q/(c_sat d^2), both clipped to [0, 1];
- * the charging-site density ratio is taken as 1.  The random numbers are
+ * chi_i = 1 + sgn(dq0_min - mu0) 4 q/(c_sat d^2), both clipped to [0, 1],
+ * and N_i/N_0 carries the particle's charging-site density c/c0 (the
+ * particles' site array; 1 where it is NULL).  Each impact then uses up the
+ * fraction a = (A/(pi d^2)) chi_i (q/q_max) of the remaining sites,
+ * c/c0 <- c/c0 (1 - a) clipped to [0, 1], with q the charge before the
+ * impact and q_max = sgn(dq0_min) c_sat d^2/4 (the paper's sum over earlier
+ * contacts, taken one contact at a time).  The random numbers are
  * Philox4x32-10 with counter (particle id, impact count before the impact,
  * 0, 0) and key (seed low word, seed high word): results do not depend on
  * the particle order.  Needs the particles' id arrays in tribo_step; not
@@ -255,8 +267,8 @@ tribo_status tribo_transfer_bytes(tribo_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
  * (Nz, Ny, Nx) double charge density [C/m^3].  phi: device (Nz, Ny, Nx)
  * double, may be NULL.  E: device (3, Nz, Ny+2, Nx) "real", the planes
  * E_x, E_y, E_z on the wall-extended lattice; the wall nodes hold E_x = E_z = 0
- * and the one-sided E_y.  rho and phi must be 16-byte aligned and E aligned
- * to its real type; TRIBO_ERR_ARG otherwise.  In TRIBO_MIXED the transforms
+ * and the one-sided E_y.  rho, phi and E must be 16-byte aligned;
+ * TRIBO_ERR_ARG otherwise.  In TRIBO_MIXED the transforms
  * are FP32: rho is first rounded to FP32 into the context's cell-sum array
  * (work space that tribo_step refills at its start).  Asynchronous. */
 tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void* E);
@@ -329,13 +341,20 @@ const char*  tribo_phase_name(int32_t phase);
  * it is an interface convenience.  rho, phi (may be NULL) and E have the
  * layouts and meaning of tribo_poisson; grid as for tribo_init; eps is the
  * gas permittivity; precision TRIBO_FP64 or TRIBO_MIXED selects the "real"
- * type of E; stream: a cudaStream_t (NULL = legacy default).  Asynchronous.
- * All scratch lives in one static device array of 32 MiB that the library
- * reserves on every device it is loaded on until the process exits; grids
- * that need more, or more than 256 cells in any direction, are rejected with
- * TRIBO_ERR_CAPACITY (tribo_last_error gives the sizes).  The first call on a
- * device looks up that array's address (so make it before any stream
- * capture).  Calls share the array: calls whose GPU work overlaps race. */
+ * type of E; stream: a cudaStream_t (NULL = legacy default).  Asynchronous:
+ * the grid tables are built on the device by the call's first kernel from
+ * values passed by value, so the call copies nothing from host memory and
+ * does not wait for earlier work on the stream.  All scratch lives in one
+ * static device array of 32 MiB that the library reserves on every device it
+ * is loaded on until the process exits.  Grids that need more, or more than
+ * 256 cells in any direction, are rejected with TRIBO_ERR_CAPACITY
+ * (tribo_last_error gives the sizes); the largest cubes that fit are 96^3 in
+ * TRIBO_MIXED (27.9 MiB with phi) and 72^3 in TRIBO_FP64 (19.4 MiB with phi),
+ * and e.g. 256 x 64 x 64 in TRIBO_MIXED fits without phi (28.6 MiB) but not
+ * with it (32.8 MiB).  A grid whose transforms need more shared memory per
+ * block than the device offers is rejected with TRIBO_ERR_UNSUPPORTED.  The
+ * first call on a device looks up that array's address (so make it before any
+ * stream capture).  Calls share the array: calls whose GPU work overlaps race. */
 tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps, int32_t precision,
                                    const double* rho, double* phi, void* E, void* stream);
 

@@ -63,22 +63,25 @@ class State:
     n_imp: np.ndarray
     q_wall: np.ndarray
     id: np.ndarray = None       # particle identities (random-number counters of the SSM)
+    site: np.ndarray = None     # SSM charging-site density c / c_0 (None: not tracked, held at 1)
 
     def __post_init__(self):
         if self.id is None:
             self.id = np.arange(self.x.shape[0], dtype=np.int64)
 
     @staticmethod
-    def from_arrays(x, y, z, vx, vy, vz, q, d, n_imp=None, q_wall=None, ids=None) -> "State":
+    def from_arrays(x, y, z, vx, vy, vz, q, d, n_imp=None, q_wall=None, ids=None, site=None) -> "State":
         n = np.asarray(x).shape[0]
         f = lambda a: np.array(a, dtype=np.float64)
         return State(f(x), f(y), f(z), f(vx), f(vy), f(vz), f(q), f(d),
                      np.zeros(n, np.int64) if n_imp is None else np.array(n_imp, np.int64),
                      np.zeros(n) if q_wall is None else f(q_wall),
-                     np.arange(n, dtype=np.int64) if ids is None else np.array(ids, np.int64))
+                     np.arange(n, dtype=np.int64) if ids is None else np.array(ids, np.int64),
+                     None if site is None else f(site))
 
     def copy(self) -> "State":
-        return State(*(np.array(getattr(self, f.name)) for f in dataclasses.fields(self)))
+        return State(*(None if getattr(self, f.name) is None else np.array(getattr(self, f.name))
+                       for f in dataclasses.fields(self)))
 
     @property
     def n(self) -> int:
@@ -373,6 +376,7 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
     q = st.q.copy()
     n_imp = st.n_imp.copy()
     q_wall = st.q_wall.copy()
+    site = None if st.site is None else st.site.copy()
     m = hit != 0
     if np.any(m):
         if p.impact_vel == IMPACT_NORMAL:
@@ -381,7 +385,10 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
             speed = np.linalg.norm(Vn[m], axis=1)
         if p.ssm is not None:
             from .ssm import ssm_wall_charge
-            dq, _ = ssm_wall_charge(p, p.ssm, st.d[m], speed, q[m], st.id[m], n_imp[m])
+            dq, det = ssm_wall_charge(p, p.ssm, st.d[m], speed, q[m], st.id[m], n_imp[m],
+                                      site=None if site is None else site[m])
+            if site is not None:
+                site[m] = det["site"]
         else:
             dq_c, dq_t, _ = condenser_wall(p, st.d[m], speed, q[m])
             dq = dq_c + dq_t
@@ -395,7 +402,7 @@ def step(g: Grid, p: Params, st: State, u_lat: np.ndarray, dt: float,
             diag.update(pairs=pairs)
     if diag is not None:
         diag.update(uf=uf, hit=hit, tau=tau, acc=acc, F_s=momentum_source(g, p, st, uf, acc, tau, dt))
-    return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall, st.id.copy())
+    return State(xn, yn, zn, vxn, vyn, vzn, q, st.d.copy(), n_imp, q_wall, st.id.copy(), site)
 
 
 def run(g: Grid, p: Params, st: State, u_lat, dt: float, nsteps: int,

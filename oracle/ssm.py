@@ -23,8 +23,19 @@ Readings:
 * gamma_i as printed (-gamma_0 N_0 / N_i), clipped to |gamma| <= 0.99, inside
   the skew-normal family's range (|gamma| < 0.99527), where the sample stays
   well conditioned;
-* the site density c / c_0 is 1 (the history term is not tracked; the paper
-  notes it matters only after about 1e4 impacts, never reached in its runs);
+* the charging-site density c / c_0 of a particle follows the printed sum
+  over its earlier contacts m = 1 .. M-1,
+    c / c_0 = 1 - sum_m (c_{m-1} / c_0)(A_m / A_p)(chi_m / chi_0)(q_m / q_max),
+  read as: A_m the Hertz area of contact m, A_p = pi d^2 the particle's
+  surface, chi_m the particle's own activity ratio chi_i at contact m, q_m
+  its charge as the contact begins, and q_max = sgn(dq0_min) C_sat d^2 / 4
+  the saturation charge the wall drives it towards (where chi_w reaches 0),
+  so that q_m / q_max >= 0 while the particle charges towards saturation.
+  Term by term the sum is the product c_M = c_{M-1} (1 - a_M) with
+  a_M = (A_M / A_p)(chi_M / chi_0)(q_M / q_max); the result is clipped to
+  [0, 1] as the paper bounds it.  Only wall contacts count (particle-particle
+  contacts charge by the condenser model here).  A particle whose history is
+  not tracked keeps c / c_0 = 1;
 * A and A_0 are the Hertz contact areas pi (d/2) alpha without kappa_A;
 * random numbers: Philox4x32-10 (Salmon et al., SC'11) with counter
   (particle id, impact count before this impact, 0, 0) and key (seed low
@@ -119,16 +130,28 @@ def saturation_charge(s: SSM, d):
     return s.c_sat * np.asarray(d, np.float64) ** 2 / 4.0
 
 
-def ssm_wall_charge(p: Params, s: SSM, d, speed, q, ids, counts):
-    """Charge of one wall impact per particle; returns (dq, details)."""
+def site_depletion(p: Params, s: SSM, d, speed, q, chi_i):
+    """a = (A / A_p)(chi_i / chi_0)(q / q_max) of one wall contact: the
+    fraction of the particle's remaining charging sites the contact uses up
+    (q_max = sgn(dq0_min) C_sat d^2 / 4, A_p = pi d^2)."""
+    d = np.asarray(d, np.float64)
+    q_max = np.sign(s.dq0_min) * saturation_charge(s, d)
+    return hertz_area(p, d, speed) / (math.pi * d ** 2) * np.asarray(chi_i, np.float64) * np.asarray(q, np.float64) / q_max
+
+
+def ssm_wall_charge(p: Params, s: SSM, d, speed, q, ids, counts, site=None):
+    """Charge of one wall impact per particle; returns (dq, details).  site:
+    the particles' charging-site density c / c_0 before the impact (None: 1,
+    not tracked); details["site"] holds its value after the impact."""
     d = np.asarray(d, np.float64)
     q = np.asarray(q, np.float64)
+    c = np.ones_like(d) if site is None else np.asarray(site, np.float64)
     area = hertz_area(p, d, speed) / float(hertz_area(p, 2.0 * s.r0, s.un0))
     x = 4.0 * q / (s.c_sat * d ** 2)
     chi_w = np.clip(1.0 - np.sign(s.dq0_min) * x, 0.0, 1.0)
     chi_i = np.clip(1.0 + np.sign(s.dq0_min - s.mu0) * x, 0.0, 1.0)
     nw = area * chi_w
-    ni = area * chi_i
+    ni = area * chi_i * c
     mu_w = s.dq0_min * nw
     mu_i = (s.dq0_min - s.mu0) * ni
     sigma_i = s.sigma0 * np.sqrt(ni)
@@ -137,5 +160,6 @@ def ssm_wall_charge(p: Params, s: SSM, d, speed, q, ids, counts):
     z0, z1 = normals(ids, counts, s.seed)
     y = xi + omega * (delta * np.abs(z0) + np.sqrt(np.maximum(1.0 - delta ** 2, 0.0)) * z1)
     dq = mu_w - y
+    c_new = np.clip(c * (1.0 - site_depletion(p, s, d, speed, q, chi_i)), 0.0, 1.0)
     return dq, dict(area_ratio=area, chi_w=chi_w, chi_i=chi_i, mu_w=mu_w, mu_i=mu_i, sigma_i=sigma_i,
-                    gamma_i=gamma_i)
+                    gamma_i=gamma_i, site=c_new if site is not None else None)

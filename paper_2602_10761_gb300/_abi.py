@@ -59,7 +59,7 @@ class tribo_ssm(C.Structure):
 class tribo_particles(C.Structure):
     _fields_ = [("n", C.c_int64)] + [(n, C.c_void_p) for n in ("x", "y", "z", "vx", "vy", "vz", "d")] + \
                [("q", C.c_void_p), ("q_wall", C.c_void_p), ("n_imp", C.c_void_p), ("id", C.c_void_p),
-                ("cell", C.c_void_p), ("on_host", C.c_int32)]
+                ("cell", C.c_void_p), ("on_host", C.c_int32), ("site", C.c_void_p)]
 
 
 _SIGS = {

@@ -82,7 +82,7 @@ def _on_host(a) -> bool:
 class Particles:
     """Structure-of-arrays particle ensemble (torch CUDA tensors or numpy)."""
     REAL = ("x", "y", "z", "vx", "vy", "vz", "d")
-    ALL = REAL + ("q", "q_wall", "n_imp", "id", "cell")
+    ALL = REAL + ("q", "q_wall", "n_imp", "id", "cell", "site")
 
     def __init__(self, **arrays):
         for name in self.ALL:
@@ -91,9 +91,10 @@ class Particles:
 
     @classmethod
     def from_numpy(cls, src, precision: int, device: Optional[str] = "cuda", with_id: bool = True,
-                   with_cell: bool = False) -> "Particles":
+                   with_cell: bool = False, with_site: bool = False) -> "Particles":
         """src: object or dict with x, y, z, vx, vy, vz, d, q (and optionally
-        q_wall, n_imp).  device=None keeps host (numpy) arrays."""
+        q_wall, n_imp, site).  with_site: carry the SSM charging-site density
+        c/c0 (src's site, else 1).  device=None keeps host (numpy) arrays."""
         get = (lambda k: src.get(k)) if isinstance(src, dict) else (lambda k: getattr(src, k, None))
         rdt = np.float64 if precision == _abi.TRIBO_FP64 else np.float32
         n = np.asarray(get("x")).shape[0]
@@ -108,6 +109,9 @@ class Particles:
             arr["id"] = np.arange(n, dtype=np.uint32) if ids is None else np.asarray(ids, np.uint32)
         if with_cell:
             arr["cell"] = np.zeros(n, np.uint32)
+        if with_site or get("site") is not None:
+            si = get("site")
+            arr["site"] = np.ones(n) if si is None else np.ascontiguousarray(np.asarray(si, np.float64))
         if device is None:
             return cls(**arr)
         import torch
@@ -264,12 +268,43 @@ def tribo_adjoint(ctx: int, particles: Particles, dt: float, nsteps: int, ckpt_e
     return J.value, dU.value, dK.value
 
 
+def _check_noalloc_args(nx, ny, nz, y_faces, precision, rho, phi, E):
+    """Layout checks of tribo_poisson_noalloc's arrays, made before the C call
+    (the C side sees raw pointers only): FP64 rho (nz, ny, nx), FP64 phi of
+    the same shape or None, E (3, nz, ny+2, nx) of the precision's real type,
+    all contiguous CUDA tensors on the current device; ny + 1 faces."""
+    import torch
+    yf = np.ascontiguousarray(np.asarray(y_faces, dtype=np.float64))
+    if yf.ndim != 1 or yf.shape[0] != ny + 1:
+        raise ValueError(f"y_faces must hold ny + 1 = {ny + 1} faces, got shape {yf.shape}")
+    real = torch.float64 if precision == _abi.TRIBO_FP64 else torch.float32
+    want = (("rho", rho, torch.float64, (nz, ny, nx)), ("phi", phi, torch.float64, (nz, ny, nx)),
+            ("E", E, real, (3, nz, ny + 2, nx)))
+    for name, t, dt, shape in want:
+        if t is None and name == "phi":
+            continue
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch CUDA tensor")
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor (got a {t.device} tensor)")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, the current device is cuda:{torch.cuda.current_device()}")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    return yf
+
+
 def tribo_poisson_noalloc(nx: int, ny: int, nz: int, lx: float, lz: float, y_faces, eps: float,
                           precision: int, rho, phi, E, stream=None) -> None:
     """Context-free Poisson solve that allocates no device memory (for callers
     that cannot allocate while running); scratch is the library's static
-    32 MiB device array, shared by all calls."""
-    yf = np.ascontiguousarray(np.asarray(y_faces, dtype=np.float64))
+    32 MiB device array, shared by all calls.  rho, phi (or None) and E are
+    torch CUDA tensors, checked for dtype, shape and device before the call."""
+    yf = _check_noalloc_args(nx, ny, nz, y_faces, precision, rho, phi, E)
     g = _abi.tribo_grid(nx, ny, nz, lx, lz, yf.ctypes.data_as(C.POINTER(C.c_double)))
     sp = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     check(load().tribo_poisson_noalloc(C.byref(g), float(eps), int(precision), _ptr(rho), _ptr(phi), _ptr(E), sp),

@@ -524,7 +524,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     TRIBO_CUDA(cudaMemsetAsync(L.acc, 0, sizeof(Accum), c->stream));
     tribo_status st;
     const double t_start = c->time;
-    const size_t qbytes = ncell * sizeof(R);
+    const size_t qbytes = ncell * sizeof(double);   // the deposit's FP64 cell charge sums
 
     // the field of every forward step kept in HBM when it fits in half of the free memory: the
     // recomputed segments then take it instead of depositing and solving again
@@ -567,7 +567,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
         StepIO fio;
         if (electro) {
             void* Es = keepE ? (void*)E_of_step(s) : c->E_lat;
-            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, Es))) return st;
+            if ((st = poisson_solve(c, c->Q, true, c->d_scale_q, true, nullptr, Es))) return st;
             fio.E = Es;
         }
         if ((st = particles_step(c, P, dt, electro && s < nsteps - 1, P.cell != nullptr && s == nsteps - 1, fio)))
@@ -606,7 +606,8 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
         for (int i = 0; i < len; ++i) {
             if ((st = copy_state<R>(c, L.seg[i], L.W, n))) return st;
             if (c->n_modes && (st = modes_eval(c, t_start + (s0 + i) * dt, c->u_lat))) return st;
-            if (electro && !keepE && (st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, L.segE[i]))) return st;
+            if (electro && !keepE && (st = poisson_solve(c, c->Q, true, c->d_scale_q, true, nullptr, L.segE[i])))
+                return st;
             if (i < len - 1) {
                 io.E = electro ? (const void*)segE(i) : nullptr;
                 if ((st = particles_step(c, Wp, dt, electro && !keepE, false, io))) return st;
@@ -631,7 +632,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             k_adj_grad<R><<<gb, 128, 0, c->stream>>>(L.Eb, L.cy, (R*)c->Q, c->nx, c->ny, c->nz,
                                                      (R)(0.5 / c->dx), (R)(0.5 / c->dz));
             TRIBO_LAUNCHED(c);
-            if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, L.psi, nullptr))) return st;
+            if ((st = poisson_solve(c, c->Q, false, c->d_scale_q, true, L.psi, nullptr))) return st;
             phase_begin(c, PH_ADJOINT);
             k_adj_deposit<R><<<grid_for(n), kThreads, 0, c->stream>>>(a, L.seg[i], n, L.psi, L.lam.q);
             TRIBO_LAUNCHED(c);

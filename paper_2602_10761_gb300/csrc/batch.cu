@@ -152,13 +152,14 @@ PView dev_view(const tribo_particles* p) {
     PView v{};
     v.n = p->n;
     v.x = p->x; v.y = p->y; v.z = p->z; v.vx = p->vx; v.vy = p->vy; v.vz = p->vz; v.d = p->d;
-    v.q = p->q; v.q_wall = p->q_wall; v.n_imp = p->n_imp; v.id = p->id; v.cell = nullptr;
+    v.q = p->q; v.q_wall = p->q_wall; v.n_imp = p->n_imp; v.id = p->id; v.cell = nullptr; v.site = p->site;
     return v;
 }
 
 PView alt_of(tribo_ctx* c, const PView& home) {
     PView o = set_view(c, c->alt, home.n);
     if (!home.id) o.id = nullptr;
+    if (!home.site) o.site = nullptr;
     o.cell = nullptr;
     return o;
 }
@@ -171,7 +172,7 @@ tribo_status upload_chans(tribo_batch* b, int slot, const std::vector<PView>& vi
     for (int i = 0; i < b->n; ++i) {
         tribo_ctx* c = b->ch[i];
         StepArgs<R> a = make_args<R>(c, dt[i]);
-        a.Q = c->P.electrostatics ? (R*)c->Q : nullptr;
+        a.Q = c->P.electrostatics ? (double*)c->Q : nullptr;
         a.hist = scratch ? nullptr : c->d_hist;
         a.acc = scratch ? b->d_scratch : c->d_acc;
         h[i].a = a;
@@ -218,7 +219,7 @@ tribo_status issue_steps(tribo_batch* b, const std::vector<PView>& home, int cou
             }
             if (!st && c->P.electrostatics) {
                 const int64_t l0 = c->launches;
-                st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat);
+                st = poisson_solve(c, c->Q, true, c->d_scale_q, true, nullptr, c->E_lat);
                 b->launches += c->launches - l0;
             }
             if (!st) {
@@ -324,7 +325,7 @@ tribo_status step_impl(tribo_batch* b, const std::vector<PView>& home, const dou
         if (!c->P.electrostatics || home[i].n == 0) continue;
         cudaStream_t keep = c->stream;
         c->stream = b->stream;
-        cudaError_t e = cudaMemsetAsync(c->Q, 0, real_bytes(c->prec) * (size_t)c->nx * c->ny * c->nz, b->stream);
+        cudaError_t e = cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, b->stream);
         st = e == cudaSuccess ? particles_deposit(c, home[i]) : cuda_fail(e, "batch deposit");
         c->stream = keep;
         if (st) return st;
@@ -344,6 +345,7 @@ tribo_status step_impl(tribo_batch* b, const std::vector<PView>& home, const dou
         std::vector<uintptr_t> key;
         for (const PView& v : home) {
             key.push_back((uintptr_t)v.x); key.push_back((uintptr_t)v.n); key.push_back((uintptr_t)v.id);
+            key.push_back((uintptr_t)v.site);
         }
         key.push_back((uintptr_t)G);
         key.push_back((uintptr_t)b->shape.nt * 1000003u + b->shape.tile * 31u + b->shape.bps);

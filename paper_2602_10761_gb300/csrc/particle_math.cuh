@@ -41,7 +41,7 @@ struct StepArgs {
     const R* u;                    // planes u_x, u_y, u_z, each `nodes` long
     const R* E;                    // planes E_x, E_y, E_z, each `nodes` long
     size_t nodes;
-    R* Q;                          // cell charge sums for the next step (may be NULL)
+    double* Q;                     // FP64 cell charge sums for the next step (may be NULL)
     unsigned long long* hist;      // ny (may be NULL)
     Accum* acc;
     // physics
@@ -264,10 +264,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 
 // dq = mu_w - Y, Y skew-normal with mean mu_i, deviation sigma_i, skewness
 // gamma_i; the sample from two Box-Muller normals of the words of the
-// counter (particle id, impact count)
+// counter (particle id, impact count).  *site: the particle's charging-site
+// density c/c0 before the impact (it scales N_i/N_0); on return, after it:
+// c/c0 (1 - a) with a = (A / (pi d^2)) chi_i (q / q_max), clipped to [0, 1]
+// (q the charge before the impact, q_max = sgn(dq0_min) c_sat d^2 / 4, so
+// q / q_max = sgn(dq0_min) 4 q / (c_sat d^2))
 template <class R>
 __device__ __noinline__ double ssm_charge(const StepArgs<R>& a, double d, double speed, double q, unsigned int id,
-                                          unsigned int count) {
+                                          unsigned int count, double* site) {
     const double r = 0.5 * d;
     const double A = M_PI * r * r * pow(a.alpha_coef * speed * speed, 0.4);
     const double area = A * a.ssm_inv_A0;
@@ -277,7 +281,9 @@ __device__ __noinline__ double ssm_charge(const StepArgs<R>& a, double d, double
     const double si = di > 0.0 ? 1.0 : (di < 0.0 ? -1.0 : 0.0);
     const double chi_w = fmin(fmax(1.0 - sw * x, 0.0), 1.0);
     const double chi_i = fmin(fmax(1.0 + si * x, 0.0), 1.0);
-    const double ni = area * chi_i;
+    const double c = *site;
+    *site = fmin(fmax(c * (1.0 - A / (M_PI * d * d) * chi_i * (sw * x)), 0.0), 1.0);
+    const double ni = area * chi_i * c;
     const double mu_w = a.ssm_dq0min * area * chi_w;
     const double mu_i = di * ni;
     const double sigma_i = a.ssm_sigma0 * sqrt(ni);
@@ -454,9 +460,14 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
         } else {
             speed = sqrt((double)vxn * (double)vxn + (double)vyn * (double)vyn + (double)vzn * (double)vzn);
         }
-        const double dq = a.ssm && speed > 0.0
-                              ? ssm_charge<R>(a, (double)d, speed, q, p.id[n], p.n_imp[n])
-                              : impact_charge<R>(a, (double)d, speed, q);
+        double dq;
+        if (a.ssm && speed > 0.0) {
+            double site = p.site ? p.site[n] : 1.0;
+            dq = ssm_charge<R>(a, (double)d, speed, q, p.id[n], p.n_imp[n], &site);
+            if (p.site) p.site[n] = site;
+        } else {
+            dq = impact_charge<R>(a, (double)d, speed, q);
+        }
         q += dq;
         p.q[n] = q;
         p.q_wall[n] += dq;
@@ -470,7 +481,7 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     VX[n] = vxn; VY[n] = vyn; VZ[n] = vzn;
     int jn;
     const uint32_t key = cell_key<R>(xn, yn, zn, a, &jn);
-    if (a.Q) atomicAdd(&a.Q[key], (R)q);
+    if (a.Q) atomicAdd(&a.Q[key], q);
     if (write_cell) p.cell[n] = key;
     if (use_hist) atomicAdd(&sh_hist[jn], 1u);
 }

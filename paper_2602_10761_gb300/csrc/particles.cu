@@ -69,7 +69,7 @@ __global__ void k_deposit(StepArgs<R> a, PView p) {
         if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
         int j;
         const uint32_t key = cell_key<R>(X[n], y, Z[n], a, &j);
-        atomicAdd(&a.Q[key], (R)p.q[n]);
+        atomicAdd(&a.Q[key], p.q[n]);
     }
     if (err) atomicOr(&a.acc->err, err);
 }
@@ -102,7 +102,7 @@ template <class R>
 tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_next, bool write_cell,
                        const StepIO& io) {
     StepArgs<R> a = make_args<R>(c, dt);
-    a.Q = deposit_next ? (R*)c->Q : nullptr;
+    a.Q = deposit_next ? (double*)c->Q : nullptr;
     a.hist = io.stats ? c->d_hist : nullptr;
     if (io.E) a.E = (const R*)io.E;
     if (io.acc) a.acc = io.acc;
@@ -122,7 +122,7 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
 template <class R>
 tribo_status deposit_impl(tribo_ctx* c, const PView& p) {
     StepArgs<R> a = make_args<R>(c, 0.0);
-    a.Q = (R*)c->Q;
+    a.Q = (double*)c->Q;
     phase_begin(c, PH_DEPOSIT);
     k_deposit<R><<<grid_for(p.n), kThreads, 0, c->stream>>>(a, p);
     TRIBO_LAUNCHED(c);
@@ -166,6 +166,7 @@ __global__ void k_sort_scatter(PView src, PView dst, const uint32_t* __restrict_
         dst.q_wall[d] = src.q_wall[n];
         dst.n_imp[d] = src.n_imp[n];
         if (src.id) dst.id[d] = src.id[n];
+        if (src.site) dst.site[d] = src.site[n];
     }
 }
 

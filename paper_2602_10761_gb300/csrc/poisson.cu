@@ -314,13 +314,14 @@ tribo_status setup_kernels(tribo_ctx* c) {
         return TRIBO_ERR_UNSUPPORTED;
     }
     TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_fwd_x<R, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_inv_x<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_fft_z<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return TRIBO_OK;
 }
 
 template <class R>
-tribo_status solve_impl(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
+tribo_status solve_impl(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src, double* phi,
                         void* Evoid) {
     const int nx = c->nx, ny = c->ny, nz = c->nz, nxh = c->nxh;
     cplx<R>* S = (cplx<R>*)c->S;
@@ -331,8 +332,12 @@ tribo_status solve_impl(tribo_ctx* c, void* src, const double* scale, bool zero_
         const int nlines = ny * nz;
         dim3 grid((nlines + lpb - 1) / lpb);
         phase_begin(c, PH_FWD_X);
-        k_fwd_x<R, R><<<grid, kThreads, smem_fwd_x<R>(nx, lpb), c->stream>>>(
-            (R*)src, scale, zero_src ? 1 : 0, S, nx, ny, nlines, nxh, c->plan_x, lpb);
+        if (src_f64 && sizeof(R) == 4)
+            k_fwd_x<R, double><<<grid, kThreads, smem_fwd_x<R>(nx, lpb), c->stream>>>(
+                (double*)src, scale, zero_src ? 1 : 0, S, nx, ny, nlines, nxh, c->plan_x, lpb);
+        else
+            k_fwd_x<R, R><<<grid, kThreads, smem_fwd_x<R>(nx, lpb), c->stream>>>(
+                (R*)src, scale, zero_src ? 1 : 0, S, nx, ny, nlines, nxh, c->plan_x, lpb);
         TRIBO_LAUNCHED(c);
     }
     {
@@ -474,12 +479,12 @@ tribo_status poisson_free(tribo_ctx* c) {
     return TRIBO_OK;
 }
 
-tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
-                           void* E) {
-    if (c->fast) return poisson_fast_solve(c, src, scale, zero_src, phi, E);
+tribo_status poisson_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,
+                           double* phi, void* E) {
+    if (c->fast) return poisson_fast_solve(c, src, src_f64, scale, zero_src, phi, E);
     if (!E) E = c->E_lat;       // the generic passes always form the field
-    if (c->prec == TRIBO_FP64) return solve_impl<double>(c, src, scale, zero_src, phi, E);
-    return solve_impl<float>(c, src, scale, zero_src, phi, E);
+    if (c->prec == TRIBO_FP64) return solve_impl<double>(c, src, true, scale, zero_src, phi, E);
+    return solve_impl<float>(c, src, src_f64, scale, zero_src, phi, E);
 }
 
 }  // namespace tribo
@@ -493,7 +498,8 @@ tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool ze
 // pre-allocated buffers.  This variant keeps its scratch (coefficient tables,
 // twiddles, spectra, Thomas sweep storage) in one fixed file-scope device
 // array instead of a context's allocations.  It has no counterpart in the
-// paper.
+// paper.  Its tables are written into the array by its first kernel, from the
+// grid passed by value, so nothing is staged in or copied from host memory.
 //
 // The array is static device memory of this library: every GPU that loads
 // the library holds it until the process exits.  Host code cannot use the
@@ -515,6 +521,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 struct NoallocDevice {
     unsigned char* base = nullptr;
+    int smem_max = 0;            // opt-in shared memory per block of the device
     bool ready = false;
 };
 NoallocDevice g_noalloc_dev[kNoallocMaxDevices];
@@ -546,33 +553,24 @@ NoallocLayout noalloc_layout(int nx, int ny, int nz, int nf, size_t rsz) {
     return L;
 }
 
-template <class R>
-void noalloc_twiddles(int n, unsigned char* dst) {
-    cplx<R>* tw = reinterpret_cast<cplx<R>*>(dst);
-    for (int e = 0; e < n; ++e) {
-        const double a = 2.0 * M_PI * (double)e / (double)n;
-        tw[e] = cplx<R>{(R)std::cos(a), (R)(-std::sin(a))};
-    }
-}
+// Everything the solve needs besides the caller's arrays, passed by value to
+// the table kernel (no host buffer is copied: the call neither blocks on nor
+// reads host memory after it returns).
+struct NoallocGeom {
+    int nx, ny, nz;
+    double dx, dz, eps;
+    double yf[kNoallocMaxN + 1];
+};
 
+// The grid tables of the solve, written into the front of the scratch array in
+// the layout of noalloc_layout: the y operator (a, b, c), the modified
+// wavenumbers, the spectral derivative factors, the E_y node coefficients, the
+// per-row RHS scale -1/eps and the x and z twiddles.  One block; the same
+// formulas as poisson_setup and make_plan (Sec. 2.2, Sec. 3.1 FV operator).
 template <class R>
-tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, double* phi, void* E,
-                           cudaStream_t stream, unsigned char* base, const NoallocLayout& L) {
-    const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = nx / 2 + 1;
-    const double* yf = g->y_faces;
-    const double dx = g->lx / nx, dz = g->lz / nz;
-    // host tables on the stack, laid out like the front of the scratch array
-    alignas(16) unsigned char hbuf[32768];
-    if (L.S > sizeof(hbuf)) {
-        set_last_error("tribo_poisson_noalloc: internal table buffer too small");
-        return TRIBO_ERR_UNSUPPORTED;
-    }
-    double yc[kNoallocMaxN], dy[kNoallocMaxN];
-    for (int j = 0; j < ny; ++j) {
-        yc[j] = 0.5 * (yf[j] + yf[j + 1]);
-        dy[j] = yf[j + 1] - yf[j];
-    }
-    double* T = reinterpret_cast<double*>(hbuf + L.tables);
+__global__ void k_noalloc_tables(NoallocGeom g, double* __restrict__ T, cplx<R>* __restrict__ twx,
+                                 cplx<R>* __restrict__ twz) {
+    const int nx = g.nx, ny = g.ny, nz = g.nz, nxh = nx / 2 + 1;
     double* a = T;
     double* b = a + ny;
     double* cc = b + ny;
@@ -582,55 +580,83 @@ tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, d
     double* sinz = sinx + nxh;
     double* ey = sinz + nz;
     double* scale = ey + 3 * (ny + 2);
-    for (int j = 0; j < ny; ++j) {
-        a[j] = (j >= 1) ? 1.0 / (dy[j] * (yc[j] - yc[j - 1])) : 0.0;
-        cc[j] = (j <= ny - 2) ? 1.0 / (dy[j] * (yc[j + 1] - yc[j])) : 0.0;
-        b[j] = -(a[j] + cc[j]);
-        scale[j] = -1.0 / eps;
-    }
-    b[0] -= 1.0 / (dy[0] * (yc[0] - yf[0]));
-    b[ny - 1] -= 1.0 / (dy[ny - 1] * (yf[ny] - yc[ny - 1]));
-    for (int m = 0; m < nx; ++m) {
-        const double s = std::sin(M_PI * m / nx);
-        lamx[m] = 4.0 / (dx * dx) * s * s;
-    }
-    for (int m = 0; m < nz; ++m) {
-        const double s = std::sin(M_PI * m / nz);
-        lamz[m] = 4.0 / (dz * dz) * s * s;
-        sinz[m] = std::sin(2.0 * M_PI * m / nz) / dz;
-    }
-    for (int m = 0; m < nxh; ++m) sinx[m] = std::sin(2.0 * M_PI * m / nx) / dx;
-    for (int i = 0; i < 3 * (ny + 2); ++i) ey[i] = 0.0;
-    for (int j = 0; j < ny; ++j) {
-        const int jn = j + 1;
+    const double* yf = g.yf;
+    auto yc = [&](int j) { return 0.5 * (yf[j] + yf[j + 1]); };
+    auto dy = [&](int j) { return yf[j + 1] - yf[j]; };
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+        const double aj = (j >= 1) ? 1.0 / (dy(j) * (yc(j) - yc(j - 1))) : 0.0;
+        const double cj = (j <= ny - 2) ? 1.0 / (dy(j) * (yc(j + 1) - yc(j))) : 0.0;
+        double bj = -(aj + cj);
+        if (j == 0) bj -= 1.0 / (dy(0) * (yc(0) - yf[0]));
+        if (j == ny - 1) bj -= 1.0 / (dy(ny - 1) * (yf[ny] - yc(ny - 1)));
+        a[j] = aj;
+        b[j] = bj;
+        cc[j] = cj;
+        scale[j] = -1.0 / g.eps;
+        // E_y at lattice node jn = j + 1: cm phi[j-1] + c0 phi[j] + cp phi[j+1]
         double cm = 0, c0 = 0, cp = 0;
         if (j >= 1) {
-            const double w = (yf[j] - yc[j - 1]) / (yc[j] - yc[j - 1]);
-            cm += (1.0 - w) / dy[j];
-            c0 += w / dy[j];
+            const double w = (yf[j] - yc(j - 1)) / (yc(j) - yc(j - 1));
+            cm += (1.0 - w) / dy(j);
+            c0 += w / dy(j);
         }
         if (j + 1 <= ny - 1) {
-            const double w = (yf[j + 1] - yc[j]) / (yc[j + 1] - yc[j]);
-            c0 -= (1.0 - w) / dy[j];
-            cp -= w / dy[j];
+            const double w = (yf[j + 1] - yc(j)) / (yc(j + 1) - yc(j));
+            c0 -= (1.0 - w) / dy(j);
+            cp -= w / dy(j);
         }
-        ey[3 * jn + 0] = cm;
-        ey[3 * jn + 1] = c0;
-        ey[3 * jn + 2] = cp;
+        ey[3 * (j + 1) + 0] = cm;
+        ey[3 * (j + 1) + 1] = c0;
+        ey[3 * (j + 1) + 2] = cp;
     }
-    ey[2] = -1.0 / (yc[0] - yf[0]);
-    ey[3 * (ny + 1)] = 1.0 / (yf[ny] - yc[ny - 1]);
-    noalloc_twiddles<R>(nx, hbuf + L.twx);
-    noalloc_twiddles<R>(nz, hbuf + L.twz);
-    cudaError_t e = cudaMemcpyAsync(base, hbuf, L.S, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: table upload");
+    if (threadIdx.x == 0) {
+        ey[0] = 0.0;
+        ey[1] = 0.0;
+        ey[2] = -1.0 / (yc(0) - yf[0]);                       // bottom wall node
+        ey[3 * (ny + 1) + 0] = 1.0 / (yf[ny] - yc(ny - 1));   // top wall node
+        ey[3 * (ny + 1) + 1] = 0.0;
+        ey[3 * (ny + 1) + 2] = 0.0;
+    }
+    for (int m = threadIdx.x; m < nx; m += blockDim.x) {
+        const double s = sin(M_PI * m / nx);
+        lamx[m] = 4.0 / (g.dx * g.dx) * s * s;
+        const double ang = 2.0 * M_PI * (double)m / (double)nx;
+        twx[m] = cplx<R>{(R)cos(ang), (R)(-sin(ang))};
+        if (m < nxh) sinx[m] = sin(ang) / g.dx;
+    }
+    for (int m = threadIdx.x; m < nz; m += blockDim.x) {
+        const double s = sin(M_PI * m / nz);
+        lamz[m] = 4.0 / (g.dz * g.dz) * s * s;
+        const double ang = 2.0 * M_PI * (double)m / (double)nz;
+        sinz[m] = sin(ang) / g.dz;
+        twz[m] = cplx<R>{(R)cos(ang), (R)(-sin(ang))};
+    }
+}
 
+template <class R>
+tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, double* phi, void* E,
+                           cudaStream_t stream, unsigned char* base, const NoallocLayout& L, int smem_max) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz, nxh = nx / 2 + 1;
+    const int lpb = lines_per_block<R>();
+    const int mt = z_tile<R>();
+    // the kernels' shared memory, as the context path checks it (poisson setup_kernels)
+    const size_t need = std::max({smem_fwd_x<R>(nx, lpb), smem_inv_x<R>(nx, lpb), sizeof(cplx<R>) * 2 * mt * nz});
+    if (need > (size_t)smem_max) {
+        set_last_error("tribo_poisson_noalloc: grid needs more shared memory per block than the device offers");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    NoallocGeom geom{};
+    geom.nx = nx; geom.ny = ny; geom.nz = nz;
+    geom.dx = g->lx / nx; geom.dz = g->lz / nz; geom.eps = eps;
+    for (int j = 0; j <= ny; ++j) geom.yf[j] = g->y_faces[j];
+    double* dT = reinterpret_cast<double*>(base + L.tables);
+    k_noalloc_tables<R><<<1, kThreads, 0, stream>>>(geom, dT, reinterpret_cast<cplx<R>*>(base + L.twx),
+                                                    reinterpret_cast<cplx<R>*>(base + L.twz));
     FftPlan px{}, pz{};
     make_plan_radices(nx, px);
     make_plan_radices(nz, pz);
     px.tw = base + L.twx;
     pz.tw = base + L.twz;
-    const double* dT = reinterpret_cast<const double*>(base + L.tables);
     const double* d_ycoef = dT;
     const double* d_lamx = dT + 3 * ny;
     const double* d_lamz = d_lamx + nx;
@@ -642,8 +668,6 @@ tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, d
     cplx<R>* F = reinterpret_cast<cplx<R>*>(base + L.F);
     double2* W = reinterpret_cast<double2*>(base + L.W);
     double* Wc = reinterpret_cast<double*>(W + (size_t)ny * nz * nxh);
-    const int lpb = lines_per_block<R>();
-    const int mt = z_tile<R>();
     const int want_phi = phi != nullptr ? 1 : 0;
     const int nf = 3 + want_phi;
     const int nlines = ny * nz;
@@ -660,7 +684,7 @@ tribo_status noalloc_solve(const tribo_grid* g, double eps, const double* rho, d
     const int nl2 = nz * (ny + 2);
     k_inv_x<R><<<(nl2 + lpb - 1) / lpb, kThreads, smem_inv_x<R>(nx, lpb), stream>>>(
         F, (R*)E, phi, nx, ny, nz, nxh, px, lpb, nf);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: kernel launch");
     return TRIBO_OK;
 }
@@ -674,7 +698,7 @@ bool noalloc_2a3b(int n) {
 
 // one-time set-up of the current device: the array's device address and the
 // kernels' shared-memory limit
-tribo_status noalloc_device(int dev, unsigned char** base) {
+tribo_status noalloc_device(int dev, unsigned char** base, int* smem_max) {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     NoallocDevice& d = g_noalloc_dev[dev];
     if (!d.ready) {
@@ -693,9 +717,11 @@ tribo_status noalloc_device(int dev, unsigned char** base) {
             if (e != cudaSuccess) return cuda_fail(e, "tribo_poisson_noalloc: shared-memory limit");
         }
         d.base = static_cast<unsigned char*>(p);
+        d.smem_max = optin;
         d.ready = true;
     }
     *base = d.base;
+    *smem_max = d.smem_max;
     return TRIBO_OK;
 }
 
@@ -750,9 +776,10 @@ extern "C" tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps
         return TRIBO_ERR_UNSUPPORTED;
     }
     unsigned char* base = nullptr;
-    tribo_status st = noalloc_device(dev, &base);
+    int smem_max = 0;
+    tribo_status st = noalloc_device(dev, &base, &smem_max);
     if (st) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (precision == TRIBO_FP64) return noalloc_solve<double>(grid, eps, rho, phi, E, s, base, L);
-    return noalloc_solve<float>(grid, eps, rho, phi, E, s, base, L);
+    if (precision == TRIBO_FP64) return noalloc_solve<double>(grid, eps, rho, phi, E, s, base, L, smem_max);
+    return noalloc_solve<float>(grid, eps, rho, phi, E, s, base, L, smem_max);
 }

@@ -67,15 +67,16 @@ __device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
 // Thread group (line, r) per line (k, j) of the charge-sum array:
 // z_n = x_2n + i x_2n+1 (scaled to -rho/eps), Z = FFT_M(z) by the register
 // four-step, X_m = (Z_m + conj Z_M-m)/2 - (i/2) W^m (Z_m - conj Z_M-m) for
-// m = 0..M.  Each thread zeroes the charge sums it has read.  The sums have
-// the real type R (a caller's FP64 density is rounded to R beforehand).
+// m = 0..M.  Each thread zeroes the charge sums it has read.  The source has
+// type QT: the FP64 cell charge sums (or a caller's FP64 density), rounded to
+// R as they are read, or the adjoint's R-typed charge adjoint.
 // six resident blocks (40 registers) where the length fits them without spilling: FP32 up to
 // M = 192 (76 -> 75.8 us at 384x256x256); one otherwise
 template <class R, int M>
 constexpr int xfwd_min_blocks() { return sizeof(R) == 4 && M <= 192 ? 6 : 1; }
 
-template <class R, int M>
-__global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(R* __restrict__ src, const double* __restrict__ scale_row,
+template <class R, int M, class QT>
+__global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT* __restrict__ src, const double* __restrict__ scale_row,
                                                     int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
                                                     const cplx<R>* __restrict__ tw_g) {
     using F4 = fft::FourStep<M, kThreads>;
@@ -93,18 +94,18 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(R* 
     cplx<R>* lb = buf + l * CS;
     if (live && r < N2) {
         const R s = from_f64<R>(scale_row[line % ny]);
-        using V2 = std::conditional_t<sizeof(R) == 8, double2, float2>;   // (x_2n, x_2n+1)
+        using V2 = std::conditional_t<sizeof(QT) == 8, double2, float2>;   // (x_2n, x_2n+1)
         V2* row = reinterpret_cast<V2*>(src) + (size_t)line * M;
         cplx<R> y[N1];
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
             const V2 v = row[N2 * n1 + r];
-            y[n1] = cplx<R>{v.x * s, v.y * s};
+            y[n1] = cplx<R>{from_f64<R>(v.x) * s, from_f64<R>(v.y) * s};
         }
         if (zero_src) {
             V2 zero;
-            zero.x = (R)0;
-            zero.y = (R)0;
+            zero.x = (QT)0;
+            zero.y = (QT)0;
 #pragma unroll
             for (int n1 = 0; n1 < N1; ++n1) row[N2 * n1 + r] = zero;
         }
@@ -621,11 +622,11 @@ int wave_blocks(K kernel, size_t smem, int num_sms, int64_t tiles, int* cache) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)*cache * num_sms));
 }
 
-template <class R, int M>
-void launch_xfwd(tribo_ctx* c, R* src, const double* scale, bool zero) {
+template <class R, int M, class QT>
+void launch_xfwd(tribo_ctx* c, QT* src, const double* scale, bool zero) {
     constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->ny * c->nz;
-    k_xfwd4<R, M><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
+    k_xfwd4<R, M, QT><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
         src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx);
 }
 template <class R, int M>
@@ -670,7 +671,8 @@ tribo_status attr_z(int optin) {
 template <class R, int M>
 tribo_status attr_x(int optin) {
     if (xfwd_smem<R, M>() > (size_t)optin || xinv_smem<R, M>() > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
-    TRIBO_CUDA(cudaFuncSetAttribute(k_xfwd4<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_xfwd4<R, M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_xfwd4<R, M, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_xinv4<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     return TRIBO_OK;
 }
@@ -687,10 +689,10 @@ bool fast_len(int n) {
     }
 }
 
-template <class R>
-bool dispatch_xfwd(tribo_ctx* c, R* src, const double* scale, bool zero) {
+template <class R, class QT>
+bool dispatch_xfwd(tribo_ctx* c, QT* src, const double* scale, bool zero) {
     switch (c->nx / 2) {
-#define CASE(N) case N: launch_xfwd<R, N>(c, src, scale, zero); return true;
+#define CASE(N) case N: launch_xfwd<R, N, QT>(c, src, scale, zero); return true;
         TRIBO_FAST_SIZES(CASE)
 #undef CASE
         default: return false;
@@ -759,10 +761,12 @@ void split_ds(double v, float* hi, float* lo) {
 }
 
 template <class R>
-tribo_status solve_fast(tribo_ctx* c, R* src, const double* scale, bool zero_src, double* phi, void* E) {
+tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src, double* phi,
+                        void* E) {
     const int ny = c->ny, nz = c->nz, nxh = c->nxh;
     phase_begin(c, PH_FWD_X);
-    dispatch_xfwd<R>(c, src, scale, zero_src);
+    if (src_f64) dispatch_xfwd<R, double>(c, (double*)src, scale, zero_src);
+    else dispatch_xfwd<R, R>(c, (R*)src, scale, zero_src);
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_FWD_Z);
     dispatch_zfwd<R>(c);
@@ -915,10 +919,10 @@ void poisson_fast_free(tribo_ctx* c) {
     c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = nullptr;
 }
 
-tribo_status poisson_fast_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
-                                void* E) {
-    if (c->prec == TRIBO_FP64) return solve_fast<double>(c, (double*)src, scale, zero_src, phi, E);
-    return solve_fast<float>(c, (float*)src, scale, zero_src, phi, E);
+tribo_status poisson_fast_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,
+                                double* phi, void* E) {
+    if (c->prec == TRIBO_FP64) return solve_fast<double>(c, src, true, scale, zero_src, phi, E);
+    return solve_fast<float>(c, src, src_f64, scale, zero_src, phi, E);
 }
 
 }  // namespace tribo

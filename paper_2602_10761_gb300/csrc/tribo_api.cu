@@ -22,24 +22,21 @@ tribo_status cuda_fail(cudaError_t e, const char* what) {
 
 namespace {
 
-__global__ void k_round_to_float(const double* __restrict__ src, float* __restrict__ dst, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
-}
-
 // A host call's list of the particles whose impact count changed (their q,
 // q_wall, n_imp are the only ones of those arrays that moved): a 16-byte
 // header holding the count, then the entries.
 struct PatchEntry {
     uint32_t i, n_imp;
     double q, q_wall;
+    double site;             // SSM charging-site density (1 when the particles carry none)
 };
 constexpr size_t kPatchHeader = 16;
 constexpr int64_t kPatchHost = 4096;       // entries sent back with the count in one copy
 constexpr int kChunks = 4;                 // a host call's last step runs in this many particle ranges
 
 __global__ void k_patch(const uint32_t* __restrict__ n_imp, const uint32_t* __restrict__ n_imp0,
-                        const double* __restrict__ q, const double* __restrict__ q_wall, int64_t n,
+                        const double* __restrict__ q, const double* __restrict__ q_wall,
+                        const double* __restrict__ site, int64_t n,
                         unsigned char* __restrict__ list, unsigned int cap) {
     unsigned int* count = reinterpret_cast<unsigned int*>(list);
     PatchEntry* out = reinterpret_cast<PatchEntry*>(list + kPatchHeader);
@@ -47,7 +44,7 @@ __global__ void k_patch(const uint32_t* __restrict__ n_imp, const uint32_t* __re
         const uint32_t m = n_imp[i];
         if (m != n_imp0[i]) {
             const unsigned int k = atomicAdd(count, 1u);
-            if (k < cap) out[k] = PatchEntry{(uint32_t)i, m, q[i], q_wall[i]};
+            if (k < cap) out[k] = PatchEntry{(uint32_t)i, m, q[i], q_wall[i], site ? site[i] : 1.0};
         }
     }
 }
@@ -147,7 +144,7 @@ tribo_status build_tables(tribo_ctx* c) {
 
 // device-resident particle arrays used for host-pointer calls
 struct Stage {
-    static size_t bytes(int64_t n, size_t rs) { return (size_t)n * (7 * rs + 2 * sizeof(double) + 3 * sizeof(uint32_t)) + 1024; }
+    static size_t bytes(int64_t n, size_t rs) { return (size_t)n * (7 * rs + 3 * sizeof(double) + 3 * sizeof(uint32_t)) + 1024; }
 };
 
 // Host <-> device copies of a particle set on `stream`.  to_device: group 1 is
@@ -173,7 +170,7 @@ tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particle
         if ((groups & 2) &&
             ((st = cp(dst.vx, src->vx, rs)) || (st = cp(dst.vy, src->vy, rs)) || (st = cp(dst.vz, src->vz, rs)) ||
              (st = cp(dst.d, src->d, rs)) || (st = cp(dst.q_wall, src->q_wall, sizeof(double))) ||
-             (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) ||
+             (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) || (st = cp(dst.site, src->site, sizeof(double))) ||
              (with_id && (st = cp(dst.id, src->id, sizeof(uint32_t))))))
             return st;
         return TRIBO_OK;
@@ -181,7 +178,7 @@ tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particle
     if ((st = cp(dst.x, src->x, rs)) || (st = cp(dst.y, src->y, rs)) || (st = cp(dst.z, src->z, rs)) ||
         (st = cp(dst.vx, src->vx, rs)) || (st = cp(dst.vy, src->vy, rs)) || (st = cp(dst.vz, src->vz, rs)) ||
         (st = cp(dst.q, src->q, sizeof(double))) || (st = cp(dst.q_wall, src->q_wall, sizeof(double))) ||
-        (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) ||
+        (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) || (st = cp(dst.site, src->site, sizeof(double))) ||
         (with_id && (st = cp(dst.id, src->id, sizeof(uint32_t)))) || (st = cp(dst.cell, src->cell, sizeof(uint32_t))))
         return st;
     return TRIBO_OK;
@@ -200,6 +197,7 @@ PView sub_view(const tribo_ctx* c, const PView& v, int64_t a0, int64_t n) {
     s.n_imp = (uint32_t*)at(v.n_imp, sizeof(uint32_t));
     s.id = (uint32_t*)at(v.id, sizeof(uint32_t));
     s.cell = (uint32_t*)at(v.cell, sizeof(uint32_t));
+    s.site = (double*)at(v.site, sizeof(double));
     return s;
 }
 
@@ -220,7 +218,8 @@ tribo_status copy_back_range(tribo_ctx* c, const PView& part, const tribo_partic
         (st = cp(host->vx, part.vx, rs)) || (st = cp(host->vy, part.vy, rs)) || (st = cp(host->vz, part.vz, rs)) ||
         (!states_only && ((st = cp(host->q, part.q, sizeof(double))) ||
                           (st = cp(host->q_wall, part.q_wall, sizeof(double))) ||
-                          (st = cp(host->n_imp, part.n_imp, sizeof(uint32_t))))) ||
+                          (st = cp(host->n_imp, part.n_imp, sizeof(uint32_t))) ||
+                          (st = cp(host->site, part.site, sizeof(double))))) ||
         (with_id && (st = cp(host->id, part.id, sizeof(uint32_t)))) || (st = cp(host->cell, part.cell, sizeof(uint32_t))))
         return st;
     return TRIBO_OK;
@@ -241,7 +240,7 @@ tribo_status copy_rest_range(tribo_ctx* c, const PView& part, const tribo_partic
     tribo_status st;
     if ((st = cp(part.vx, host->vx, rs)) || (st = cp(part.vy, host->vy, rs)) || (st = cp(part.vz, host->vz, rs)) ||
         (st = cp(part.d, host->d, rs)) || (st = cp(part.q_wall, host->q_wall, sizeof(double))) ||
-        (st = cp(part.n_imp, host->n_imp, sizeof(uint32_t))) ||
+        (st = cp(part.n_imp, host->n_imp, sizeof(uint32_t))) || (st = cp(part.site, host->site, sizeof(double))) ||
         (with_id && (st = cp(part.id, host->id, sizeof(uint32_t)))))
         return st;
     return TRIBO_OK;
@@ -273,6 +272,7 @@ tribo_status apply_patch(tribo_ctx* c, const PView& dev, const tribo_particles* 
         host->q[e[k].i] = e[k].q;
         host->q_wall[e[k].i] = e[k].q_wall;
         host->n_imp[e[k].i] = e[k].n_imp;
+        if (host->site) host->site[e[k].i] = e[k].site;
     }
     return TRIBO_OK;
 }
@@ -317,6 +317,7 @@ PView set_view(tribo_ctx* c, void* base, int64_t n) {
     v.n_imp = (uint32_t*)take(sizeof(uint32_t));
     v.id = (uint32_t*)take(sizeof(uint32_t));
     v.cell = (uint32_t*)take(sizeof(uint32_t));
+    v.site = (double*)take(sizeof(double));
     return v;
 }
 
@@ -336,7 +337,8 @@ tribo_status copy_view(tribo_ctx* c, const PView& dst, const PView& src) {
         (st = cp(dst.vx, src.vx, rs)) || (st = cp(dst.vy, src.vy, rs)) || (st = cp(dst.vz, src.vz, rs)) ||
         (st = cp(dst.d, src.d, rs)) || (st = cp(dst.q, src.q, sizeof(double))) ||
         (st = cp(dst.q_wall, src.q_wall, sizeof(double))) || (st = cp(dst.n_imp, src.n_imp, sizeof(uint32_t))) ||
-        (st = cp(dst.id, src.id, sizeof(uint32_t))) || (st = cp(dst.cell, src.cell, sizeof(uint32_t))))
+        (st = cp(dst.id, src.id, sizeof(uint32_t))) || (st = cp(dst.cell, src.cell, sizeof(uint32_t))) ||
+        (st = cp(dst.site, src.site, sizeof(double))))
         return st;
     return TRIBO_OK;
 }
@@ -397,7 +399,7 @@ PView device_view(const tribo_particles* p) {
     v.n = p->n;
     v.x = p->x; v.y = p->y; v.z = p->z;
     v.vx = p->vx; v.vy = p->vy; v.vz = p->vz; v.d = p->d;
-    v.q = p->q; v.q_wall = p->q_wall; v.n_imp = p->n_imp; v.id = p->id; v.cell = p->cell;
+    v.q = p->q; v.q_wall = p->q_wall; v.n_imp = p->n_imp; v.id = p->id; v.cell = p->cell; v.site = p->site;
     return v;
 }
 
@@ -645,6 +647,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         const bool ids = p->id && (sorts || c->ssm_on);
         if (!ids) v.id = nullptr;
         if (!p->cell) v.cell = nullptr;
+        if (!p->site) v.site = nullptr;
         // each stream and event on its own, so that a failed creation is retried by the next call
         if (!c->copy_stream) TRIBO_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         if (!c->back_stream) TRIBO_CUDA(cudaStreamCreateWithFlags(&c->back_stream, cudaStreamNonBlocking));
@@ -712,8 +715,9 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
         PView home = v, cur = v, other = S > 0 ? set_view(c, c->alt, p->n) : v;
         if (!v.id) other.id = nullptr;
         if (!v.cell) other.cell = nullptr;
+        if (!v.site) other.site = nullptr;
         if (electro) {
-            TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, real_size(c) * (size_t)c->nx * c->ny * c->nz, c->stream));
+            TRIBO_CUDA(cudaMemsetAsync(c->Q, 0, sizeof(double) * (size_t)c->nx * c->ny * c->nz, c->stream));
             if ((st = particles_deposit(c, cur))) return st;
         }
         // the cell lists the collisions built at the end of a step serve the next step's near
@@ -730,7 +734,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                 if ((st = modes_eval(c, c->time, c->u_lat))) return st;
             }
             if (electro) {
-                if ((st = poisson_solve(c, c->Q, c->d_scale_q, true, nullptr, c->E_lat))) return st;
+                if ((st = poisson_solve(c, c->Q, true, c->d_scale_q, true, nullptr, c->E_lat))) return st;
             }
             if (!one_chunked && (st = await_rest())) return st;
             if (near) {
@@ -759,7 +763,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                     // the changed particles' list, its count and first entries in one copy
                     TRIBO_CUDA(cudaMemsetAsync(c->patch, 0, kPatchHeader, c->stream));
                     const int blocks = (int)std::min<int64_t>((cur.n + 255) / 256, (int64_t)c->num_sms * 8);
-                    k_patch<<<blocks, 256, 0, c->stream>>>(cur.n_imp, c->n_imp0, cur.q, cur.q_wall, cur.n,
+                    k_patch<<<blocks, 256, 0, c->stream>>>(cur.n_imp, c->n_imp0, cur.q, cur.q_wall, cur.site, cur.n,
                                                            (unsigned char*)c->patch, (unsigned int)c->patch_cap);
                     TRIBO_LAUNCHED(c);
                     const size_t hb = kPatchHeader + sizeof(PatchEntry) * (size_t)std::min<int64_t>(c->patch_cap,
@@ -820,18 +824,12 @@ tribo_status tribo_transfer_bytes(tribo_ctx* c, uint64_t* h2d, uint64_t* d2h) {
 
 tribo_status tribo_poisson(tribo_ctx* c, const double* rho, double* phi, void* E) {
     if (!c || !rho || !E) { set_last_error("ctx, rho and E must not be NULL"); return TRIBO_ERR_ARG; }
-    if (((uintptr_t)rho | (uintptr_t)phi) % 16 || (uintptr_t)E % real_size(c)) {
-        set_last_error("rho and phi must be 16-byte aligned, E aligned to its real type");
+    if (((uintptr_t)rho | (uintptr_t)phi | (uintptr_t)E) % 16) {
+        set_last_error("rho, phi and E must be 16-byte aligned");
         return TRIBO_ERR_ARG;
     }
-    if (c->prec == TRIBO_FP64) return poisson_solve(c, const_cast<double*>(rho), c->d_scale_rho, false, phi, E);
-    // mixed: the solve reads FP32 sources; round the density into the charge-sum
-    // array (scratch between calls: every step call deposits afresh)
-    const size_t ncell = (size_t)c->nx * c->ny * c->nz;
-    k_round_to_float<<<(unsigned)std::min<size_t>((ncell + 255) / 256, 4096), 256, 0, c->stream>>>(
-        rho, (float*)c->Q, ncell);
-    TRIBO_LAUNCHED(c);
-    return poisson_solve(c, c->Q, c->d_scale_rho, false, phi, E);
+    // the caller's FP64 density feeds the forward x transform directly (read, not modified)
+    return poisson_solve(c, const_cast<double*>(rho), true, c->d_scale_rho, false, phi, E);
 }
 
 tribo_status tribo_stats(tribo_ctx* c, const tribo_particles* p, double* sum_q, uint64_t* n_impacts,

@@ -120,7 +120,8 @@ struct tribo_ctx {
     // fields
     void* u_lat = nullptr;       // (3, nz, ny+2, nx) real: u_x, u_y, u_z planes
     void* E_lat = nullptr;       // (3, nz, ny+2, nx) real: E_x, E_y, E_z planes
-    void* Q = nullptr;           // (nz, ny, nx) cell charge sums, real type (room for doubles)
+    void* Q = nullptr;           // (nz, ny, nx) FP64 cell charge sums (the adjoint's real-typed charge
+                                 // adjoint uses the same array between its solves)
     void* S = nullptr;           // (nz, ny, nxh) cplx<real> spectrum
     void* F = nullptr;           // (4, nz, ny+2, nxh) cplx<real> field spectra
     void* W = nullptr;           // (ny, nz*nxh) cplx<double> Thomas scratch (generic path)
@@ -212,20 +213,21 @@ tribo_status cuda_fail(cudaError_t e, const char* what);
 // Poisson (poisson.cu)
 tribo_status poisson_setup(tribo_ctx* c);
 tribo_status poisson_free(tribo_ctx* c);
-// src: device (nz, ny, nx) of the real type (charge sums or a density);
+// src: device (nz, ny, nx) of doubles (src_f64: the FP64 cell charge sums or a
+// caller's FP64 density) or of the real type (the adjoint's charge adjoint);
 // scale: device ny per-row factor giving the RHS -rho/eps; zero_src: write
 // zeros back into src after reading.  phi may be NULL.  E: (3, nz, ny+2, nx)
 // real (E_x, E_y, E_z), or NULL for the potential alone (phi then non-NULL;
 // the generic-length passes still form the field, into the context's E_lat).
-tribo_status poisson_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src,
+tribo_status poisson_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,
                            double* phi, void* E);
 
 // compile-time-length Poisson path (poisson_fast.cu)
 bool poisson_fast_supported(int nx, int nz);
 tribo_status poisson_fast_setup(tribo_ctx* c);
 void poisson_fast_free(tribo_ctx* c);
-tribo_status poisson_fast_solve(tribo_ctx* c, void* src, const double* scale, bool zero_src, double* phi,
-                                void* E);
+tribo_status poisson_fast_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,
+                                double* phi, void* E);
 
 // particles (particles.cu)
 struct PView {               // device views of one particle ensemble
@@ -236,6 +238,7 @@ struct PView {               // device views of one particle ensemble
     uint32_t* n_imp;
     uint32_t* id;
     uint32_t* cell;
+    double* site;            // SSM charging-site density c/c0, or NULL (held at 1)
 };
 tribo_status particles_deposit(tribo_ctx* c, const PView& p);
 struct StepIO {               // per-call overrides of the context's buffers

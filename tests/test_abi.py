@@ -96,3 +96,30 @@ def test_ssm_defaults_are_the_reference_impact_of_sec_3_1():
     import paper_2602_10761_gb300 as T
     from oracle.ssm import SSM
     assert dataclasses.asdict(T.SSMParams()) == dataclasses.asdict(SSM())
+
+
+def test_noalloc_binding_rejects_bad_arrays_before_the_call():
+    """tribo_poisson_noalloc's binding checks dtype, shape, device and the
+    face count before anything reaches the C side (which sees raw pointers)."""
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    from paper_2602_10761_gb300 import api
+    nx, ny, nz = 8, 6, 4
+    faces = np.linspace(0.0, 0.04, ny + 1)
+    rho = torch.zeros((nz, ny, nx), dtype=torch.float64)
+    E = torch.zeros((3, nz, ny + 2, nx), dtype=torch.float32)
+    cases = [
+        dict(y_faces=faces[:-1]),                                   # ny faces instead of ny + 1
+        dict(rho=rho),                                              # host tensor
+        dict(rho=rho.float()),                                      # wrong dtype
+        dict(E=E[:, :, 1:-1]),                                      # no wall rows
+        dict(E=E.double()),                                         # FP64 E in mixed mode
+        dict(phi=torch.zeros((nz, ny, nx), dtype=torch.float32)),   # phi not FP64
+        dict(rho=np.zeros((nz, ny, nx))),                           # not a tensor
+    ]
+    for kw in cases:
+        args = dict(y_faces=faces, rho=rho, phi=None, E=E)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            api._check_noalloc_args(nx, ny, nz, args["y_faces"], _abi.TRIBO_MIXED, args["rho"], args["phi"],
+                                    args["E"])

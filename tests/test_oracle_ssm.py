@@ -123,3 +123,97 @@ def test_step_uses_the_ssm_with_the_impact_counter():
     assert np.array_equal(out.q_wall, dq)
     other = oracle.step(g, p.with_(ssm=SSM(seed=6)), st, lat, 1e-5)
     assert not np.array_equal(other.q, out.q)
+
+
+# ---------------------------------------------------------------- charging-site history c / c_0
+
+def _det(s):
+    """The deterministic limit of the SSM (no scatter, no skew)."""
+    return SSM(r0=s.r0, un0=s.un0, mu0=s.mu0, sigma0=0.0, gamma0=0.0, dq0_min=s.dq0_min, c_sat=s.c_sat,
+               seed=s.seed)
+
+
+def test_site_history_is_inert_for_an_uncharged_particle():
+    """A first impact of an uncharged particle uses up no sites (q_m = 0 in
+    the printed sum), so tracking the history changes neither its charge nor
+    its site density."""
+    p = oracle.Params(rho_p=1150.0)
+    s = SSM(seed=5)
+    n = 1000
+    d = np.full(n, 80e-6)
+    sp = np.linspace(0.1, 2.0, n)
+    dq0, _ = ssm_wall_charge(p, s, d, sp, np.zeros(n), np.arange(n), np.zeros(n, np.int64))
+    dq1, det = ssm_wall_charge(p, s, d, sp, np.zeros(n), np.arange(n), np.zeros(n, np.int64), site=np.ones(n))
+    assert np.array_equal(dq0, dq1)
+    assert np.array_equal(det["site"], np.ones(n))
+
+
+def test_site_history_is_the_printed_sum_over_earlier_contacts():
+    """Many impacts of one particle, its charge taken as each contact begins:
+    the product form the oracle carries equals the printed sum
+    1 - sum_m (c_{m-1}/c_0)(A_m/A_p)(chi_m/chi_0)(q_m/q_max) term by term, and
+    with the charge and speed held fixed it is the closed form (1 - a)^M."""
+    p = oracle.Params(rho_p=1150.0)
+    s = _det(SSM(seed=1))
+    d = np.array([60e-6])
+    q_max = -saturation_charge(s, d)[0]          # dq0_min < 0: the wall charges the particle negative
+    site = np.ones(1)
+    q = np.zeros(1)
+    hist_a, hist_c = [], [1.0]
+    rng = np.random.default_rng(3)
+    for m in range(60):
+        sp = rng.uniform(0.2, 3.0, 1)
+        dq, det = ssm_wall_charge(p, s, d, sp, q, np.zeros(1, np.int64), np.full(1, m), site=site)
+        # the contact's share A_m / A_p (chi_m / chi_0)(q_m / q_max), with the Hertz area of Sec. 2.3.1
+        a = hertz_area(p, d, sp)[0] / (math.pi * d[0] ** 2) * det["chi_i"][0] * q[0] / q_max
+        hist_a.append(a)
+        site = det["site"]
+        hist_c.append(site[0])
+        q = q + dq
+        # the printed sum over the contacts so far
+        printed = 1.0 - sum(hist_c[k] * hist_a[k] for k in range(len(hist_a)))
+        assert abs(site[0] - printed) <= 1e-13, (m, site[0], printed)
+    assert hist_c[-1] < 1.0 - 1e-6 and q[0] < 0
+    # fixed charge and speed: (1 - a)^M
+    qf = np.array([0.4 * q_max])
+    site = np.ones(1)
+    for m in range(200):
+        _, det = ssm_wall_charge(p, s, d, np.array([1.5]), qf, np.zeros(1, np.int64), np.full(1, m), site=site)
+        site = det["site"]
+    a = hertz_area(p, d, 1.5)[0] / (math.pi * d[0] ** 2) * det["chi_i"][0] * 0.4
+    assert abs(site[0] - (1.0 - a) ** 200) <= 1e-12
+
+
+def test_site_density_scales_the_particle_sites_linearly():
+    """N_i / N_0 carries c / c_0: in the deterministic limit the impact charge
+    is affine in c (c = 1/2 lies halfway between c = 0 and c = 1), and c = 0
+    leaves only the wall's share mu_w."""
+    p = oracle.Params(rho_p=1150.0)
+    s = _det(SSM(seed=2))
+    n = 50
+    d = np.full(n, 120e-6)
+    sp = np.linspace(0.3, 2.5, n)
+    q = -np.linspace(0.0, 0.8, n) * saturation_charge(s, d)
+    args = (p, s, d, sp, q, np.arange(n), np.zeros(n, np.int64))
+    dq = {c: ssm_wall_charge(*args, site=np.full(n, c))[0] for c in (0.0, 0.5, 1.0)}
+    assert np.allclose(dq[0.5], 0.5 * (dq[0.0] + dq[1.0]), rtol=1e-13, atol=0)
+    _, det = ssm_wall_charge(*args, site=np.zeros(n))
+    assert np.allclose(dq[0.0], det["mu_w"], rtol=1e-15, atol=0)
+
+
+def test_site_history_counts_the_charge_before_the_contact_and_stays_in_bounds():
+    """The depletion of a contact is formed from the charge the particle
+    brings to it (a first contact with q0 = 0 uses up nothing even though it
+    leaves the particle charged); a particle charged against the wall's
+    direction (q / q_max < 0) keeps c / c_0 = 1, and c / c_0 never leaves
+    [0, 1]."""
+    p = oracle.Params(rho_p=1150.0)
+    s = SSM(seed=8)
+    d = np.full(3, 90e-6)
+    qs = saturation_charge(s, d)
+    q = np.array([0.0, 0.5 * qs[1], -0.999 * qs[2]])     # uncharged, against, nearly saturated
+    dq, det = ssm_wall_charge(p, s, d, np.full(3, 1.0), q, np.arange(3), np.zeros(3, np.int64),
+                              site=np.array([1.0, 1.0, 1e-12]))
+    assert det["site"][0] == 1.0 and dq[0] != 0.0
+    assert det["site"][1] == 1.0
+    assert 0.0 <= det["site"][2] < 1e-12
