@@ -11,5 +11,5 @@ drawn here, on the host, from numpy's counter-based Philox generator.
 from .channel import (  # noqa: F401
     Case, CASES, case, y_faces, node_y, friction_velocity, reichardt_uplus,
     Modes, draw_modes, fluid_lattice, Particles, draw_particles, ensemble_cases,
-    Q_SAT, mean_velocity, damping,
+    Q_SAT, mean_velocity, damping, replay_state,
 )

@@ -294,3 +294,30 @@ def draw_particles(c: Case, n: Optional[int] = None) -> Particles:
     vz = np.zeros(n)
     q = rng.standard_normal(n) * c.q0_sigma if c.q0_sigma > 0 else np.zeros(n)
     return Particles(x, y, z, vx, vy, vz, q, d)
+
+
+def replay_state(c: Case, parts: dict, sample_every: int = 1000, wall_every: int = 2000,
+                 seed: int = 77) -> dict:
+    """A copy of a particle state (arrays indexed by particle id) prepared for
+    a one-step replay against the oracle on a subsample: every particle gets a
+    Gaussian charge (std 0.01 q_sat, so that the mesh field matters), and the
+    particles whose id is a multiple of `wall_every` (half of the 1-in-
+    `sample_every` subsample) are placed just inside their reach of a wall,
+    moving towards it, so that the replayed step has wall impacts to compare.
+    Positions and velocities keep the precision of the input arrays."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    out = {k: np.array(v) for k, v in parts.items()}
+    n = out["x"].shape[0]
+    out["q"] = rng.standard_normal(n) * 0.01 * Q_SAT
+    m = np.arange(n) % wall_every == 0
+    k = int(m.sum())
+    d = np.asarray(out["d"][m], np.float64)
+    r = 0.5 * d
+    top = rng.random(k) < 0.5
+    speed = np.abs(rng.standard_normal(k)) * 0.5 + 0.05
+    gap = rng.uniform(0.0, 0.5, k) * speed * c.dt
+    y = np.where(top, c.ly - r - gap, r + gap)
+    dt = out["y"].dtype
+    out["y"][m] = y.astype(dt)
+    out["vy"][m] = np.where(top, speed, -speed).astype(dt)
+    return out
