@@ -200,3 +200,35 @@ def test_adjoint_with_and_without_the_kept_forward_fields():
     a, b = got
     assert abs(a["J"] - b["J"]) <= 1e-12 * abs(a["J"])
     assert np.abs(a["dd"] - b["dd"]).max() <= 1e-11 * np.abs(a["dd"]).max()
+
+
+@pytest.fixture(scope="module")
+def grid128_case():
+    """The differentiation workload's grid (Re_tau 180, 128^3) with 1,000
+    particles near the walls and the oracle gradient of 12 steps."""
+    c, faces, lat, parts = problem(128, 128, 128, n=1000, q_scale=2e-13, vy_scale=0.4, near_wall=0.3, seed=14,
+                                   dplus=(1.0, 1.0))
+    dt, nsteps = 2 * c.dt, 12
+    ref = mean_charge_gradient(oracle.Grid(c.nx, c.nz, c.lx, c.lz, faces), oracle_params(c, U_c=2e3),
+                               oracle_state(parts), lat, dt, nsteps)
+    return c, faces, lat, parts, dt, nsteps, ref
+
+
+@pytest.mark.parametrize("budget", [-1, 0])
+def test_adjoint_on_the_differentiation_grid_matches_oracle_gradient(grid128_case, budget):
+    """Twelve coupled steps on 128^3 with a state kept every 5, so that two of
+    the three segments are recomputed, with the forward fields kept (budget
+    -1) and solved again (budget 0); J, dJ/dU_c, dJ/dkappa_A and every dJ/dd_p
+    against the oracle gradient (FP64 1e-9)."""
+    c, faces, lat, parts, dt, nsteps, ref = grid128_case
+    assert ref["final"]["n_imp"].sum() > 50
+    params = T.Params(precision=T.TRIBO_FP64, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=2e3)
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, torch.from_numpy(lat).cuda(),
+                   max_particles=len(parts["x"]))
+    T.tribo_set_adjoint_memory(ch.ctx, budget)
+    P = T.Particles.from_numpy(parts, T.TRIBO_FP64)
+    J, dU, dK, dd = ch.adjoint(P, dt, nsteps, 5)
+    fin = P.to_numpy()
+    ch.close()
+    assert np.array_equal(fin["n_imp"].astype(np.int64), ref["final"]["n_imp"])
+    check(dict(J=J, dU_c=dU, dkappa_A=dK, dd=dd.cpu().numpy()), ref, 1e-9, f"128^3 budget {budget}")
