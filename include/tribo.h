@@ -57,6 +57,8 @@ typedef int32_t tribo_status;
 #define TRIBO_DEV_ESCAPED   0x1u /* a particle was still outside the contact planes after one reflection */
 #define TRIBO_DEV_NONFINITE 0x2u /* a particle state became NaN or Inf */
 #define TRIBO_DEV_OUTSIDE   0x4u /* a particle position was outside the channel before a step */
+#define TRIBO_DEV_TIMEOUT   0x8u /* a bounded wait between the tasks of a persistent kernel ran out
+                                    (the results of that call are not valid) */
 
 #define TRIBO_FP64  0   /* everything in FP64 */
 #define TRIBO_MIXED 1   /* FP32 particle state, interpolation, force math, cell

@@ -8,7 +8,7 @@ the library is not built or no GPU is present.
 from ._abi import (  # noqa: F401
     TRIBO_FP64, TRIBO_MIXED, TRIBO_DRAG_STOKES, TRIBO_DRAG_SCHILLER_NAUMANN, TRIBO_DRAG_OFF,
     TRIBO_IMPACT_SPEED, TRIBO_IMPACT_NORMAL, TRIBO_DEV_ESCAPED, TRIBO_DEV_NONFINITE,
-    TRIBO_DEV_OUTSIDE, TriboError, load, library_path, exported_names,
+    TRIBO_DEV_OUTSIDE, TRIBO_DEV_TIMEOUT, TriboError, load, library_path, exported_names,
 )
 from .api import (  # noqa: F401
     Params, Particles, Channel, tribo_init, tribo_set_fluid, tribo_set_params, tribo_step,

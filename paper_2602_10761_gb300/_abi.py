@@ -17,6 +17,7 @@ TRIBO_ERR_CAPACITY = 6
 TRIBO_DEV_ESCAPED = 0x1
 TRIBO_DEV_NONFINITE = 0x2
 TRIBO_DEV_OUTSIDE = 0x4
+TRIBO_DEV_TIMEOUT = 0x8
 
 TRIBO_FP64 = 0
 TRIBO_MIXED = 1

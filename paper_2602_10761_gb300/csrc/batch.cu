@@ -219,7 +219,9 @@ tribo_status issue_steps(tribo_batch* b, const std::vector<PView>& home, int cou
             }
             if (!st && c->P.electrostatics) {
                 const int64_t l0 = c->launches;
+                c->in_batch = true;          // the channels solve side by side: split passes
                 st = poisson_solve(c, c->Q, true, c->d_scale_q, true, nullptr, c->E_lat);
+                c->in_batch = false;
                 b->launches += c->launches - l0;
             }
             if (!st) {

@@ -16,6 +16,8 @@
 // Per element: one shared-memory write and one read.
 #pragma once
 
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace tribo {
@@ -90,11 +92,45 @@ struct FourStep {
     static constexpr int BUF = W * CS;                      // complex elements of the transpose buffer
 };
 
+// cache policy of a column transform's loads and stores
+enum Cache {
+    kCached = 0,     // default
+    kL2Only = 1,     // loads through L2 only (ld.global.cg): data other blocks of the same launch
+                     // wrote (this SM's L1 may hold an older copy)
+    kStream = 2,     // read or written once: evict-first in L2 (ld/st.global.cs), so that streams
+                     // do not push out the data a launch keeps in L2
+};
+
+template <class R, int C>
+__device__ __forceinline__ cplx<R> ld_cplx(const cplx<R>* p) {
+    using V = std::conditional_t<sizeof(R) == 4, float2, double2>;
+    if constexpr (C == kL2Only) {
+        const V v = __ldcg(reinterpret_cast<const V*>(p));
+        return cplx<R>{v.x, v.y};
+    } else if constexpr (C == kStream) {
+        const V v = __ldcs(reinterpret_cast<const V*>(p));
+        return cplx<R>{v.x, v.y};
+    } else {
+        return *p;
+    }
+}
+
+template <class R, int C>
+__device__ __forceinline__ void st_cplx(cplx<R>* p, cplx<R> a) {
+    using V = std::conditional_t<sizeof(R) == 4, float2, double2>;
+    V v;
+    v.x = a.re;
+    v.y = a.im;
+    if constexpr (C == kStream) __stcs(reinterpret_cast<V*>(p), v);
+    else *reinterpret_cast<V*>(p) = v;
+}
+
 // Transform W columns: column `col` of the block starts at src + col (dst +
 // col) and its element n sits n * rs_src (rs_dst) further.  MUL: multiply the
-// input element n by -i mul[n] first (spectral derivative).  All threads of
-// the block call this; it synchronises twice.
-template <class R, int SIGN, int N, int NT, bool MUL>
+// input element n by -i mul[n] first (spectral derivative).  LD, ST: cache
+// policies of the loads from src and the stores to dst (Cache).  All threads
+// of the block call this; it synchronises twice.
+template <class R, int SIGN, int N, int NT, bool MUL, int LD = kCached, int ST = kCached>
 __device__ __forceinline__ void column_fft(const cplx<R>* src, size_t rs_src, cplx<R>* dst, size_t rs_dst,
                                            int ncol, const cplx<R>* __restrict__ tw, const R* __restrict__ mul,
                                            cplx<R>* buf) {
@@ -106,7 +142,7 @@ __device__ __forceinline__ void column_fft(const cplx<R>* src, size_t rs_src, cp
     if (live && r < N2) {
         cplx<R> y[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) y[n1] = src[col + (size_t)(N2 * n1 + r) * rs_src];
+        for (int n1 = 0; n1 < N1; ++n1) y[n1] = ld_cplx<R, LD>(src + col + (size_t)(N2 * n1 + r) * rs_src);
         if constexpr (MUL) {
 #pragma unroll
             for (int n1 = 0; n1 < N1; ++n1) {
@@ -133,7 +169,7 @@ __device__ __forceinline__ void column_fft(const cplx<R>* src, size_t rs_src, cp
         for (int n2 = 0; n2 < N2; ++n2) z[n2] = b[n2 * (N1 + 1)];
         reg_dft<R, SIGN, N2, N1>(z, tw);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) dst[col + (size_t)(r + N1 * k2) * rs_dst] = z[k2];
+        for (int k2 = 0; k2 < N2; ++k2) st_cplx<R, ST>(dst + col + (size_t)(r + N1 * k2) * rs_dst, z[k2]);
     }
     __syncthreads();
 }

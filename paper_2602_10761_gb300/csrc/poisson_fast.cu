@@ -501,10 +501,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_zinv4(const cplx<R>* __restrict
 // inverse of length M = N1 N2, and the group stores x_2n, x_2n+1 as pairs.
 // Wall lines (jn = 0, ny+1) carry E_x = E_z = 0.
 template <class R>
-__device__ __forceinline__ void store_pair(R* p, R a, R b) {
-    if constexpr (sizeof(R) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
-    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
-}
+__device__ __forceinline__ void store_pair(R* p, R a, R b);
 
 template <class R, int M>
 __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict__ F, R* __restrict__ E,
@@ -595,6 +592,382 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
         }
     }
     }
+}
+
+// ---------------------------------------------------------------- fused inverse pipeline
+// The inverse z transforms of a node plane and its inverse x transforms with
+// the field run as ONE persistent launch, the two transforms of a plane being
+// tasks of one queue: producer tasks = tiles of m_x columns (inverse z
+// transforms of phi-hat, of -i sin(2 pi m_z / nz)/dz phi-hat and of the E_y
+// spectrum into three fields of a plane slot), consumer tasks = groups of x
+// lines (inverse real x transforms of the slot's fields to E_x, E_y, E_z and
+// phi).  The slots form a ring of P planes that stays in L2: the three
+// intermediate fields never reach HBM, where the split passes wrote them
+// (0.31 GB at 384x256x256) and read them back.  The spectra read and the
+// field written pass with evict-first hints, so that they do not push the
+// ring out of L2.
+//
+// Tasks are claimed in order from one counter.  Stage s holds the producer
+// tasks of plane s and then the consumer tasks of plane s - L.  A consumer
+// waits until all producer tasks of its plane are done; a producer of plane
+// p >= P waits until all consumers of plane p - P (the slot's previous plane)
+// are done, and P > L.  Every task therefore waits only on tasks claimed
+// before it by blocks that are already running, so the queue drains whatever
+// the residency; each wait is bounded, and a wait that runs out sets
+// TRIBO_DEV_TIMEOUT in the device error word instead of hanging.  Data a
+// task reads from the ring is loaded through L2 (ld.global.cg), never from a
+// possibly stale L1 line; producers publish with a release increment after
+// the barrier that ends the task, consumers acquire the counter before
+// reading.  Both waits need slack: the resident blocks hold about 21 stages
+// at once (608 blocks over 29 tasks per plane at 384x256x256), so a consumer
+// should trail its producers by L = 32 stages and a producer its slot's
+// previous consumers by P - L = 40 (FP32, 384x256x256: 302 us with L = 24,
+// P = 32; 265 us with 40, 48; 248 us with 24, 64; 245 us with 32, 72, the
+// ring then 86 MB of L2).  The split passes move the three fields through
+// HBM only when they do not fit in L2: the pipeline is used where they take
+// at least 64 MiB (at 128^3, 26 MB, the split passes measured 106 against
+// 121 us for the whole solve).
+constexpr int kMaxPlanes = 1026;            // node planes of the tallest grid (ny = 1024)
+#ifndef TRIBO_PIPE_LOOK
+#define TRIBO_PIPE_LOOK 32
+#endif
+#ifndef TRIBO_PIPE_SLOTS
+#define TRIBO_PIPE_SLOTS 72
+#endif
+constexpr int kPipeLook = TRIBO_PIPE_LOOK;  // L: stages a plane's consumers trail its producers
+constexpr int kPipeSlots = TRIBO_PIPE_SLOTS;  // P: ring slots (> L)
+constexpr unsigned kSpinLimit = 1u << 22;   // polls of a wait (>= ~1 s with the back-off)
+
+struct PipeSync {                           // one launch's counters, zeroed before it
+    unsigned next;                          // next task to claim
+    unsigned pad[31];
+    unsigned a_done[kMaxPlanes];            // finished producer tasks per plane
+    unsigned b_done[kMaxPlanes];            // finished consumer tasks per plane
+};
+
+struct Pipe {
+    int planes;      // planes of the stage
+    int na, nb;      // producer and consumer tasks per plane
+    int L, P;        // lookahead in stages, ring slots
+    unsigned total;  // planes * (na + nb)
+};
+
+Pipe make_pipe(int planes, int na, int nb) {
+    Pipe p{};
+    p.planes = planes;
+    p.na = na;
+    p.nb = nb;
+    p.L = std::min(kPipeLook, planes);
+    p.P = kPipeSlots;
+    p.total = (unsigned)planes * (unsigned)(na + nb);
+    return p;
+}
+
+// task t -> (consumer?, plane, index within the plane's tasks of that kind)
+__device__ __forceinline__ void pipe_task(const Pipe& p, unsigned t, bool& cons, int& plane, int& idx) {
+    const unsigned head = (unsigned)p.L * p.na;
+    const unsigned per = (unsigned)(p.na + p.nb);
+    const unsigned body = (unsigned)(p.planes - p.L) * per;
+    if (t < head) {
+        cons = false;
+        plane = (int)(t / p.na);
+        idx = (int)(t % p.na);
+    } else if (t - head < body) {
+        const unsigned u = t - head;
+        const int st = p.L + (int)(u / per);
+        const int r = (int)(u % per);
+        cons = r >= p.na;
+        plane = cons ? st - p.L : st;
+        idx = cons ? r - p.na : r;
+    } else {
+        const unsigned u = t - head - body;
+        cons = true;
+        plane = p.planes - p.L + (int)(u / p.nb);
+        idx = (int)(u % p.nb);
+    }
+}
+
+// thread 0: wait until *ctr >= target (acquire), bounded
+__device__ __forceinline__ void pipe_wait(const unsigned* ctr, unsigned target, unsigned* err) {
+    unsigned it = 0;
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return;
+        if (++it >= kSpinLimit) {
+            atomicOr(err, TRIBO_DEV_TIMEOUT);
+            return;
+        }
+        __nanosleep(256);
+    }
+}
+
+// Task loop of a fused launch.  A block claims its next task only when it
+// can start it (claims in order are what keeps every wait pointed at tasks
+// that are running), thread 0 issuing the claim as its own part of the
+// current task ends, so that the round trip overlaps the rest of the block's
+// work.  Thread 0 waits for a task's dependency before the block starts it,
+// and publishes a finished task with a release increment after the barrier
+// that ends it (the release covers every write the barrier ordered before it).
+struct PipeLoop {
+    unsigned* s_next;    // shared: the block's next task
+    unsigned t;          // current task
+};
+
+__device__ __forceinline__ void pipe_start(PipeLoop& L, PipeSync* sy) {
+    if (threadIdx.x == 0) *L.s_next = atomicAdd(&sy->next, 1u);
+    __syncthreads();
+    L.t = *L.s_next;
+}
+
+// thread 0 waits for the task's dependency; then the block may read
+__device__ __forceinline__ void pipe_acquire(PipeLoop& L, const Pipe& p, PipeSync* sy, bool cons, int plane,
+                                             unsigned* err) {
+    if (threadIdx.x == 0) {
+        if (cons) pipe_wait(&sy->a_done[plane], (unsigned)p.na, err);
+        else if (plane >= p.P) pipe_wait(&sy->b_done[plane - p.P], (unsigned)p.nb, err);
+    }
+    __syncthreads();
+}
+
+// the block's writes of the task are done: claim the next task, publish this one
+__device__ __forceinline__ void pipe_release(PipeLoop& L, PipeSync* sy, bool cons, int plane) {
+    unsigned nt = 0;
+    if (threadIdx.x == 0) nt = atomicAdd(&sy->next, 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* ctr = cons ? &sy->b_done[plane] : &sy->a_done[plane];
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+        *L.s_next = nt;
+    }
+    __syncthreads();
+    L.t = *L.s_next;
+}
+
+template <class R, int M, int NZ>
+constexpr int fused_min_blocks() { return sizeof(R) == 4 ? 4 : 2; }
+
+// inverse producer: node plane jn, m_x columns of a tile: the three slot fields
+// (0: IFFT_z phi-hat, 1: IFFT_z E_y spectrum, 2: IFFT_z -i sin_z phi-hat);
+// without E only field 0
+template <class R, int NZ>
+__device__ __noinline__ void inv_ztask(const cplx<R>* __restrict__ S, const cplx<R>* __restrict__ Fy,
+                                       cplx<R>* slot, int ny, int nxh, int jn, int tile, int want_e,
+                                       const cplx<R>* __restrict__ tw, const R* __restrict__ sz, cplx<R>* buf) {
+    using F4 = fft::FourStep<NZ, kThreads>;
+    const int mx0 = tile * F4::W;
+    const int ncol = min(F4::W, nxh - mx0);
+    const size_t fs = (size_t)NZ * nxh;
+    // the spectra are read once (phi-hat twice, the second time from L1): evict-first in L2
+    if (want_e)
+        fft::column_fft<R, 1, NZ, kThreads, false, fft::kStream>(Fy + (size_t)jn * nxh + mx0, (size_t)(ny + 2) * nxh,
+                                                                 slot + fs + mx0, (size_t)nxh, ncol, tw, nullptr, buf);
+    if (jn >= 1 && jn <= ny) {
+        const cplx<R>* ph = S + (size_t)(jn - 1) * nxh + mx0;
+        if (want_e) {
+            fft::column_fft<R, 1, NZ, kThreads, false>(ph, (size_t)ny * nxh, slot + mx0, (size_t)nxh, ncol, tw,
+                                                       nullptr, buf);
+            fft::column_fft<R, 1, NZ, kThreads, true, fft::kStream>(ph, (size_t)ny * nxh, slot + 2 * fs + mx0,
+                                                                    (size_t)nxh, ncol, tw, sz, buf);
+        } else {
+            fft::column_fft<R, 1, NZ, kThreads, false, fft::kStream>(ph, (size_t)ny * nxh, slot + mx0, (size_t)nxh,
+                                                                     ncol, tw, nullptr, buf);
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void store_pair(R* p, R a, R b) {
+    if constexpr (sizeof(R) == 4) *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    else *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// inverse consumer: node lines (k, jn), k = grp * LPB + l: E_x (the slot's field 0
+// with the x multiplier -i sin(2 pi m / nx) / dx), E_y (field 1), E_z (field 2),
+// phi (field 0); wall lines carry E_x = E_z = 0
+template <class R, int M>
+__device__ __noinline__ void inv_xtask(const cplx<R>* slot, R* __restrict__ E, double* __restrict__ phi, int ny,
+                                       int nz, int jn, int grp, int want_phi, int want_e, R norm, size_t nodes,
+                                       const cplx<R>* __restrict__ tw, const cplx<R>* __restrict__ t2,
+                                       const R* __restrict__ sx, cplx<R>* buf) {
+    using F4 = fft::FourStep<M, kThreads>;
+    constexpr int N1 = F4::N1, N2 = F4::N2, TPC = F4::TPC, LPB = F4::W, CS = F4::CS;
+    constexpr int NX = 2 * M, NXH = M + 1;
+    const int nyn = ny + 2;
+    const int r = threadIdx.x % TPC;
+    const int l = threadIdx.x / TPC;
+    const int k = grp * LPB + l;
+    const bool live = l < LPB && k < nz;
+    const bool interior = jn >= 1 && jn <= ny;
+    const size_t fs = (size_t)nz * NXH;
+    const size_t line = (size_t)k * nyn + jn;
+    const int nf = want_phi ? 4 : 3;
+    for (int f = want_e ? 0 : 3; f < nf; ++f) {
+        const bool active = live && (f == 1 || interior);
+        const int src = f == 3 ? 0 : f;
+        if (active && r < N2) {
+            const cplx<R>* X = slot + (size_t)src * fs + (size_t)k * NXH;
+            cplx<R> y[N1];
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+                const int m = N2 * n1 + r;
+                cplx<R> xa = fft::ld_cplx<R, fft::kL2Only>(X + m), xb = fft::ld_cplx<R, fft::kL2Only>(X + M - m);
+                if (f == 0) {     // E_x multiplier -i sin(2 pi m / nx) / dx
+                    xa = cplx<R>{sx[m] * xa.im, -sx[m] * xa.re};
+                    xb = cplx<R>{sx[M - m] * xb.im, -sx[M - m] * xb.re};
+                }
+                const cplx<R> cb = conj(xb);
+                const cplx<R> sum = xa + cb;
+                const cplx<R> t = conj(tw[m]) * (xa - cb);
+                y[n1] = cplx<R>{sum.re - t.im, sum.im + t.re};
+            }
+            fft::reg_dft<R, 1, N1, 2 * N2>(y, tw);
+#pragma unroll
+            for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * conj(t2[k1 * N2 + r]);
+            cplx<R>* b = buf + l * CS + r * (N1 + 1);
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) b[k1] = y[k1];
+        }
+        __syncthreads();
+        if (active && r < N1) {
+            cplx<R> z[N2];
+            const cplx<R>* b = buf + l * CS + r;
+#pragma unroll
+            for (int n2 = 0; n2 < N2; ++n2) z[n2] = b[n2 * (N1 + 1)];
+            fft::reg_dft<R, 1, N2, 2 * N1>(z, tw);
+            if (f < 3) {       // written once: evict-first in L2
+                cplx<R>* row = reinterpret_cast<cplx<R>*>(E + (size_t)f * nodes + line * NX);
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2)
+                    fft::st_cplx<R, fft::kStream>(row + r + N1 * k2, cplx<R>{z[k2].re * norm, z[k2].im * norm});
+            } else {
+                double2* prow = reinterpret_cast<double2*>(phi + ((size_t)k * ny + (jn - 1)) * NX);
+#pragma unroll
+                for (int k2 = 0; k2 < N2; ++k2)
+                    __stcs(prow + r + N1 * k2, make_double2((double)(z[k2].re * norm), (double)(z[k2].im * norm)));
+            }
+        }
+        __syncthreads();
+    }
+    if (want_e && live && !interior) {
+        R* ex = E + line * NX;
+        R* ez = E + 2 * nodes + line * NX;
+        for (int i = r; i < NX; i += TPC) {
+            ex[i] = (R)0;
+            ez[i] = (R)0;
+        }
+    }
+}
+
+template <class R, int M, int NZ>
+__global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, M, NZ>())) k_inv_fused(
+    const cplx<R>* __restrict__ S, const cplx<R>* __restrict__ Fy, cplx<R>* ring, R* __restrict__ E,
+    double* __restrict__ phi, int ny, int want_phi, int want_e, R norm, size_t nodes,
+    const double* __restrict__ sinx, const double* __restrict__ sinz, const cplx<R>* __restrict__ twx_g,
+    const cplx<R>* __restrict__ twz_g, PipeSync* sy, Pipe pipe, unsigned* err) {
+    using FX = fft::FourStep<M, kThreads>;
+    constexpr int NX = 2 * M, NXH = M + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<R>* twx = reinterpret_cast<cplx<R>*>(smem_raw);     // exp(-2 pi i e / NX)
+    cplx<R>* t2 = twx + NX;                                    // t2[k1 N2 + r] = W_M^(r k1)
+    cplx<R>* twz = t2 + FX::N1 * FX::N2;
+    cplx<R>* buf = twz + NZ;
+    constexpr int BZ = fft::FourStep<NZ, kThreads>::BUF;
+    R* sx = reinterpret_cast<R*>(buf + (FX::BUF > BZ ? FX::BUF : BZ));
+    R* sz = sx + NXH;
+    __shared__ unsigned s_next;
+    for (int i = threadIdx.x; i < NX; i += kThreads) twx[i] = twx_g[i];
+    for (int i = threadIdx.x; i < FX::N1 * FX::N2; i += kThreads) t2[i] = twx_g[2 * (i % FX::N2) * (i / FX::N2)];
+    for (int i = threadIdx.x; i < NXH; i += kThreads) sx[i] = from_f64<R>(sinx[i]);
+    for (int i = threadIdx.x; i < NZ; i += kThreads) {
+        twz[i] = twz_g[i];
+        sz[i] = from_f64<R>(sinz[i]);
+    }
+    const size_t slot_elems = 3 * (size_t)NZ * NXH;
+    PipeLoop L{&s_next, 0u};
+    pipe_start(L, sy);
+    while (L.t < pipe.total) {
+        bool cons;
+        int plane, idx;
+        pipe_task(pipe, L.t, cons, plane, idx);
+        pipe_acquire(L, pipe, sy, cons, plane, err);
+        cplx<R>* slot = ring + (size_t)(plane % pipe.P) * slot_elems;
+        if (cons) inv_xtask<R, M>(slot, E, phi, ny, NZ, plane, idx, want_phi, want_e, norm, nodes, twx, t2, sx, buf);
+        else inv_ztask<R, NZ>(S, Fy, slot, ny, NXH, plane, idx, want_e, twz, sz, buf);
+        pipe_release(L, sy, cons, plane);
+    }
+}
+
+template <class R, int M, int NZ>
+size_t inv_fused_smem() {
+    using FX = fft::FourStep<M, kThreads>;
+    return sizeof(cplx<R>) * (2 * M + FX::N1 * FX::N2 + NZ + std::max(FX::BUF, fft::FourStep<NZ, kThreads>::BUF)) +
+           sizeof(R) * (M + 1 + NZ);
+}
+
+// resident blocks per SM of a fused kernel (queried once per instantiation)
+template <class K>
+int fused_grid(K kernel, size_t smem, int num_sms, unsigned tasks, int* cache) {
+    if (*cache == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kThreads, smem) != cudaSuccess || b < 1) b = 1;
+        *cache = b;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)tasks, (int64_t)*cache * num_sms));
+}
+
+template <class R, int M, int NZ>
+tribo_status launch_inv_fused(tribo_ctx* c, void* E, double* phi) {
+    const Pipe pipe = make_pipe(c->ny + 2, (c->nxh + fft::FourStep<NZ, kThreads>::W - 1) / fft::FourStep<NZ, kThreads>::W,
+                                (NZ + fft::FourStep<M, kThreads>::W - 1) / fft::FourStep<M, kThreads>::W);
+    PipeSync* sy = (PipeSync*)c->d_pipe;
+    TRIBO_CUDA(cudaMemsetAsync(sy, 0, sizeof(PipeSync), c->stream));
+    static int occ = 0;
+    const size_t smem = inv_fused_smem<R, M, NZ>();
+    const int grid = fused_grid(k_inv_fused<R, M, NZ>, smem, c->num_sms, pipe.total, &occ);
+    const size_t fstride = (size_t)NZ * (c->ny + 2) * c->nxh;
+    k_inv_fused<R, M, NZ><<<grid, kThreads, smem, c->stream>>>(
+        (const cplx<R>*)c->S, (const cplx<R>*)c->F + fstride, (cplx<R>*)c->ring, (R*)E, phi, c->ny,
+        phi != nullptr ? 1 : 0, E != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)NZ)),
+        (size_t)NZ * (c->ny + 2) * c->nx, c->d_sinx, c->d_sinz, (const cplx<R>*)c->d_twx,
+        (const cplx<R>*)c->d_twz, sy, pipe, &c->d_acc->err);
+    return TRIBO_OK;
+}
+
+template <class R, int M, int NZ>
+tribo_status attr_fused(int optin) {
+    if (inv_fused_smem<R, M, NZ>() + 64 > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
+    // the fused kernel also holds a few bytes of static shared memory: its dynamic limit is its
+    // own (fixed) need, which leaves room for it
+    TRIBO_CUDA(cudaFuncSetAttribute(k_inv_fused<R, M, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)inv_fused_smem<R, M, NZ>()));
+    return TRIBO_OK;
+}
+
+// (nx/2, nz) pairs with a fused inverse pipeline (the grids whose intermediate fields
+// outgrow L2 at the usual heights); other lengths run the split passes
+#define TRIBO_FUSED_PAIRS(X) X(128, 256) X(192, 256) X(256, 256)
+
+bool fused_pair(int m, int nz) {
+#define CASE(M, NZ) if (m == M && nz == NZ) return true;
+    TRIBO_FUSED_PAIRS(CASE)
+#undef CASE
+    return false;
+}
+
+template <class R>
+tribo_status dispatch_inv_fused(tribo_ctx* c, void* E, double* phi) {
+#define CASE(M, NZ) if (c->nx / 2 == M && c->nz == NZ) return launch_inv_fused<R, M, NZ>(c, E, phi);
+    TRIBO_FUSED_PAIRS(CASE)
+#undef CASE
+    return TRIBO_ERR_UNSUPPORTED;
+}
+template <class R>
+tribo_status dispatch_attr_fused(int m, int nz, int optin) {
+#define CASE(M, NZ) if (m == M && nz == NZ) return attr_fused<R, M, NZ>(optin);
+    TRIBO_FUSED_PAIRS(CASE)
+#undef CASE
+    return TRIBO_ERR_UNSUPPORTED;
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -764,6 +1137,11 @@ template <class R>
 tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src, double* phi,
                         void* E) {
     const int ny = c->ny, nz = c->nz, nxh = c->nxh;
+    // the inverse transforms as one pipelined launch where the grid has one, except in a batch,
+    // whose channels solve side by side on their own streams (a launch that waits on its own
+    // tasks would hold SMs the other channels' passes could use)
+    // (the potential-only solves of the adjoint also keep the split passes)
+    const bool fused = c->ring != nullptr && !c->in_batch && E != nullptr;
     phase_begin(c, PH_FWD_X);
     if (src_f64) dispatch_xfwd<R, double>(c, (double*)src, scale, zero_src);
     else dispatch_xfwd<R, R>(c, (R*)src, scale, zero_src);
@@ -805,6 +1183,13 @@ tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* sca
             (const float4*)c->d_yec, ny, nz, nxh);
     }
     TRIBO_LAUNCHED(c);
+    if (fused) {
+        phase_begin(c, PH_INV_Z);
+        tribo_status st = dispatch_inv_fused<R>(c, E, phi);
+        if (st) return st;
+        TRIBO_LAUNCHED(c);
+        return TRIBO_OK;
+    }
     phase_begin(c, PH_INV_Z);
     dispatch_zinv<R>(c, E == nullptr);
     TRIBO_LAUNCHED(c);
@@ -894,6 +1279,20 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     TRIBO_CUDA(cudaGetDevice(&dev));
     TRIBO_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     tribo_status st;
+    // grids with a fused inverse pipeline: the ring of plane slots (three fields per slot) and
+    // the launch's task counters
+    const size_t csz0 = c->prec == TRIBO_FP64 ? sizeof(cplx<double>) : sizeof(cplx<float>);
+    if (fused_pair(nx / 2, nz) && 3 * (size_t)nz * (ny + 2) * nxh * csz0 >= ((size_t)64 << 20)) {
+        const size_t csz = c->prec == TRIBO_FP64 ? sizeof(cplx<double>) : sizeof(cplx<float>);
+        st = c->prec == TRIBO_FP64 ? dispatch_attr_fused<double>(nx / 2, nz, optin)
+                                   : dispatch_attr_fused<float>(nx / 2, nz, optin);
+        if (st == TRIBO_OK) {
+            TRIBO_CUDA(cudaMalloc(&c->ring, (size_t)kPipeSlots * 3 * nz * nxh * csz));
+            TRIBO_CUDA(cudaMalloc(&c->d_pipe, sizeof(PipeSync)));
+        } else if (st != TRIBO_ERR_UNSUPPORTED) {
+            return st;
+        }
+    }
     if (c->prec == TRIBO_FP64) {
         if ((st = twiddles<double>(nx, &c->d_twx)) || (st = twiddles<double>(nz, &c->d_twz))) return st;
         return dispatch_attr<double>(nx, nz, optin);
@@ -916,7 +1315,9 @@ void poisson_fast_free(tribo_ctx* c) {
     cudaFree(c->d_twz);
     cudaFree(c->d_yads);
     cudaFree(c->d_yec);
-    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = nullptr;
+    cudaFree(c->ring);
+    cudaFree(c->d_pipe);
+    c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = c->ring = c->d_pipe = nullptr;
 }
 
 tribo_status poisson_fast_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,
