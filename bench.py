@@ -119,12 +119,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, workload=WORKLOAD):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
     when the kernel's sources changed after the counters were taken."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", f"{kernel}_re550_384.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     m = re.search(r"<!-- traffic: (\{.*\}) -->", open(path).read())
@@ -492,16 +492,22 @@ def oracle_subsample_report(T, torch, c, faces, lat, state, every=1000):
             "seconds": time.perf_counter() - t0}
 
 
-def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world=1, channels=64, scale=1.0):
+def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world=1, channels=64, scale=1.0,
+                 timed_steps=40):
     """Batched ensemble of 64 independent channels (Re_tau in {180, 300, 395,
     550}, grids 64^3 to 192x128x128, 50k-2M particles each, d+ in [0.5, 3]):
     aggregate particle-steps/s of the batch (graph-captured steps, persistent
     particle kernel over all channels, autotuned shape) against the same
     channels stepped one after another with tribo_step.  With several ranks the
-    channels are sharded over the ranks (independent problems, no exchange)."""
+    channels are sharded over the ranks (independent problems, no exchange).
+    The roofline of the batch particle kernel: per launch, every channel's
+    particles x PARTICLE_BYTES + its touched lattice nodes (of the drawn
+    positions) x NODE_BYTES + its cells x CELL_BYTES, over the kernel's mean
+    event-timed duration in `timed_steps` further steps."""
     all_cases = synth.ensemble_cases(channels, scale=scale)
     cases = shard(all_cases, rank, world)
     chans, Ps, dts = [], [], []
+    alg_bytes = 0                      # the batch particle kernel's algorithmic bytes per launch
     for c in cases:
         faces = synth.y_faces(c.ny, c.delta, c.gamma)
         params = T.Params(precision=T.TRIBO_MIXED, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1.0,
@@ -512,6 +518,8 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
         T.tribo_eval_modes(ch.ctx, 0.0, None)          # frozen lattice from the device mode sum
         ch.set_modes(None)
         P = synth.draw_particles(c)
+        alg_bytes += (c.n_particles * PARTICLE_BYTES + touched_nodes(c, faces, P.x, P.y, P.z) * NODE_BYTES
+                      + c.nx * c.ny * c.nz * CELL_BYTES)
         Ps.append(T.Particles.from_numpy(dict(x=P.x, y=P.y, z=P.z, vx=P.vx, vy=P.vy, vz=P.vz, d=P.d, q=P.q),
                                          T.TRIBO_MIXED, device="cuda"))
         chans.append(ch)
@@ -533,6 +541,15 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
     B.sync()
     batch_ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     launches = B.launches - l0
+    # the particle kernel alone: events around its launches (direct launches while timed)
+    B.timing(True)
+    B.step(Ps, dts, timed_steps)
+    kern_ms, kern_n = B.kernel_time()
+    B.timing(False)
+    B.sync()
+    kern_ms = max_over_ranks(kern_ms / max(kern_n, 1), "cuda")
+    hbm_peak, peak_kind = measured_peaks()
+    ach = alg_bytes / (kern_ms * 1e-3) / 1e9
     B.close()
     # the same channels one after another (tribo_step per channel)
     seq_ms = 0.0
@@ -555,7 +572,11 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
             "steps": steps, "ms_per_step": batch_ms / steps, "particle_steps_per_s": batch_rate,
             "sequential_particle_steps_per_s": seq_rate, "sequential_steps": seq_steps,
             "speedup_vs_sequential": batch_rate / seq_rate, "autotuned_shape": shape, "autotune_s": tune_s,
-            "kernels_per_step": launches / steps, "vs_fp64_gpu": check}
+            "kernels_per_step": launches / steps, "vs_fp64_gpu": check,
+            "roofline": {"bound": "hbm", "kernel": "k_step_batch", "achieved": ach, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": ach / hbm_peak, "peak_kind": peak_kind,
+                         "alg_bytes": alg_bytes, "ms_per_launch": kern_ms, "timed_launches": kern_n,
+                         "traffic": measured_traffic("k_step_batch", "ensemble")}}
 
 
 def batch_vs_fp64(T, torch, cases, steps=10, sort_every=5):

@@ -366,7 +366,9 @@ tribo_status tribo_poisson_noalloc(const tribo_grid* grid, double eps, int32_t p
  * size (Sec. 4).  Every step forks one branch per channel (cell sort when
  * due, Poisson solve and field) and joins in ONE persistent particle kernel
  * over all channels' particles; steps are captured into a CUDA graph and
- * replayed.  The channels must share precision and device and use frozen
+ * replayed.  Mixed-precision channels that share a grid whose transform
+ * lengths are compiled in solve together: each pass of their Poisson solves
+ * is one launch over all of them.  The channels must share precision and device and use frozen
  * gas lattices (no tribo_set_modes).  While a batch exists, its channels must
  * not be stepped or solved (tribo_step, tribo_poisson, tribo_adjoint) on their
  * own concurrently with it: they share the channel's work arrays.  sort_every: re-sort each
@@ -396,6 +398,20 @@ tribo_status tribo_batch_sync(tribo_batch* b);
 /* Kernels the batch has executed (direct launches plus the kernels of each
  * graph replay). */
 int64_t      tribo_batch_launch_count(const tribo_batch* b);
+
+/* Time the batch's particle kernel (the step of Sec. 2.1-2.3 over all
+ * channels): enable != 0 starts an empty record, 0 stops recording.  While it
+ * is on, tribo_batch_step issues every step as direct launches (no graph
+ * replay) and brackets each particle-kernel launch with CUDA events on the
+ * batch's stream.  TRIBO_ERR_ARG for b NULL; TRIBO_ERR_CUDA if events cannot
+ * be made. */
+tribo_status tribo_batch_timing(tribo_batch* b, int32_t enable);
+
+/* Wait for the timed launches and read the record: *total_ms, the summed
+ * device time of the particle-kernel launches since tribo_batch_timing (or the
+ * last read), and *launches, their number; the record restarts empty.
+ * TRIBO_ERR_ARG for a NULL argument. */
+tribo_status tribo_batch_kernel_time(tribo_batch* b, double* total_ms, int64_t* launches);
 void         tribo_batch_destroy(tribo_batch* b);
 
 const char*  tribo_strerror(tribo_status s);

@@ -100,6 +100,8 @@ _SIGS = {
                                      C.c_int32]),
     "tribo_batch_sync": (C.c_int32, [C.c_void_p]),
     "tribo_batch_launch_count": (C.c_int64, [C.c_void_p]),
+    "tribo_batch_timing": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "tribo_batch_kernel_time": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "tribo_batch_destroy": (None, [C.c_void_p]),
     "tribo_strerror": (C.c_char_p, [C.c_int32]),
     "tribo_last_error": (C.c_char_p, []),

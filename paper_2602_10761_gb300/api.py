@@ -406,6 +406,17 @@ class Batch:
     def launches(self) -> int:
         return int(load().tribo_batch_launch_count(self.handle))
 
+    def timing(self, enable: bool) -> None:
+        """Start (True) or stop timing the particle kernel; while on, steps run as direct launches."""
+        check(load().tribo_batch_timing(self.handle, 1 if enable else 0), "tribo_batch_timing")
+
+    def kernel_time(self):
+        """(total milliseconds, launches) of the timed particle-kernel launches; restarts the record."""
+        ms = C.c_double()
+        n = C.c_int64()
+        check(load().tribo_batch_kernel_time(self.handle, C.byref(ms), C.byref(n)), "tribo_batch_kernel_time")
+        return float(ms.value), int(n.value)
+
     def close(self) -> None:
         if self.handle:
             load().tribo_batch_destroy(self.handle)

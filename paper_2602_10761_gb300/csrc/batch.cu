@@ -141,6 +141,17 @@ struct tribo_batch {
     int graph_steps = 0;
     int64_t graph_kernels = 0;
     int64_t launches = 0;
+    // channels solved together: groups of mixed-precision channels with one compiled-length
+    // grid (each split pass one launch over the group), and each channel's group (-1: alone)
+    std::vector<void*> groups;
+    std::vector<std::vector<int>> members;
+    std::vector<int> group_of;
+    // timing of the particle kernel's direct launches (graph replays are not timed)
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    int tev_used = 0;
+    double t_ms = 0.0;
+    int64_t t_n = 0;
 };
 
 namespace tribo {
@@ -197,6 +208,20 @@ tribo_status upload_tiles(tribo_batch* b, const std::vector<PView>& views, int t
     return TRIBO_OK;
 }
 
+// add the timed launches recorded so far to the total (waits for the last one)
+tribo_status flush_batch_timing(tribo_batch* b) {
+    if (b->tev_used == 0) return TRIBO_OK;
+    TRIBO_CUDA(cudaEventSynchronize(b->tev[b->tev_used - 1]));
+    for (int k = 0; k < b->tev_used; k += 2) {
+        float ms = 0.f;
+        TRIBO_CUDA(cudaEventElapsedTime(&ms, b->tev[k], b->tev[k + 1]));
+        b->t_ms += ms;
+        b->t_n += 1;
+    }
+    b->tev_used = 0;
+    return TRIBO_OK;
+}
+
 // issue `count` steps starting at batch step b->steps (capture or direct);
 // alt: whether the current particle sets are the contexts' second sets
 template <class R>
@@ -205,8 +230,16 @@ tribo_status issue_steps(tribo_batch* b, const std::vector<PView>& home, int cou
     for (int s = 0; s < count; ++s) {
         const bool sort_now = b->sort_every > 0 && (b->steps % b->sort_every) == 0;
         TRIBO_CUDA(cudaEventRecord(b->fork, b->stream));
+        // a group solves together when all its channels have the field on
+        std::vector<bool> grouped(b->groups.size(), true);
+        for (int i = 0; i < b->n; ++i)
+            if (b->group_of[i] >= 0 && !b->ch[i]->P.electrostatics) grouped[b->group_of[i]] = false;
         for (int i = 0; i < b->n; ++i) {
             tribo_ctx* c = b->ch[i];
+            const int gi = b->group_of[i];
+            const bool lead = gi >= 0 && grouped[gi] && b->members[gi][0] == i;
+            const bool solve = c->P.electrostatics && (gi < 0 || !grouped[gi]);
+            if (!(sort_now && home[i].n > 0) && !solve && !lead) continue;
             cudaStream_t keep = c->stream;
             c->stream = b->br[i];
             st = TRIBO_OK;
@@ -214,16 +247,18 @@ tribo_status issue_steps(tribo_batch* b, const std::vector<PView>& home, int cou
             if (e != cudaSuccess) st = cuda_fail(e, "batch fork");
             if (!st && sort_now && home[i].n > 0) {
                 const PView hv = home[i], ov = alt_of(c, home[i]);
+                const int64_t l0 = c->launches;
                 st = alt ? particles_sort(c, ov, hv) : particles_sort(c, hv, ov);
-                b->launches += 5;
+                b->launches += c->launches - l0;
             }
-            if (!st && c->P.electrostatics) {
+            if (!st && solve) {
                 const int64_t l0 = c->launches;
                 c->in_batch = true;          // the channels solve side by side: split passes
                 st = poisson_solve(c, c->Q, true, c->d_scale_q, true, nullptr, c->E_lat);
                 c->in_batch = false;
                 b->launches += c->launches - l0;
             }
+            if (!st && lead) st = poisson_group_solve(b->groups[gi], b->br[i], &b->launches);
             if (!st) {
                 e = cudaEventRecord(b->join[i], b->br[i]);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[i], 0);
@@ -233,9 +268,18 @@ tribo_status issue_steps(tribo_batch* b, const std::vector<PView>& home, int cou
             if (st) return st;
         }
         if (sort_now) alt = !alt;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        TRIBO_CUDA(cudaStreamIsCapturing(b->stream, &cs));
+        const bool timed = b->timing && cs == cudaStreamCaptureStatusNone;
+        if (timed && b->tev_used + 2 > (int)b->tev.size() && (st = flush_batch_timing(b))) return st;
+        if (timed) TRIBO_CUDA(cudaEventRecord(b->tev[b->tev_used], b->stream));
         launch_batch<R>(b->shape, b->stream, (const BatchChan<R>*)b->d_chans[alt ? 1 : 0], b->d_tiles, b->n,
                         b->ntiles, b->shmem);
         TRIBO_CUDA(cudaGetLastError());
+        if (timed) {
+            TRIBO_CUDA(cudaEventRecord(b->tev[b->tev_used + 1], b->stream));
+            b->tev_used += 2;
+        }
         b->launches += 1;
         for (tribo_ctx* c : b->ch) c->steps_done++;
         b->steps++;
@@ -343,7 +387,8 @@ tribo_status step_impl(tribo_batch* b, const std::vector<PView>& home, const dou
         if ((st = issue_steps<R>(b, home, lead, alt))) return st;
         left -= lead;
     }
-    if (left >= G) {
+    // while the particle kernel is timed every step is a direct launch
+    if (left >= G && !b->timing) {
         std::vector<uintptr_t> key;
         for (const PView& v : home) {
             key.push_back((uintptr_t)v.x); key.push_back((uintptr_t)v.n); key.push_back((uintptr_t)v.id);
@@ -419,6 +464,9 @@ void destroy_batch(tribo_batch* b) {
     if (b->ev_in) cudaEventDestroy(b->ev_in);
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->stream) cudaStreamDestroy(b->stream);
+    for (void* g : b->groups) poisson_group_free(g);
+    for (cudaEvent_t e : b->tev)
+        if (e) cudaEventDestroy(e);
     void* ptrs[] = {b->d_chans[0], b->d_chans[1], b->d_tiles, b->d_scratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -491,6 +539,27 @@ tribo_status tribo_batch_create(tribo_batch** out, int32_t n_channels, tribo_ctx
         destroy_batch(b);
         return st;
     }
+    // Poisson groups: two or more mixed-precision channels on one compiled-length grid
+    b->group_of.assign(n_channels, -1);
+    for (int i = 0; i < n_channels; ++i) {
+        tribo_ctx* c = channels[i];
+        if (b->group_of[i] >= 0 || !poisson_group_ok(c)) continue;
+        std::vector<int> m{i};
+        for (int k = i + 1; k < n_channels; ++k) {
+            const tribo_ctx* o = channels[k];
+            if (b->group_of[k] < 0 && poisson_group_ok(o) && o->nx == c->nx && o->ny == c->ny && o->nz == c->nz)
+                m.push_back(k);
+        }
+        if (m.size() < 2) continue;
+        std::vector<tribo_ctx*> cs;
+        for (int k : m) cs.push_back(channels[k]);
+        void* g = nullptr;
+        tribo_status st = poisson_group_create(cs.data(), (int)cs.size(), &g);
+        if (st) { destroy_batch(b); return st; }
+        for (int k : m) b->group_of[k] = (int)b->groups.size();
+        b->groups.push_back(g);
+        b->members.push_back(m);
+    }
     (void)real_bytes;
     *out = b;
     return TRIBO_OK;
@@ -541,6 +610,30 @@ tribo_status tribo_batch_sync(tribo_batch* b) {
 }
 
 int64_t tribo_batch_launch_count(const tribo_batch* b) { return b ? b->launches : 0; }
+
+tribo_status tribo_batch_timing(tribo_batch* b, int32_t enable) {
+    if (!b) { set_last_error("batch is NULL"); return TRIBO_ERR_ARG; }
+    if (enable && b->tev.empty()) {
+        b->tev.assign(512, nullptr);
+        for (cudaEvent_t& e : b->tev) TRIBO_CUDA(cudaEventCreate(&e));
+    }
+    b->timing = enable != 0;
+    b->tev_used = 0;
+    b->t_ms = 0.0;
+    b->t_n = 0;
+    return TRIBO_OK;
+}
+
+tribo_status tribo_batch_kernel_time(tribo_batch* b, double* total_ms, int64_t* launches) {
+    if (!b || !total_ms || !launches) { set_last_error("batch and outputs must not be NULL"); return TRIBO_ERR_ARG; }
+    tribo_status st = flush_batch_timing(b);
+    if (st) return st;
+    *total_ms = b->t_ms;
+    *launches = b->t_n;
+    b->t_ms = 0.0;
+    b->t_n = 0;
+    return TRIBO_OK;
+}
 
 void tribo_batch_destroy(tribo_batch* b) { destroy_batch(b); }
 

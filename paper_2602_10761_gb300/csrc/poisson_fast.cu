@@ -23,6 +23,7 @@
 //    element passes through shared memory once, in one transpose.
 // Passes: xfwd (zeroes the charge buffer), zfwd, ysolve, zinv, xinv.
 #include <algorithm>
+#include <new>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -63,6 +64,28 @@ __device__ __forceinline__ ds ds_mul(ds a, ds b) {
 __device__ __forceinline__ ds ds_neg(ds a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ float ds_f(ds a) { return a.hi + a.lo; }
 
+// ---------------------------------------------------------------- channel tables
+// The split passes also run for a group of channels with the same grid in
+// one launch each (a batch's channels, blockIdx.y = channel): a pass given a
+// table takes its channel's arrays from tab[blockIdx.y] instead of its
+// pointer arguments.
+template <class R>
+struct FastTab {
+    void* src;                  // FP64 cell charge sums (forward x source)
+    const double* scale;        // per-row RHS factor
+    cplx<R>* S;                 // spectrum
+    cplx<R>* F;                 // field spectra (the E_y spectrum at F + fstride)
+    R* E;                       // field lattice
+    const cplx<R>* twx;
+    const cplx<R>* twz;
+    const double* sinx;
+    const double* sinz;
+    const float2* tinv;         // y solve (mixed): 1/pivot, c' (double-single), sub-diagonal, E_y coefficients
+    const float2* tcp;
+    const float2* yads;
+    const float4* yec;
+};
+
 // ---------------------------------------------------------------- x forward
 // Thread group (line, r) per line (k, j) of the charge-sum array:
 // z_n = x_2n + i x_2n+1 (scaled to -rho/eps), Z = FFT_M(z) by the register
@@ -78,7 +101,15 @@ constexpr int xfwd_min_blocks() { return sizeof(R) == 4 && M <= 192 ? 6 : 1; }
 template <class R, int M, class QT>
 __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT* __restrict__ src, const double* __restrict__ scale_row,
                                                     int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
-                                                    const cplx<R>* __restrict__ tw_g) {
+                                                    const cplx<R>* __restrict__ tw_g,
+                                                    const FastTab<R>* __restrict__ tab) {
+    if (tab) {
+        const FastTab<R>& t = tab[blockIdx.y];
+        src = reinterpret_cast<QT*>(t.src);
+        scale_row = t.scale;
+        S = t.S;
+        tw_g = t.twx;
+    }
     using F4 = fft::FourStep<M, kThreads>;
     constexpr int N1 = F4::N1, N2 = F4::N2, TPC = F4::TPC, LPB = F4::W, CS = F4::CS;
     constexpr int NX = 2 * M, NXH = M + 1;
@@ -244,7 +275,16 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
                                                       const float2* __restrict__ tinv,
                                                       const float2* __restrict__ tcp,
                                                       const float2* __restrict__ a_ds, const float4* __restrict__ ec,
-                                                      int ny, int nz, int nxh) {
+                                                      int ny, int nz, int nxh, const FastTab<float>* __restrict__ tab) {
+    if (tab) {
+        const FastTab<float>& t = tab[blockIdx.y];
+        S = t.S;
+        Fy = t.F + (size_t)nz * (ny + 2) * nxh;
+        tinv = t.tinv;
+        tcp = t.tcp;
+        a_ds = t.yads;
+        ec = t.yec;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* ck = reinterpret_cast<float4*>(smem_raw);                 // [chunk][thread]
     const int nch = (ny + C - 1) / C;
@@ -426,7 +466,12 @@ __device__ __noinline__ void zfwd_tile(cplx<R>* __restrict__ S, int ny, int nxh,
 
 template <class R, int NZ>
 __global__ void __launch_bounds__(kThreads, 4) k_zfwd4(cplx<R>* __restrict__ S, int ny, int nxh,
-                                                    const cplx<R>* __restrict__ tw_g) {
+                                                    const cplx<R>* __restrict__ tw_g,
+                                                    const FastTab<R>* __restrict__ tab) {
+    if (tab) {
+        S = tab[blockIdx.y].S;
+        tw_g = tab[blockIdx.y].twz;
+    }
     using F4 = fft::FourStep<NZ, kThreads>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
@@ -477,7 +522,15 @@ __device__ __noinline__ void zinv_tile_phi(const cplx<R>* __restrict__ S, cplx<R
 template <class R, int NZ>
 __global__ void __launch_bounds__(kThreads, 4) k_zinv4(const cplx<R>* __restrict__ S, cplx<R>* __restrict__ F,
                                                     int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
-                                                    const cplx<R>* __restrict__ tw_g, int phi_only) {
+                                                    const cplx<R>* __restrict__ tw_g, int phi_only,
+                                                    const FastTab<R>* __restrict__ tab) {
+    if (tab) {
+        const FastTab<R>& t = tab[blockIdx.y];
+        S = t.S;
+        F = t.F;
+        sinz = t.sinz;
+        tw_g = t.twz;
+    }
     using F4 = fft::FourStep<NZ, kThreads>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
@@ -508,7 +561,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
                                                     double* __restrict__ phi, int ny, int nz, size_t fstride,
                                                     const double* __restrict__ sinx,
                                                     const cplx<R>* __restrict__ tw_g, int want_phi, int want_e,
-                                                    R norm, size_t nodes) {
+                                                    R norm, size_t nodes, const FastTab<R>* __restrict__ tab) {
+    if (tab) {
+        const FastTab<R>& t = tab[blockIdx.y];
+        F = t.F;
+        E = t.E;
+        sinx = t.sinx;
+        tw_g = t.twx;
+    }
     using F4 = fft::FourStep<M, kThreads>;
     constexpr int N1 = F4::N1, N2 = F4::N2, TPC = F4::TPC, LPB = F4::W, CS = F4::CS;
     constexpr int NX = 2 * M, NXH = M + 1;
@@ -1000,7 +1060,7 @@ void launch_xfwd(tribo_ctx* c, QT* src, const double* scale, bool zero) {
     constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->ny * c->nz;
     k_xfwd4<R, M, QT><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
-        src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx);
+        src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx, nullptr);
 }
 template <class R, int M>
 void launch_xinv(tribo_ctx* c, void* E, double* phi) {
@@ -1012,7 +1072,7 @@ void launch_xinv(tribo_ctx* c, void* E, double* phi) {
     k_xinv4<R, M><<<g, kThreads, xinv_smem<R, M>(), c->stream>>>(
         (const cplx<R>*)c->F, (R*)E, phi, c->ny, c->nz, fstride, c->d_sinx, (const cplx<R>*)c->d_twx,
         phi != nullptr ? 1 : 0, E != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)c->nz)),
-        (size_t)c->nz * (c->ny + 2) * c->nx);
+        (size_t)c->nz * (c->ny + 2) * c->nx, nullptr);
 }
 template <class R, int NZ>
 void launch_zfwd(tribo_ctx* c) {
@@ -1021,7 +1081,7 @@ void launch_zfwd(tribo_ctx* c) {
     const int grid = wave_blocks(k_zfwd4<R, NZ>, zfwd_smem<R, NZ>(), c->num_sms,
                                  (int64_t)c->ny * ((c->nxh + W - 1) / W), &occ);
     k_zfwd4<R, NZ><<<grid, kThreads, zfwd_smem<R, NZ>(), c->stream>>>((cplx<R>*)c->S, c->ny, c->nxh,
-                                                                      (const cplx<R>*)c->d_twz);
+                                                                      (const cplx<R>*)c->d_twz, nullptr);
 }
 template <class R, int NZ>
 void launch_zinv(tribo_ctx* c, bool phi_only) {
@@ -1032,7 +1092,7 @@ void launch_zinv(tribo_ctx* c, bool phi_only) {
     const size_t fstride = (size_t)c->nz * (c->ny + 2) * c->nxh;
     k_zinv4<R, NZ><<<grid, kThreads, zinv_smem<R, NZ>(), c->stream>>>(
         (const cplx<R>*)c->S, (cplx<R>*)c->F, c->ny, c->nxh, fstride, c->d_sinz, (const cplx<R>*)c->d_twz,
-        phi_only ? 1 : 0);
+        phi_only ? 1 : 0, nullptr);
 }
 template <class R, int NZ>
 tribo_status attr_z(int optin) {
@@ -1180,7 +1240,7 @@ tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* sca
                        : (E ? k_ysolve_chunk<12, false> : k_ysolve_chunk<12, false, false>);
         ys<<<(unsigned)nblk, 128, few && shc <= (size_t)c->smem_optin ? shc : sh12, c->stream>>>(
             (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
-            (const float4*)c->d_yec, ny, nz, nxh);
+            (const float4*)c->d_yec, ny, nz, nxh, nullptr);
     }
     TRIBO_LAUNCHED(c);
     if (fused) {
@@ -1197,6 +1257,96 @@ tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* sca
     dispatch_xinv<R>(c, E, phi);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
+}
+
+// ---------------------------------------------------------------- channel groups
+// Channels with the same grid, solved together: each split pass is one launch
+// over all of them (grid y = channel), on the caller's stream.
+struct Group {
+    int n = 0;
+    int nx = 0, ny = 0, nz = 0, nxh = 0;
+    int num_sms = 152, smem_optin = 48 * 1024;
+    FastTab<float>* d_tab = nullptr;
+};
+
+template <int M>
+void group_xfwd(const Group& g, cudaStream_t st) {
+    constexpr int LPB = fft::FourStep<M, kThreads>::W;
+    const int nlines = g.ny * g.nz;
+    k_xfwd4<float, M, double><<<dim3((nlines + LPB - 1) / LPB, g.n), kThreads, xfwd_smem<float, M>(), st>>>(
+        nullptr, nullptr, 1, nullptr, g.ny, nlines, nullptr, g.d_tab);
+}
+template <int NZ>
+void group_zfwd(const Group& g, cudaStream_t st) {
+    constexpr int W = fft::FourStep<NZ, kThreads>::W;
+    static int occ = 0;
+    const int64_t tiles = (int64_t)g.ny * ((g.nxh + W - 1) / W);
+    const int gx = std::max(1, wave_blocks(k_zfwd4<float, NZ>, zfwd_smem<float, NZ>(), g.num_sms, tiles, &occ) / g.n);
+    k_zfwd4<float, NZ><<<dim3(gx, g.n), kThreads, zfwd_smem<float, NZ>(), st>>>(nullptr, g.ny, g.nxh, nullptr, g.d_tab);
+}
+template <int NZ>
+void group_zinv(const Group& g, cudaStream_t st) {
+    constexpr int W = fft::FourStep<NZ, kThreads>::W;
+    static int occ = 0;
+    const int64_t tiles = (int64_t)(g.ny + 2) * ((g.nxh + W - 1) / W);
+    const int gx = std::max(1, wave_blocks(k_zinv4<float, NZ>, zinv_smem<float, NZ>(), g.num_sms, tiles, &occ) / g.n);
+    const size_t fstride = (size_t)g.nz * (g.ny + 2) * g.nxh;
+    k_zinv4<float, NZ><<<dim3(gx, g.n), kThreads, zinv_smem<float, NZ>(), st>>>(nullptr, nullptr, g.ny, g.nxh,
+                                                                              fstride, nullptr, nullptr, 0, g.d_tab);
+}
+template <int M>
+void group_xinv(const Group& g, cudaStream_t st) {
+    constexpr int LPB = fft::FourStep<M, kThreads>::W;
+    static int occ = 0;
+    const int nlines = g.nz * (g.ny + 2);
+    const int gx = std::max(1, wave_blocks(k_xinv4<float, M>, xinv_smem<float, M>(), g.num_sms,
+                                           (nlines + LPB - 1) / LPB, &occ) / g.n);
+    const size_t fstride = (size_t)g.nz * (g.ny + 2) * g.nxh;
+    k_xinv4<float, M><<<dim3(gx, g.n), kThreads, xinv_smem<float, M>(), st>>>(
+        nullptr, nullptr, nullptr, g.ny, g.nz, fstride, nullptr, nullptr, 0, 1,
+        (float)(1.0 / ((double)g.nx * (double)g.nz)), (size_t)g.nz * (g.ny + 2) * g.nx, g.d_tab);
+}
+void group_ysolve(const Group& g, cudaStream_t st) {
+    // the chunking of the single-channel solve, for the group's pencils together
+    const int64_t nblk = ((int64_t)g.nz * g.nxh + 127) / 128;
+    const bool few = nblk * g.n < 2 * (int64_t)g.num_sms;
+    const int ch = few ? 8 : 12;
+    const size_t shc = sizeof(float4) * ((size_t)((g.ny + ch - 1) / ch) * 128 + g.ny + 1) + sizeof(float2) * g.ny;
+    const size_t sh12 = sizeof(float4) * ((size_t)((g.ny + 11) / 12) * 128 + g.ny + 1) + sizeof(float2) * g.ny;
+    const bool pf = few && shc <= (size_t)g.smem_optin;
+    auto* ys = pf ? k_ysolve_chunk<8, true> : k_ysolve_chunk<12, false>;
+    ys<<<dim3((unsigned)nblk, g.n), 128, pf ? shc : sh12, st>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                g.ny, g.nz, g.nxh, g.d_tab);
+}
+
+bool group_dispatch(const Group& g, cudaStream_t st) {
+    bool ok = true;
+    switch (g.nx / 2) {
+#define CASE(N) case N: group_xfwd<N>(g, st); break;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: ok = false;
+    }
+    switch (g.nz) {
+#define CASE(N) case N: group_zfwd<N>(g, st); break;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: ok = false;
+    }
+    group_ysolve(g, st);
+    switch (g.nz) {
+#define CASE(N) case N: group_zinv<N>(g, st); break;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: ok = false;
+    }
+    switch (g.nx / 2) {
+#define CASE(N) case N: group_xinv<N>(g, st); break;
+        TRIBO_FAST_SIZES(CASE)
+#undef CASE
+        default: ok = false;
+    }
+    return ok;
 }
 
 }  // namespace
@@ -1318,6 +1468,70 @@ void poisson_fast_free(tribo_ctx* c) {
     cudaFree(c->ring);
     cudaFree(c->d_pipe);
     c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = c->ring = c->d_pipe = nullptr;
+}
+
+bool poisson_group_ok(const tribo_ctx* c) { return c->fast && c->prec == TRIBO_MIXED; }
+
+tribo_status poisson_group_create(tribo_ctx* const* chans, int n, void** out) {
+    *out = nullptr;
+    if (n < 1) return TRIBO_ERR_ARG;
+    const tribo_ctx* c0 = chans[0];
+    std::vector<FastTab<float>> t(n);
+    for (int i = 0; i < n; ++i) {
+        tribo_ctx* c = chans[i];
+        if (!poisson_group_ok(c) || c->nx != c0->nx || c->ny != c0->ny || c->nz != c0->nz) {
+            set_last_error("a Poisson group needs mixed-precision channels of one compiled-length grid");
+            return TRIBO_ERR_ARG;
+        }
+        const int ni = (c->nz / 2 + 1) * c->nxh;
+        FastTab<float>& f = t[i];
+        f.src = c->Q;
+        f.scale = c->d_scale_q;
+        f.S = (cplx<float>*)c->S;
+        f.F = (cplx<float>*)c->F;
+        f.E = (float*)c->E_lat;
+        f.twx = (const cplx<float>*)c->d_twx;
+        f.twz = (const cplx<float>*)c->d_twz;
+        f.sinx = c->d_sinx;
+        f.sinz = c->d_sinz;
+        f.tinv = (const float2*)c->d_ytab;
+        f.tcp = f.tinv + (size_t)c->ny * ni;
+        f.yads = (const float2*)c->d_yads;
+        f.yec = (const float4*)c->d_yec;
+    }
+    Group* g = new (std::nothrow) Group();
+    if (!g) { set_last_error("host allocation failed"); return TRIBO_ERR_OOM; }
+    g->n = n;
+    g->nx = c0->nx; g->ny = c0->ny; g->nz = c0->nz; g->nxh = c0->nxh;
+    g->num_sms = c0->num_sms;
+    g->smem_optin = c0->smem_optin;
+    cudaError_t e = cudaMalloc((void**)&g->d_tab, sizeof(FastTab<float>) * n);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_tab, t.data(), sizeof(FastTab<float>) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_tab);
+        delete g;
+        return cuda_fail(e, "Poisson group tables");
+    }
+    *out = g;
+    return TRIBO_OK;
+}
+
+tribo_status poisson_group_solve(void* grp, cudaStream_t stream, int64_t* launches) {
+    const Group* g = static_cast<const Group*>(grp);
+    if (!group_dispatch(*g, stream)) {
+        set_last_error("Poisson group: length without a compiled transform");
+        return TRIBO_ERR_UNSUPPORTED;
+    }
+    TRIBO_CUDA(cudaGetLastError());
+    if (launches) *launches += 5;
+    return TRIBO_OK;
+}
+
+void poisson_group_free(void* grp) {
+    Group* g = static_cast<Group*>(grp);
+    if (!g) return;
+    cudaFree(g->d_tab);
+    delete g;
 }
 
 tribo_status poisson_fast_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,

@@ -225,6 +225,15 @@ tribo_status poisson_free(tribo_ctx* c);
 tribo_status poisson_solve(tribo_ctx* c, void* src, bool src_f64, const double* scale, bool zero_src,
                            double* phi, void* E);
 
+// groups of mixed-precision channels with one compiled-length grid: every split
+// pass of their solves as one launch over all of them (poisson_fast.cu); the
+// solve reads each channel's FP64 cell sums, zeroes them and writes its field
+// lattice, on `stream`
+bool poisson_group_ok(const tribo_ctx* c);
+tribo_status poisson_group_create(tribo_ctx* const* chans, int n, void** out);
+tribo_status poisson_group_solve(void* grp, cudaStream_t stream, int64_t* launches);
+void poisson_group_free(void* grp);
+
 // compile-time-length Poisson path (poisson_fast.cu)
 bool poisson_fast_supported(int nx, int nz);
 tribo_status poisson_fast_setup(tribo_ctx* c);

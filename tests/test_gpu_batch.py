@@ -142,3 +142,85 @@ def test_batch_rejects_mode_fields_and_oversize():
         B.step([big], [c.dt], 1)
     B.close()
     ch.close()
+
+
+GROUP_SPECS = [  # channels sharing a grid solve their Poisson passes as one launch each
+    (32, 24, 32, 1500, 180.0, (0.5, 3.0), 11),
+    (32, 24, 32, 0, 300.0, (1.0, 2.0), 12),        # an empty member: its field solves to zero
+    (32, 24, 32, 800, 550.0, (0.8, 2.5), 13),
+    (24, 16, 12, 600, 395.0, (1.0, 3.0), 14),
+    (24, 16, 12, 900, 180.0, (0.5, 1.5), 15),
+    (36, 12, 18, 300, 300.0, (1.0, 2.0), 16),      # no compiled transform length: solved alone
+]
+
+
+def _group_data():
+    out = []
+    for nx, ny, nz, n, re, dp, seed in GROUP_SPECS:
+        out.append(problem(nx, ny, nz, n=n, re_tau=re, dplus=dp, q_scale=1e-13, vy_scale=0.3, near_wall=0.1,
+                           seed=seed))
+    return out
+
+
+@pytest.mark.parametrize("sort_every,nsteps", [(0, 19), (3, 14)])
+def test_batch_grouped_poisson_matches_single_channels(sort_every, nsteps):
+    data = _group_data()
+    U_c = 500.0
+    singles, chans, Ps, dts = [], [], [], []
+    for c, faces, lat, parts in data:
+        ch, P = _make(c, faces, lat, parts, T.TRIBO_MIXED, sort_every, U_c)
+        ch.step(P, c.dt, nsteps)
+        ch.sync()
+        singles.append((_sorted(P), ch.stats(P)))
+        ch.close()
+        ch, P = _make(c, faces, lat, parts, T.TRIBO_MIXED, sort_every, U_c)
+        chans.append(ch)
+        Ps.append(P)
+        dts.append(c.dt)
+    B = T.Batch(chans, sort_every=sort_every)
+    B.step(Ps, dts, nsteps - 4)          # graph replays and direct launches
+    B.step(Ps, dts, 4)
+    B.sync()
+    for (c, faces, lat, parts), (ref, rst), ch, P in zip(data, singles, chans, Ps):
+        if len(parts["x"]) == 0:
+            continue
+        got = _sorted(P)
+        st = ch.stats(P)
+        for k in ("x", "y", "z", "vx", "vy", "vz", "q", "q_wall"):
+            s = max(np.abs(ref[k]).max(), 1e-40)
+            assert np.abs(got[k].astype(np.float64) - ref[k].astype(np.float64)).max() <= 1e-6 * s, (c.name, k)
+        assert np.array_equal(got["n_imp"], ref["n_imp"])
+        assert st["n_impacts"] == rst["n_impacts"]
+        assert np.array_equal(st["hist_y"], rst["hist_y"])
+    B.close()
+    for ch in chans:
+        ch.close()
+
+
+def test_batch_group_launch_count_and_kernel_timing():
+    # five channels in two groups, no sort: each step is the particle kernel plus five
+    # passes per group, whether replayed from the graph or launched directly
+    data = _group_data()[:5]
+    chans, Ps, dts = [], [], []
+    for c, faces, lat, parts in data:
+        ch, P = _make(c, faces, lat, parts, T.TRIBO_MIXED, 0, 500.0)
+        chans.append(ch)
+        Ps.append(P)
+        dts.append(c.dt)
+    B = T.Batch(chans, sort_every=0)
+    B.autotune(Ps, dts)
+    l0 = B.launches
+    B.step(Ps, dts, 9)                   # one 8-step graph and one direct step
+    B.sync()
+    deposits = sum(1 for _, _, _, parts in data if len(parts["x"]) > 0)
+    assert B.launches - l0 == deposits + 9 * (1 + 2 * 5)
+    B.timing(True)
+    B.step(Ps, dts, 3)
+    B.sync()
+    ms, n = B.kernel_time()
+    assert n == 3 and ms > 0.0
+    assert B.kernel_time() == (0.0, 0)
+    B.timing(False)
+    B.close()
+    for ch in chans:
+        ch.close()
