@@ -37,7 +37,7 @@ struct BatchChan {
 };
 
 template <class R, int NT>
-__global__ void __launch_bounds__(NT, 768 / NT)
+__global__ void __launch_bounds__(NT, 1024 / NT)
 k_step_batch(const BatchChan<R>* __restrict__ chans, const int64_t* __restrict__ tstart, int nch, int64_t ntiles,
              int tile, int64_t tiles_per_block) {
     __shared__ __align__(16) unsigned char raw[sizeof(BatchChan<R>)];
@@ -49,6 +49,7 @@ k_step_batch(const BatchChan<R>* __restrict__ chans, const int64_t* __restrict__
     (void)tiles_per_block;
     int cur = -1;
     unsigned int err = 0;
+    bool use_hist = false;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         // channel of tile t: the last c with tstart[c] <= t
         int lo = 0, hi = nch - 1;
@@ -57,31 +58,41 @@ k_step_batch(const BatchChan<R>* __restrict__ chans, const int64_t* __restrict__
             if (tstart[mid] <= t) lo = mid;
             else hi = mid - 1;
         }
-        __syncthreads();
         if (lo != cur) {
-            if (cur >= 0 && err) { atomicOr(&sc.a.acc->err, err); err = 0; }
+            // a new channel: flush the previous one's histogram and error word, load its arguments
+            __syncthreads();
+            if (cur >= 0) {
+                if (use_hist)
+                    for (int b = threadIdx.x; b < sc.a.ny; b += NT) {
+                        const unsigned int v = sh_hist[b];
+                        if (v) atomicAdd(&sc.a.hist[b], (unsigned long long)v);
+                    }
+                if (err) { atomicOr(&sc.a.acc->err, err); err = 0; }
+            }
             __syncthreads();
             const uint32_t* src = reinterpret_cast<const uint32_t*>(chans + lo);
             uint32_t* dst = reinterpret_cast<uint32_t*>(raw);
             for (int w = threadIdx.x; w < (int)(sizeof(BatchChan<R>) / 4); w += NT) dst[w] = __ldg(src + w);
             cur = lo;
             __syncthreads();
+            use_hist = sc.a.hist != nullptr;
+            if (use_hist)
+                for (int b = threadIdx.x; b < sc.a.ny; b += NT) sh_hist[b] = 0u;
+            __syncthreads();
         }
-        const bool use_hist = sc.a.hist != nullptr;
-        if (use_hist)
-            for (int b = threadIdx.x; b < sc.a.ny; b += NT) sh_hist[b] = 0u;
-        __syncthreads();
         const int64_t base = (t - tstart[cur]) * (int64_t)tile;
         const int64_t end = min(base + (int64_t)tile, sc.p.n);
         for (int64_t n = base + threadIdx.x; n < end; n += NT) step_one<R>(sc.a, sc.p, n, 0, sh_hist, use_hist, err);
+    }
+    if (cur >= 0) {
         __syncthreads();
         if (use_hist)
             for (int b = threadIdx.x; b < sc.a.ny; b += NT) {
                 const unsigned int v = sh_hist[b];
                 if (v) atomicAdd(&sc.a.hist[b], (unsigned long long)v);
             }
+        if (err) atomicOr(&sc.a.acc->err, err);
     }
-    if (cur >= 0 && err) atomicOr(&sc.a.acc->err, err);
 }
 
 // candidate shapes of the particle kernel
@@ -89,9 +100,9 @@ struct Shape {
     int nt, tile, bps;         // threads per block, particles per tile, blocks per SM
 };
 const Shape kShapes[] = {
-    {128, 1024, 6}, {128, 4096, 6}, {128, 16384, 6}, {128, 1024, 12}, {128, 4096, 12}, {128, 16384, 12},
-    {256, 1024, 3}, {256, 4096, 3}, {256, 16384, 3}, {256, 1024, 6}, {256, 4096, 6}, {256, 16384, 6},
-    {512, 2048, 1}, {512, 8192, 1}, {512, 32768, 1}, {512, 2048, 2}, {512, 8192, 2}, {512, 32768, 2},
+    {128, 256, 8},  {128, 1024, 8}, {128, 4096, 8}, {128, 256, 16}, {128, 1024, 16}, {128, 4096, 16},
+    {256, 256, 4},  {256, 1024, 4}, {256, 4096, 4}, {256, 256, 8},  {256, 1024, 8},  {256, 4096, 8},
+    {256, 16384, 8}, {512, 512, 2}, {512, 2048, 2}, {512, 8192, 2}, {512, 2048, 4}, {512, 8192, 4},
 };
 constexpr int kNumSMs = 152;
 
