@@ -119,9 +119,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic(kernel, workload=WORKLOAD):
+def measured_traffic(kernel, workload=WORKLOAD, alg_bytes=None):
     """DRAM bytes per launch of `kernel` from its committed ncu summary, or None
-    when the kernel's sources changed after the counters were taken."""
+    when the kernel's sources changed after the counters were taken.  A summary
+    taken on a smaller case than the bench's records its algorithmic bytes; its
+    traffic is then scaled to the bench's launch by the ratio of the
+    algorithmic bytes (`alg_bytes`)."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
@@ -135,7 +138,11 @@ def measured_traffic(kernel, workload=WORKLOAD):
     for f in info["files"]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return info["bytes_per_launch"] if h.hexdigest()[:16] == info["source_hash"] else None
+    if h.hexdigest()[:16] != info["source_hash"]:
+        return None
+    if info.get("alg_bytes_per_launch") and alg_bytes:
+        return info["bytes_per_launch"] * alg_bytes / info["alg_bytes_per_launch"]
+    return info["bytes_per_launch"]
 
 
 def touched_nodes(c, faces, x, y, z):
@@ -576,7 +583,7 @@ def batch_report(T, torch, steps=500, seq_steps=40, sort_every=20, rank=0, world
             "roofline": {"bound": "hbm", "kernel": "k_step_batch", "achieved": ach, "peak": hbm_peak,
                          "unit": "GB/s", "frac": ach / hbm_peak, "peak_kind": peak_kind,
                          "alg_bytes": alg_bytes, "ms_per_launch": kern_ms, "timed_launches": kern_n,
-                         "traffic": measured_traffic("k_step_batch", "ensemble")}}
+                         "traffic": measured_traffic("k_step_batch", "ensemble", alg_bytes)}}
 
 
 def batch_vs_fp64(T, torch, cases, steps=10, sort_every=5):

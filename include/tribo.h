@@ -61,11 +61,11 @@ typedef int32_t tribo_status;
                                     (the results of that call are not valid) */
 
 #define TRIBO_FP64  0   /* everything in FP64 */
-#define TRIBO_MIXED 1   /* FP32 particle state, interpolation, force math, cell
-                           charge sums, FFT and fields; FP64-class y-tridiagonal
-                           solve (FP64 factors, double-single sweeps); FP64
-                           wall-impact charge, time of flight and per-particle
-                           charges */
+#define TRIBO_MIXED 1   /* FP32 particle state, interpolation, force math, FFT
+                           and fields; FP64-class y-tridiagonal solve (FP64
+                           factors, double-single sweeps); FP64 cell charge
+                           sums, wall-impact charge, time of flight and
+                           per-particle charges */
 
 #define TRIBO_DRAG_STOKES           0
 #define TRIBO_DRAG_SCHILLER_NAUMANN 1
@@ -270,9 +270,9 @@ tribo_status tribo_transfer_bytes(tribo_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
  * double, may be NULL.  E: device (3, Nz, Ny+2, Nx) "real", the planes
  * E_x, E_y, E_z on the wall-extended lattice; the wall nodes hold E_x = E_z = 0
  * and the one-sided E_y.  rho, phi and E must be 16-byte aligned;
- * TRIBO_ERR_ARG otherwise.  In TRIBO_MIXED the transforms
- * are FP32: rho is first rounded to FP32 into the context's cell-sum array
- * (work space that tribo_step refills at its start).  Asynchronous. */
+ * TRIBO_ERR_ARG otherwise.  In TRIBO_MIXED the transforms are FP32: the
+ * first pass reads the FP64 rho and rounds each value as it transforms it.
+ * Asynchronous. */
 tribo_status tribo_poisson(tribo_ctx* ctx, const double* rho, double* phi, void* E);
 
 /* Reverse-mode derivative of the mean particle charge after nsteps coupled
