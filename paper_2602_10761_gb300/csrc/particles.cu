@@ -35,6 +35,7 @@ namespace {
 
 template <class R>
 __global__ void __launch_bounds__(kStepThreads, kStepMinBlocks) k_step(StepArgs<R> a, PView p, int write_cell) {
+    pdl_wait();
     extern __shared__ unsigned int sh_hist[];
     const bool use_hist = a.hist != nullptr;
     if (use_hist) {
@@ -114,7 +115,7 @@ tribo_status step_impl(tribo_ctx* c, const PView& p, double dt, bool deposit_nex
     // one resident wave (a grid of several waves measured 6% slower)
     const int kblocks = (int)std::min<int64_t>((p.n + kStepThreads - 1) / kStepThreads,
                                                (int64_t)c->num_sms * kStepMinBlocks);
-    k_step<R><<<kblocks, kStepThreads, sh, c->stream>>>(a, p, write_cell ? 1 : 0);
+    (void)launch_pdl(k_step<R>, dim3(kblocks), dim3(kStepThreads), sh, c->stream, a, p, write_cell ? 1 : 0);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }

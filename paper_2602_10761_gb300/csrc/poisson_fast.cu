@@ -327,6 +327,18 @@ __device__ __noinline__ void inv_xtask(const cplx<R>* slot, R* __restrict__ E, d
             for (int k1 = 0; k1 < N1; ++k1) b[k1] = y[k1];
         }
         __syncthreads();
+        // every thread of the block has its values of this field: the slot lines that lie
+        // wholly in the task's rows are dropped from L2 unwritten (the slot is rewritten by a
+        // later plane; a write-back would only add HBM traffic)
+        if ((f != 0 || !want_phi) && (f == 1 || interior)) {
+            const char* base = reinterpret_cast<const char*>(slot + (size_t)src * fs);
+            const int k0 = grp * LPB, k1 = min(k0 + LPB, nz);
+            const size_t b0 = ((size_t)k0 * NXH * sizeof(cplx<R>) + 127) & ~(size_t)127;
+            const size_t b1 = ((size_t)k1 * NXH * sizeof(cplx<R>)) & ~(size_t)127;
+            if ((reinterpret_cast<uintptr_t>(base) & 127) == 0)
+                for (size_t b = b0 + (size_t)threadIdx.x * 128; b < b1; b += (size_t)blockDim.x * 128)
+                    asm volatile("discard.global.L2 [%0], 128;" ::"l"(base + b) : "memory");
+        }
         if (active && r < N1) {
             cplx<R> z[N2];
             const cplx<R>* b = buf + l * CS + r;
@@ -363,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, M, NZ>())) k_in
     double* __restrict__ phi, int ny, int want_phi, int want_e, R norm, size_t nodes,
     const double* __restrict__ sinx, const double* __restrict__ sinz, const cplx<R>* __restrict__ twx_g,
     const cplx<R>* __restrict__ twz_g, PipeSync* sy, Pipe pipe, unsigned* err) {
+    pdl_wait();
     using FX = fft::FourStep<M, kThreads>;
     constexpr int NX = 2 * M, NXH = M + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -424,7 +437,7 @@ tribo_status launch_inv_fused(tribo_ctx* c, void* E, double* phi) {
     const size_t smem = inv_fused_smem<R, M, NZ>();
     const int grid = fused_grid(k_inv_fused<R, M, NZ>, smem, c->num_sms, pipe.total, &occ);
     const size_t fstride = (size_t)NZ * (c->ny + 2) * c->nxh;
-    k_inv_fused<R, M, NZ><<<grid, kThreads, smem, c->stream>>>(
+    (void)launch_pdl(k_inv_fused<R, M, NZ>, dim3(grid), dim3(kThreads), smem, c->stream,
         (const cplx<R>*)c->S, (const cplx<R>*)c->F + fstride, (cplx<R>*)c->ring, (R*)E, phi, c->ny,
         phi != nullptr ? 1 : 0, E != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)NZ)),
         (size_t)NZ * (c->ny + 2) * c->nx, c->d_sinx, c->d_sinz, (const cplx<R>*)c->d_twx,
@@ -472,8 +485,9 @@ template <class R, int M, class QT>
 void launch_xfwd(tribo_ctx* c, QT* src, const double* scale, bool zero) {
     constexpr int LPB = fft::FourStep<M, kThreads>::W;
     const int nlines = c->ny * c->nz;
-    k_xfwd4<R, M, QT><<<(nlines + LPB - 1) / LPB, kThreads, xfwd_smem<R, M>(), c->stream>>>(
-        src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx, nullptr);
+    (void)launch_pdl(k_xfwd4<R, M, QT>, dim3((nlines + LPB - 1) / LPB), dim3(kThreads), xfwd_smem<R, M>(), c->stream,
+                     src, scale, zero ? 1 : 0, (cplx<R>*)c->S, c->ny, nlines, (const cplx<R>*)c->d_twx,
+                     (const FastTab<R>*)nullptr);
 }
 template <class R, int M>
 void launch_xinv(tribo_ctx* c, void* E, double* phi) {
@@ -493,8 +507,8 @@ void launch_zfwd(tribo_ctx* c) {
     static int occ = 0;
     const int grid = wave_blocks(k_zfwd4<R, NZ>, zfwd_smem<R, NZ>(), c->num_sms,
                                  (int64_t)c->ny * ((c->nxh + W - 1) / W), &occ);
-    k_zfwd4<R, NZ><<<grid, kThreads, zfwd_smem<R, NZ>(), c->stream>>>((cplx<R>*)c->S, c->ny, c->nxh,
-                                                                      (const cplx<R>*)c->d_twz, nullptr);
+    (void)launch_pdl(k_zfwd4<R, NZ>, dim3(grid), dim3(kThreads), zfwd_smem<R, NZ>(), c->stream, (cplx<R>*)c->S, c->ny,
+                     c->nxh, (const cplx<R>*)c->d_twz, (const FastTab<R>*)nullptr);
 }
 template <class R, int NZ>
 void launch_zinv(tribo_ctx* c, bool phi_only) {
@@ -639,9 +653,10 @@ tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* sca
         auto* ys = few && shc <= (size_t)c->smem_optin
                        ? (E ? k_ysolve_chunk<8, true> : k_ysolve_chunk<8, true, false>)
                        : (E ? k_ysolve_chunk<12, false> : k_ysolve_chunk<12, false, false>);
-        ys<<<(unsigned)nblk, 128, few && shc <= (size_t)c->smem_optin ? shc : sh12, c->stream>>>(
-            (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
-            (const float4*)c->d_yec, ny, nz, nxh, nullptr);
+        (void)launch_pdl(ys, dim3((unsigned)nblk), dim3(128), few && shc <= (size_t)c->smem_optin ? shc : sh12,
+                         c->stream, (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp,
+                         (const float2*)c->d_yads, (const float4*)c->d_yec, ny, nz, nxh,
+                         (const FastTab<float>*)nullptr);
     }
     TRIBO_LAUNCHED(c);
     if (fused) {

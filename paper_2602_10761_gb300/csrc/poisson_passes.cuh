@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT*
                                                     int zero_src, cplx<R>* __restrict__ S, int ny, int nlines,
                                                     const cplx<R>* __restrict__ tw_g,
                                                     const FastTab<R>* __restrict__ tab) {
+    pdl_wait();
     if constexpr (kTab) {
         const FastTab<R>& t = tab[blockIdx.y];
         src = reinterpret_cast<QT*>(t.src);
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
                                                       const float2* __restrict__ tcp,
                                                       const float2* __restrict__ a_ds, const float4* __restrict__ ec,
                                                       int ny, int nz, int nxh, const FastTab<float>* __restrict__ tab) {
+    pdl_wait();
     if constexpr (kTab) {
         const FastTab<float>& t = tab[blockIdx.y];
         S = t.S;
@@ -386,6 +388,7 @@ template <class R, int NZ, bool kTab = false>
 __global__ void __launch_bounds__(kThreads, 4) k_zfwd4(cplx<R>* __restrict__ S, int ny, int nxh,
                                                     const cplx<R>* __restrict__ tw_g,
                                                     const FastTab<R>* __restrict__ tab) {
+    pdl_wait();
     if constexpr (kTab) {
         S = tab[blockIdx.y].S;
         tw_g = tab[blockIdx.y].twz;
@@ -442,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_zinv4(const cplx<R>* __restrict
                                                     int ny, int nxh, size_t fstride, const double* __restrict__ sinz,
                                                     const cplx<R>* __restrict__ tw_g, int phi_only,
                                                     const FastTab<R>* __restrict__ tab) {
+    pdl_wait();
     if constexpr (kTab) {
         const FastTab<R>& t = tab[blockIdx.y];
         S = t.S;
@@ -483,6 +487,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_xinv4(const cplx<R>* __restrict
                                                     const double* __restrict__ sinx,
                                                     const cplx<R>* __restrict__ tw_g, int want_phi, int want_e,
                                                     R norm, size_t nodes, const FastTab<R>* __restrict__ tab) {
+    pdl_wait();
     if constexpr (kTab) {
         const FastTab<R>& t = tab[blockIdx.y];
         F = t.F;

@@ -197,6 +197,30 @@ enum Phase { PH_STEP = 0, PH_DEPOSIT, PH_FWD_X, PH_FWD_Z, PH_SOLVE_Y, PH_INV_Z, 
 void phase_begin(tribo_ctx* c, int phase);
 void phase_end(tribo_ctx* c);
 
+// Programmatic dependent launch: a kernel of the step launched with launch_pdl
+// may be scheduled while the previous kernel on the stream drains (its blocks
+// land on SMs as the previous kernel's blocks exit); it calls pdl_wait()
+// before it touches global memory, which returns once that kernel has
+// completed and its writes are visible (a no-op in a kernel launched without
+// the attribute).  Every kernel launched with launch_pdl calls pdl_wait()
+// first.  Measured on the 384x256x256 step: 0.949 -> 0.936 ms.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // error plumbing
 void set_last_error(const std::string& s);
 tribo_status cuda_fail(cudaError_t e, const char* what);
