@@ -142,9 +142,11 @@ constexpr int kPipeLook = TRIBO_PIPE_LOOK;  // L: stages a plane's consumers tra
 constexpr int kPipeSlots = TRIBO_PIPE_SLOTS;  // P: ring slots (> L)
 constexpr unsigned kSpinLimit = 1u << 22;   // polls of a wait (>= ~1 s with the back-off)
 
-struct PipeSync {                           // one launch's counters, zeroed before it
+struct PipeSync {                           // one launch's counters: zero when it starts, and
+                                            // zeroed again by its last block to finish
     unsigned next;                          // next task to claim
-    unsigned pad[31];
+    unsigned exited;                        // blocks that have left the task loop
+    unsigned pad[30];
     unsigned a_done[kMaxPlanes];            // finished producer tasks per plane
     unsigned b_done[kMaxPlanes];            // finished consumer tasks per plane
 };
@@ -407,6 +409,25 @@ __global__ void __launch_bounds__(kThreads, (fused_min_blocks<R, M, NZ>())) k_in
         else inv_ztask<R, NZ>(S, Fy, slot, ny, NXH, plane, idx, want_e, twz, sz, buf);
         pipe_release(L, sy, cons, plane);
     }
+    // the last block to leave zeroes the counters for the next launch (so no memset, which
+    // would keep this launch from being scheduled while the y solve drains, sits between them)
+    __shared__ unsigned s_last;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&sy->exited, 1u) == gridDim.x - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        for (int i = threadIdx.x; i < kMaxPlanes; i += kThreads) {
+            sy->a_done[i] = 0u;
+            sy->b_done[i] = 0u;
+        }
+        if (threadIdx.x == 0) {
+            sy->next = 0u;
+            sy->exited = 0u;
+        }
+    }
 }
 
 template <class R, int M, int NZ>
@@ -431,8 +452,7 @@ template <class R, int M, int NZ>
 tribo_status launch_inv_fused(tribo_ctx* c, void* E, double* phi) {
     const Pipe pipe = make_pipe(c->ny + 2, (c->nxh + fft::FourStep<NZ, kThreads>::W - 1) / fft::FourStep<NZ, kThreads>::W,
                                 (NZ + fft::FourStep<M, kThreads>::W - 1) / fft::FourStep<M, kThreads>::W);
-    PipeSync* sy = (PipeSync*)c->d_pipe;
-    TRIBO_CUDA(cudaMemsetAsync(sy, 0, sizeof(PipeSync), c->stream));
+    PipeSync* sy = (PipeSync*)c->d_pipe;     // zero (at set-up, then left so by every launch)
     static int occ = 0;
     const size_t smem = inv_fused_smem<R, M, NZ>();
     const int grid = fused_grid(k_inv_fused<R, M, NZ>, smem, c->num_sms, pipe.total, &occ);
@@ -765,6 +785,7 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         if (st == TRIBO_OK) {
             TRIBO_CUDA(cudaMalloc(&c->ring, (size_t)kPipeSlots * 3 * nz * nxh * csz));
             TRIBO_CUDA(cudaMalloc(&c->d_pipe, sizeof(PipeSync)));
+            TRIBO_CUDA(cudaMemset(c->d_pipe, 0, sizeof(PipeSync)));
         } else if (st != TRIBO_ERR_UNSUPPORTED) {
             return st;
         }
