@@ -7,9 +7,11 @@
 //  * the x transforms are real: a length-nx/2 complex FFT of the packed line
 //    plus the split step (half the work and shared memory);
 //  * the y factorisation depends only on lam = lam_x + lam_z, so the factors
-//    (1/pivot_j, c'_j) are computed once in FP64 at set-up, one table row per
-//    (|m_z|, m_x); each thread solves the pencils m_z and N_z - m_z, which
-//    share the table row;
+//    are computed once in FP64 at set-up, one table row per (|m_z|, m_x)
+//    (FP64: the Thomas factors (1/pivot_j, c'_j), each thread solving the
+//    pencils m_z and N_z - m_z, which share the row; mixed: the factors of a
+//    twisted elimination from both walls to the middle row, one thread per
+//    pencil running both halves);
 //  * E_y is formed from phi in the y sweep, where phi still carries more than
 //    FP32 precision (a difference of FP32 values would lose the near-wall
 //    field); E_z takes its spectral multiplier before the inverse z transform
@@ -654,29 +656,12 @@ tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* sca
     } else {
         const float2* tinv = (const float2*)c->d_ytab;
         const float2* tcp = tinv + (size_t)ny * ni;
-        // Many pencils (384x256x256: 386 blocks): 12-row chunks, 168 registers, three blocks per
-        // SM (160 us; 10 rows at 176 registers, two blocks per SM: 250 us; 16 rows at 249
-        // registers: 264 us).  Few pencils (fewer than two blocks per SM, e.g. 128^3): 8-row
-        // chunks with the next chunk's loads issued before the current one is computed (a 128^3
-        // solve 130 -> 113 us).  At 384x256x256 the prefetch loses although 8 rows (164
-        // registers) keep three blocks per SM: 201 us, 6 rows 215 us.
-        const int64_t nblk = ((int64_t)nz * nxh + 127) / 128;
-        const bool few = nblk < 2 * (int64_t)c->num_sms;
-        const int ch = few ? 8 : 12;
-        const int nch = (ny + ch - 1) / ch;
-        // the chunk checkpoints of a block, one float4 per chunk and thread: at ny = 1024 (the
-        // largest grid) 264 KB with 8-row chunks, 196 KB with 12; the prefetching kernel runs
-        // only where the checkpoints fit
-        const size_t shc = sizeof(float4) * ((size_t)nch * 128 + ny + 1) + sizeof(float2) * ny;
-        const size_t sh12 = sizeof(float4) * ((size_t)((ny + 11) / 12) * 128 + ny + 1) + sizeof(float2) * ny;
         // without E (the adjoint's potential-only solves) the E_y spectrum is not written
-        auto* ys = few && shc <= (size_t)c->smem_optin
-                       ? (E ? k_ysolve_chunk<8, true> : k_ysolve_chunk<8, true, false>)
-                       : (E ? k_ysolve_chunk<12, false> : k_ysolve_chunk<12, false, false>);
-        (void)launch_pdl(ys, dim3((unsigned)nblk), dim3(128), few && shc <= (size_t)c->smem_optin ? shc : sh12,
-                         c->stream, (cplx<float>*)c->S, (cplx<float>*)c->F + fstride, tinv, tcp,
-                         (const float2*)c->d_yads, (const float4*)c->d_yec, ny, nz, nxh,
-                         (const FastTab<float>*)nullptr);
+        const int64_t nblk = ((int64_t)nz * nxh + 127) / 128;
+        auto* ys = E ? k_ysolve_twist<kTwistC> : k_ysolve_twist<kTwistC, false>;
+        (void)launch_pdl(ys, dim3((unsigned)nblk), dim3(128), ysolve_twist_smem(ny), c->stream, (cplx<float>*)c->S,
+                         (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
+                         (const float4*)c->d_yec, (float4*)c->d_yck, ny, nz, nxh, (const FastTab<float>*)nullptr);
     }
     TRIBO_LAUNCHED(c);
     if (fused) {
@@ -729,19 +714,37 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     std::vector<float2> tab32;
     if (ds_mode) tab32.resize(2 * (size_t)ny * ni);
     else tab64.resize((size_t)ny * ni);
+    const int kmid = ny / 2;         // the twisted solve's middle row (mixed mode)
     for (int item = 0; item < ni; ++item) {
         const double lam = lamz[item / nxh] + lamx[item % nxh];
-        double cp = 0.0;
-        for (int j = 0; j < ny; ++j) {
-            const double inv = 1.0 / ((b[j] - lam) - a[j] * cp);
-            cp = cc[j] * inv;
-            if (ds_mode) {
-                float2 ti, tc;
-                split_ds(inv, &ti.x, &ti.y);
-                split_ds(cp, &tc.x, &tc.y);
-                tab32[(size_t)j * ni + item] = ti;
-                tab32[(size_t)ny * ni + (size_t)j * ni + item] = tc;
-            } else {
+        if (ds_mode) {
+            // twisted factors: forward (1/pivot_j, c'_j) for rows 0..k-1, backward (1/pivot'_j,
+            // a''_j) for rows ny-1..k+1, and (1/gamma_k, 0) for row k
+            auto put = [&](int j, double u, double v) {
+                float2 t0, t1;
+                split_ds(u, &t0.x, &t0.y);
+                split_ds(v, &t1.x, &t1.y);
+                tab32[(size_t)j * ni + item] = t0;
+                tab32[(size_t)ny * ni + (size_t)j * ni + item] = t1;
+            };
+            double cp = 0.0;
+            for (int j = 0; j < kmid; ++j) {
+                const double inv = 1.0 / ((b[j] - lam) - a[j] * cp);
+                cp = cc[j] * inv;
+                put(j, inv, cp);
+            }
+            double ap = 0.0;
+            for (int j = ny - 1; j > kmid; --j) {
+                const double inv = 1.0 / ((b[j] - lam) - cc[j] * ap);
+                ap = a[j] * inv;
+                put(j, inv, ap);
+            }
+            put(kmid, 1.0 / ((b[kmid] - lam) - a[kmid] * cp - cc[kmid] * ap), 0.0);
+        } else {
+            double cp = 0.0;
+            for (int j = 0; j < ny; ++j) {
+                const double inv = 1.0 / ((b[j] - lam) - a[j] * cp);
+                cp = cc[j] * inv;
                 tab64[(size_t)j * ni + item] = make_double2(inv, cp);
             }
         }
@@ -752,9 +755,11 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
                           cudaMemcpyHostToDevice));
     if (!ds_mode) TRIBO_CUDA(cudaMalloc(&c->W2, 32 * (size_t)ny * ni));
     if (ds_mode) {
-        // sub-diagonal in double-single, E_y coefficients per cell and walls
-        std::vector<float2> ads(ny);
-        for (int j = 0; j < ny; ++j) split_ds(a[j], &ads[j].x, &ads[j].y);
+        // couplings of the twisted sweeps in double-single: a_j (rows 0..k), c_j (rows k+1..ny-1),
+        // c_k at ny; E_y coefficients per cell and walls
+        std::vector<float2> ads(ny + 1);
+        for (int j = 0; j < ny; ++j) split_ds(j <= kmid ? a[j] : cc[j], &ads[j].x, &ads[j].y);
+        split_ds(cc[kmid], &ads[ny].x, &ads[ny].y);
         auto w = [&](int f) { return (yf[f] - yc[f - 1]) / (yc[f] - yc[f - 1]); };
         std::vector<float4> ec(ny + 1, make_float4(0, 0, 0, 0));
         for (int j = 0; j < ny; ++j) {
@@ -766,8 +771,11 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
             ec[j] = make_float4((float)A, (float)Bm, (float)Bp, 0.f);
         }
         ec[ny] = make_float4((float)(-1.0 / (yc[0] - yf[0])), (float)(1.0 / (yf[ny] - yc[ny - 1])), 0.f, 0.f);
-        TRIBO_CUDA(cudaMalloc(&c->d_yads, sizeof(float2) * ny));
-        TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * ny, cudaMemcpyHostToDevice));
+        TRIBO_CUDA(cudaMalloc(&c->d_yads, sizeof(float2) * (ny + 1)));
+        TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * (ny + 1), cudaMemcpyHostToDevice));
+        // chunk checkpoints of the twisted sweeps
+        const size_t nck = (size_t)std::max(1, (kmid + kTwistC - 1) / kTwistC - 1) * 2 * (size_t)nz * nxh;
+        TRIBO_CUDA(cudaMalloc(&c->d_yck, sizeof(float4) * nck));
         TRIBO_CUDA(cudaMalloc(&c->d_yec, sizeof(float4) * (ny + 1)));
         TRIBO_CUDA(cudaMemcpy(c->d_yec, ec.data(), sizeof(float4) * (ny + 1), cudaMemcpyHostToDevice));
     }
@@ -795,11 +803,9 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         return dispatch_attr<double>(nx, nz, optin);
     }
     if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
-    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<12, false>), cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<8, true>), cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<12, false, false>), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    optin));
-    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<8, true, false>), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (ysolve_twist_smem(ny) > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
+    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_twist<kTwistC>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_twist<kTwistC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin));
     c->smem_optin = optin;
     return dispatch_attr<float>(nx, nz, optin);
@@ -812,6 +818,8 @@ void poisson_fast_free(tribo_ctx* c) {
     cudaFree(c->d_twz);
     cudaFree(c->d_yads);
     cudaFree(c->d_yec);
+    cudaFree(c->d_yck);
+    c->d_yck = nullptr;
     cudaFree(c->ring);
     cudaFree(c->d_pipe);
     c->d_ytab = c->W2 = c->d_twx = c->d_twz = c->d_yads = c->d_yec = c->ring = c->d_pipe = nullptr;

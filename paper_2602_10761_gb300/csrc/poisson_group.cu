@@ -57,16 +57,9 @@ void group_xinv(const Group& g, cudaStream_t st) {
         (float)(1.0 / ((double)g.nx * (double)g.nz)), (size_t)g.nz * (g.ny + 2) * g.nx, g.d_tab);
 }
 void group_ysolve(const Group& g, cudaStream_t st) {
-    // the chunking of the single-channel solve, for the group's pencils together
     const int64_t nblk = ((int64_t)g.nz * g.nxh + 127) / 128;
-    const bool few = nblk * g.n < 2 * (int64_t)g.num_sms;
-    const int ch = few ? 8 : 12;
-    const size_t shc = sizeof(float4) * ((size_t)((g.ny + ch - 1) / ch) * 128 + g.ny + 1) + sizeof(float2) * g.ny;
-    const size_t sh12 = sizeof(float4) * ((size_t)((g.ny + 11) / 12) * 128 + g.ny + 1) + sizeof(float2) * g.ny;
-    const bool pf = few && shc <= (size_t)g.smem_optin;
-    auto* ys = pf ? k_ysolve_chunk<8, true, true, true> : k_ysolve_chunk<12, false, true, true>;
-    ys<<<dim3((unsigned)nblk, g.n), 128, pf ? shc : sh12, st>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                g.ny, g.nz, g.nxh, g.d_tab);
+    k_ysolve_twist<kTwistC, true, true><<<dim3((unsigned)nblk, g.n), 128, ysolve_twist_smem(g.ny), st>>>(
+        nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g.ny, g.nz, g.nxh, g.d_tab);
 }
 
 bool group_dispatch(const Group& g, cudaStream_t st) {
@@ -132,9 +125,8 @@ tribo_status group_attr(const Group& g) {
         default: break;
     }
     if (st) return st;
-    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<12, false, true, true>),
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem_optin));
-    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_chunk<8, true, true, true>),
+    if (ysolve_twist_smem(g.ny) > (size_t)g.smem_optin) return TRIBO_ERR_UNSUPPORTED;
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_twist<kTwistC, true, true>),
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem_optin));
     return TRIBO_OK;
 }
@@ -169,6 +161,7 @@ tribo_status poisson_group_create(tribo_ctx* const* chans, int n, void** out) {
         f.tcp = f.tinv + (size_t)c->ny * ni;
         f.yads = (const float2*)c->d_yads;
         f.yec = (const float4*)c->d_yec;
+        f.yck = (float4*)c->d_yck;
     }
     Group* g = new (std::nothrow) Group();
     if (!g) { set_last_error("host allocation failed"); return TRIBO_ERR_OOM; }

@@ -65,8 +65,9 @@ struct FastTab {
     const double* sinz;
     const float2* tinv;         // y solve (mixed): 1/pivot, c' (double-single), sub-diagonal, E_y coefficients
     const float2* tcp;
-    const float2* yads;
+    const float2* yads;         // y couplings (twisted solve: a_j, c_j), E_y coefficients, chunk checkpoints
     const float4* yec;
+    float4* yck;
 };
 
 // ---------------------------------------------------------------- x forward
@@ -155,15 +156,7 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT*
     }
 }
 
-// ---------------------------------------------------------------- y solve, chunked Thomas
-// One thread per pencil (m_z, m_x); the factors are those of |m_z|.  Thomas
-// in double-single: the forward sweep keeps only the value entering each
-// chunk of C rows (checkpoints in shared memory); the backward sweep walks
-// the chunks from the top, recomputes each chunk's forward values into
-// registers from its checkpoint and substitutes back.  E_y per cell j is
-// A_j phi_j + Bm_j (phi_j - phi_j-1) + Bp_j (phi_j+1 - phi_j), the
-// differences formed from the double-single values, written one row behind
-// the backward sweep; wall nodes E_y = ew0 phi_0 (bottom), ewN phi_ny-1 (top).
+// ---------------------------------------------------------------- y solve, double-single steps
 // a r - b c with one normalisation: the two products' high parts are combined
 // by a two-sum and their error terms (each exact to FP32 rounding of an
 // O(u) correction) are added to the low part.
@@ -189,12 +182,44 @@ __device__ __forceinline__ ds ds_sub_mul(ds d, ds b, ds c) {
 // otherwise, so the result is within a few roundings of the difference
 __device__ __forceinline__ float ds_diff_f(ds a, ds b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
-template <int C, bool PF, bool EY = true, bool kTab = false>
-__global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
+// ---------------------------------------------------------------- y solve, twisted (two-ended) Thomas
+// One thread per pencil (m_z, m_x); the factors are those of |m_z|.  The
+// elimination runs from both walls towards the middle row k = ny/2 at once (a twisted
+// factorisation): the top half (rows 0..k-1) eliminates downwards with the
+// forward factors 1/pivot_j, c'_j = c_j/pivot_j, the bottom half (rows
+// ny-1..k+1) upwards with the backward factors 1/pivot'_j, a''_j =
+// a_j/pivot'_j, and row k joins them with 1/gamma_k, gamma_k = b_k - lam -
+// a_k c'_k-1 - c_k a''_k+1 (all FP64-computed at set-up, one table row per
+// (|m_z|, m_x)).  The two halves are independent chains of half the length,
+// interleaved in one thread: four double-single recurrences (real and
+// imaginary part of each half) instead of two.  In local index t of a half
+// (t = j in the top half, t = ny-1-j in the bottom half) both halves run the
+// same recurrences: p_t = (1/pivot)(r - coupling p_t-1), coupling = a_j
+// (top) or c_j (bottom), and x_t = p_t - (c' or a'') x_t+1 with x at local
+// index H (the half's length) = x_k.  The forward sweep keeps only the value
+// entering each chunk of C rows (in global memory, where they stay in L2),
+// and the substitution walks the chunks back from the middle, recomputing
+// each chunk's forward values into registers from its checkpoint.  E_y per cell j is A_j x_j + Bm_j (x_j - x_j-1) + Bp_j (x_j+1 -
+// x_j) from the double-single values, one cell behind the substitution (the
+// bottom half, walking j upwards, takes Bm and Bp with their roles and signs
+// exchanged); the top half writes cell k; wall nodes E_y = ew0 phi_0 (bottom
+// wall), ewN phi_ny-1 (top wall).
+// coup: ny + 1 double-single couplings, a_j (j <= k), c_j (j > k), c_k at ny.
+// ck: (ceil(k / C) - 1) x 2 x (nz nxh) float4 of chunk checkpoints.
+#ifndef TRIBO_TWIST_C
+#define TRIBO_TWIST_C 5
+#endif
+constexpr int kTwistC = TRIBO_TWIST_C;       // rows per chunk of the twisted solve
+// shared memory of a twisted solve: E_y coefficients and couplings, ny + 1 each
+inline size_t ysolve_twist_smem(int ny) { return (sizeof(float4) + sizeof(float2)) * (size_t)(ny + 1); }
+
+template <int C, bool EY = true, bool kTab = false>
+__global__ void __launch_bounds__(128, 3) k_ysolve_twist(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
                                                       const float2* __restrict__ tinv,
                                                       const float2* __restrict__ tcp,
-                                                      const float2* __restrict__ a_ds, const float4* __restrict__ ec,
-                                                      int ny, int nz, int nxh, const FastTab<float>* __restrict__ tab) {
+                                                      const float2* __restrict__ coup, const float4* __restrict__ ec,
+                                                      float4* __restrict__ ck, int ny, int nz, int nxh,
+                                                      const FastTab<float>* __restrict__ tab) {
     pdl_wait();
     if constexpr (kTab) {
         const FastTab<float>& t = tab[blockIdx.y];
@@ -202,171 +227,187 @@ __global__ void __launch_bounds__(128) k_ysolve_chunk(cplx<float>* __restrict__ 
         Fy = t.F + (size_t)nz * (ny + 2) * nxh;
         tinv = t.tinv;
         tcp = t.tcp;
-        a_ds = t.yads;
+        coup = t.yads;
         ec = t.yec;
+        ck = t.yck;
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* ck = reinterpret_cast<float4*>(smem_raw);                 // [chunk][thread]
-    const int nch = (ny + C - 1) / C;
-    float4* se = ck + (size_t)nch * blockDim.x;                        // ny + 1
-    float2* sa = reinterpret_cast<float2*>(se + ny + 1);              // ny
-    for (int j = threadIdx.x; j < ny; j += blockDim.x) sa[j] = a_ds[j];
-    for (int j = threadIdx.x; j <= ny; j += blockDim.x) se[j] = ec[j];
+    float4* se = reinterpret_cast<float4*>(smem_raw);                 // ny + 1
+    float2* sa = reinterpret_cast<float2*>(se + ny + 1);              // ny + 1
+    for (int j = threadIdx.x; j <= ny; j += blockDim.x) {
+        sa[j] = coup[j];
+        se[j] = ec[j];
+    }
     __syncthreads();
+    const int np = nz * nxh;
     const int pencil = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pencil >= nz * nxh) return;
+    if (pencil >= np) return;
     const int ni = (nz / 2 + 1) * nxh;
     const int mz = pencil / nxh;
     const int mx = pencil - mz * nxh;
     const int item = min(mz, nz - mz) * nxh + mx;
     cplx<float>* srow = S + (size_t)mz * ny * nxh + mx;
     cplx<float>* frow = Fy + (size_t)mz * (ny + 2) * nxh + mx;
-    const int tid = threadIdx.x;
-    // forward sweep, checkpoints at the end of each chunk
-    ds pr = {0.f, 0.f}, pim = {0.f, 0.f};
-    float2 tvn[C];                  // prefetch buffers (PF): the next chunk's loads
-    cplx<float> rvn[C];
-    if constexpr (PF) {
-#pragma unroll
-        for (int i = 0; i < C; ++i) {
-            if (i < ny) {
-                tvn[i] = tinv[(size_t)i * ni + item];
-                rvn[i] = srow[(size_t)i * nxh];
-            }
-        }
-    }
+    const int k = ny >> 1;
+    const int hl[2] = {k, ny - 1 - k};            // rows of the top and the bottom half
+    const int nch = (k + C - 1) / C;
+    // forward elimination of both halves, checkpoints at the end of each chunk but the last
+    ds p[2][2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};     // [half][re, im]
     for (int c = 0; c < nch; ++c) {
-        float2 tv[C];
-        cplx<float> rv[C];
-        if constexpr (PF) {
+        float2 tv[2][C];
+        cplx<float> rv[2][C];
 #pragma unroll
-            for (int i = 0; i < C; ++i) { tv[i] = tvn[i]; rv[i] = rvn[i]; }
-#pragma unroll
-            for (int i = 0; i < C; ++i) {
-                const int j = (c + 1) * C + i;
-                if (j < ny) {
-                    tvn[i] = tinv[(size_t)j * ni + item];
-                    rvn[i] = srow[(size_t)j * nxh];
-                }
-            }
-        } else {
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int i = 0; i < C; ++i) {
-                const int j = c * C + i;
-                if (j < ny) {
-                    tv[i] = tinv[(size_t)j * ni + item];
-                    rv[i] = srow[(size_t)j * nxh];
+                const int t = c * C + i;
+                if (t < hl[h]) {
+                    const int j = h == 0 ? t : ny - 1 - t;
+                    tv[h][i] = tinv[(size_t)j * ni + item];
+                    rv[h][i] = srow[(size_t)j * nxh];
                 }
             }
-        }
 #pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const int j = c * C + i;
-            if (j < ny) {
-                const ds inv = {tv[i].x, tv[i].y};
-                const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
-                pr = ds_fms(inv, rv[i].re, at, pr);
-                pim = ds_fms(inv, rv[i].im, at, pim);
-            }
-        }
-        ck[(size_t)c * blockDim.x + tid] = make_float4(pr.hi, pr.lo, pim.hi, pim.lo);
-    }
-    const float4 walls = se[ny];
-    ds xr1 = {0.f, 0.f}, xi1 = {0.f, 0.f};      // x[j+1]
-    float dnr = 0.f, dni = 0.f;                 // x[j+2] - x[j+1]
-    float2 tvb[C], cvb[C];          // prefetch buffers (PF): the previous chunk's loads
-    cplx<float> rvb[C];
-    if constexpr (PF) {
+        for (int i = 0; i < C; ++i)
 #pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const int j = (nch - 1) * C + i;
-            if (j < ny) {
-                tvb[i] = tinv[(size_t)j * ni + item];
-                cvb[i] = tcp[(size_t)j * ni + item];
-                rvb[i] = srow[(size_t)j * nxh];
+            for (int h = 0; h < 2; ++h) {
+                const int t = c * C + i;
+                if (t < hl[h]) {
+                    const int j = h == 0 ? t : ny - 1 - t;
+                    const ds inv = {tv[h][i].x, tv[h][i].y};
+                    const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
+                    p[h][0] = ds_fms(inv, rv[h][i].re, at, p[h][0]);
+                    p[h][1] = ds_fms(inv, rv[h][i].im, at, p[h][1]);
+                }
             }
+        if (c + 1 < nch)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                ck[((size_t)c * 2 + h) * np + pencil] = make_float4(p[h][0].hi, p[h][0].lo, p[h][1].hi, p[h][1].lo);
+    }
+    // the middle row: x_k = (r_k - a_k d_k-1 - c_k e_k+1) / gamma_k (d, e zero for an empty half)
+    const float2 tk = tinv[(size_t)k * ni + item];
+    const ds ig = {tk.x, tk.y};
+    const cplx<float> rk = srow[(size_t)k * nxh];
+    const ds ga = ds_mul(ig, ds{sa[k].x, sa[k].y});
+    const ds gc = ds_mul(ig, ds{sa[ny].x, sa[ny].y});
+    ds xk[2];
+    xk[0] = ds_sub_mul(ds_fms(ig, rk.re, ga, p[0][0]), gc, p[1][0]);
+    xk[1] = ds_sub_mul(ds_fms(ig, rk.im, ga, p[0][1]), gc, p[1][1]);
+    srow[(size_t)k * nxh] = cplx<float>{ds_f(xk[0]), ds_f(xk[1])};
+    // each half's row next to k (x_k-1, x_k+1): the start of the other half's E_y differences
+    ds xn[2][2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        xn[h][0] = xk[0];
+        xn[h][1] = xk[1];
+        if (hl[h] > 0) {
+            const int j = h == 0 ? k - 1 : k + 1;
+            const float2 cv = tcp[(size_t)j * ni + item];
+            const ds cp = {cv.x, cv.y};
+            xn[h][0] = ds_sub_mul(p[h][0], cp, xk[0]);
+            xn[h][1] = ds_sub_mul(p[h][1], cp, xk[1]);
         }
     }
+    ds x1[2][2];                    // x at local index t + 1
+    float dn[2][2];                 // x(t + 2) - x(t + 1)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        x1[h][0] = xk[0];
+        x1[h][1] = xk[1];
+        const bool other = hl[1 - h] > 0;
+        dn[h][0] = other ? ds_diff_f(xn[1 - h][0], xk[0]) : 0.f;
+        dn[h][1] = other ? ds_diff_f(xn[1 - h][1], xk[1]) : 0.f;
+    }
+    // substitution, chunks from the middle outwards, each recomputed from its checkpoint
     for (int c = nch - 1; c >= 0; --c) {
-        ds qr = {0.f, 0.f}, qi = {0.f, 0.f};
-        if (c > 0) {
-            const float4 v = ck[(size_t)(c - 1) * blockDim.x + tid];
-            qr = ds{v.x, v.y};
-            qi = ds{v.z, v.w};
-        }
-        float2 tv[C], cv[C];
-        cplx<float> rv[C];
-        if constexpr (PF) {
+        ds q[2][2];
 #pragma unroll
-            for (int i = 0; i < C; ++i) { tv[i] = tvb[i]; cv[i] = cvb[i]; rv[i] = rvb[i]; }
+        for (int h = 0; h < 2; ++h) {
             if (c > 0) {
-#pragma unroll
-                for (int i = 0; i < C; ++i) {
-                    const int j = (c - 1) * C + i;
-                    tvb[i] = tinv[(size_t)j * ni + item];
-                    cvb[i] = tcp[(size_t)j * ni + item];
-                    rvb[i] = srow[(size_t)j * nxh];
-                }
+                const float4 v = ck[((size_t)(c - 1) * 2 + h) * np + pencil];
+                q[h][0] = ds{v.x, v.y};
+                q[h][1] = ds{v.z, v.w};
+            } else {
+                q[h][0] = ds{0.f, 0.f};
+                q[h][1] = ds{0.f, 0.f};
             }
-        } else {
+        }
+        float2 tv[2][C], cv[2][C];
+        cplx<float> rv[2][C];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int i = 0; i < C; ++i) {
-                const int j = c * C + i;
-                if (j < ny) {
-                    tv[i] = tinv[(size_t)j * ni + item];
-                    cv[i] = tcp[(size_t)j * ni + item];
-                    rv[i] = srow[(size_t)j * nxh];
+                const int t = c * C + i;
+                if (t < hl[h]) {
+                    const int j = h == 0 ? t : ny - 1 - t;
+                    tv[h][i] = tinv[(size_t)j * ni + item];
+                    cv[h][i] = tcp[(size_t)j * ni + item];
+                    rv[h][i] = srow[(size_t)j * nxh];
                 }
             }
-        }
-        ds dr[C], di[C];
+        ds dr[2][C], di[2][C];
 #pragma unroll
-        for (int i = 0; i < C; ++i) {
-            const int j = c * C + i;
-            if (j < ny) {
-                const ds inv = {tv[i].x, tv[i].y};
-                const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
-                qr = ds_fms(inv, rv[i].re, at, qr);
-                qi = ds_fms(inv, rv[i].im, at, qi);
-                dr[i] = qr;
-                di[i] = qi;
-            }
-        }
+        for (int i = 0; i < C; ++i)
 #pragma unroll
-        for (int i = C - 1; i >= 0; --i) {
-            const int j = c * C + i;
-            if (j < ny) {
-                ds xr = dr[i], xi = di[i];
-                if (j != ny - 1) {
-                    const ds cp = {cv[i].x, cv[i].y};
-                    xr = ds_sub_mul(xr, cp, xr1);
-                    xi = ds_sub_mul(xi, cp, xi1);
+            for (int h = 0; h < 2; ++h) {
+                const int t = c * C + i;
+                if (t < hl[h]) {
+                    const int j = h == 0 ? t : ny - 1 - t;
+                    const ds inv = {tv[h][i].x, tv[h][i].y};
+                    const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
+                    q[h][0] = ds_fms(inv, rv[h][i].re, at, q[h][0]);
+                    q[h][1] = ds_fms(inv, rv[h][i].im, at, q[h][1]);
+                    dr[h][i] = q[h][0];
+                    di[h][i] = q[h][1];
                 }
-                const float fr = ds_f(xr), fi = ds_f(xi);
-                srow[(size_t)j * nxh] = cplx<float>{fr, fi};
-                if (EY && j == ny - 1) frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * fr, walls.y * fi};
-                float d0r = 0.f, d0i = 0.f;
-                if (EY && j + 1 <= ny - 1) {     // E_y of cell j+1 (node j+2)
-                    d0r = ds_diff_f(xr1, xr);
-                    d0i = ds_diff_f(xi1, xi);
-                    const float4 cf = se[j + 1];
-                    frow[(size_t)(j + 2) * nxh] = cplx<float>{cf.x * ds_f(xr1) + cf.y * d0r + cf.z * dnr,
-                        cf.x * ds_f(xi1) + cf.y * d0i + cf.z * dni};
-                }
-                dnr = d0r;
-                dni = d0i;
-                xr1 = xr;
-                xi1 = xi;
             }
-        }
+#pragma unroll
+        for (int i = C - 1; i >= 0; --i)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = c * C + i;
+                if (t < hl[h]) {
+                    const int j = h == 0 ? t : ny - 1 - t;
+                    const ds cp = {cv[h][i].x, cv[h][i].y};
+                    const ds xr = ds_sub_mul(dr[h][i], cp, x1[h][0]);
+                    const ds xi = ds_sub_mul(di[h][i], cp, x1[h][1]);
+                    srow[(size_t)j * nxh] = cplx<float>{ds_f(xr), ds_f(xi)};
+                    const float d0r = ds_diff_f(x1[h][0], xr), d0i = ds_diff_f(x1[h][1], xi);
+                    // E_y of the cell at local index t + 1 (the bottom half leaves cell k to the top)
+                    if (EY && (h == 0 || t + 1 < hl[1])) {
+                        const int jc = h == 0 ? t + 1 : ny - 2 - t;
+                        const float4 cf = se[jc];
+                        const float bm = h == 0 ? cf.y : -cf.z, bp = h == 0 ? cf.z : -cf.y;
+                        frow[(size_t)(jc + 1) * nxh] = cplx<float>{
+                            cf.x * ds_f(x1[h][0]) + bm * d0r + bp * dn[h][0],
+                            cf.x * ds_f(x1[h][1]) + bm * d0i + bp * dn[h][1]};
+                    }
+                    dn[h][0] = d0r;
+                    dn[h][1] = d0i;
+                    x1[h][0] = xr;
+                    x1[h][1] = xi;
+                }
+            }
     }
     if (!EY) return;
-    const float4 cf = se[0];
-    const float x0r = ds_f(xr1), x0i = ds_f(xi1);
-    frow[(size_t)1 * nxh] = cplx<float>{cf.x * x0r + cf.z * dnr, cf.x * x0i + cf.z * dni};
-    frow[0] = cplx<float>{walls.x * x0r, walls.x * x0i};
+    const float4 walls = se[ny];
+    {   // top: cell 0 (node 1) and the wall node 0
+        const float4 cf = se[0];
+        const float xr = ds_f(x1[0][0]), xi = ds_f(x1[0][1]);
+        frow[(size_t)1 * nxh] = cplx<float>{cf.x * xr + cf.z * dn[0][0], cf.x * xi + cf.z * dn[0][1]};
+        frow[0] = cplx<float>{walls.x * xr, walls.x * xi};
+    }
+    {   // bottom: cell ny-1 (node ny) unless it is cell k, and the wall node ny+1
+        const float xr = ds_f(x1[1][0]), xi = ds_f(x1[1][1]);
+        if (hl[1] > 0) {
+            const float4 cf = se[ny - 1];
+            frow[(size_t)ny * nxh] = cplx<float>{cf.x * xr - cf.y * dn[1][0], cf.x * xi - cf.y * dn[1][1]};
+        }
+        frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * xr, walls.y * xi};
+    }
 }
-
 
 // ---------------------------------------------------------------- z passes (four-step)
 // Forward z transform of S in place: block (cell plane j, W columns of m_x).
