@@ -133,8 +133,9 @@ tribo_status deposit_impl(tribo_ctx* c, const PView& p) {
 // ---------------------------------------------------------------- sort by cell
 // Counting sort on the cell key: count (the atomic's return value is the
 // particle's rank inside its cell), exclusive scan of the counts over all
-// cells, scatter of every particle array to offset[key] + rank.  The order
-// inside a cell follows the atomics and is not deterministic.
+// cells, the inverse permutation (slot offset[key] + rank takes the
+// particle), and a gather of every particle array into the sorted order.
+// The order inside a cell follows the atomics and is not deterministic.
 template <class R>
 __global__ void k_sort_count(StepArgs<R> a, PView p, uint32_t* __restrict__ counts, uint32_t* __restrict__ key,
                              uint32_t* __restrict__ rank) {
@@ -150,12 +151,14 @@ __global__ void k_sort_count(StepArgs<R> a, PView p, uint32_t* __restrict__ coun
     }
 }
 
+// the same move as a gather: slot d of the sorted set takes source particle perm[d] (the
+// inverse permutation, from k_cell_members), so the stores are coalesced and the loads
+// nearly so (the particles move little between sorts)
 template <class R>
-__global__ void k_sort_scatter(PView src, PView dst, const uint32_t* __restrict__ offsets,
-                               const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank) {
+__global__ void k_sort_gather(PView src, PView dst, const uint32_t* __restrict__ perm) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < src.n; n += stride) {
-        const uint32_t d = offsets[key[n]] + rank[n];
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < src.n; d += stride) {
+        const uint32_t n = perm[d];
         ((R*)dst.x)[d] = ((const R*)src.x)[n];
         ((R*)dst.y)[d] = ((const R*)src.y)[n];
         ((R*)dst.z)[d] = ((const R*)src.z)[n];
@@ -208,9 +211,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(const uint32_t* __r
     __shared__ uint32_t sh[32];
     const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
     uint32_t s = 0;
-#pragma unroll
-    for (int i = 0; i < kScanPer; ++i)
-        if (base + i < n) s += in[base + i];
+    if (base + kScanPer <= n) {       // two 16-byte loads (base is a multiple of 8 values)
+        const uint4 u0 = reinterpret_cast<const uint4*>(in + base)[0];
+        const uint4 u1 = reinterpret_cast<const uint4*>(in + base)[1];
+        s = u0.x + u0.y + u0.z + u0.w + u1.x + u1.y + u1.z + u1.w;
+    } else {
+        for (int i = 0; i < kScanPer; ++i)
+            if (base + i < n) s += in[base + i];
+    }
     uint32_t total;
     block_exclusive_scan(s, sh, &total);
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
@@ -239,17 +247,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* __restric
     const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)threadIdx.x * kScanPer;
     uint32_t v[kScanPer];
     uint32_t s = 0;
+    const bool whole = base + kScanPer <= n;
+    if (whole) {                      // two 16-byte loads and stores (base is a multiple of 8 values)
+        const uint4 u0 = reinterpret_cast<const uint4*>(data + base)[0];
+        const uint4 u1 = reinterpret_cast<const uint4*>(data + base)[1];
+        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+    } else {
 #pragma unroll
-    for (int i = 0; i < kScanPer; ++i) {
-        v[i] = base + i < n ? data[base + i] : 0u;
-        s += v[i];
+        for (int i = 0; i < kScanPer; ++i) v[i] = base + i < n ? data[base + i] : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) s += v[i];
     uint32_t total;
     uint32_t run = tile_off[blockIdx.x] + block_exclusive_scan(s, sh, &total);
+    uint32_t o[kScanPer];
 #pragma unroll
     for (int i = 0; i < kScanPer; ++i) {
-        if (base + i < n) data[base + i] = run;
+        o[i] = run;
         run += v[i];
+    }
+    if (whole) {
+        reinterpret_cast<uint4*>(data + base)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<uint4*>(data + base)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i)
+            if (base + i < n) data[base + i] = o[i];
     }
 }
 
@@ -309,7 +333,10 @@ tribo_status sort_impl(tribo_ctx* c, const PView& src, const PView& dst) {
     k_scan_apply<<<ntiles, kScanThreads, 0, c->stream>>>(counts, ncell, c->sort_tiles);
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_SORT);
-    k_sort_scatter<R><<<grid_for(src.n), kThreads, 0, c->stream>>>(src, dst, counts, key, rank);
+    k_cell_members<<<grid_for(src.n), kThreads, 0, c->stream>>>(counts, key, rank, src.n, c->sort_perm);
+    TRIBO_LAUNCHED(c);
+    phase_begin(c, PH_SORT);
+    k_sort_gather<R><<<grid_for(src.n), kThreads, 0, c->stream>>>(src, dst, c->sort_perm);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }

@@ -359,7 +359,7 @@ void free_ctx(tribo_ctx* c) {
     modes_free(c);
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
                     c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
-                    c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank,
+                    c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank, c->sort_perm,
                     c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner, c->d_inv_vol,
                     c->adj_E, c->n_imp0, c->patch};
     for (void* p : ptrs)
@@ -503,6 +503,7 @@ tribo_status tribo_init(tribo_ctx** out, const tribo_grid* grid, const tribo_flu
         TRYC(cudaMalloc(&c->sort_counts, sizeof(uint32_t) * ncell));
         TRYC(cudaMalloc(&c->sort_key, sizeof(uint32_t) * max_particles));
         TRYC(cudaMalloc(&c->sort_rank, sizeof(uint32_t) * max_particles));
+        TRYC(cudaMalloc(&c->sort_perm, sizeof(uint32_t) * max_particles));
         TRYC(cudaMalloc(&c->sort_tiles, sizeof(uint32_t) * (ncell / 8192 + 2)));
     }
     TRY(poisson_setup(c));

@@ -157,6 +157,7 @@ struct tribo_ctx {
     uint32_t* sort_counts = nullptr;   // ncells: counts, then offsets
     uint32_t* sort_key = nullptr;      // max_particles
     uint32_t* sort_rank = nullptr;     // max_particles
+    uint32_t* sort_perm = nullptr;     // max_particles: source particle of each sorted slot
     uint32_t* sort_tiles = nullptr;    // scan tile sums
     int64_t steps_done = 0;            // steps taken by this context (sort schedule)
     uint32_t* nf_members = nullptr;    // near field: particle indices grouped by cell
