@@ -45,9 +45,20 @@ struct RegPass {
                 if constexpr (LS > 1) {
 #pragma unroll
                     for (int t = 1; t < RAD; ++t) {
-                        cplx<R> w = tw[t * k * TWM * STEP];
-                        if constexpr (SIGN > 0) w = conj(w);
-                        y[t] = y[t] * w;
+                        // W_L^e with e = t k TWM: a power of i where 4 e is a multiple of L (k = 0
+                        // among them), taken exactly without the table; the table otherwise
+                        const int e = t * k * TWM;
+                        if ((4 * e) % L == 0) {
+                            const int q = ((4 * e) / L) & 3;        // W = (SIGN i)^q
+                            const cplx<R> v = y[t];
+                            if (q == 1) y[t] = SIGN > 0 ? cplx<R>{-v.im, v.re} : cplx<R>{v.im, -v.re};
+                            else if (q == 2) y[t] = cplx<R>{-v.re, -v.im};
+                            else if (q == 3) y[t] = SIGN > 0 ? cplx<R>{v.im, -v.re} : cplx<R>{-v.im, v.re};
+                        } else {
+                            cplx<R> w = tw[e * STEP];
+                            if constexpr (SIGN > 0) w = conj(w);
+                            y[t] = y[t] * w;
+                        }
                     }
                 }
                 dft<R, SIGN, RAD>(y);
