@@ -321,6 +321,17 @@ tribo_status tribo_sync(tribo_ctx* ctx);
 uint32_t     tribo_error_bits(const tribo_ctx* ctx);
 tribo_status tribo_clear_error(tribo_ctx* ctx);
 
+/* Testing aid for the bounded waits of the pipelined inverse transform (the
+ * persistent launch whose tasks wait on one another): from the next solve on,
+ * the consumer tasks of node plane `plane` wait for one producer task more than
+ * exists, so each of their waits runs out after its iteration limit (about a
+ * second), sets TRIBO_DEV_TIMEOUT in the device error word and returns; the
+ * launch still ends and the context stays usable (tribo_clear_error), but that
+ * solve's field is not valid.  plane = -1 (the default) clears it.  Grids
+ * solved without the pipeline ignore it.  TRIBO_ERR_ARG for ctx NULL or
+ * plane < -1. */
+tribo_status tribo_test_pipeline_wait(tribo_ctx* ctx, int32_t plane);
+
 /* Number of kernel launches the library issued since the context was made. */
 int64_t      tribo_launch_count(const tribo_ctx* ctx);
 

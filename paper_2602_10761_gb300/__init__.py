@@ -13,7 +13,7 @@ from ._abi import (  # noqa: F401
 from .api import (  # noqa: F401
     Params, Particles, Channel, tribo_init, tribo_set_fluid, tribo_set_params, tribo_step,
     tribo_poisson, tribo_poisson_noalloc, tribo_stats, tribo_reset_stats, tribo_sync, tribo_error_bits,
-    tribo_clear_error, tribo_launch_count, tribo_destroy, tribo_timing_enable, tribo_timing_read,
+    tribo_clear_error, tribo_test_pipeline_wait, tribo_launch_count, tribo_destroy, tribo_timing_enable, tribo_timing_read,
     tribo_phase_name, tribo_set_modes, tribo_eval_modes, tribo_adjoint, mean_charge, Batch, tribo_set_ssm,
     SSMParams, tribo_set_momentum_source, tribo_set_adjoint_memory, tribo_transfer_bytes,
 )

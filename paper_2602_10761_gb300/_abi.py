@@ -88,6 +88,7 @@ _SIGS = {
     "tribo_sync": (C.c_int32, [C.c_void_p]),
     "tribo_error_bits": (C.c_uint32, [C.c_void_p]),
     "tribo_clear_error": (C.c_int32, [C.c_void_p]),
+    "tribo_test_pipeline_wait": (C.c_int32, [C.c_void_p, C.c_int32]),
     "tribo_launch_count": (C.c_int64, [C.c_void_p]),
     "tribo_timing_enable": (C.c_int32, [C.c_void_p, C.c_int32]),
     "tribo_timing_read": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int32]),

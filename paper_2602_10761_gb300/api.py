@@ -342,6 +342,10 @@ def tribo_clear_error(ctx: int) -> None:
     check(load().tribo_clear_error(ctx), "tribo_clear_error")
 
 
+def tribo_test_pipeline_wait(ctx: int, plane: int) -> None:
+    check(load().tribo_test_pipeline_wait(ctx, int(plane)), "tribo_test_pipeline_wait")
+
+
 def tribo_launch_count(ctx: int) -> int:
     return int(load().tribo_launch_count(ctx))
 

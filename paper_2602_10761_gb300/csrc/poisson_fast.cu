@@ -158,6 +158,8 @@ struct Pipe {
     int na, nb;      // producer and consumer tasks per plane
     int L, P;        // lookahead in stages, ring slots
     unsigned total;  // planes * (na + nb)
+    int stall;       // testing: the plane whose consumers wait for a producer task that never
+                     // comes (their bounded waits run out), or -1
 };
 
 Pipe make_pipe(int planes, int na, int nb) {
@@ -168,6 +170,7 @@ Pipe make_pipe(int planes, int na, int nb) {
     p.L = std::min(kPipeLook, planes);
     p.P = kPipeSlots;
     p.total = (unsigned)planes * (unsigned)(na + nb);
+    p.stall = -1;
     return p;
 }
 
@@ -232,7 +235,7 @@ __device__ __forceinline__ void pipe_start(PipeLoop& L, PipeSync* sy) {
 __device__ __forceinline__ void pipe_acquire(PipeLoop& L, const Pipe& p, PipeSync* sy, bool cons, int plane,
                                              unsigned* err) {
     if (threadIdx.x == 0) {
-        if (cons) pipe_wait(&sy->a_done[plane], (unsigned)p.na, err);
+        if (cons) pipe_wait(&sy->a_done[plane], (unsigned)p.na + (plane == p.stall ? 1u : 0u), err);
         else if (plane >= p.P) pipe_wait(&sy->b_done[plane - p.P], (unsigned)p.nb, err);
     }
     __syncthreads();
@@ -455,6 +458,8 @@ tribo_status launch_inv_fused(tribo_ctx* c, void* E, double* phi) {
     const Pipe pipe = make_pipe(c->ny + 2, (c->nxh + fft::FourStep<NZ, kThreads>::W - 1) / fft::FourStep<NZ, kThreads>::W,
                                 (NZ + fft::FourStep<M, kThreads>::W - 1) / fft::FourStep<M, kThreads>::W);
     PipeSync* sy = (PipeSync*)c->d_pipe;     // zero (at set-up, then left so by every launch)
+    Pipe pipe_t = pipe;
+    pipe_t.stall = c->test_stall_plane;
     static int occ = 0;
     const size_t smem = inv_fused_smem<R, M, NZ>();
     const int grid = fused_grid(k_inv_fused<R, M, NZ>, smem, c->num_sms, pipe.total, &occ);
@@ -463,7 +468,7 @@ tribo_status launch_inv_fused(tribo_ctx* c, void* E, double* phi) {
         (const cplx<R>*)c->S, (const cplx<R>*)c->F + fstride, (cplx<R>*)c->ring, (R*)E, phi, c->ny,
         phi != nullptr ? 1 : 0, E != nullptr ? 1 : 0, (R)(1.0 / ((double)c->nx * (double)NZ)),
         (size_t)NZ * (c->ny + 2) * c->nx, c->d_sinx, c->d_sinz, (const cplx<R>*)c->d_twx,
-        (const cplx<R>*)c->d_twz, sy, pipe, &c->d_acc->err);
+        (const cplx<R>*)c->d_twz, sy, pipe_t, &c->d_acc->err);
     return TRIBO_OK;
 }
 

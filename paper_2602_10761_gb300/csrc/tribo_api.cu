@@ -893,6 +893,13 @@ tribo_status tribo_clear_error(tribo_ctx* c) {
 
 int64_t tribo_launch_count(const tribo_ctx* c) { return c ? c->launches : 0; }
 
+tribo_status tribo_test_pipeline_wait(tribo_ctx* c, int32_t plane) {
+    if (!c) { set_last_error("ctx is NULL"); return TRIBO_ERR_ARG; }
+    if (plane < -1) { set_last_error("plane must be -1 or a node plane"); return TRIBO_ERR_ARG; }
+    c->test_stall_plane = plane;
+    return TRIBO_OK;
+}
+
 void tribo_destroy(tribo_ctx* c) { free_ctx(c); }
 
 }  // extern "C"

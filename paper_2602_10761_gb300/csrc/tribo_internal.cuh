@@ -135,6 +135,7 @@ struct tribo_ctx {
     void* d_yads = nullptr;      // ny float2: y sub-diagonal in double-single (mixed mode)
     void* d_yec = nullptr;       // ny+1 float4: E_y coefficients per cell, walls (mixed mode)
     void* d_yck = nullptr;       // chunk checkpoints of the twisted y sweeps (mixed mode)
+    int test_stall_plane = -1;   // testing: a pipelined-inverse plane whose consumers' waits run out
     void* ring = nullptr;        // fused inverse pipeline: ring of plane slots of the intermediate fields
     void* d_pipe = nullptr;      // ... and the launch's task counters
     bool in_batch = false;       // a batch holds the context: solves run the split passes
