@@ -618,15 +618,28 @@ tribo_status dispatch_attr(int nx, int nz, int optin) {
     }
 }
 
+// tw[e] = exp(-2 pi i e / n), e < n; for the x length (with_inner) also the four-step's inner
+// twiddles of M = n/2 = N1 N2 laid out by thread: tw[n + k1 N2 + r] = W_M^(r k1), so that the
+// 16 threads of a column read 16 consecutive values (the lookup tw[2 r k1] hits one shared-memory
+// bank several times over)
 template <class R>
-tribo_status twiddles(int n, void** dst) {
-    std::vector<cplx<R>> tw(n);
+tribo_status twiddles(int n, void** dst, bool with_inner = false) {
+    int n1 = 1, n2 = 0;
+    if (with_inner) {
+        const int m = n / 2;
+        for (int d = 1; d * d <= m; ++d)
+            if (m % d == 0) n1 = d;
+        n2 = m / n1;
+    }
+    std::vector<cplx<R>> tw(n + (size_t)n1 * n2);
     for (int e = 0; e < n; ++e) {
         const double a = 2.0 * M_PI * (double)e / (double)n;
         tw[e] = cplx<R>{(R)std::cos(a), (R)(-std::sin(a))};
     }
-    TRIBO_CUDA(cudaMalloc(dst, sizeof(cplx<R>) * n));
-    TRIBO_CUDA(cudaMemcpy(*dst, tw.data(), sizeof(cplx<R>) * n, cudaMemcpyHostToDevice));
+    for (int k1 = 0; k1 < n1 && with_inner; ++k1)
+        for (int r = 0; r < n2; ++r) tw[n + (size_t)k1 * n2 + r] = tw[(size_t)2 * r * k1];
+    TRIBO_CUDA(cudaMalloc(dst, sizeof(cplx<R>) * tw.size()));
+    TRIBO_CUDA(cudaMemcpy(*dst, tw.data(), sizeof(cplx<R>) * tw.size(), cudaMemcpyHostToDevice));
     return TRIBO_OK;
 }
 
@@ -804,10 +817,10 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         }
     }
     if (c->prec == TRIBO_FP64) {
-        if ((st = twiddles<double>(nx, &c->d_twx)) || (st = twiddles<double>(nz, &c->d_twz))) return st;
+        if ((st = twiddles<double>(nx, &c->d_twx, true)) || (st = twiddles<double>(nz, &c->d_twz))) return st;
         return dispatch_attr<double>(nx, nz, optin);
     }
-    if ((st = twiddles<float>(nx, &c->d_twx)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
+    if ((st = twiddles<float>(nx, &c->d_twx, true)) || (st = twiddles<float>(nz, &c->d_twz))) return st;
     if (ysolve_twist_smem(ny) > (size_t)optin) return TRIBO_ERR_UNSUPPORTED;
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_twist<kTwistC>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_twist<kTwistC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

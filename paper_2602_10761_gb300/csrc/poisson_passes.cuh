@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT*
             for (int n1 = 0; n1 < N1; ++n1) row[N2 * n1 + r] = zero;
         }
         fft::reg_dft<R, -1, N1, 2 * N2>(y, tw);
+        // W_M^(r k1) from the thread-ordered copy after the table (consecutive in r)
 #pragma unroll
-        for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * tw[2 * r * k1];
+        for (int k1 = 1; k1 < N1; ++k1) y[k1] = y[k1] * tw_g[NX + k1 * N2 + r];
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) lb[r * (N1 + 1) + k1] = y[k1];
     }

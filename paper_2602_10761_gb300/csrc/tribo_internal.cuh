@@ -130,7 +130,7 @@ struct tribo_ctx {
     bool fast = false;
     void* d_ytab = nullptr;      // (ny, (nz/2+1)*nxh) double2: 1/pivot, c' per wavenumber pair
     void* W2 = nullptr;          // (ny, (nz/2+1)*nxh, 2) double2 Thomas scratch
-    void* d_twx = nullptr;       // nx twiddles exp(-2 pi i e / nx), real precision
+    void* d_twx = nullptr;       // nx twiddles exp(-2 pi i e / nx), then the x transform's inner twiddles by thread
     void* d_twz = nullptr;       // nz twiddles
     void* d_yads = nullptr;      // ny float2: y sub-diagonal in double-single (mixed mode)
     void* d_yec = nullptr;       // ny+1 float4: E_y coefficients per cell, walls (mixed mode)
