@@ -24,7 +24,10 @@ namespace {
 
 // A host call's list of the particles whose impact count changed (their q,
 // q_wall, n_imp are the only ones of those arrays that moved): a 16-byte
-// header holding the count, then the entries.
+// header holding the count, then the entries.  A call in increments mode (no
+// SSM) never copies q_wall and n_imp in: the device arrays start at zero and
+// collect the call's wall charge and impact count, and the entries carry
+// those increments (with the new q), which the host adds to its arrays.
 struct PatchEntry {
     uint32_t i, n_imp;
     double q, q_wall;
@@ -42,7 +45,7 @@ __global__ void k_patch(const uint32_t* __restrict__ n_imp, const uint32_t* __re
     PatchEntry* out = reinterpret_cast<PatchEntry*>(list + kPatchHeader);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t m = n_imp[i];
-        if (m != n_imp0[i]) {
+        if (m != (n_imp0 ? n_imp0[i] : 0u)) {
             const unsigned int k = atomicAdd(count, 1u);
             if (k < cap) out[k] = PatchEntry{(uint32_t)i, m, q[i], q_wall[i], site ? site[i] : 1.0};
         }
@@ -152,7 +155,7 @@ struct Stage {
 // copied only when `with_id`.  Back to the host: every state array, the ids
 // when `with_id`.
 tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particles* src, cudaMemcpyKind kind,
-                            bool to_device, int groups, bool with_id, cudaStream_t stream) {
+                            bool to_device, int groups, bool with_id, cudaStream_t stream, bool incr = false) {
     const size_t rs = real_size(c);
     const size_t n = (size_t)src->n;
     auto cp = [&](void* dev, void* host, size_t elem) -> tribo_status {
@@ -169,10 +172,15 @@ tribo_status copy_particles(tribo_ctx* c, const PView& dst, const tribo_particle
             return st;
         if ((groups & 2) &&
             ((st = cp(dst.vx, src->vx, rs)) || (st = cp(dst.vy, src->vy, rs)) || (st = cp(dst.vz, src->vz, rs)) ||
-             (st = cp(dst.d, src->d, rs)) || (st = cp(dst.q_wall, src->q_wall, sizeof(double))) ||
-             (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t))) || (st = cp(dst.site, src->site, sizeof(double))) ||
+             (st = cp(dst.d, src->d, rs)) || (!incr && (st = cp(dst.q_wall, src->q_wall, sizeof(double)))) ||
+             (!incr && (st = cp(dst.n_imp, src->n_imp, sizeof(uint32_t)))) ||
+             (st = cp(dst.site, src->site, sizeof(double))) ||
              (with_id && (st = cp(dst.id, src->id, sizeof(uint32_t))))))
             return st;
+        if ((groups & 2) && incr) {
+            TRIBO_CUDA(cudaMemsetAsync(dst.q_wall, 0, sizeof(double) * n, stream));
+            TRIBO_CUDA(cudaMemsetAsync(dst.n_imp, 0, sizeof(uint32_t) * n, stream));
+        }
         return TRIBO_OK;
     }
     if ((st = cp(dst.x, src->x, rs)) || (st = cp(dst.y, src->y, rs)) || (st = cp(dst.z, src->z, rs)) ||
@@ -228,7 +236,7 @@ tribo_status copy_back_range(tribo_ctx* c, const PView& part, const tribo_partic
 // the arrays of the caller's particles [a0, a0 + part.n) that the deposit does not need
 // (group 2 of copy_particles) into device particles `part`
 tribo_status copy_rest_range(tribo_ctx* c, const PView& part, const tribo_particles* host, int64_t a0, bool with_id,
-                             cudaStream_t stream) {
+                             cudaStream_t stream, bool incr) {
     const size_t rs = real_size(c);
     const size_t n = (size_t)part.n;
     auto cp = [&](void* d, const void* h, size_t elem) -> tribo_status {
@@ -239,25 +247,41 @@ tribo_status copy_rest_range(tribo_ctx* c, const PView& part, const tribo_partic
     };
     tribo_status st;
     if ((st = cp(part.vx, host->vx, rs)) || (st = cp(part.vy, host->vy, rs)) || (st = cp(part.vz, host->vz, rs)) ||
-        (st = cp(part.d, host->d, rs)) || (st = cp(part.q_wall, host->q_wall, sizeof(double))) ||
-        (st = cp(part.n_imp, host->n_imp, sizeof(uint32_t))) || (st = cp(part.site, host->site, sizeof(double))) ||
-        (with_id && (st = cp(part.id, host->id, sizeof(uint32_t)))))
+        (st = cp(part.d, host->d, rs)) || (!incr && (st = cp(part.q_wall, host->q_wall, sizeof(double)))) ||
+        (!incr && (st = cp(part.n_imp, host->n_imp, sizeof(uint32_t)))) ||
+        (st = cp(part.site, host->site, sizeof(double))) || (with_id && (st = cp(part.id, host->id, sizeof(uint32_t)))))
         return st;
+    if (incr) {
+        TRIBO_CUDA(cudaMemsetAsync(part.q_wall, 0, sizeof(double) * n, stream));
+        TRIBO_CUDA(cudaMemsetAsync(part.n_imp, 0, sizeof(uint32_t) * n, stream));
+    }
     return TRIBO_OK;
 }
 
 // After a host call in patch mode (stream idle): write the listed particles'
 // q, q_wall, n_imp into the caller's arrays; a list longer than its capacity
 // gives way to copying the three arrays whole.
-tribo_status apply_patch(tribo_ctx* c, const PView& dev, const tribo_particles* host) {
+tribo_status apply_patch(tribo_ctx* c, const PView& dev, const tribo_particles* host, bool incr) {
     const int64_t cnt = *static_cast<const unsigned int*>(c->patch_host);
     const int64_t hn = std::min<int64_t>(c->patch_cap, kPatchHost);
     const size_t n = (size_t)dev.n;
     if (cnt > c->patch_cap) {
         TRIBO_CUDA(cudaMemcpy(host->q, dev.q, sizeof(double) * n, cudaMemcpyDeviceToHost));
-        TRIBO_CUDA(cudaMemcpy(host->q_wall, dev.q_wall, sizeof(double) * n, cudaMemcpyDeviceToHost));
-        TRIBO_CUDA(cudaMemcpy(host->n_imp, dev.n_imp, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
         c->d2h_bytes += (2 * sizeof(double) + sizeof(uint32_t)) * n;
+        if (!incr) {
+            TRIBO_CUDA(cudaMemcpy(host->q_wall, dev.q_wall, sizeof(double) * n, cudaMemcpyDeviceToHost));
+            TRIBO_CUDA(cudaMemcpy(host->n_imp, dev.n_imp, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+            return TRIBO_OK;
+        }
+        std::vector<double> dqw(n);
+        std::vector<uint32_t> dni(n);
+        TRIBO_CUDA(cudaMemcpy(dqw.data(), dev.q_wall, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        TRIBO_CUDA(cudaMemcpy(dni.data(), dev.n_imp, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i)
+            if (dni[i]) {
+                host->q_wall[i] += dqw[i];
+                host->n_imp[i] += dni[i];
+            }
         return TRIBO_OK;
     }
     unsigned char* hl = static_cast<unsigned char*>(c->patch_host) + kPatchHeader;
@@ -270,8 +294,13 @@ tribo_status apply_patch(tribo_ctx* c, const PView& dev, const tribo_particles* 
     const PatchEntry* e = reinterpret_cast<const PatchEntry*>(hl);
     for (int64_t k = 0; k < cnt; ++k) {
         host->q[e[k].i] = e[k].q;
-        host->q_wall[e[k].i] = e[k].q_wall;
-        host->n_imp[e[k].i] = e[k].n_imp;
+        if (incr) {
+            host->q_wall[e[k].i] += e[k].q_wall;
+            host->n_imp[e[k].i] += e[k].n_imp;
+        } else {
+            host->q_wall[e[k].i] = e[k].q_wall;
+            host->n_imp[e[k].i] = e[k].n_imp;
+        }
         if (host->site) host->site[e[k].i] = e[k].site;
     }
     return TRIBO_OK;
@@ -631,6 +660,9 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
     // ... and when that call's one step is also its last, it runs in chunks that each wait only
     // for their own particles' arrays, so the copies back overlap the copies in
     const bool one_chunked = patch && nsteps == 1;
+    // ... and, unless the SSM reads the impact counts, without copying q_wall and n_imp in: the
+    // device collects the call's increments and the host adds them
+    const bool incr = patch && !c->ssm_on;
     if (patch && !(c->n_imp0 && c->patch && c->patch_host)) {
         // each buffer on its own, so that a failed allocation is retried by the next call
         TRIBO_CUDA(cudaStreamSynchronize(c->stream));
@@ -671,24 +703,25 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             // may run and count impacts)
             for (int ci = 0; ci < kChunks; ++ci) {
                 const int64_t a0 = p->n * ci / kChunks, a1 = p->n * (ci + 1) / kChunks;
-                if (a1 > a0 && (st = copy_rest_range(c, sub_view(c, v, a0, a1 - a0), p, a0, ids, c->copy_stream))) {
+                if (a1 > a0 &&
+                    (st = copy_rest_range(c, sub_view(c, v, a0, a1 - a0), p, a0, ids, c->copy_stream, incr))) {
                     cudaStreamSynchronize(c->copy_stream);
                     cudaStreamSynchronize(c->stream);
                     return st;
                 }
-                if (a1 > a0)
+                if (a1 > a0 && !incr)
                     TRIBO_CUDA(cudaMemcpyAsync(c->n_imp0 + a0, v.n_imp + a0, sizeof(uint32_t) * (size_t)(a1 - a0),
                                                cudaMemcpyDeviceToDevice, c->copy_stream));
                 TRIBO_CUDA(cudaEventRecord(c->rest_done[ci], c->copy_stream));
             }
         } else {
-            if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream))) {
+            if ((st = copy_particles(c, v, p, cudaMemcpyHostToDevice, true, 2, ids, c->copy_stream, incr))) {
                 cudaStreamSynchronize(c->copy_stream);
                 cudaStreamSynchronize(c->stream);
                 return st;
             }
             // the first step waits for copy_done, recorded after this copy
-            if (patch)
+            if (patch && !incr)
                 TRIBO_CUDA(cudaMemcpyAsync(c->n_imp0, v.n_imp, sizeof(uint32_t) * (size_t)p->n,
                                            cudaMemcpyDeviceToDevice, c->copy_stream));
         }
@@ -764,7 +797,8 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
                     // the changed particles' list, its count and first entries in one copy
                     TRIBO_CUDA(cudaMemsetAsync(c->patch, 0, kPatchHeader, c->stream));
                     const int blocks = (int)std::min<int64_t>((cur.n + 255) / 256, (int64_t)c->num_sms * 8);
-                    k_patch<<<blocks, 256, 0, c->stream>>>(cur.n_imp, c->n_imp0, cur.q, cur.q_wall, cur.site, cur.n,
+                    k_patch<<<blocks, 256, 0, c->stream>>>(cur.n_imp, incr ? nullptr : c->n_imp0, cur.q, cur.q_wall,
+                                                           cur.site, cur.n,
                                                            (unsigned char*)c->patch, (unsigned int)c->patch_cap);
                     TRIBO_LAUNCHED(c);
                     const size_t hb = kPatchHeader + sizeof(PatchEntry) * (size_t)std::min<int64_t>(c->patch_cap,
@@ -792,7 +826,7 @@ tribo_status tribo_step(tribo_ctx* c, tribo_particles* p, double dt, int32_t nst
             TRIBO_CUDA(cudaStreamSynchronize(c->copy_stream));
             if (patch) {
                 TRIBO_CUDA(cudaStreamSynchronize(c->stream));
-                if ((st = apply_patch(c, cur, p))) return st;
+                if ((st = apply_patch(c, cur, p, incr))) return st;
             }
             return sync_and_check(c);
         }

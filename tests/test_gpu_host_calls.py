@@ -79,11 +79,12 @@ def test_mixed_host_calls_match_device_calls():
 def test_transfer_bytes_of_host_calls():
     n = 1000
     c, faces, lat, parts = problem(16, 12, 8, n=n, q_scale=1e-13, seed=33)
-    # no re-sort: every state array in (7 FP32 + q, q_wall FP64 + n_imp u32 = 48 B), positions
-    # and velocities out (24 B), and the list's count with its first entries (capacity 1024 entries
-    # of 32 B: index, impact count, q, q_wall, site density)
+    # no re-sort and no SSM: the state arrays in except q_wall and n_imp (7 FP32 + q FP64 = 36 B:
+    # the device collects the call's wall charge and impact count from zero and the host adds
+    # them), positions and velocities out (24 B), and the list's count with its first entries
+    # (capacity 1024 entries of 32 B: index, impact count, q, q_wall, site density)
     _, nb, _ = _run(c, faces, lat, parts, T.TRIBO_MIXED, host=True, calls=1)
-    assert nb == (48 * n, 24 * n + 16 + 32 * 1024)
+    assert nb == (36 * n, 24 * n + 16 + 32 * 1024)
     # a call that sorts: the ids both ways, and every array back (44 B + 4 B of ids)
     _, nb, _ = _run(c, faces, lat, parts, T.TRIBO_MIXED, host=True, calls=1, sort_every=1)
     assert nb == (52 * n, 48 * n)
