@@ -675,8 +675,14 @@ tribo_status solve_fast(tribo_ctx* c, void* src, bool src_f64, const double* sca
         const float2* tinv = (const float2*)c->d_ytab;
         const float2* tcp = tinv + (size_t)ny * ni;
         // without E (the adjoint's potential-only solves) the E_y spectrum is not written
-        const int64_t nblk = ((int64_t)nz * nxh + 127) / 128;
-        auto* ys = E ? k_ysolve_twist<kTwistC> : k_ysolve_twist<kTwistC, false>;
+        // fewer pencils than one 128-thread block per SM (e.g. 128^3: 65 blocks): two threads per
+        // pencil, one half each, meeting through warp shuffles (54 -> 37 us at 128^3, chunks of 8
+        // rows; 5 and 12 rows: 43 and 39 us); otherwise one thread runs both halves
+        const int64_t np = (int64_t)nz * nxh;
+        const bool split = np < 128 * (int64_t)c->num_sms;
+        const int64_t nblk = ((split ? 2 : 1) * np + 127) / 128;
+        auto* ys = split ? (E ? k_ysolve_twist<kTwistC2, true, false, 2> : k_ysolve_twist<kTwistC2, false, false, 2>)
+                         : (E ? k_ysolve_twist<kTwistC> : k_ysolve_twist<kTwistC, false>);
         (void)launch_pdl(ys, dim3((unsigned)nblk), dim3(128), ysolve_twist_smem(ny), c->stream, (cplx<float>*)c->S,
                          (cplx<float>*)c->F + fstride, tinv, tcp, (const float2*)c->d_yads,
                          (const float4*)c->d_yec, (float4*)c->d_yck, ny, nz, nxh, (const FastTab<float>*)nullptr);
@@ -792,7 +798,8 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
         TRIBO_CUDA(cudaMalloc(&c->d_yads, sizeof(float2) * (ny + 1)));
         TRIBO_CUDA(cudaMemcpy(c->d_yads, ads.data(), sizeof(float2) * (ny + 1), cudaMemcpyHostToDevice));
         // chunk checkpoints of the twisted sweeps
-        const size_t nck = (size_t)std::max(1, (kmid + kTwistC - 1) / kTwistC - 1) * 2 * (size_t)nz * nxh;
+        const int cmin = std::min(kTwistC, kTwistC2);        // the launch with more chunks
+        const size_t nck = (size_t)std::max(1, (kmid + cmin - 1) / cmin - 1) * 2 * (size_t)nz * nxh;
         TRIBO_CUDA(cudaMalloc(&c->d_yck, sizeof(float4) * nck));
         TRIBO_CUDA(cudaMalloc(&c->d_yec, sizeof(float4) * (ny + 1)));
         TRIBO_CUDA(cudaMemcpy(c->d_yec, ec.data(), sizeof(float4) * (ny + 1), cudaMemcpyHostToDevice));
@@ -825,6 +832,10 @@ tribo_status poisson_fast_setup(tribo_ctx* c) {
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_twist<kTwistC>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     TRIBO_CUDA(cudaFuncSetAttribute(k_ysolve_twist<kTwistC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     optin));
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_twist<kTwistC2, true, false, 2>),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    TRIBO_CUDA(cudaFuncSetAttribute((k_ysolve_twist<kTwistC2, false, false, 2>),
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     c->smem_optin = optin;
     return dispatch_attr<float>(nx, nz, optin);
 }

@@ -211,16 +211,24 @@ __device__ __forceinline__ float ds_diff_f(ds a, ds b) { return (a.hi - b.hi) + 
 #define TRIBO_TWIST_C 5
 #endif
 constexpr int kTwistC = TRIBO_TWIST_C;       // rows per chunk of the twisted solve
+#ifndef TRIBO_TWIST_C2
+#define TRIBO_TWIST_C2 8
+#endif
+constexpr int kTwistC2 = TRIBO_TWIST_C2;     // ... with two threads per pencil
 // shared memory of a twisted solve: E_y coefficients and couplings, ny + 1 each
 inline size_t ysolve_twist_smem(int ny) { return (sizeof(float4) + sizeof(float2)) * (size_t)(ny + 1); }
 
-template <int C, bool EY = true, bool kTab = false>
+// SPLIT = 1: one thread runs both halves of its pencil (many pencils); SPLIT = 2: two adjacent
+// threads run one half each and meet through warp shuffles (few pencils, where a thread's
+// instruction stream, not the number of warps, sets the time).
+template <int C, bool EY = true, bool kTab = false, int SPLIT = 1>
 __global__ void __launch_bounds__(128, 3) k_ysolve_twist(cplx<float>* __restrict__ S, cplx<float>* __restrict__ Fy,
-                                                      const float2* __restrict__ tinv,
-                                                      const float2* __restrict__ tcp,
-                                                      const float2* __restrict__ coup, const float4* __restrict__ ec,
-                                                      float4* __restrict__ ck, int ny, int nz, int nxh,
-                                                      const FastTab<float>* __restrict__ tab) {
+                                                         const float2* __restrict__ tinv,
+                                                         const float2* __restrict__ tcp,
+                                                         const float2* __restrict__ coup,
+                                                         const float4* __restrict__ ec, float4* __restrict__ ck,
+                                                         int ny, int nz, int nxh,
+                                                         const FastTab<float>* __restrict__ tab) {
     pdl_wait();
     if constexpr (kTab) {
         const FastTab<float>& t = tab[blockIdx.y];
@@ -240,8 +248,13 @@ __global__ void __launch_bounds__(128, 3) k_ysolve_twist(cplx<float>* __restrict
         se[j] = ec[j];
     }
     __syncthreads();
+    constexpr int NH = SPLIT == 2 ? 1 : 2;                            // halves per thread
     const int np = nz * nxh;
-    const int pencil = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int pencil = SPLIT == 2 ? gtid >> 1 : gtid;
+    const int h0 = SPLIT == 2 ? (gtid & 1) : 0;                        // this thread's first half
+    // the two threads of a pencil are both in or both out
+    const unsigned live = SPLIT == 2 ? __ballot_sync(0xffffffffu, pencil < np) : 0u;
     if (pencil >= np) return;
     const int ni = (nz / 2 + 1) * nxh;
     const int mz = pencil / nxh;
@@ -252,39 +265,57 @@ __global__ void __launch_bounds__(128, 3) k_ysolve_twist(cplx<float>* __restrict
     const int k = ny >> 1;
     const int hl[2] = {k, ny - 1 - k};            // rows of the top and the bottom half
     const int nch = (k + C - 1) / C;
-    // forward elimination of both halves, checkpoints at the end of each chunk but the last
-    ds p[2][2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};     // [half][re, im]
-    for (int c = 0; c < nch; ++c) {
-        float2 tv[2][C];
-        cplx<float> rv[2][C];
+    // forward elimination of the thread's halves, checkpoints at the end of each chunk but the last
+    ds p[NH][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+    for (int hh = 0; hh < NH; ++hh) p[hh][0] = p[hh][1] = ds{0.f, 0.f};
+    for (int c = 0; c < nch; ++c) {
+        float2 tv[NH][C];
+        cplx<float> rv[NH][C];
+#pragma unroll
+        for (int hh = 0; hh < NH; ++hh)
 #pragma unroll
             for (int i = 0; i < C; ++i) {
-                const int t = c * C + i;
+                const int h = h0 + hh, t = c * C + i;
                 if (t < hl[h]) {
                     const int j = h == 0 ? t : ny - 1 - t;
-                    tv[h][i] = tinv[(size_t)j * ni + item];
-                    rv[h][i] = srow[(size_t)j * nxh];
+                    tv[hh][i] = tinv[(size_t)j * ni + item];
+                    rv[hh][i] = srow[(size_t)j * nxh];
                 }
             }
 #pragma unroll
         for (int i = 0; i < C; ++i)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t = c * C + i;
+            for (int hh = 0; hh < NH; ++hh) {
+                const int h = h0 + hh, t = c * C + i;
                 if (t < hl[h]) {
                     const int j = h == 0 ? t : ny - 1 - t;
-                    const ds inv = {tv[h][i].x, tv[h][i].y};
+                    const ds inv = {tv[hh][i].x, tv[hh][i].y};
                     const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
-                    p[h][0] = ds_fms(inv, rv[h][i].re, at, p[h][0]);
-                    p[h][1] = ds_fms(inv, rv[h][i].im, at, p[h][1]);
+                    p[hh][0] = ds_fms(inv, rv[hh][i].re, at, p[hh][0]);
+                    p[hh][1] = ds_fms(inv, rv[hh][i].im, at, p[hh][1]);
                 }
             }
         if (c + 1 < nch)
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
-                ck[((size_t)c * 2 + h) * np + pencil] = make_float4(p[h][0].hi, p[h][0].lo, p[h][1].hi, p[h][1].lo);
+            for (int hh = 0; hh < NH; ++hh)
+                ck[((size_t)c * 2 + h0 + hh) * np + pencil] =
+                    make_float4(p[hh][0].hi, p[hh][0].lo, p[hh][1].hi, p[hh][1].lo);
+    }
+    // both halves' last forward values (the other thread's through a shuffle)
+    ds pa[2][2];
+    if constexpr (SPLIT == 2) {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            pa[h0][m] = p[0][m];
+            pa[1 - h0][m] = ds{__shfl_xor_sync(live, p[0][m].hi, 1), __shfl_xor_sync(live, p[0][m].lo, 1)};
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            pa[0][m] = p[0][m];
+            pa[1][m] = p[NH - 1][m];
+        }
     }
     // the middle row: x_k = (r_k - a_k d_k-1 - c_k e_k+1) / gamma_k (d, e zero for an empty half)
     const float2 tk = tinv[(size_t)k * ni + item];
@@ -293,9 +324,9 @@ __global__ void __launch_bounds__(128, 3) k_ysolve_twist(cplx<float>* __restrict
     const ds ga = ds_mul(ig, ds{sa[k].x, sa[k].y});
     const ds gc = ds_mul(ig, ds{sa[ny].x, sa[ny].y});
     ds xk[2];
-    xk[0] = ds_sub_mul(ds_fms(ig, rk.re, ga, p[0][0]), gc, p[1][0]);
-    xk[1] = ds_sub_mul(ds_fms(ig, rk.im, ga, p[0][1]), gc, p[1][1]);
-    srow[(size_t)k * nxh] = cplx<float>{ds_f(xk[0]), ds_f(xk[1])};
+    xk[0] = ds_sub_mul(ds_fms(ig, rk.re, ga, pa[0][0]), gc, pa[1][0]);
+    xk[1] = ds_sub_mul(ds_fms(ig, rk.im, ga, pa[0][1]), gc, pa[1][1]);
+    if (h0 == 0) srow[(size_t)k * nxh] = cplx<float>{ds_f(xk[0]), ds_f(xk[1])};
     // each half's row next to k (x_k-1, x_k+1): the start of the other half's E_y differences
     ds xn[2][2];
 #pragma unroll
@@ -306,107 +337,109 @@ __global__ void __launch_bounds__(128, 3) k_ysolve_twist(cplx<float>* __restrict
             const int j = h == 0 ? k - 1 : k + 1;
             const float2 cv = tcp[(size_t)j * ni + item];
             const ds cp = {cv.x, cv.y};
-            xn[h][0] = ds_sub_mul(p[h][0], cp, xk[0]);
-            xn[h][1] = ds_sub_mul(p[h][1], cp, xk[1]);
+            xn[h][0] = ds_sub_mul(pa[h][0], cp, xk[0]);
+            xn[h][1] = ds_sub_mul(pa[h][1], cp, xk[1]);
         }
     }
-    ds x1[2][2];                    // x at local index t + 1
-    float dn[2][2];                 // x(t + 2) - x(t + 1)
+    ds x1[NH][2];                   // x at local index t + 1
+    float dn[NH][2];                // x(t + 2) - x(t + 1)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        x1[h][0] = xk[0];
-        x1[h][1] = xk[1];
+    for (int hh = 0; hh < NH; ++hh) {
+        const int h = h0 + hh;
+        x1[hh][0] = xk[0];
+        x1[hh][1] = xk[1];
         const bool other = hl[1 - h] > 0;
-        dn[h][0] = other ? ds_diff_f(xn[1 - h][0], xk[0]) : 0.f;
-        dn[h][1] = other ? ds_diff_f(xn[1 - h][1], xk[1]) : 0.f;
+        dn[hh][0] = other ? ds_diff_f(xn[1 - h][0], xk[0]) : 0.f;
+        dn[hh][1] = other ? ds_diff_f(xn[1 - h][1], xk[1]) : 0.f;
     }
     // substitution, chunks from the middle outwards, each recomputed from its checkpoint
     for (int c = nch - 1; c >= 0; --c) {
-        ds q[2][2];
+        ds q[NH][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int hh = 0; hh < NH; ++hh) {
             if (c > 0) {
-                const float4 v = ck[((size_t)(c - 1) * 2 + h) * np + pencil];
-                q[h][0] = ds{v.x, v.y};
-                q[h][1] = ds{v.z, v.w};
+                const float4 v = ck[((size_t)(c - 1) * 2 + h0 + hh) * np + pencil];
+                q[hh][0] = ds{v.x, v.y};
+                q[hh][1] = ds{v.z, v.w};
             } else {
-                q[h][0] = ds{0.f, 0.f};
-                q[h][1] = ds{0.f, 0.f};
+                q[hh][0] = ds{0.f, 0.f};
+                q[hh][1] = ds{0.f, 0.f};
             }
         }
-        float2 tv[2][C], cv[2][C];
-        cplx<float> rv[2][C];
+        float2 tv[NH][C], cv[NH][C];
+        cplx<float> rv[NH][C];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int hh = 0; hh < NH; ++hh)
 #pragma unroll
             for (int i = 0; i < C; ++i) {
-                const int t = c * C + i;
+                const int h = h0 + hh, t = c * C + i;
                 if (t < hl[h]) {
                     const int j = h == 0 ? t : ny - 1 - t;
-                    tv[h][i] = tinv[(size_t)j * ni + item];
-                    cv[h][i] = tcp[(size_t)j * ni + item];
-                    rv[h][i] = srow[(size_t)j * nxh];
+                    tv[hh][i] = tinv[(size_t)j * ni + item];
+                    cv[hh][i] = tcp[(size_t)j * ni + item];
+                    rv[hh][i] = srow[(size_t)j * nxh];
                 }
             }
-        ds dr[2][C], di[2][C];
+        ds dr[NH][C], di[NH][C];
 #pragma unroll
         for (int i = 0; i < C; ++i)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t = c * C + i;
+            for (int hh = 0; hh < NH; ++hh) {
+                const int h = h0 + hh, t = c * C + i;
                 if (t < hl[h]) {
                     const int j = h == 0 ? t : ny - 1 - t;
-                    const ds inv = {tv[h][i].x, tv[h][i].y};
+                    const ds inv = {tv[hh][i].x, tv[hh][i].y};
                     const ds at = ds_mul(ds{sa[j].x, sa[j].y}, inv);
-                    q[h][0] = ds_fms(inv, rv[h][i].re, at, q[h][0]);
-                    q[h][1] = ds_fms(inv, rv[h][i].im, at, q[h][1]);
-                    dr[h][i] = q[h][0];
-                    di[h][i] = q[h][1];
+                    q[hh][0] = ds_fms(inv, rv[hh][i].re, at, q[hh][0]);
+                    q[hh][1] = ds_fms(inv, rv[hh][i].im, at, q[hh][1]);
+                    dr[hh][i] = q[hh][0];
+                    di[hh][i] = q[hh][1];
                 }
             }
 #pragma unroll
         for (int i = C - 1; i >= 0; --i)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t = c * C + i;
+            for (int hh = 0; hh < NH; ++hh) {
+                const int h = h0 + hh, t = c * C + i;
                 if (t < hl[h]) {
                     const int j = h == 0 ? t : ny - 1 - t;
-                    const ds cp = {cv[h][i].x, cv[h][i].y};
-                    const ds xr = ds_sub_mul(dr[h][i], cp, x1[h][0]);
-                    const ds xi = ds_sub_mul(di[h][i], cp, x1[h][1]);
+                    const ds cp = {cv[hh][i].x, cv[hh][i].y};
+                    const ds xr = ds_sub_mul(dr[hh][i], cp, x1[hh][0]);
+                    const ds xi = ds_sub_mul(di[hh][i], cp, x1[hh][1]);
                     srow[(size_t)j * nxh] = cplx<float>{ds_f(xr), ds_f(xi)};
-                    const float d0r = ds_diff_f(x1[h][0], xr), d0i = ds_diff_f(x1[h][1], xi);
+                    const float d0r = ds_diff_f(x1[hh][0], xr), d0i = ds_diff_f(x1[hh][1], xi);
                     // E_y of the cell at local index t + 1 (the bottom half leaves cell k to the top)
                     if (EY && (h == 0 || t + 1 < hl[1])) {
                         const int jc = h == 0 ? t + 1 : ny - 2 - t;
                         const float4 cf = se[jc];
                         const float bm = h == 0 ? cf.y : -cf.z, bp = h == 0 ? cf.z : -cf.y;
                         frow[(size_t)(jc + 1) * nxh] = cplx<float>{
-                            cf.x * ds_f(x1[h][0]) + bm * d0r + bp * dn[h][0],
-                            cf.x * ds_f(x1[h][1]) + bm * d0i + bp * dn[h][1]};
+                            cf.x * ds_f(x1[hh][0]) + bm * d0r + bp * dn[hh][0],
+                            cf.x * ds_f(x1[hh][1]) + bm * d0i + bp * dn[hh][1]};
                     }
-                    dn[h][0] = d0r;
-                    dn[h][1] = d0i;
-                    x1[h][0] = xr;
-                    x1[h][1] = xi;
+                    dn[hh][0] = d0r;
+                    dn[hh][1] = d0i;
+                    x1[hh][0] = xr;
+                    x1[hh][1] = xi;
                 }
             }
     }
     if (!EY) return;
     const float4 walls = se[ny];
-    {   // top: cell 0 (node 1) and the wall node 0
-        const float4 cf = se[0];
-        const float xr = ds_f(x1[0][0]), xi = ds_f(x1[0][1]);
-        frow[(size_t)1 * nxh] = cplx<float>{cf.x * xr + cf.z * dn[0][0], cf.x * xi + cf.z * dn[0][1]};
-        frow[0] = cplx<float>{walls.x * xr, walls.x * xi};
-    }
-    {   // bottom: cell ny-1 (node ny) unless it is cell k, and the wall node ny+1
-        const float xr = ds_f(x1[1][0]), xi = ds_f(x1[1][1]);
-        if (hl[1] > 0) {
-            const float4 cf = se[ny - 1];
-            frow[(size_t)ny * nxh] = cplx<float>{cf.x * xr - cf.y * dn[1][0], cf.x * xi - cf.y * dn[1][1]};
+#pragma unroll
+    for (int hh = 0; hh < NH; ++hh) {
+        const float xr = ds_f(x1[hh][0]), xi = ds_f(x1[hh][1]);
+        if (h0 + hh == 0) {         // top: cell 0 (node 1) and the wall node 0
+            const float4 cf = se[0];
+            frow[(size_t)1 * nxh] = cplx<float>{cf.x * xr + cf.z * dn[hh][0], cf.x * xi + cf.z * dn[hh][1]};
+            frow[0] = cplx<float>{walls.x * xr, walls.x * xi};
+        } else {                    // bottom: cell ny-1 (node ny) unless it is cell k, and the wall node ny+1
+            if (hl[1] > 0) {
+                const float4 cf = se[ny - 1];
+                frow[(size_t)ny * nxh] = cplx<float>{cf.x * xr - cf.y * dn[hh][0], cf.x * xi - cf.y * dn[hh][1]};
+            }
+            frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * xr, walls.y * xi};
         }
-        frow[(size_t)(ny + 1) * nxh] = cplx<float>{walls.y * xr, walls.y * xi};
     }
 }
 
