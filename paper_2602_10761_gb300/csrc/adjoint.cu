@@ -101,6 +101,7 @@ __device__ __forceinline__ ImpactGrad impact_grad(const StepArgs<R>& a, double k
 
 template <class R>
 __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs<R> g) {
+    pdl_wait();
     double pU = 0.0, pK = 0.0;
     unsigned int err = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_adj_step(StepArgs<R> a, AdjArgs
 template <class R>
 __global__ void k_adj_grad(const R* __restrict__ Eb, const R* __restrict__ cy, R* __restrict__ out,
                            int nx, int ny, int nz, R cx, R cz) {
+    pdl_wait();
     const size_t nodes = (size_t)nz * (ny + 2) * nx;
     const R* Ey = Eb + nodes;
     const R* Ez = Eb + 2 * nodes;
@@ -380,6 +382,7 @@ __global__ void k_adj_grad(const R* __restrict__ Eb, const R* __restrict__ cy, R
 template <class R>
 __global__ void k_adj_deposit(StepArgs<R> a, SView<R> s, int64_t n, const double* __restrict__ Qb,
                               double* __restrict__ qb) {
+    pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
         R y = s.y[p];
@@ -624,17 +627,18 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             phase_begin(c, PH_ADJOINT);
             // one resident wave (two blocks per SM), as for the forward step
             const int ab = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)c->num_sms * 2);
-            k_adj_step<R><<<ab, kThreads, 0, c->stream>>>(a, ga);
+            (void)launch_pdl(k_adj_step<R>, dim3(ab), dim3(kThreads), 0, c->stream, a, ga);
             TRIBO_LAUNCHED(c);
             if (!electro) continue;
             const int gb = (int)std::min<int64_t>((int64_t)c->nz * c->ny, (int64_t)c->num_sms * 16);
             phase_begin(c, PH_ADJOINT);
-            k_adj_grad<R><<<gb, 128, 0, c->stream>>>(L.Eb, L.cy, (R*)c->Q, c->nx, c->ny, c->nz,
-                                                     (R)(0.5 / c->dx), (R)(0.5 / c->dz));
+            (void)launch_pdl(k_adj_grad<R>, dim3(gb), dim3(128), 0, c->stream, (const R*)L.Eb, (const R*)L.cy,
+                             (R*)c->Q, c->nx, c->ny, c->nz, (R)(0.5 / c->dx), (R)(0.5 / c->dz));
             TRIBO_LAUNCHED(c);
             if ((st = poisson_solve(c, c->Q, false, c->d_scale_q, true, L.psi, nullptr))) return st;
             phase_begin(c, PH_ADJOINT);
-            k_adj_deposit<R><<<grid_for(n), kThreads, 0, c->stream>>>(a, L.seg[i], n, L.psi, L.lam.q);
+            (void)launch_pdl(k_adj_deposit<R>, dim3(grid_for(n)), dim3(kThreads), 0, c->stream, a, L.seg[i], n,
+                             (const double*)L.psi, L.lam.q);
             TRIBO_LAUNCHED(c);
         }
     }
