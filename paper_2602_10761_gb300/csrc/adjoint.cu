@@ -381,7 +381,7 @@ __global__ void k_adj_grad(const R* __restrict__ Eb, const R* __restrict__ cy, R
 // q-bar_p += Q-bar[cell of x_p]
 template <class R>
 __global__ void k_adj_deposit(StepArgs<R> a, SView<R> s, int64_t n, const double* __restrict__ Qb,
-                              double* __restrict__ qb) {
+                              double* __restrict__ qb, uint2* __restrict__ eb, int64_t eb_words) {
     pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
@@ -391,6 +391,10 @@ __global__ void k_adj_deposit(StepArgs<R> a, SView<R> s, int64_t n, const double
         const uint32_t key = cell_key<R>(s.x[p], y, s.z[p], a, &j);
         qb[p] += Qb[key];
     }
+    // the field adjoint this step scattered has been consumed (k_adj_grad): zero it for the
+    // next step's scatter (in place of a separate memset)
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < eb_words; w += stride)
+        eb[w] = make_uint2(0u, 0u);
 }
 
 }  // namespace
@@ -467,12 +471,22 @@ size_t layout(AdjLayout<R>& L, char* base, int64_t n, int nseg, int C, bool elec
 }
 
 template <class R>
+__global__ void k_copy_state(SView<R> dst, SView<R> src, int64_t n) {
+    pdl_wait();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        dst.x[i] = src.x[i]; dst.y[i] = src.y[i]; dst.z[i] = src.z[i];
+        dst.vx[i] = src.vx[i]; dst.vy[i] = src.vy[i]; dst.vz[i] = src.vz[i];
+        dst.q[i] = src.q[i];
+    }
+}
+
+// the stored state of a step (positions, velocities, charges) in one launch
+template <class R>
 tribo_status copy_state(tribo_ctx* c, const SView<R>& dst, const SView<R>& src, int64_t n) {
-    R* d[6] = {dst.x, dst.y, dst.z, dst.vx, dst.vy, dst.vz};
-    const R* s[6] = {src.x, src.y, src.z, src.vx, src.vy, src.vz};
-    for (int k = 0; k < 6; ++k)
-        TRIBO_CUDA(cudaMemcpyAsync(d[k], s[k], n * sizeof(R), cudaMemcpyDeviceToDevice, c->stream));
-    TRIBO_CUDA(cudaMemcpyAsync(dst.q, src.q, n * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (n == 0) return TRIBO_OK;
+    (void)launch_pdl(k_copy_state<R>, dim3(grid_for(n)), dim3(kThreads), 0, c->stream, dst, src, n);
+    TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }
 
@@ -588,6 +602,9 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
     phase_begin(c, PH_ADJOINT);
     k_fill_adjoint_start<<<grid_for(n), kThreads, 0, c->stream>>>(L.lam.q, n, 1.0 / (double)n);
     TRIBO_LAUNCHED(c);
+    // the field adjoint starts zero; each step's k_adj_deposit leaves it zero again
+    const size_t eb_bytes = eb_reals<R>() * nodes * sizeof(R);
+    if (electro) TRIBO_CUDA(cudaMemsetAsync(L.Eb, 0, eb_bytes, c->stream));
     PView Wp{};
     Wp.n = n;
     Wp.x = L.W.x; Wp.y = L.W.y; Wp.z = L.W.z; Wp.vx = L.W.vx; Wp.vy = L.W.vy; Wp.vz = L.W.vz;
@@ -619,10 +636,7 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
         for (int i = len - 1; i >= 0; --i) {
             if (c->n_modes && i < len - 1 && (st = modes_eval(c, t_start + (s0 + i) * dt, c->u_lat))) return st;
             StepArgs<R> a = make_args<R>(c, dt);
-            if (electro) {
-                a.E = segE(i);
-                TRIBO_CUDA(cudaMemsetAsync(L.Eb, 0, eb_reals<R>() * nodes * sizeof(R), c->stream));
-            }
+            if (electro) a.E = segE(i);
             AdjArgs<R> ga{L.seg[i], (const R*)P.d, L.lam, db, L.Eb, L.pacc, n, c->P.kappa_A};
             phase_begin(c, PH_ADJOINT);
             // one resident wave (two blocks per SM), as for the forward step
@@ -638,7 +652,8 @@ tribo_status adjoint_impl(tribo_ctx* c, const PView& P, double dt, int nsteps, i
             if ((st = poisson_solve(c, c->Q, false, c->d_scale_q, true, L.psi, nullptr))) return st;
             phase_begin(c, PH_ADJOINT);
             (void)launch_pdl(k_adj_deposit<R>, dim3(grid_for(n)), dim3(kThreads), 0, c->stream, a, L.seg[i], n,
-                             (const double*)L.psi, L.lam.q);
+                             (const double*)L.psi, L.lam.q, reinterpret_cast<uint2*>(L.Eb),
+                             (int64_t)(eb_bytes / sizeof(uint2)));
             TRIBO_LAUNCHED(c);
         }
     }
