@@ -127,6 +127,27 @@ __device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a
     return ((uint32_t)k * (uint32_t)a.ny + (uint32_t)j) * (uint32_t)a.nx + (uint32_t)i;
 }
 
+// cell key with a guess for the y row: the guess is taken when y lies in its row (the row a
+// particle started the step in, which it mostly still occupies), else the row is searched; the
+// result equals cell_key's
+template <class R>
+__device__ __forceinline__ uint32_t cell_key_near(R x, R y, R z, const StepArgs<R>& a, int jg, int* jout) {
+    int i, k;
+    if constexpr (sizeof(R) == 8) {
+        i = cell_uniform((double)x, a.dx, a.nx, a.xf_up, 0.0);
+        k = cell_uniform((double)z, a.dz, a.nz, a.zf_up, 0.0);
+    } else {
+        i = cell_uniform((float)x, (float)a.inv_dx, a.nx, a.xf_up);
+        k = cell_uniform((float)z, (float)a.inv_dz, a.nz, a.zf_up);
+    }
+    bool in;
+    if constexpr (sizeof(R) == 8) in = (double)y >= a.yf[jg] && (double)y < a.yf[jg + 1];
+    else in = (float)y >= a.yf_up[jg] && (float)y < a.yf_up[jg + 1];
+    const int j = in ? jg : cell_y(y, a);
+    *jout = j;
+    return ((uint32_t)k * (uint32_t)a.ny + (uint32_t)j) * (uint32_t)a.nx + (uint32_t)i;
+}
+
 // corners and weights of the trilinear gather at (x, y, z) given the cell j:
 // corner c has z bit 2, y bit 1, x bit 0; weights are linear in the physical
 // coordinates (wx, wy, wz are the upper-node fractions)
@@ -480,7 +501,7 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     X[n] = xn; Y[n] = yn; Z[n] = zn;
     VX[n] = vxn; VY[n] = vyn; VZ[n] = vzn;
     int jn;
-    const uint32_t key = cell_key<R>(xn, yn, zn, a, &jn);
+    const uint32_t key = cell_key_near<R>(xn, yn, zn, a, j, &jn);
     if (a.Q) atomicAdd(&a.Q[key], q);
     if (write_cell) p.cell[n] = key;
     if (use_hist) atomicAdd(&sh_hist[jn], 1u);
