@@ -37,6 +37,8 @@ struct StepArgs {
     int ybins;
     R ybin_scale;                  // ybins / ly
     const R* Yr;                   // ny+2 lattice nodes
+    const float4* yrow;            // FP32: per cell row j two float4, (yf_up[j], yf_up[j+1], Y[j], Y[j+1])
+                                   // and (1/(Y[j+1]-Y[j]), 1/(Y[j+2]-Y[j+1]), 0, 0); NULL in FP64
     const R* invdY;                // ny+1 inverse node spacings
     const R* u;                    // planes u_x, u_y, u_z, each `nodes` long
     const R* E;                    // planes E_x, E_y, E_z, each `nodes` long
@@ -112,6 +114,23 @@ __device__ __forceinline__ int cell_y(R y, const StepArgs<R>& a) {
     return j;
 }
 
+// the y row of a cell with the row's faces, nodes and node spacings in two 16-byte loads
+struct YRow {
+    float4 f;                      // yf_up[j], yf_up[j+1], Y[j], Y[j+1]
+    float4 g;                      // 1/(Y[j+1]-Y[j]), 1/(Y[j+2]-Y[j+1])
+};
+// FP32 row search on the row table: the same j as cell_y
+__device__ __forceinline__ int cell_y_row(float y, const StepArgs<float>& a, YRow& r) {
+    int b = (int)(y * a.ybin_scale);
+    b = min(max(b, 0), a.ybins - 1);
+    int j = a.ybin[b];
+    r.f = a.yrow[2 * j];
+    while (j > 0 && y < r.f.x) r.f = a.yrow[2 * --j];
+    while (j < a.ny - 1 && y >= r.f.y) r.f = a.yrow[2 * ++j];
+    r.g = a.yrow[2 * j + 1];
+    return j;
+}
+
 template <class R>
 __device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a, int* jout) {
     int i, k;
@@ -131,7 +150,8 @@ __device__ __forceinline__ uint32_t cell_key(R x, R y, R z, const StepArgs<R>& a
 // particle started the step in, which it mostly still occupies), else the row is searched; the
 // result equals cell_key's
 template <class R>
-__device__ __forceinline__ uint32_t cell_key_near(R x, R y, R z, const StepArgs<R>& a, int jg, int* jout) {
+__device__ __forceinline__ uint32_t cell_key_near(R x, R y, R z, const StepArgs<R>& a, int jg, int* jout,
+                                                  const YRow* rg = nullptr) {
     int i, k;
     if constexpr (sizeof(R) == 8) {
         i = cell_uniform((double)x, a.dx, a.nx, a.xf_up, 0.0);
@@ -142,6 +162,7 @@ __device__ __forceinline__ uint32_t cell_key_near(R x, R y, R z, const StepArgs<
     }
     bool in;
     if constexpr (sizeof(R) == 8) in = (double)y >= a.yf[jg] && (double)y < a.yf[jg + 1];
+    else if (rg) in = (float)y >= rg->f.x && (float)y < rg->f.y;
     else in = (float)y >= a.yf_up[jg] && (float)y < a.yf_up[jg + 1];
     const int j = in ? jg : cell_y(y, a);
     *jout = j;
@@ -161,7 +182,7 @@ struct Corners {
 
 template <class R>
 __device__ __forceinline__ void corners(const StepArgs<R>& a, R x, R y, R z, int j, Corners<R>& cr,
-                                        unsigned int* err) {
+                                        unsigned int* err, const YRow* yr = nullptr) {
     R sx = x * a.inv_dx - (R)0.5;
     R fx = rfloor(sx);
     R wx = sx - fx;
@@ -178,9 +199,18 @@ __device__ __forceinline__ void corners(const StepArgs<R>& a, R x, R y, R z, int
     if (i1 >= a.nx) i1 -= a.nx;
     if (k0 < 0) k0 += a.nz;
     if (k1 >= a.nz) k1 -= a.nz;
-    const int jn0 = (y >= a.Yr[j + 1]) ? j + 1 : j;
-    cr.inv_dy = a.invdY[jn0];
-    const R wy = (y - a.Yr[jn0]) * cr.inv_dy;
+    int jn0;
+    R wy;
+    if (sizeof(R) == 4 && yr) {
+        const bool up = y >= (R)yr->f.w;
+        jn0 = up ? j + 1 : j;
+        cr.inv_dy = (R)(up ? yr->g.y : yr->g.x);
+        wy = (y - (R)(up ? yr->f.w : yr->f.z)) * cr.inv_dy;
+    } else {
+        jn0 = (y >= a.Yr[j + 1]) ? j + 1 : j;
+        cr.inv_dy = a.invdY[jn0];
+        wy = (y - a.Yr[jn0]) * cr.inv_dy;
+    }
     const R wx0 = (R)1 - wx, wy0 = (R)1 - wy, wz0 = (R)1 - wz;
     const uint32_t r00 = ((uint32_t)k0 * (uint32_t)a.nyn + (uint32_t)jn0) * (uint32_t)a.nx;
     const uint32_t r01 = r00 + (uint32_t)a.nx;
@@ -196,9 +226,9 @@ __device__ __forceinline__ void corners(const StepArgs<R>& a, R x, R y, R z, int
 // trilinear gather of the gas velocity (and the field) at (x, y, z), cell j
 template <class R>
 __device__ __forceinline__ void gather(const StepArgs<R>& a, R x, R y, R z, int j, R uf[3], R Ef[3],
-                                       bool withE, unsigned int* err) {
+                                       bool withE, unsigned int* err, const YRow* yr = nullptr) {
     Corners<R> cr;
-    corners<R>(a, x, y, z, j, cr, err);
+    corners<R>(a, x, y, z, j, cr, err, yr);
     R u0 = 0, u1 = 0, u2 = 0, e0 = 0, e1 = 0, e2 = 0;
     // one base pointer per plane: each load is base + 32-bit index
     const R* __restrict__ U0 = a.u;
@@ -340,6 +370,7 @@ StepArgs<R> make_args(tribo_ctx* c, double dt) {
     a.yf = c->d_yf; a.yf_up = c->d_yf_up; a.xf_up = c->d_xf_up; a.zf_up = c->d_zf_up;
     a.ybin = c->d_ybin; a.ybins = c->ybins; a.ybin_scale = (R)((double)c->ybins / c->ly);
     a.Yr = (const R*)c->d_Yr; a.invdY = (const R*)c->d_invdY;
+    a.yrow = sizeof(R) == 4 ? (const float4*)c->d_yrow : nullptr;
     a.u = (const R*)c->u_lat; a.E = (const R*)c->E_lat;
     a.nodes = (size_t)c->nz * (c->ny + 2) * c->nx;
     a.Q = nullptr; a.hist = nullptr; a.acc = c->d_acc;
@@ -397,9 +428,17 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     double q = p.q[n];
     if (!(y >= (R)0 && y <= a.ly)) { err |= TRIBO_DEV_OUTSIDE; y = a.ly * (R)0.5; }
     int j;
-    (void)cell_key<R>(x, y, z, a, &j);
+    YRow yr;                        // FP32: the start row's faces, nodes and spacings
+    bool rows = false;
+    if constexpr (sizeof(R) == 4) {
+        rows = a.yrow != nullptr;
+        if (rows) j = cell_y_row(y, a, yr);
+        else (void)cell_key<R>(x, y, z, a, &j);
+    } else {
+        (void)cell_key<R>(x, y, z, a, &j);
+    }
     R uf[3], Ef[3];
-    gather<R>(a, x, y, z, j, uf, Ef, a.electro != 0, &err);
+    gather<R>(a, x, y, z, j, uf, Ef, a.electro != 0, &err, rows ? &yr : nullptr);
     // acceleration q E / m
     R ax = 0, ay = 0, az = 0;
     if (a.electro) {
@@ -501,7 +540,7 @@ __device__ __forceinline__ void step_one(const StepArgs<R>& a, const PView& p, i
     X[n] = xn; Y[n] = yn; Z[n] = zn;
     VX[n] = vxn; VY[n] = vyn; VZ[n] = vzn;
     int jn;
-    const uint32_t key = cell_key_near<R>(xn, yn, zn, a, j, &jn);
+    const uint32_t key = cell_key_near<R>(xn, yn, zn, a, j, &jn, rows ? &yr : nullptr);
     if (a.Q) atomicAdd(&a.Q[key], q);
     if (write_cell) p.cell[n] = key;
     if (use_hist) atomicAdd(&sh_hist[jn], 1u);

@@ -141,6 +141,15 @@ tribo_status build_tables(tribo_ctx* c) {
         TRIBO_CUDA(cudaMemcpy(c->d_Yr, Yf.data(), rs * (ny + 2), cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMemcpy(c->d_invdY, invf.data(), rs * (ny + 1), cudaMemcpyHostToDevice));
         TRIBO_CUDA(cudaMemcpy(c->d_inv_vol, ivf.data(), rs * ny, cudaMemcpyHostToDevice));
+        // per cell row, the values the particle step's row search and y weights use, from the
+        // same rounded tables
+        std::vector<float4> rows(2 * (size_t)ny);
+        for (int j = 0; j < ny; ++j) {
+            rows[2 * j] = make_float4(yfu[j], yfu[j + 1], Yf[j], Yf[j + 1]);
+            rows[2 * j + 1] = make_float4(invf[j], invf[j + 1], 0.f, 0.f);
+        }
+        TRIBO_CUDA(cudaMalloc(&c->d_yrow, sizeof(float4) * rows.size()));
+        TRIBO_CUDA(cudaMemcpy(c->d_yrow, rows.data(), sizeof(float4) * rows.size(), cudaMemcpyHostToDevice));
     }
     return TRIBO_OK;
 }
@@ -387,7 +396,7 @@ void free_ctx(tribo_ctx* c) {
     poisson_free(c);
     modes_free(c);
     void* ptrs[] = {c->d_yf, c->d_Y, c->d_scale_q, c->d_scale_rho, c->d_yf_up, c->d_xf_up, c->d_zf_up,
-                    c->d_ybin, c->d_Yr, c->d_invdY, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
+                    c->d_ybin, c->d_Yr, c->d_invdY, c->d_yrow, c->u_lat, c->E_lat, c->Q, c->stage, c->d_acc,
                     c->d_hist, c->d_scalar, c->alt, c->sort_counts, c->sort_key, c->sort_rank, c->sort_perm,
                     c->sort_tiles, c->adj, c->nf_members, c->nf_acc, c->pp_partner, c->d_inv_vol,
                     c->adj_E, c->n_imp0, c->patch};

@@ -110,6 +110,7 @@ struct tribo_ctx {
     int ybins = 0;
     void* d_Yr = nullptr;        // ny+2 lattice nodes in real precision
     void* d_invdY = nullptr;     // ny+1 inverse node spacings in real precision
+    void* d_yrow = nullptr;      // mixed mode: per cell row two float4 (faces, nodes, spacings)
     double* d_ycoef = nullptr;   // 3*ny: a, b, c of the y FV operator
     double* d_lamx = nullptr;    // nx modified wavenumbers
     double* d_lamz = nullptr;    // nz
