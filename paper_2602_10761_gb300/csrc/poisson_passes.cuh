@@ -113,17 +113,22 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT*
         using V2 = std::conditional_t<sizeof(QT) == 8, double2, float2>;   // (x_2n, x_2n+1)
         V2* row = reinterpret_cast<V2*>(src) + (size_t)line * M;
         cplx<R> y[N1];
+        unsigned nz_mask = 0;        // which element pairs hold a nonzero sum
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
             const V2 v = row[N2 * n1 + r];
+            nz_mask |= (v.x != (QT)0 || v.y != (QT)0) ? 1u << n1 : 0u;
             y[n1] = cplx<R>{from_f64<R>(v.x) * s, from_f64<R>(v.y) * s};
         }
         if (zero_src) {
+            // most cells hold no particle: only pairs with a nonzero sum are rewritten, so the
+            // sectors of empty cells stay clean in L2 and are never written back
             V2 zero;
             zero.x = (QT)0;
             zero.y = (QT)0;
 #pragma unroll
-            for (int n1 = 0; n1 < N1; ++n1) row[N2 * n1 + r] = zero;
+            for (int n1 = 0; n1 < N1; ++n1)
+                if (nz_mask & (1u << n1)) row[N2 * n1 + r] = zero;
         }
         fft::reg_dft<R, -1, N1, 2 * N2>(y, tw);
         // W_M^(r k1) from the thread-ordered copy after the table (consecutive in r)
