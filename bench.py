@@ -303,10 +303,15 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
     adj64_p = (dd64 * d64)[sel]
     adj32_p = (dd * d32)[sel]
 
-    def per_particle_fd(hh):
+    def per_particle_fd(hh, fd_other=None):
         (qp, ip), (qm, im) = q64_of(+1, hh), q64_of(-1, hh)
         fd_p = (qp[sel] - qm[sel]) / (2 * hh * n)
         keep = (ip[sel] == im[sel]) & (dd64[sel] != 0)
+        smooth = None
+        if fd_other is not None:
+            # the map is smooth at a particle where the differences at two steps h agree
+            # (a jump between -h and +h makes the difference quotient scale with 1/h)
+            smooth = keep & (np.abs(fd_p - fd_other) <= 1e-3 * np.abs(fd_other))
         r64 = np.abs(fd_p - adj64_p)[keep] / np.abs(adj64_p)[keep]
         r32 = np.abs(fd_p - adj32_p)[keep] / np.abs(fd_p)[keep].clip(1e-300)
         q_ = lambda r, x: float(np.percentile(r, x)) if r.size else None
@@ -317,7 +322,13 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
                                          "frac_within_1e-3": float((r64 <= 1e-3).mean()) if r64.size else None},
                 "mixed_adjoint_rel_err": {"median": q_(r32, 50), "p90": q_(r32, 90), "p99": q_(r32, 99),
                                           "frac_within_1e-3": float((r32 <= 1e-3).mean()) if r32.size else None},
-                "sum_rel_err_fp64": rel(float(adj64_p[keep].sum()), float(fd_p[keep].sum())) if keep.any() else None}
+                "sum_rel_err_fp64": rel(float(adj64_p[keep].sum()), float(fd_p[keep].sum())) if keep.any() else None,
+                **({} if smooth is None else {
+                    "smooth_particles": int(smooth.sum()),
+                    "sum_rel_err_fp64_smooth": rel(float(adj64_p[smooth].sum()), float(fd_p[smooth].sum()))
+                    if smooth.any() else None,
+                    "sum_rel_err_mixed_smooth": rel(float(adj32_p[smooth].sum()), float(fd_p[smooth].sum()))
+                    if smooth.any() else None}), "_fd": fd_p}
 
     fd_particles = {
         "note": ("FP64 GPU path, the diameters of the particles that hit a wall changed by +-h; each such "
@@ -325,7 +336,12 @@ def adjoint_report(T, torch, steps=None, ckpt=50, h=1e-4):
                  "impact count at +h and -h).  The few that differ by O(1) cross a cell face or change the "
                  "step of an impact between -h and +h (a jump of the map, not of its derivative); their "
                  "share falls with h"),
-        "h_1e-4": per_particle_fd(h), "h_1e-6": per_particle_fd(1e-6)}
+        "smooth": ("h_1e-6 also sums over the particles whose differences at h = 1e-4 and 1e-6 agree "
+                   "to 1e-3 (no jump of the map between -h and +h at either step)")}
+    fd_particles["h_1e-4"] = per_particle_fd(h)
+    fd_particles["h_1e-6"] = per_particle_fd(1e-6, fd_other=fd_particles["h_1e-4"]["_fd"])
+    for k_ in ("h_1e-4", "h_1e-6"):
+        del fd_particles[k_]["_fd"]
     fp64.close()
     match = fin32["n_imp"] == fin64["n_imp"]
     return {
