@@ -174,6 +174,78 @@ __global__ void k_sort_gather(PView src, PView dst, const uint32_t* __restrict__
     }
 }
 
+// Four sorted slots per thread: one 16-byte load of their sources, every array's four gathers
+// issued before any store, then one 16-byte store per array (two for 8-byte elements); the
+// destination arrays must be 16-byte aligned (the scalar gather above otherwise).  Block 0
+// copies the last n % 4 slots one by one.
+template <class T>
+struct Four {
+    T v[4];
+};
+template <class T>
+__device__ __forceinline__ Four<T> gather4(const void* src, const uint32_t n[4]) {
+    const T* sp = static_cast<const T*>(src);
+    return Four<T>{{sp[n[0]], sp[n[1]], sp[n[2]], sp[n[3]]}};
+}
+template <class T>
+__device__ __forceinline__ void store4(void* dst, int64_t t, const Four<T>& f) {
+    uint4* dp = static_cast<uint4*>(dst) + t * (int64_t)(sizeof(T) / 4);
+    uint4 w[sizeof(T) / 4];
+    memcpy(w, f.v, sizeof(f.v));
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) dp[i] = w[i];
+}
+
+template <class R>
+__global__ void k_sort_gather4(PView src, PView dst, const uint32_t* __restrict__ perm) {
+    const int64_t n4 = src.n / 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += stride) {
+        const uint4 pn = reinterpret_cast<const uint4*>(perm)[t];
+        const uint32_t n[4] = {pn.x, pn.y, pn.z, pn.w};
+        const Four<R> x = gather4<R>(src.x, n), y = gather4<R>(src.y, n), z = gather4<R>(src.z, n);
+        const Four<R> vx = gather4<R>(src.vx, n), vy = gather4<R>(src.vy, n), vz = gather4<R>(src.vz, n);
+        const Four<R> d = gather4<R>(src.d, n);
+        const Four<double> q = gather4<double>(src.q, n), qw = gather4<double>(src.q_wall, n);
+        const Four<uint32_t> ni = gather4<uint32_t>(src.n_imp, n);
+        Four<uint32_t> id{};
+        Four<double> site{};
+        if (src.id) id = gather4<uint32_t>(src.id, n);
+        if (src.site) site = gather4<double>(src.site, n);
+        store4(dst.x, t, x); store4(dst.y, t, y); store4(dst.z, t, z);
+        store4(dst.vx, t, vx); store4(dst.vy, t, vy); store4(dst.vz, t, vz);
+        store4(dst.d, t, d);
+        store4(dst.q, t, q); store4(dst.q_wall, t, qw); store4(dst.n_imp, t, ni);
+        if (src.id) store4(dst.id, t, id);
+        if (src.site) store4(dst.site, t, site);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (unsigned)(src.n - 4 * n4)) {
+        const int64_t dd = 4 * n4 + threadIdx.x;
+        const uint32_t n = perm[dd];
+        ((R*)dst.x)[dd] = ((const R*)src.x)[n];
+        ((R*)dst.y)[dd] = ((const R*)src.y)[n];
+        ((R*)dst.z)[dd] = ((const R*)src.z)[n];
+        ((R*)dst.vx)[dd] = ((const R*)src.vx)[n];
+        ((R*)dst.vy)[dd] = ((const R*)src.vy)[n];
+        ((R*)dst.vz)[dd] = ((const R*)src.vz)[n];
+        ((R*)dst.d)[dd] = ((const R*)src.d)[n];
+        dst.q[dd] = src.q[n];
+        dst.q_wall[dd] = src.q_wall[n];
+        dst.n_imp[dd] = src.n_imp[n];
+        if (src.id) dst.id[dd] = src.id[n];
+        if (src.site) dst.site[dd] = src.site[n];
+    }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+bool gather4_ok(const PView& s, const PView& d) {
+    if ((s.id == nullptr) != (d.id == nullptr) || (s.site == nullptr) != (d.site == nullptr)) return false;
+    const void* const ptrs[] = {d.x, d.y, d.z, d.vx, d.vy, d.vz, d.d, d.q, d.q_wall, d.n_imp};
+    for (const void* p : ptrs)
+        if (!aligned16(p)) return false;
+    return (d.id == nullptr || aligned16(d.id)) && (d.site == nullptr || aligned16(d.site));
+}
+
 // exclusive scan of n uint32 values in place: per-tile sums, a scan of the
 // tile sums in one block, then the per-tile scans
 constexpr int kScanThreads = 1024;
@@ -336,7 +408,10 @@ tribo_status sort_impl(tribo_ctx* c, const PView& src, const PView& dst) {
     k_cell_members<<<grid_for(src.n), kThreads, 0, c->stream>>>(counts, key, rank, src.n, c->sort_perm);
     TRIBO_LAUNCHED(c);
     phase_begin(c, PH_SORT);
-    k_sort_gather<R><<<grid_for(src.n), kThreads, 0, c->stream>>>(src, dst, c->sort_perm);
+    if (gather4_ok(src, dst))
+        k_sort_gather4<R><<<grid_for((src.n + 3) / 4), kThreads, 0, c->stream>>>(src, dst, c->sort_perm);
+    else
+        k_sort_gather<R><<<grid_for(src.n), kThreads, 0, c->stream>>>(src, dst, c->sort_perm);
     TRIBO_LAUNCHED(c);
     return TRIBO_OK;
 }

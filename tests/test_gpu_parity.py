@@ -137,6 +137,45 @@ def test_ten_steps_match_oracle(prec, sort_every):
     print("max relative errors", errs)
 
 
+@pytest.mark.parametrize("prec", [T.TRIBO_FP64, T.TRIBO_MIXED])
+def test_sort_into_unaligned_arrays_matches_oracle(prec):
+    """The cell sort gathers four particles per thread with 16-byte stores when every
+    destination array is 16-byte aligned, else one particle per thread.  Here the caller's x, q
+    and n_imp start one element past an aligned address: of the two sorts in ten steps, the
+    first writes the context's aligned set (four per thread), the second the caller's arrays
+    (one per thread); 2,001 particles leave a ragged tail of one."""
+    c, faces, lat, parts = problem(64, 64, 64, n=2001, q_scale=1e-12, vy_scale=0.3, near_wall=0.05)
+    real = _real(prec)
+    lat_r, parts_r = round_inputs(lat, parts, real)
+    tol = TOL_FP64 if prec == T.TRIBO_FP64 else TOL_MIXED
+    params = T.Params(precision=prec, rho_p=c.rho_p, nu=c.nu, rho=c.rho_f, U_c=1e3, sort_every=4)
+    u = torch.from_numpy(np.ascontiguousarray(lat_r.astype(real))).cuda()
+    ch = T.Channel(c.nx, c.ny, c.nz, c.lx, c.lz, faces, params, u, max_particles=len(parts_r["x"]))
+    P = T.Particles.from_numpy(parts_r, prec, with_cell=True)
+
+    def shifted(t):
+        buf = torch.empty(t.numel() + 1, dtype=t.dtype, device=t.device)
+        v = buf[1:]
+        v.copy_(t)
+        assert v.data_ptr() % 16 != 0
+        return v
+
+    P.x, P.q, P.n_imp = shifted(P.x), shifted(P.q), shifted(P.n_imp)
+    ch.step(P, c.dt, 10)
+    ch.sync()
+    out = P.to_numpy()
+    ch.close()
+    order = np.argsort(out["id"])
+    got = {k: np.asarray(v)[order].astype(np.float64) if k not in ("n_imp", "id", "cell")
+           else np.asarray(v)[order] for k, v in out.items()}
+    g, ref = run_oracle(c, faces, lat_r, parts_r, 10, U_c=1e3)
+    assert ref.n_imp.sum() >= 50
+    compare_states(g, got, ref, tol, label=f"prec={prec}")
+    assert np.array_equal(got["n_imp"].astype(np.int64), ref.n_imp)
+    assert np.array_equal(np.sort(got["id"]), np.arange(len(parts_r["x"])))
+    check_cells(g, got, ref, tol)
+
+
 @pytest.mark.parametrize("variant", [
     dict(drag_law=T.TRIBO_DRAG_SCHILLER_NAUMANN),
     dict(drag_law=T.TRIBO_DRAG_OFF),
