@@ -101,18 +101,18 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT*
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);   // exp(-2 pi i e / NX)
     cplx<R>* buf = tw + NX;
-    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = tw_g[i];
-    __syncthreads();
     const int r = threadIdx.x % TPC;
     const int l = threadIdx.x / TPC;
     const int line = blockIdx.x * LPB + l;
     const bool live = l < LPB && line < nlines;
     cplx<R>* lb = buf + l * CS;
+    // the line's sums are loaded (and the nonzero ones rewritten with zero) before the block
+    // fills its twiddle table, so that the table's round trip overlaps the loads
+    cplx<R> y[N1];
     if (live && r < N2) {
         const R s = from_f64<R>(scale_row[line % ny]);
         using V2 = std::conditional_t<sizeof(QT) == 8, double2, float2>;   // (x_2n, x_2n+1)
         V2* row = reinterpret_cast<V2*>(src) + (size_t)line * M;
-        cplx<R> y[N1];
         unsigned nz_mask = 0;        // which element pairs hold a nonzero sum
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) {
@@ -130,6 +130,10 @@ __global__ void __launch_bounds__(kThreads, xfwd_min_blocks<R, M>()) k_xfwd4(QT*
             for (int n1 = 0; n1 < N1; ++n1)
                 if (nz_mask & (1u << n1)) row[N2 * n1 + r] = zero;
         }
+    }
+    for (int i = threadIdx.x; i < NX; i += kThreads) tw[i] = tw_g[i];
+    __syncthreads();
+    if (live && r < N2) {
         fft::reg_dft<R, -1, N1, 2 * N2>(y, tw);
         // W_M^(r k1) from the thread-ordered copy after the table (consecutive in r)
 #pragma unroll
