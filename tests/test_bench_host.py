@@ -6,7 +6,9 @@
   is nodes j+1 and j+2);
 * measured_traffic, which reports a profile's DRAM bytes only while the
   sources it was taken from are unchanged;
-* measured_peaks, which falls back when the peak file is absent."""
+* measured_peaks, which falls back when the peak file is absent;
+* per_particle_errors, the per-particle reading of the parity bar behind the
+  bench's error reports, checked against values worked out by hand."""
 import hashlib
 import json
 import os
@@ -62,3 +64,29 @@ def test_measured_peaks_fallback(tmp_path, monkeypatch):
     assert bench.measured_peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6794.1}))
     assert bench.measured_peaks() == (6794.1, "measured")
+
+
+def test_per_particle_errors_by_hand():
+    """Two particles in a box 2 x 1 x 4.  Particle 0: x off by 0.02 across the periodic
+    seam (1.99 against 0.01: a distance of 0.02, 1% of L_x), velocity (3, 4, 0) against
+    (3, 4, 0.05) (0.05 of a speed of 5: 1%), q -2e-15 against -1e-15 with q_wall -1e-15
+    (charge scale max(1e-15, 1e-15, 0) = 1e-15: q off by 100%, q_wall exact).  Particle 1:
+    exact.  The largest errors are those; the 99th percentile of two values interpolates."""
+    ref = dict(x=np.array([0.01, 1.0]), y=np.array([0.5, 0.5]), z=np.array([1.0, 2.0]),
+               vx=np.array([3.0, 1.0]), vy=np.array([4.0, 0.0]), vz=np.array([0.05, 0.0]),
+               q=np.array([-1e-15, 2e-15]), q_wall=np.array([-1e-15, 0.0]))
+    got = {k: v.copy() for k, v in ref.items()}
+    got["x"][0] = 1.99
+    got["vz"][0] = 0.0
+    got["q"][0] = -2e-15
+    e = bench.per_particle_errors(got, ref, 2.0, 1.0, 4.0)
+    speed0 = np.sqrt(3.0 ** 2 + 4.0 ** 2 + 0.05 ** 2)
+    assert e["x"]["max"] == pytest.approx(0.01, rel=1e-9)
+    assert e["y"]["max"] == 0.0 and e["z"]["max"] == 0.0
+    assert e["v"]["max"] == pytest.approx(0.05 / speed0, rel=1e-12)
+    assert e["q"]["max"] == pytest.approx(1.0, rel=1e-12)
+    assert e["q_wall"]["max"] == 0.0
+    assert e["x"]["p99"] == pytest.approx(0.01 * 0.99, rel=1e-9)
+    # a selection keeps only the chosen particles
+    e1 = bench.per_particle_errors(got, ref, 2.0, 1.0, 4.0, sel=np.array([False, True]))
+    assert all(e1[k]["max"] == 0.0 for k in ("x", "y", "z", "v", "q", "q_wall"))
